@@ -1,0 +1,245 @@
+"""Plain FP64 CPU oracle of the anisotropic 3PCF estimator (Python side).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package's smoke() and the benchmark's
+CPU-baseline / reference leg are the only callers.  Nothing here is shared
+with, imported by, or imports the CUDA path.
+
+The heavy loop (neighbour search, a_l^m, the local products) lives in
+``tpcf_oracle.c``; this module builds and loads it, assembles the
+data-minus-random field, forms the normaliser and applies the TripoSH
+projection of Eq. slep2sugy:
+
+    zeta_{l1 l2 L}(r1, r2) = (2L+1) H_{l1 l2 L}
+        sum_m (l1 l2 L; m -m 0) (-1)^m zeta^m_{l1 l2}(r1, r2),
+
+with H_{l1 l2 L} = (l1 l2 L; 0 0 0) (Sec. 2.2, TripoSH basis) and
+zeta^m = NNN^m / RRR_{00}^0 (Eq. ssest: (D-R)^3 / R^3, bin-wise by the l = 0
+random triplet count).
+
+Readings of the paper recorded here (the same list is in the design doc):
+  * the second a_l^m of Eq. measured_mult is conjugated (Eq. zeta_meas puts
+    Y* on r_hat_2);
+  * degenerate j = k triangles are removed (remove_self = 1);
+  * periodic boxes use analytic randoms: a_0^0[b] is offset by
+    c_b = (W - 1)/L^3 V_b Y_0^0 and RRR_00^0[b1][b2] = W c_b1 c_b2;
+  * non-periodic volumes use explicit randoms with weights -W_D/W_R, and
+    RRR_00^0 from the randoms alone with weights +W_D/W_R;
+  * ``convention="PAPER_EQ"`` is Eq. slep2sugy as printed with orthonormal
+    Y; ``"S_COEFF"`` (default) multiplies it by sqrt((2 l1 + 1)(2 l2 + 1)), the
+    coefficient of the Schmidt-normalised basis function S_{l1 l2 L} of
+    Eq. TSHbasis.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "tpcf_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP, -O2, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("r_min", ctypes.c_double), ("r_max", ctypes.c_double),
+                ("n_bins", ctypes.c_int32), ("l_max", ctypes.c_int32),
+                ("periodic", ctypes.c_int32), ("remove_self", ctypes.c_int32),
+                ("box", ctypes.c_double), ("offset_weight", ctypes.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        L.ora_run.argtypes = [ctypes.POINTER(_Cfg), P, P, ctypes.c_int64, P, ctypes.c_int64,
+                              P, P, P, P, P, P, P, ctypes.c_int]
+        L.ora_run.restype = ctypes.c_int
+        L.ora_edges.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_double, P, P]
+        L.ora_edges.restype = None
+        L.ora_wigner3j.argtypes = [ctypes.c_int] * 6
+        L.ora_wigner3j.restype = ctypes.c_double
+        L.ora_ylm.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int, P]
+        L.ora_ylm.restype = None
+        L.ora_max_threads.argtypes = []
+        L.ora_max_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+@dataclass
+class Config:
+    r_min: float
+    r_max: float
+    n_bins: int
+    l_max: int
+    Ls: tuple = (0, 2, 4)
+    periodic: bool = True
+    box: float = 500.0
+    remove_self: bool = True
+    convention: str = "S_COEFF"
+
+
+def edges(cfg: Config):
+    """(E uint64 [nb+1], r float64 [nb+1]): exact integer edges^2 and physical edges."""
+    E = np.zeros(cfg.n_bins + 1, dtype=np.uint64)
+    r = np.zeros(cfg.n_bins + 1, dtype=np.float64)
+    lib().ora_edges(cfg.r_min, cfg.r_max, cfg.n_bins, cfg.box, _p(E), _p(r))
+    return E, r
+
+
+def wigner3j(j1, j2, j3, m1, m2, m3) -> float:
+    return lib().ora_wigner3j(j1, j2, j3, m1, m2, m3)
+
+
+def ylm(vec, lmax):
+    """Orthonormal complex Y_l^m at a unit vector, index l*l + l + m."""
+    out = np.zeros((lmax + 1) ** 2, dtype=np.complex128)
+    lib().ora_ylm(float(vec[0]), float(vec[1]), float(vec[2]), lmax, _p(out))
+    return out
+
+
+def multipoles(l_max: int, Ls) -> list:
+    """(l1, l2, L) kept by the TripoSH projection: triangle rule and even l1+l2+L."""
+    out = []
+    for L in Ls:
+        for l1 in range(l_max + 1):
+            for l2 in range(l_max + 1):
+                if abs(l1 - l2) <= L <= l1 + l2 and (l1 + l2 + L) % 2 == 0:
+                    out.append((l1, l2, L))
+    return out
+
+
+def shell_offsets(cfg: Config, weight_sum: float):
+    """c_b = (W - 1)/L^3 * V_b * Y_0^0 with V_b the volume of radial shell b."""
+    _, r = edges(cfg)
+    nbar = (weight_sum - 1.0) / cfg.box ** 3
+    vb = 4.0 * math.pi / 3.0 * (r[1:] ** 3 - r[:-1] ** 3)
+    return nbar * vb / math.sqrt(4.0 * math.pi)
+
+
+@dataclass
+class RunOut:
+    nnn: np.ndarray            # complex [2L+1][L+1][L+1][nb][nb], m index m + L
+    pair_counts: np.ndarray    # int64 [nb]
+    trip_counts: np.ndarray    # int64 [nb][nb]
+    alm: np.ndarray | None = None   # complex [n_prim][nb][(L+1)^2]
+    cnt: np.ndarray | None = None   # int32 [n_prim][nb]
+
+
+def run(cfg: Config, xyz, w, offset_weight=-1.0, prim=None, want_alm=False, nthreads=0,
+        l_max=None) -> RunOut:
+    """One pass of the estimator loop over a single signed-weight field."""
+    L = cfg.l_max if l_max is None else l_max
+    xyz = np.ascontiguousarray(xyz, dtype=np.uint32)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    n = xyz.shape[0]
+    nb = cfg.n_bins
+    c = _Cfg(cfg.r_min, cfg.r_max, nb, L, int(cfg.periodic), int(cfg.remove_self), cfg.box,
+             float(offset_weight))
+    nm = 2 * L + 1
+    re = np.zeros((nm, L + 1, L + 1, nb, nb))
+    im = np.zeros_like(re)
+    pc = np.zeros(nb, dtype=np.int64)
+    tc = np.zeros((nb, nb), dtype=np.int64)
+    pr = None
+    npr = 0
+    if prim is not None:
+        pr = np.ascontiguousarray(prim, dtype=np.int64)
+        npr = pr.shape[0]
+    nlm = (L + 1) ** 2
+    ar = ai = cn = None
+    if want_alm:
+        k = npr if prim is not None else n
+        ar = np.zeros((k, nb, nlm))
+        ai = np.zeros((k, nb, nlm))
+        cn = np.zeros((k, nb), dtype=np.int32)
+    rc = lib().ora_run(ctypes.byref(c), _p(xyz), _p(w), n, _p(pr), npr,
+                       _p(re), _p(im), _p(pc), _p(tc), _p(ar), _p(ai), _p(cn), int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle rejected the configuration")
+    out = RunOut(re + 1j * im, pc, tc)
+    if want_alm:
+        out.alm = ar + 1j * ai
+        out.cnt = cn
+    return out
+
+
+def project(cfg: Config, nnn: np.ndarray, rrr: np.ndarray, mults=None, l_max=None):
+    """Eq. slep2sugy applied bin by bin, divided by RRR_00^0; returns (real, imag)."""
+    L = cfg.l_max if l_max is None else l_max
+    mults = multipoles(L, cfg.Ls) if mults is None else mults
+    nb = cfg.n_bins
+    z = np.zeros((len(mults), nb, nb), dtype=np.complex128)
+    for k, (l1, l2, LL) in enumerate(mults):
+        H = wigner3j(l1, l2, LL, 0, 0, 0)
+        s = np.zeros((nb, nb), dtype=np.complex128)
+        for m in range(-min(l1, l2), min(l1, l2) + 1):
+            s += wigner3j(l1, l2, LL, m, -m, 0) * (-1.0) ** m * nnn[m + L, l1, l2]
+        v = (2 * LL + 1) * H * s / rrr
+        if cfg.convention == "S_COEFF":
+            v = v * math.sqrt((2 * l1 + 1) * (2 * l2 + 1))
+        elif cfg.convention != "PAPER_EQ":
+            raise ValueError(cfg.convention)
+        z[k] = v
+    return z.real, z.imag
+
+
+@dataclass
+class Estimate:
+    zeta: np.ndarray
+    zeta_imag: np.ndarray
+    mults: list
+    nnn: np.ndarray
+    rrr: np.ndarray
+    pair_counts: np.ndarray
+    trip_counts: np.ndarray
+    extra: dict = field(default_factory=dict)
+
+
+def estimate(cfg: Config, d_xyz, d_w, r_xyz=None, r_w=None, nthreads=0) -> Estimate:
+    """Full estimator: (D - R)^3 / R^3 multipoles (Eq. ssest with Eq. slep2sugy).
+
+    Without randoms (periodic only) the analytic-random form is used."""
+    d_w = np.asarray(d_w, dtype=np.float64)
+    WD = float(d_w.sum())
+    if r_xyz is None:
+        if not cfg.periodic:
+            raise ValueError("analytic randoms need a periodic box")
+        o = run(cfg, d_xyz, d_w, offset_weight=WD, nthreads=nthreads)
+        cb = shell_offsets(cfg, WD)
+        rrr = WD * np.outer(cb, cb)
+    else:
+        r_w = np.asarray(r_w, dtype=np.float64)
+        alpha = WD / float(r_w.sum())
+        xyz = np.concatenate([np.asarray(d_xyz, np.uint32), np.asarray(r_xyz, np.uint32)])
+        w = np.concatenate([d_w, -alpha * r_w])
+        o = run(cfg, xyz, w, nthreads=nthreads)
+        orr = run(cfg, r_xyz, alpha * r_w, nthreads=nthreads, l_max=0)
+        rrr = orr.nnn[0, 0, 0].real
+    mults = multipoles(cfg.l_max, cfg.Ls)
+    zr, zi = project(cfg, o.nnn, rrr, mults)
+    return Estimate(zr, zi, mults, o.nnn, rrr, o.pair_counts, o.trip_counts)
+
+
+def max_threads() -> int:
+    return lib().ora_max_threads()
