@@ -1,0 +1,339 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 anisotropic 3PCF estimator (primaries per second).
+
+Workload (the clustered-halo configuration): a seeded lognormal catalogue of
+N_D = 400,000 points (Gaussian field on a 512^3 mesh, P_G(k) ~ k^-1.5
+exp(-(k/0.5)^2), sigma_G = 1, Kaiser-like LOS shift f = 0.8) in an open cube of
+side 1000 Mpc/h, with N_R = 1,200,000 uniform randoms for the data-minus-random
+edge correction; 20 linear bins 10-150 Mpc/h, l_max = 4, L in {0, 2, 4}.
+A step is one full tpcf_estimate_3pcf: grids, the pair stage on the D-R field,
+the random-only RRR pass, the coupling and the TripoSH projection.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3PCF primaries/s & mocks/hour at l_max=4 (mixed vs plain FP32 GPU, err≤1e-4)"
+UNIT = "primaries/s"
+ND, NR, BOX, MESH = 400_000, 1_200_000, 1000.0, 512
+SEED_D, SEED_R = 2, 3
+WORKLOAD = ("clustered lognormal halos N_D=400000 (512^3 mesh, P~k^-1.5 exp(-(k/0.5)^2), sigma_G=1, "
+            "LOS shift f=0.8) + N_R=1200000 randoms, open cube L=1000 Mpc/h, 20 bins 10-150 Mpc/h, "
+            "l_max=4, L={0,2,4}")
+FLOP_PER_PAIR = 4 * 25 + 15   # algorithmic FP32 work per accepted pair at l_max = 4
+
+
+def config(precision="fp32"):
+    from paper_2408_03036_gb300 import tpcf
+    return tpcf.Config(r_min=10.0, r_max=150.0, n_bins=20, l_max=4, Ls=(0, 2, 4), periodic=False,
+                       box=BOX, precision=precision)
+
+
+def make_inputs(rank=0):
+    from paper_2408_03036_gb300 import synth
+    d, dw = synth.lognormal(ND, BOX, SEED_D + 1000 * rank, mesh=MESH)
+    r, rw = synth.randoms(NR, SEED_R + 1000 * rank)
+    return d, dw, r, rw
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(target_s=12.0, max_prim=20000):
+    """The FP64 oracle as it stands, on a bounded random sample of primaries of
+    the same workload (numerator pass over the D-R field plus the proportional
+    random-only RRR pass), on all host cores."""
+    import numpy as np
+    from oracle import oracle as ora
+    d, dw, r, rw = make_inputs()
+    o = ora.Config(10.0, 150.0, 20, 4, (0, 2, 4), False, BOX)
+    alpha = float(dw.astype(np.float64).sum() / rw.astype(np.float64).sum())
+    fx = np.concatenate([d, r])
+    fw = np.concatenate([dw.astype(np.float64), -alpha * rw.astype(np.float64)])
+    rng = np.random.default_rng(11)
+    ntot = ND + NR
+
+    def timed(nprim):
+        pf = np.sort(rng.choice(ntot, size=nprim, replace=False))
+        pr = np.sort(rng.choice(NR, size=max(1, int(round(nprim * NR / ntot))), replace=False))
+        t = time.perf_counter()
+        ora.run(o, fx, fw, prim=pf)
+        ora.run(o, r, alpha * rw.astype(np.float64), prim=pr, l_max=0)
+        return time.perf_counter() - t
+
+    n = 64
+    t = timed(n)
+    n2 = int(min(max_prim, max(n, n * target_s / max(t, 1e-3))))
+    t2 = timed(n2)
+    return {"value": n2 / t2, "unit": UNIT, "cores": ora.max_threads(), "kind": "oracle",
+            "sample": "%d random primaries of the D-R field (+%d of the random-only RRR pass) against all "
+                      "%d points, %.1f s" % (n2, int(round(n2 * NR / ntot)), ntot, t2)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import oracle as ora
+    d, dw, r, rw = make_inputs()
+    o = ora.Config(10.0, 150.0, 20, 4, (0, 2, 4), False, BOX)
+    alpha = float(dw.astype(np.float64).sum() / rw.astype(np.float64).sum())
+    fx = np.concatenate([d, r])
+    fw = np.concatenate([dw.astype(np.float64), -alpha * rw.astype(np.float64)])
+    ntot = ND + NR
+    rng = np.random.default_rng(12)
+    per_step_s = max(2.0, min(15.0, 150.0 / max(1, args.steps + args.warmup)))
+
+    def step(nprim):
+        pf = np.sort(rng.choice(ntot, size=nprim, replace=False))
+        pr = np.sort(rng.choice(NR, size=max(1, int(round(nprim * NR / ntot))), replace=False))
+        t = time.perf_counter()
+        ora.run(o, fx, fw, prim=pf)
+        ora.run(o, r, alpha * rw.astype(np.float64), prim=pr, l_max=0)
+        return time.perf_counter() - t
+
+    t = step(32)
+    nprim = int(max(32, min(50000, 32 * per_step_s / max(t, 1e-3))))
+    for _ in range(args.warmup):
+        step(max(8, nprim // 16))
+    times = [step(nprim) for _ in range(args.steps)]
+    total = sum(times)
+    value = nprim * args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_primaries_per_step": nprim},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ora.max_threads(), "kind": "oracle",
+                             "sample": "%d random primaries per step (+%d random-only RRR primaries) of the "
+                                       "%d-point D-R field" % (nprim, int(round(nprim * NR / ntot)), ntot)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2408_03036_gb300 import build as B
+    from paper_2408_03036_gb300 import tpcf
+
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    dev = torch.device("cuda", local)
+    cfg = config(args.precision)
+    d, dw, r, rw = make_inputs(rank)
+    dx = torch.from_numpy(d.view(np.int32)).to(dev)
+    dwt = torch.from_numpy(dw).to(dev)
+    rx = torch.from_numpy(r.view(np.int32)).to(dev)
+    rwt = torch.from_numpy(rw).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        return tpcf.estimate_3pcf(cfg, dx, dwt, rx, rwt, stream=stream, device=dev)
+
+    for _ in range(args.warmup):
+        res = step()
+    torch.cuda.synchronize(dev)
+    tpcf.stream_status(stream)
+    pairs_per_step = int(res.pair_counts.sum().item())
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = tpcf.kernel_launches()
+    with ClockSampler(dev.index) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+    launches = tpcf.kernel_launches() - launches0
+    tpcf.stream_status(stream)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    prim_per_step = ND + NR
+    value = ws * prim_per_step * args.steps / (ms_max / 1000.0)
+
+    # dominant kernel: the pair stage on the D-R field, timed alone with events
+    roof = roofline(cfg, d, dw, r, rw, dev, stream, tpcf)
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e = end_to_end(cfg, d, dw, r, rw, args, stream, tpcf)
+
+    if rank != 0:
+        return 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": args.precision, "parallelism": "replicas",
+                       "primaries_per_step": prim_per_step, "pairs_per_step": pairs_per_step,
+                       "l2": "flushed between timed steps (256 MB write, outside the events)"},
+            "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof, "e2e": e2e}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def fp32_peak_tflops(dev):
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return 2.0 * 128 * sms * 2070e6 / 1e12
+
+
+def roofline(cfg, d, dw, r, rw, dev, stream, tpcf, reps=3):
+    """Pair stage alone: algorithmic FP32 FLOP / kernel time, against the FP32 FMA peak."""
+    import numpy as np
+    import torch
+    alpha = float(dw.astype(np.float64).sum() / rw.astype(np.float64).sum())
+    fx = np.concatenate([d, r])
+    fw = np.concatenate([dw, (-alpha * rw.astype(np.float64)).astype(np.float32)])
+    grid = tpcf.Grid(cfg, fx, fw, stream=stream, device=dev)
+    out = None
+    for _ in range(2):
+        out = tpcf.accumulate_alm(grid, cfg, stream=stream)
+    torch.cuda.synchronize(dev)
+    pairs = int(out[4].sum().item())
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(reps):
+        s.record(stream)
+        tpcf.accumulate_alm(grid, cfg, stream=stream)
+        e.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(s.elapsed_time(e))
+    grid.close()
+    t = statistics.median(ms) / 1000.0
+    achieved = FLOP_PER_PAIR * pairs / t / 1e12
+    peak = fp32_peak_tflops(dev)
+    return {"bound": "alu", "kernel": "k_pairs (pair stage, D-R field)", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "per_launch": {"pairs": pairs, "flop_per_pair": FLOP_PER_PAIR, "ms": t * 1000.0},
+            "peak_note": "FP32 FMA pipe: 2 x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)"}
+
+
+def end_to_end(cfg, d, dw, r, rw, args, stream, tpcf):
+    import numpy as np
+    import torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+    hd, hdw, hr, hrw = pin(d), pin(dw), pin(r), pin(rw)
+    steps = max(1, min(args.steps, 3))
+    tpcf.estimate_3pcf_host(cfg, hd, hdw, hr, hrw, stream=stream)   # warm
+    s = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(steps):
+        s.record(stream)
+        res = tpcf.estimate_3pcf_host(cfg, hd, hdw, hr, hrw, stream=stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        tot += s.elapsed_time(e)
+    bi = hd.nbytes + hdw.nbytes + hr.nbytes + hrw.nbytes
+    bo = res.zeta.nbytes + res.nnn.nbytes + res.rrr.nbytes + res.pair_counts.nbytes + res.triplet_counts.nbytes
+    return {"value": (ND + NR) * steps / (tot / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(bi),
+            "d2h_bytes_per_step": int(bo), "steps": steps}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3", "tf32x3"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

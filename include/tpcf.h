@@ -1,0 +1,204 @@
+/*
+ * tpcf.h - C ABI of the GB300 (sm_103a) anisotropic three-point correlation
+ * function estimator (Slepian-Eisenstein pair-count estimator with TripoSH
+ * multipoles about a fixed line of sight along z).
+ *
+ * Method (arXiv:2408.03036, Sec. 4.2 "3PCF estimator" and Sec. 4, Eq. ssest):
+ *   for every primary x_i and radial bin b (step function phi of Eq. alm)
+ *       a_l^m[b](x_i) = sum_{j in b} w_j Y_l^m(r_hat_ij)            (Eq. alm)
+ *   the local products of Eq. measured_mult, kept for m = m' with the second
+ *   factor conjugated, summed over primaries with the primary's weight
+ *       NNN^m_{l1 l2}[b1][b2] = sum_i w_i ( a_{l1}^m[b1] a_{l2}^m[b2]*
+ *                                - delta_{b1 b2} sum_j w_j^2 Y_{l1}^m Y_{l2}^m* )
+ *   (the subtracted term removes degenerate j = k triangles), and the
+ *   TripoSH projection of Eq. slep2sugy, divided by the random triplet
+ *   normaliser RRR_00^0 (Eq. ssest, (D-R)^3 / R^3):
+ *       zeta_{l1 l2 L} = (2L+1) H_{l1 l2 L} sum_m (l1 l2 L; m -m 0) (-1)^m
+ *                        Re NNN^m_{l1 l2} / RRR_00^0.
+ *
+ * Coordinates are uint32 fixed point: u = floor(x / L * 2^32).  Separations are
+ * exact integer differences (modulo 2^32 in periodic boxes), r^2 is an exact
+ * 64-bit integer, and a pair is in bin b iff E_b <= r^2 < E_{b+1} with
+ * E_b = ceil(s_b^2), s_b = (r_b * 2^32) / L, r_b = r_min + ((r_max - r_min) * b) / n_bins
+ * (all in IEEE double).  Pair and triplet counts are therefore exact integers.
+ *
+ * General rules for every entry point:
+ *   - returns TPCF_OK (0) or a negative tpcf_status; a message for the last
+ *     error of the calling thread is available from tpcf_last_error();
+ *   - never aborts or traps; arguments are validated on the host;
+ *   - pointers marked "dev" are device pointers owned by the caller; "host"
+ *     pointers are host memory owned by the caller;
+ *   - "stream" is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream); work is enqueued asynchronously on it unless stated otherwise;
+ *     data errors found on the device (coordinates outside [0, 2^32), NaN
+ *     weights) are latched in a device flag and reported by
+ *     tpcf_stream_status();
+ *   - scratch memory is taken with stream-ordered allocation on the given
+ *     stream and returned before the call's work completes.
+ */
+#ifndef TPCF_H
+#define TPCF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TPCF_OK = 0,
+    TPCF_ERR_ARG = -1,          /* invalid argument or configuration */
+    TPCF_ERR_OOM = -2,          /* device allocation failed */
+    TPCF_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    TPCF_ERR_TIMEOUT = -4,      /* a bounded device-side wait ran out */
+    TPCF_ERR_UNSUPPORTED = -5,  /* valid request this build does not implement */
+    TPCF_ERR_DATA = -6          /* bad input data detected on the device */
+} tpcf_status;
+
+/* Precision of the coupling sum over primaries (the pair stage is always FP32,
+ * final sums FP64). */
+enum {
+    TPCF_PREC_FP32 = 0,     /* plain FP32 SIMT Gram, FP64 flush */
+    TPCF_PREC_BF16X3 = 1,   /* tcgen05 tensor cores, bf16 hi/lo split, 3 products, FP32 accumulate */
+    TPCF_PREC_TF32X3 = 2    /* tcgen05 tensor cores, tf32 hi/lo split, 3 products, FP32 accumulate */
+};
+
+/* Normalisation of the reported multipoles. */
+enum {
+    TPCF_CONV_S_COEFF = 0,  /* coefficient of the Schmidt basis S_{l1 l2 L} (Eq. TSHbasis):
+                               sqrt((2 l1 + 1)(2 l2 + 1)) times Eq. slep2sugy */
+    TPCF_CONV_PAPER_EQ = 1  /* Eq. slep2sugy as printed with orthonormal Y */
+};
+
+typedef struct {
+    double r_min;           /* inner edge of the first radial bin, > 0 */
+    double r_max;           /* outer edge of the last radial bin, < box / 2 */
+    int32_t n_bins;         /* number of linear radial bins, 1..32 */
+    int32_t l_max;          /* harmonics l1, l2 <= l_max, 0..6 */
+    int32_t n_L;            /* number of TripoSH L values in L[], 1..8 */
+    int32_t L[8];           /* the L values (even, 0..2 l_max) */
+    int32_t periodic;       /* 1: periodic cube (minimum image), 0: open volume */
+    double box;             /* cube side L in the same length unit as r */
+    int32_t precision;      /* TPCF_PREC_* */
+    int32_t remove_self;    /* 1: drop degenerate j = k triangles (default) */
+    int32_t convention;     /* TPCF_CONV_* */
+    int32_t cell_div;       /* cells per r_max along an axis, 1..6; 0 = automatic */
+    int32_t tile_primaries; /* primaries processed together by one CTA, 1..8 (capped so that
+                               tile_primaries * n_bins <= 128); 0 = automatic */
+    int32_t chunk;          /* staged pairs per CTA chunk (multiple of 256, 512..8192); 0 = automatic */
+} tpcf_config;
+
+typedef struct tpcf_grid_s *tpcf_grid;   /* library-owned cell list (opaque) */
+
+/* Message describing the calling thread's most recent error ("" if none). */
+const char *tpcf_last_error(void);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int tpcf_version(void);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (a diagnostic: the difference around a call is that call's launch count). */
+int64_t tpcf_kernel_launches(void);
+
+/* Number of (l1, l2, L) multipoles the configuration produces.  These are all
+ * triples with l1, l2 <= l_max, L in cfg->L, |l1 - l2| <= L <= l1 + l2 and
+ * l1 + l2 + L even (Eq. slep2sugy with H_{l1 l2 L} != 0), ordered by the
+ * position of L in cfg->L, then l1, then l2. */
+int tpcf_multipole_count(const tpcf_config *cfg, int32_t *n_mult);
+
+/* Writes the multipole triples, host l1l2L[n_mult][3] (capacity cap triples). */
+int tpcf_multipole_index(const tpcf_config *cfg, int32_t *l1l2L, int32_t cap);
+
+/* The exact integer bin edges E_b (b = 0..n_bins), host E[n_bins + 1]. */
+int tpcf_bin_edges(const tpcf_config *cfg, uint64_t *E);
+
+/* Cell list of a catalogue (the linked-list partition of Sec. 4.1, built as a
+ * counting sort by cell).  dev xyz[n][3] uint32 fixed point, dev w[n] float
+ * weights (NULL: unit weights).  The grid copies what it needs; the inputs may
+ * be freed once the stream has passed this call.  *out receives a handle that
+ * must be released with tpcf_grid_destroy. */
+int tpcf_build_grid(const uint32_t *xyz, const float *w, int64_t n, const tpcf_config *cfg,
+                    tpcf_grid *out, void *stream);
+
+/* Releases a grid (synchronises its stream first). NULL is accepted. */
+int tpcf_grid_destroy(tpcf_grid grid);
+
+/* Number of points and cells per axis of a grid. */
+int tpcf_grid_info(tpcf_grid grid, int64_t *n_points, int32_t *cells_per_axis);
+
+/* Copies the grid's points in grid (cell) order: dev xyz[n][3], dev w[n], and
+ * dev order[n] = input index of each point.  Any output may be NULL. */
+int tpcf_grid_points(tpcf_grid grid, uint32_t *xyz, float *w, int64_t *order, void *stream);
+
+/* Pair stage (Eq. alm): for every primary, the neighbour search to r_max over
+ * the secondaries in `grid`, exact radial binning and the FP32 harmonic sums.
+ *   prim_xyz/prim_w: dev primaries [n_prim][3] / [n_prim] (NULL: unit weights).
+ *     If prim_xyz is NULL the primaries are the grid's own points in grid order
+ *     (n_prim must then equal the grid's point count).
+ *   monopole_weight: >= 0 enables the periodic analytic-random offset
+ *     a_0^0[b] -= (monopole_weight - 1) / L^3 * V_b * Y_0^0; < 0 disables it.
+ *   Outputs (dev, any may be NULL):
+ *     alm[n_prim][n_bins][(l_max+1)^2]  real harmonic sums, per (l, m >= 0) the
+ *        real part at index l^2 + max(2m - 1, 0) and, for m > 0, the imaginary
+ *        part at l^2 + 2m (orthonormal Y with the Condon-Shortley phase);
+ *     counts[n_prim][n_bins] int32 pair counts per primary;
+ *     diag[(l_max+1)(l_max+2)/2][n_bins]  += sum_i w_i (|a_l^m[b]|^2 - s_{ll}^m[b]),
+ *        (l, m) in the order l = 0..l_max, m = 0..l, where s is the j = k term
+ *        (omitted when cfg->remove_self is 0);
+ *     wsp[l_max+1][n_bins]  += sum_i w_i sum_j w_j^2 f_k(mu_ij), k = 0..l_max, with f_0 = 1
+ *        and f_k = (2k)! P_{2k} (an intermediate consumed by tpcf_couple_multipoles
+ *        for the j = k term of the l1 != l2 entries);
+ *     pair_counts[n_bins]  int64, += total pairs per bin. */
+int tpcf_accumulate_alm(tpcf_grid grid, const uint32_t *prim_xyz, const float *prim_w, int64_t n_prim,
+                        const tpcf_config *cfg, double monopole_weight,
+                        float *alm, int32_t *counts, double *diag, double *wsp, int64_t *pair_counts,
+                        void *stream);
+
+/* Coupling over primaries (Eq. measured_mult summed over x): with the outputs of
+ * tpcf_accumulate_alm for the same primaries (dev alm, dev prim_w or NULL for
+ * unit weights, dev counts or NULL, dev diag, dev wsp), writes
+ *   nnn[m][l1][l2][n_bins][n_bins]  (m, l1, l2 = 0..l_max; zero where l < m)
+ *       = Re NNN^m_{l1 l2}, with the j = k term removed per cfg->remove_self;
+ *   triplet_counts[n_bins][n_bins] = sum_i n_b1(i) (n_b2(i) - delta_b1b2)  (if counts given).
+ * Outputs are overwritten (not accumulated).  cfg->precision selects the Gram
+ * arithmetic. */
+int tpcf_couple_multipoles(const float *alm, const float *prim_w, const int32_t *counts, int64_t n_prim,
+                           const tpcf_config *cfg, const double *diag, const double *wsp,
+                           double *nnn, int64_t *triplet_counts, void *stream);
+
+/* TripoSH projection (Eq. slep2sugy) of dev nnn (layout as above) divided bin
+ * by bin by dev rrr[n_bins][n_bins]; writes dev zeta[n_mult][n_bins][n_bins]. */
+int tpcf_project(const tpcf_config *cfg, const double *nnn, const double *rrr, double *zeta, void *stream);
+
+/* Full estimator, Eq. ssest with Eq. slep2sugy.
+ *   Periodic box with analytic randoms: r_xyz = NULL, nr = 0 (cfg->periodic = 1).
+ *   Explicit randoms (any geometry): the neighbour field is D - (W_D/W_R) R for
+ *   primaries and secondaries, and RRR_00^0 comes from the randoms alone.
+ * Inputs dev d_xyz[nd][3], d_w[nd] (NULL: unit), r_xyz[nr][3], r_w[nr] (NULL: unit).
+ * Outputs dev: zeta[n_mult][n_bins][n_bins] (required), and optionally
+ *   nnn (as tpcf_couple_multipoles), rrr[n_bins][n_bins], pair_counts[n_bins]
+ *   (pairs of the neighbour field), triplet_counts[n_bins][n_bins]. */
+int tpcf_estimate_3pcf(const tpcf_config *cfg,
+                       const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                       const uint32_t *r_xyz, const float *r_w, int64_t nr,
+                       double *zeta, double *nnn, double *rrr,
+                       int64_t *pair_counts, int64_t *triplet_counts, void *stream);
+
+/* As tpcf_estimate_3pcf, but every pointer is HOST memory (pinned memory gives
+ * the fastest copies).  Copies in, runs, copies out, and synchronises the
+ * stream before returning. */
+int tpcf_estimate_3pcf_host(const tpcf_config *cfg,
+                            const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                            const uint32_t *r_xyz, const float *r_w, int64_t nr,
+                            double *zeta, double *nnn, double *rrr,
+                            int64_t *pair_counts, int64_t *triplet_counts, void *stream);
+
+/* Synchronises the stream and reports any latched device-side error
+ * (TPCF_ERR_DATA, TPCF_ERR_TIMEOUT) or CUDA error; clears the latch. */
+int tpcf_stream_status(void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPCF_H */

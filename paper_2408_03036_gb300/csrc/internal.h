@@ -1,0 +1,103 @@
+// Internal declarations shared by the CUDA translation units of libtpcf.
+// Not part of the public ABI (include/tpcf.h is).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/tpcf.h"
+
+#define TPCF_MAX_BINS 32
+#define TPCF_MAX_LMAX 6
+#define TPCF_MAX_TILE 8
+
+namespace tpcf {
+
+// Device-side error latch values (first error wins).
+enum : int { DEV_OK = 0, DEV_ERR_DATA = 1, DEV_ERR_TIMEOUT = 2, DEV_ERR_CAPACITY = 3 };
+
+// Cell list in device memory.  Records are int4 {x, y, z, float_as_int(w)} with
+// x, y, z uint32 fixed-point bit patterns, sorted by cell index
+// ((cz * nc + cy) * nc + cx), cell = floor(u * nc / 2^32).
+struct GridDev {
+    int4 *rec = nullptr;
+    int64_t *order = nullptr;      // input index of each record
+    int32_t *cell_start = nullptr; // [ncell + 1]
+    int64_t n = 0;
+    int nc = 0;
+    int64_t ncell = 0;
+};
+
+// Parameters of the pair-stage kernel (one struct, passed by value).
+struct PairParams {
+    const int4 *rec;
+    const int32_t *cell_start;
+    int nc;
+    int s;              // cells scanned on each side of the primary's cell
+    int periodic;
+    const int4 *prim;   // primaries as records
+    int64_t n_prim;
+    int nb;
+    int P;              // primaries per tile
+    int chunk;          // staged pairs per chunk
+    unsigned long long E[TPCF_MAX_BINS + 1];
+    float Ef[TPCF_MAX_BINS + 1];
+    float rmin_u, inv_dr_u;   // float bin estimate b = (sqrt(r2) - rmin_u) * inv_dr_u
+    float r2_lo, r2_hi;       // float prefilter window (conservative)
+    float rmax_trim;          // conservative r_max (units) for row trimming
+    float h_u;                // cell side in units (2^32 / nc)
+    double mono_coef[TPCF_MAX_BINS];  // c_b = (W - 1) * mono_coef[b]
+    double mono_w;            // W used when mono_w_dev is null
+    const double *mono_w_dev; // device W (overrides mono_w)
+    int use_mono;
+    int remove_self;
+    float *alm;
+    int32_t *counts;
+    double *diag;
+    double *wsp;
+    unsigned long long *pair_counts;
+    int *work;                // tile counter (zeroed before launch)
+    int *err;                 // device error latch
+};
+
+// Counts kernel launches made by the library (reported by tpcf_kernel_launches).
+void note_launch(int n = 1);
+
+// Host-side launchers (defined in the .cu files).
+cudaError_t build_grid_dev(const uint32_t *xyz, const float *w, int64_t n,
+                           const uint32_t *xyz2, const float *w2, int64_t n2, const double *wsums,
+                           int nc, GridDev &g, int *err, cudaStream_t st);
+void free_grid_dev(GridDev &g, cudaStream_t st);
+
+cudaError_t pack_records(const uint32_t *xyz, const float *w, int64_t n, int4 *out, int *err,
+                         cudaStream_t st);
+cudaError_t weight_sums(const float *w1, int64_t n1, const float *w2, int64_t n2, double *out2,
+                        cudaStream_t st);
+
+// Coupling (Gram over primaries) and assembly.
+cudaError_t couple_gram_fp32(const float *alm, const float *w, int64_t K, int nb, int lmax,
+                             double *G, cudaStream_t st);
+cudaError_t triplet_counts(const int32_t *counts, int64_t K, int nb, unsigned long long *T,
+                           cudaStream_t st);
+cudaError_t assemble_nnn(const double *G, const double *diag, const double *wsp, int nb, int lmax,
+                         int remove_self, const double *gaunt, double *nnn, cudaStream_t st);
+cudaError_t project_zeta(const double *nnn, const double *rrr, int nb, int lmax, int n_mult,
+                         const double *coef, const int *mults, double *zeta, cudaStream_t st);
+cudaError_t rrr_analytic(const double *wsum, const double *coef, int nb, double *rrr, cudaStream_t st);
+cudaError_t rrr_from_counts(const unsigned long long *T, const double *wsums, int nb, double *rrr,
+                            cudaStream_t st);
+cudaError_t i64_from_u64(const unsigned long long *src, int64_t *dst, int n, cudaStream_t st);
+
+// Offsets of the per-m Gram blocks in the packed G array: block m is
+// n_m x n_m doubles with n_m = nb * (lmax - m + 1); row index (l - m) * nb + b.
+__host__ __device__ inline int64_t gram_offset(int nb, int lmax, int m)
+{
+    int64_t off = 0;
+    for (int k = 0; k < m; ++k) {
+        int64_t n = (int64_t)nb * (lmax - k + 1);
+        off += n * n;
+    }
+    return off;
+}
+
+}  // namespace tpcf

@@ -1,0 +1,701 @@
+// Pair stage of the anisotropic 3PCF estimator (Eq. alm of arXiv:2408.03036,
+// Sec. 4.2): for every primary, neighbour search to r_max over a cell list,
+// exact integer radial binning, and per-bin sums of w_j Y_l^m(r_hat_ij) with
+// the line of sight along z.  Also the per-bin sums of w_j^2 P_L(mu) that give
+// the degenerate j = k triangle term, and integer pair counts.
+//
+// One CTA works on a tile of P primaries at a time (persistent grid, tiles taken
+// from an atomic counter).  For a tile:
+//   1. the cell rows within reach of each primary are listed as contiguous
+//      point ranges (cells are stored in x-fastest order, so a run of cells
+//      along x is one range), trimmed per primary to the sphere of radius r_max;
+//   2. all threads stride over the concatenated candidates; a float prefilter
+//      with a proven error bound takes the bin decision, falling back to the
+//      exact 64-bit integer test near any edge; accepted pairs (unit vector,
+//      weight, key = slot * n_bins + bin) are appended to a shared-memory chunk;
+//   3. when the chunk fills, it is counting-sorted by key, cut into contiguous
+//      per-lane segments, and each lane accumulates its run of same-bin pairs in
+//      registers (harmonics by Horner polynomials in z^2 times (x + i y)^m),
+//      flushing to the tile's shared accumulators only when its key changes;
+//   4. the tile's sums are written out, and the diagonal-bin residuals
+//      w_i (|a_l^m[b]|^2 - s^m_ll[b]) are summed per CTA, flushed to FP64.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace tpcf {
+
+// Constant tables passed by value (kernel parameter space is a constant bank).
+//
+// Harmonics are accumulated unnormalised: for a unit vector (x, y, z),
+//     Y_l^m = K_lm V_l^m(z) (x + i y)^m,
+// where V_m^m = 1, V_{m+1}^m = (2m + 1) z and
+//     V_l^m = (2l - 1) z V_{l-1}^m - (l + m - 1)(l - m - 1) V_{l-2}^m,
+// (the associated-Legendre recurrence divided through by (l - m)! / (2m - 1)!!),
+// and K_lm = (-1)^m N_lm (2m - 1)!! / (l - m)!.  Every recurrence coefficient is
+// a small integer, exact in single precision, so the float evaluation carries
+// only rounding error; the normalisation enters once, as K_lm at write-out.
+// (Rounded polynomial coefficients would instead give Y_l^m a small non-zero
+// mean over the sphere, a coherent bias that grows with the pair count.)
+struct HarmTables {
+    double K[TPCF_MAX_LMAX + 1][TPCF_MAX_LMAX + 1];
+    // The self accumulator j sums w^2 f_j(z) with f_0 = 1 and f_j = V_{2j}^0 = (2j)! P_{2j}.
+    // gd_hi + gd_lo [jd][j]: V_l^m(z)^2 (1 - z^2)^m = sum_j gd[jd][j] f_j(z) exactly,
+    // jd = (l, m >= 0); the j = k term of the diagonal is K_lm^2 sum_j gd[jd][j] * acc_j.
+    float gd_hi[(TPCF_MAX_LMAX + 1) * (TPCF_MAX_LMAX + 2) / 2][TPCF_MAX_LMAX + 1];
+    float gd_lo[(TPCF_MAX_LMAX + 1) * (TPCF_MAX_LMAX + 2) / 2][TPCF_MAX_LMAX + 1];
+};
+
+template <int LMAX>
+struct Layout {
+    static constexpr int NLM = (LMAX + 1) * (LMAX + 1);
+    static constexpr int NSP = LMAX + 1;
+    static constexpr int NACC = NLM + NSP;
+    static constexpr int NACCP = NACC | 1;  // odd row stride: distinct banks for distinct keys
+    static constexpr int NDIAG = (LMAX + 1) * (LMAX + 2) / 2;
+};
+
+__device__ __forceinline__ void latch_error(int *err, int code)
+{
+    atomicCAS(err, 0, code);
+}
+
+// Accumulates one pair (unit vector x, y, z and weight w) into acc:
+// acc[l^2 + ...] += w V_l^m(z) (x + i y)^m (real / imaginary parts), and the
+// self sums acc[NLM + j] += w^2 f_j(z).
+template <int LMAX>
+__device__ __forceinline__ void accum_pair(float x, float y, float z, float w, float (&acc)[Layout<LMAX>::NACC])
+{
+    constexpr int NLM = Layout<LMAX>::NLM;
+    constexpr int LZ = (2 * LMAX > 1) ? 2 * LMAX : 1;
+    float wc[LMAX + 1], ws[LMAX + 1];
+    wc[0] = w;
+    ws[0] = 0.f;
+    if (LMAX >= 1) {
+        wc[1] = w * x;
+        ws[1] = w * y;
+    }
+#pragma unroll
+    for (int m = 2; m <= LMAX; ++m) {
+        wc[m] = fmaf(wc[m - 1], x, -ws[m - 1] * y);
+        ws[m] = fmaf(wc[m - 1], y, ws[m - 1] * x);
+    }
+    float zl[LZ + 1];                 // zl[l] = (2l - 1) z
+    zl[0] = 0.f;
+#pragma unroll
+    for (int l = 1; l <= LZ; ++l) zl[l] = (float)(2 * l - 1) * z;
+    float v0[LZ + 1];                 // V_l^0, kept for the self sums
+#pragma unroll
+    for (int m = 0; m <= LMAX; ++m) {
+        float vm2 = 0.f, vm1 = 0.f;
+#pragma unroll
+        for (int l = m; l <= LMAX; ++l) {
+            float v;
+            if (l == m) v = 1.f;
+            else if (l == m + 1) v = zl[m + 1];
+            else v = fmaf(zl[l], vm1, -(float)((l + m - 1) * (l - m - 1)) * vm2);
+            vm2 = vm1;
+            vm1 = v;
+            if (m == 0) {
+                v0[l] = v;
+                if (l == 0) acc[0] += w;
+                else acc[l * l] = fmaf(v, wc[0], acc[l * l]);
+            } else {
+                if (l == m) {
+                    acc[l * l + 2 * m - 1] += wc[m];
+                    acc[l * l + 2 * m] += ws[m];
+                } else {
+                    acc[l * l + 2 * m - 1] = fmaf(v, wc[m], acc[l * l + 2 * m - 1]);
+                    acc[l * l + 2 * m] = fmaf(v, ws[m], acc[l * l + 2 * m]);
+                }
+            }
+        }
+    }
+    // continue V_l^0 up to l = 2 LMAX for the self sums
+#pragma unroll
+    for (int l = LMAX + 1; l <= 2 * LMAX; ++l) {
+        if (l == 1) v0[1] = zl[1];
+        else v0[l] = fmaf(zl[l], v0[l - 1], -(float)((l - 1) * (l - 1)) * v0[l - 2]);
+    }
+    const float w2 = w * w;
+    acc[NLM] += w2;
+#pragma unroll
+    for (int j = 1; j <= LMAX; ++j) acc[NLM + j] = fmaf(w2, v0[2 * j], acc[NLM + j]);
+}
+
+// Shared-memory carve-up of the pair kernel (byte offsets).
+struct SmemMap {
+    int off_E, off_Ef, off_prim, off_pf, off_pc;
+    int off_rstart, off_pref, off_rslot;
+    int off_hist, off_cur, off_cnt, off_cstart, off_clen, off_gfirst, off_gsize, off_lanekey;
+    int off_acc, off_ent, off_key, off_sent;
+    int off_d32, off_w32, off_d64, off_w64, off_pairs, off_misc;
+    int total;
+    int maxr;
+};
+
+__host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+template <int LMAX, bool COUNTS>
+__host__ __device__ inline SmemMap make_smem_map(int P, int nb, int s, int chunk, int block)
+{
+    SmemMap m;
+    const int rows = (2 * s + 1) * (2 * s + 1);
+    const int W = block / 32;
+    m.maxr = 2 * P * rows;
+    int o = 0;
+    m.off_E = o;       o = align_up(o + 8 * (TPCF_MAX_BINS + 1), 16);
+    m.off_Ef = o;      o = align_up(o + 4 * (TPCF_MAX_BINS + 1), 16);
+    m.off_prim = o;    o = align_up(o + 16 * TPCF_MAX_TILE, 16);
+    m.off_pf = o;      o = align_up(o + 16 * TPCF_MAX_TILE, 16);
+    m.off_pc = o;      o = align_up(o + 16 * TPCF_MAX_TILE, 16);
+    m.off_rstart = o;  o = align_up(o + 4 * m.maxr, 16);
+    m.off_pref = o;    o = align_up(o + 4 * (m.maxr + 1), 16);
+    m.off_rslot = o;   o = align_up(o + 4 * m.maxr, 16);
+    const int nk = P * nb;
+    m.off_hist = o;    o = align_up(o + 4 * nk, 16);
+    m.off_cur = o;     o = align_up(o + 4 * nk, 16);
+    m.off_cnt = o;     o = align_up(o + 4 * nk, 16);
+    m.off_cstart = o;  o = align_up(o + 4 * nk, 16);
+    m.off_clen = o;    o = align_up(o + 4 * nk, 16);
+    m.off_gfirst = o;  o = align_up(o + 4 * nk, 16);
+    m.off_gsize = o;   o = align_up(o + 4 * nk, 16);
+    m.off_lanekey = o; o = align_up(o + 4 * block, 16);
+    const int naccp = COUNTS ? 0 : Layout<LMAX>::NACCP;
+    const int ndiag = COUNTS ? 0 : Layout<LMAX>::NDIAG;
+    const int nsp = COUNTS ? 0 : Layout<LMAX>::NSP;
+    const int cap = COUNTS ? 0 : chunk;
+    // one accumulator copy per warp (warp-private: plain adds, no atomics)
+    m.off_acc = o;     o = align_up(o + 4 * W * nk * naccp, 16);
+    // unsorted staging; reused as the per-warp transpose area once sorted
+    const int ent_bytes = 16 * cap;
+    const int stage_bytes = COUNTS ? 0 : 4 * block * naccp;
+    m.off_ent = o;     o = align_up(o + (ent_bytes > stage_bytes ? ent_bytes : stage_bytes), 16);
+    m.off_key = o;     o = align_up(o + 4 * cap, 16);
+    m.off_sent = o;    o = align_up(o + 16 * cap, 16);
+    m.off_d32 = o;     o = align_up(o + 4 * nb * ndiag, 16);
+    m.off_w32 = o;     o = align_up(o + 4 * nb * nsp, 16);
+    m.off_d64 = o;     o = align_up(o + 8 * nb * ndiag, 16);
+    m.off_w64 = o;     o = align_up(o + 8 * nb * nsp, 16);
+    m.off_pairs = o;   o = align_up(o + 8 * nb, 16);
+    m.off_misc = o;    o = align_up(o + 64, 16);
+    m.total = o;
+    return m;
+}
+
+// Block-wide exclusive scan of n ints in place at a (any n); returns the total.
+__device__ inline int block_exclusive_scan(int *a, int n, int *scratch32)
+{
+    const int tid = threadIdx.x, T = blockDim.x;
+    const int per = (n + T - 1) / T;
+    const int b0 = tid * per;
+    int local = 0;
+    for (int i = 0; i < per; ++i)
+        if (b0 + i < n) local += a[b0 + i];
+    // warp scan of local sums
+    const int lane = tid & 31, warp = tid >> 5;
+    int v = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) scratch32[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = T >> 5;
+        int x = lane < nw ? scratch32[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        if (lane < nw) scratch32[lane] = x;   // inclusive warp totals
+    }
+    __syncthreads();
+    int run = v - local + (warp > 0 ? scratch32[warp - 1] : 0);
+    const int total = scratch32[(T >> 5) - 1];
+    for (int i = 0; i < per; ++i) {
+        if (b0 + i < n) {
+            int x = a[b0 + i];
+            a[b0 + i] = run;
+            run += x;
+        }
+    }
+    __syncthreads();
+    return total;
+}
+
+template <int LMAX, bool COUNTS>
+__global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairParams p, const HarmTables H)
+{
+    constexpr int NLM = Layout<LMAX>::NLM;
+    constexpr int NACC = Layout<LMAX>::NACC;
+    constexpr int NACCP = Layout<LMAX>::NACCP;
+    constexpr int NDIAG = Layout<LMAX>::NDIAG;
+    constexpr int NSP = Layout<LMAX>::NSP;
+    constexpr int KR = 8;                 // at most this many candidate sweeps between barriers
+    constexpr float TOL = 1.0e-6f;        // > 5 * 2^-24 relative error of the float r^2
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = T >> 5;
+    const int nb = p.nb, P = p.P, s = p.s, nc = p.nc;
+    const int side = 2 * s + 1, rows = side * side;
+    const SmemMap M = make_smem_map<LMAX, COUNTS>(P, nb, s, p.chunk, T);
+
+    unsigned long long *sE = reinterpret_cast<unsigned long long *>(smem + M.off_E);
+    float *sEf = reinterpret_cast<float *>(smem + M.off_Ef);
+    int4 *sPrim = reinterpret_cast<int4 *>(smem + M.off_prim);
+    float4 *sPf = reinterpret_cast<float4 *>(smem + M.off_pf);
+    int4 *sPc = reinterpret_cast<int4 *>(smem + M.off_pc);
+    int *rstart = reinterpret_cast<int *>(smem + M.off_rstart);
+    int *pref = reinterpret_cast<int *>(smem + M.off_pref);
+    int *rslot = reinterpret_cast<int *>(smem + M.off_rslot);
+    int *hist = reinterpret_cast<int *>(smem + M.off_hist);
+    int *cursor = reinterpret_cast<int *>(smem + M.off_cur);
+    int *cnt = reinterpret_cast<int *>(smem + M.off_cnt);
+    int *cstart = reinterpret_cast<int *>(smem + M.off_cstart);
+    int *clen = reinterpret_cast<int *>(smem + M.off_clen);
+    int *gfirst = reinterpret_cast<int *>(smem + M.off_gfirst);
+    int *gsize = reinterpret_cast<int *>(smem + M.off_gsize);
+    int *lanekey = reinterpret_cast<int *>(smem + M.off_lanekey);
+    float *saccw = reinterpret_cast<float *>(smem + M.off_acc);   // [W][P * nb][NACCP]
+    float *sacc = saccw;                                         // copy 0 holds the tile total
+    float4 *ent = reinterpret_cast<float4 *>(smem + M.off_ent);
+    float *stage = reinterpret_cast<float *>(smem + M.off_ent);  // [T][NACCP] after the scatter
+    int *key = reinterpret_cast<int *>(smem + M.off_key);
+    float4 *sent = reinterpret_cast<float4 *>(smem + M.off_sent);
+    float *d32 = reinterpret_cast<float *>(smem + M.off_d32);
+    float *w32 = reinterpret_cast<float *>(smem + M.off_w32);
+    double *d64 = reinterpret_cast<double *>(smem + M.off_d64);
+    double *w64 = reinterpret_cast<double *>(smem + M.off_w64);
+    unsigned long long *spairs = reinterpret_cast<unsigned long long *>(smem + M.off_pairs);
+    int *misc = reinterpret_cast<int *>(smem + M.off_misc);
+    int &s_tile = misc[0];
+    int &s_count = misc[1];
+    int *scratch32 = misc + 8;   // 8 ints: per-warp totals for the scans (W <= 8)
+
+    for (int i = tid; i <= nb; i += T) {
+        sE[i] = p.E[i];
+        sEf[i] = p.Ef[i];
+    }
+    if (!COUNTS) {
+        for (int i = tid; i < nb * NDIAG; i += T) { d32[i] = 0.f; d64[i] = 0.0; }
+        for (int i = tid; i < nb * NSP; i += T) { w32[i] = 0.f; w64[i] = 0.0; }
+    }
+    for (int i = tid; i < nb; i += T) spairs[i] = 0ull;
+    for (int i = tid; i < P * nb; i += T) hist[i] = 0;
+    if (tid == 0) s_count = 0;
+    double mono_w = p.use_mono ? (p.mono_w_dev ? *p.mono_w_dev : p.mono_w) : 0.0;
+    int tiles_since_flush = 0;
+    __syncthreads();
+
+    const int nk = P * nb;
+    const int accw = nk * NACCP;   // floats per warp copy
+
+    // a_0^0[b] from the raw weight sum, in double: Y_0^0 sum w - c_b
+    auto a00 = [&](float wsum, int b) -> float {
+        double v = (double)wsum * H.K[0][0];
+        if (p.use_mono) v -= (mono_w - 1.0) * p.mono_coef[b];
+        return (float)v;
+    };
+
+    // Exact radial bin of an integer separation (-1 if outside [r_min, r_max)).
+    // A float estimate decides unless r^2 is within a relative TOL of an edge,
+    // where the exact 64-bit integer comparison decides.
+    auto exact_bin = [&](int dx, int dy, int dz) -> int {
+        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+        const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+        if (!(r2f >= p.r2_lo && r2f < p.r2_hi)) return -1;
+        int b = (int)((r2f * rsqrtf(r2f) - p.rmin_u) * p.inv_dr_u);
+        b = min(max(b, 0), nb - 1);
+        if ((r2f >= sEf[b] * (1.f + TOL)) && (r2f < sEf[b + 1] * (1.f - TOL))) return b;
+        const long long lx = dx, ly = dy, lz = dz;
+        const unsigned long long r2 = (unsigned long long)(lx * lx) + (unsigned long long)(ly * ly)
+                                    + (unsigned long long)(lz * lz);
+        if (r2 < sE[0] || r2 >= sE[nb]) return -1;
+        while (b > 0 && r2 < sE[b]) --b;
+        while (b < nb - 1 && r2 >= sE[b + 1]) ++b;
+        return b;
+    };
+
+    // ----- chunk processing
+    // 1. warp 0 turns the key histogram into run starts, and assigns every key a
+    //    contiguous group of lanes sized to its run: lam = ceil(n / (T - K)) pairs
+    //    per lane at most (K = keys present), g_k = ceil(len_k / lam) lanes;
+    // 2. counting-sort scatter with warp-aggregated ranks;
+    // 3. every lane accumulates its key's run (stride g_k) in registers;
+    // 4. per warp, a transpose through shared memory sums the lanes of each key
+    //    into the warp's private accumulator copy (no atomics, no conflicts).
+    auto process_chunk = [&]() {
+        __syncthreads();
+        const int n = s_count;
+        if (n > 0) {
+            // 0. exact radial bin and unit vector of every staged pair (converged:
+            //    one pair per thread); pairs outside [r_min, r_max) get key -1
+            for (int base = 0; base < n; base += T) {
+                const int e = base + tid;
+                int k = -1 - lane;   // unique per lane: never matches a real key
+                if (e < n) {
+                    const int4 q = reinterpret_cast<const int4 *>(ent)[e];
+                    const int b = exact_bin(q.x, q.y, q.z);
+                    if (b >= 0) {
+                        const float fx = (float)q.x, fy = (float)q.y, fz = (float)q.z;
+                        const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                        // correctly rounded 1/sqrt: |n|^2 = 1 up to unbiased rounding,
+                        // which the j = k cancellation on diagonal bins needs
+                        const float inv = __frsqrt_rn(r2f);
+                        ent[e] = make_float4(fx * inv, fy * inv, fz * inv, __int_as_float(q.w));
+                        k = key[e] * nb + b;
+                    }
+                    key[e] = k < 0 ? -1 : k;
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, k);
+                if (k >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[k], __popc(peers));
+            }
+            __syncthreads();
+            if (warp == 0) {
+                const int per = (nk + 31) >> 5;     // <= 4 keys per lane (nk <= 128)
+                const int k0 = lane * per;
+                int len[4], loc = 0, act = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    len[i] = (i < per && k0 + i < nk) ? hist[k0 + i] : 0;
+                    loc += len[i];
+                    act += len[i] > 0;
+                }
+                int v = loc, a = act;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t1 = __shfl_up_sync(0xffffffffu, v, o);
+                    const int t2 = __shfl_up_sync(0xffffffffu, a, o);
+                    if (lane >= o) { v += t1; a += t2; }
+                }
+                const int K = __shfl_sync(0xffffffffu, a, 31);
+                const int lam = (n + (T - K) - 1) / (T - K);
+                int gl[4], gsum = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    gl[i] = (len[i] + lam - 1) / lam;
+                    gsum += gl[i];
+                }
+                int gv = gsum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t1 = __shfl_up_sync(0xffffffffu, gv, o);
+                    if (lane >= o) gv += t1;
+                }
+                for (int i = lane; i < T; i += 32) lanekey[i] = -1;
+                __syncwarp();
+                int run = v - loc, g0 = gv - gsum;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (i < per && k0 + i < nk) {
+                        const int k = k0 + i;
+                        cstart[k] = run;
+                        cursor[k] = run;
+                        clen[k] = len[i];
+                        gfirst[k] = g0;
+                        gsize[k] = gl[i];
+                        cnt[k] += len[i];
+                        hist[k] = 0;
+                        for (int q = 0; q < gl[i]; ++q) lanekey[g0 + q] = k;
+                        run += len[i];
+                        g0 += gl[i];
+                    }
+                }
+            }
+            __syncthreads();
+            for (int base = 0; base < n; base += T) {
+                const int e = base + tid;
+                const int k0 = e < n ? key[e] : -1;
+                const bool valid = k0 >= 0;
+                const int k = valid ? k0 : -1 - lane;
+                const unsigned peers = __match_any_sync(0xffffffffu, k);
+                const int leader = __ffs(peers) - 1;
+                int b0 = 0;
+                if (valid && lane == leader) b0 = atomicAdd(&cursor[k], __popc(peers));
+                b0 = __shfl_sync(0xffffffffu, b0, leader);
+                if (valid) sent[b0 + __popc(peers & ((1u << lane) - 1u))] = ent[e];
+            }
+            __syncthreads();
+            float acc[NACC];
+#pragma unroll
+            for (int j = 0; j < NACC; ++j) acc[j] = 0.f;
+            const int myk = lanekey[tid];
+            if (myk >= 0) {
+                const int g = gsize[myk];
+                const int end = cstart[myk] + clen[myk];
+                for (int e = cstart[myk] + (tid - gfirst[myk]); e < end; e += g) {
+                    const float4 v = sent[e];
+                    accum_pair<LMAX>(v.x, v.y, v.z, v.w, acc);
+                }
+            }
+            float *st = stage + (size_t)tid * NACCP;
+#pragma unroll
+            for (int j = 0; j < NACC; ++j) st[j] = acc[j];
+            __syncwarp();
+            float *mine = saccw + (size_t)warp * accw;
+            const float *wst = stage + (size_t)warp * 32 * NACCP;
+            const int *wkey = lanekey + warp * 32;
+            for (int j = lane; j < NACC; j += 32) {
+                int cur = -1;
+                float part = 0.f;
+                for (int l = 0; l < 32; ++l) {
+                    const int kl = wkey[l];
+                    if (kl != cur) {
+                        if (cur >= 0) mine[cur * NACCP + j] += part;
+                        part = 0.f;
+                        cur = kl;
+                    }
+                    if (kl >= 0) part += wst[l * NACCP + j];
+                }
+                if (cur >= 0) mine[cur * NACCP + j] += part;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) s_count = 0;
+        __syncthreads();
+    };
+
+    for (;;) {
+        if (tid == 0) s_tile = atomicAdd(p.work, 1);
+        __syncthreads();
+        const long long t0 = (long long)s_tile * P;
+        if (t0 >= p.n_prim) break;
+        const int np = (int)min((long long)P, p.n_prim - t0);
+
+        // primaries of the tile
+        if (tid < np) {
+            const int4 q = p.prim[t0 + tid];
+            sPrim[tid] = q;
+            const uint32_t ux = (uint32_t)q.x, uy = (uint32_t)q.y, uz = (uint32_t)q.z;
+            sPf[tid] = make_float4((float)ux, (float)uy, (float)uz, __int_as_float(q.w));
+            sPc[tid] = make_int4((int)(((unsigned long long)ux * nc) >> 32),
+                                 (int)(((unsigned long long)uy * nc) >> 32),
+                                 (int)(((unsigned long long)uz * nc) >> 32), 0);
+            const float wq = __int_as_float(q.w);
+            if (!(wq == wq) || isinf(wq)) latch_error(p.err, DEV_ERR_DATA);
+        }
+        for (int i = tid; i < np * nb; i += T) cnt[i] = 0;
+        if (!COUNTS)
+            for (int i = tid; i < W * accw; i += T) saccw[i] = 0.f;
+        __syncthreads();
+
+        // candidate ranges: per (slot, row) up to two contiguous runs of cells
+        const int nr = 2 * np * rows;
+        for (int r = tid; r < np * rows; r += T) {
+            const int slot = r / rows, row = r % rows;
+            const int dz = row / side - s, dy = row % side - s;
+            const int4 pc = sPc[slot];
+            const float4 pf = sPf[slot];
+            const int cy = pc.y + dy, cz = pc.z + dz;
+            int a0 = 0, l0 = 0, a1 = 0, l1 = 0;
+            const float ylo = (float)cy * p.h_u, zlo = (float)cz * p.h_u;
+            const float dyv = fmaxf(0.f, fmaxf(ylo - pf.y, pf.y - (ylo + p.h_u)));
+            const float dzv = fmaxf(0.f, fmaxf(zlo - pf.z, pf.z - (zlo + p.h_u)));
+            const float rr = p.rmax_trim;
+            const float d2 = dyv * dyv + dzv * dzv;
+            bool row_ok = d2 <= rr * rr;
+            int wy = cy, wz = cz;
+            if (p.periodic) {
+                wy = (cy % nc + nc) % nc;
+                wz = (cz % nc + nc) % nc;
+            } else if (cy < 0 || cz < 0 || cy >= nc || cz >= nc) {
+                row_ok = false;
+            }
+            if (row_ok) {
+                const float wx = sqrtf(fmaxf(rr * rr - d2, 0.f)) * 1.0001f + 4096.f;
+                int x0 = (int)floorf((pf.x - wx) / p.h_u);
+                int x1 = (int)floorf((pf.x + wx) / p.h_u);
+                x0 = max(x0, pc.x - s);
+                x1 = min(x1, pc.x + s);
+                if (!p.periodic) {
+                    x0 = max(x0, 0);
+                    x1 = min(x1, nc - 1);
+                }
+                if (x1 >= x0) {
+                    const long long base = ((long long)wz * nc + wy) * nc;
+                    int sa = x0, sb = x1, ta = 1, tb = 0;   // second run empty
+                    if (p.periodic) {
+                        if (x0 < 0) { sa = x0 + nc; sb = nc - 1; ta = 0; tb = x1; }
+                        else if (x1 >= nc) { sa = x0; sb = nc - 1; ta = 0; tb = x1 - nc; }
+                    }
+                    a0 = p.cell_start[base + sa];
+                    l0 = p.cell_start[base + sb + 1] - a0;
+                    if (tb >= ta) {
+                        a1 = p.cell_start[base + ta];
+                        l1 = p.cell_start[base + tb + 1] - a1;
+                    }
+                }
+            }
+            rstart[2 * r] = a0; pref[2 * r] = l0; rslot[2 * r] = slot;
+            rstart[2 * r + 1] = a1; pref[2 * r + 1] = l1; rslot[2 * r + 1] = slot;
+        }
+        __syncthreads();
+        const int total = block_exclusive_scan(pref, nr, scratch32);
+        if (tid == 0) pref[nr] = total;
+        __syncthreads();
+
+        int cur = 0;
+        for (int base = 0; base < total;) {
+            int kr = KR;
+            if (!COUNTS) {
+                __syncthreads();
+                const int c = s_count;   // every thread reads before anyone appends again
+                __syncthreads();
+                kr = (p.chunk - c) / T;  // a sweep adds at most T pairs
+                if (kr < 1) {
+                    process_chunk();
+                    kr = p.chunk / T;
+                }
+                kr = min(kr, KR);
+            }
+            for (int k = 0; k < kr; ++k) {
+                const int pos = base + k * T + tid;
+                bool ok = false;
+                int slot = 0, dx = 0, dy = 0, dz = 0, wbits = 0;
+                if (pos < total) {
+                    while (pref[cur + 1] <= pos) ++cur;
+                    slot = rslot[cur];
+                    const int idx = rstart[cur] + (pos - pref[cur]);
+                    const int4 q = p.rec[idx];
+                    const int4 pr = sPrim[slot];
+                    dx = (int)((uint32_t)q.x - (uint32_t)pr.x);
+                    dy = (int)((uint32_t)q.y - (uint32_t)pr.y);
+                    dz = (int)((uint32_t)q.z - (uint32_t)pr.z);
+                    wbits = q.w;
+                    if (COUNTS) {
+                        const int b = exact_bin(dx, dy, dz);
+                        if (b >= 0) atomicAdd(&cnt[slot * nb + b], 1);
+                    } else {
+                        // cheap window test only; binning happens at chunk time
+                        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+                        const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                        ok = (r2f >= p.r2_lo && r2f < p.r2_hi);
+                    }
+                }
+                if (!COUNTS) {
+                    const unsigned bal = __ballot_sync(0xffffffffu, ok);
+                    if (bal) {
+                        const int leader = __ffs(bal) - 1;
+                        int b0 = 0;
+                        if (lane == leader) b0 = atomicAdd(&s_count, __popc(bal));
+                        b0 = __shfl_sync(0xffffffffu, b0, leader);
+                        if (ok) {
+                            const int at = b0 + __popc(bal & ((1u << lane) - 1u));
+                            reinterpret_cast<int4 *>(ent)[at] = make_int4(dx, dy, dz, wbits);
+                            key[at] = slot;
+                        }
+                    }
+                }
+            }
+            base += kr * T;
+        }
+        if (!COUNTS) {
+            process_chunk();
+            for (int i = tid; i < np * nb * NACCP; i += T) {
+                float t = 0.f;
+                for (int w = 0; w < W; ++w) t += saccw[(size_t)w * accw + i];
+                sacc[i] = t;
+            }
+        }
+        __syncthreads();
+
+        // ----- tile outputs
+        const long long g0 = t0;
+        if (!COUNTS && p.alm) {
+            for (int i = tid; i < np * nb * NLM; i += T) {
+                const int slot = i / (nb * NLM), rem = i % (nb * NLM);
+                const int b = rem / NLM, k = rem % NLM;
+                const float raw = sacc[(slot * nb + b) * NACCP + k];
+                float v;
+                if (k == 0) {
+                    v = a00(raw, b);
+                } else {
+                    int l = 1;
+                    while ((l + 1) * (l + 1) <= k) ++l;
+                    const int m = (k - l * l + 1) >> 1;
+                    v = (float)((double)raw * H.K[l][m]);
+                }
+                p.alm[(g0 + slot) * nb * NLM + rem] = v;
+            }
+        }
+        if (p.counts)
+            for (int i = tid; i < np * nb; i += T) p.counts[g0 * nb + i] = cnt[i];
+        for (int b = tid; b < nb; b += T) {
+            unsigned long long t = 0;
+            for (int sl = 0; sl < np; ++sl) t += (unsigned long long)cnt[sl * nb + b];
+            spairs[b] += t;
+        }
+        if (!COUNTS) {
+            // diagonal-bin residuals and self sums, FP32 per tile
+            for (int i = tid; i < nb * NDIAG; i += T) {
+                const int b = i / NDIAG, jd = i % NDIAG;
+                int l = 0;
+                while ((l + 1) * (l + 2) / 2 <= jd) ++l;
+                const int m = jd - l * (l + 1) / 2;
+                // residual in unnormalised units, then one common scale K_lm^2, so the
+                // cancellation between |a|^2 and the j = k term is exact in exact arithmetic
+                float acc = 0.f;
+                const float k2 = (float)(H.K[l][m] * H.K[l][m]);
+                for (int sl = 0; sl < np; ++sl) {
+                    const float *a = sacc + (sl * nb + b) * NACCP;
+                    float self = 0.f;
+                    if (p.remove_self)
+                        for (int j = 0; j <= LMAX; ++j) {
+                            self = fmaf(H.gd_hi[jd][j], a[NLM + j], self);
+                            self = fmaf(H.gd_lo[jd][j], a[NLM + j], self);
+                        }
+                    float d;
+                    if (l == 0) {
+                        const float re = a00(a[0], b);   // includes the analytic-random offset
+                        d = fmaf(re, re, -k2 * self);
+                    } else {
+                        const float re = a[l * l + (m ? 2 * m - 1 : 0)];
+                        const float im = m ? a[l * l + 2 * m] : 0.f;
+                        d = k2 * (fmaf(re, re, im * im) - self);
+                    }
+                    acc += __int_as_float(sPrim[sl].w) * d;
+                }
+                d32[i] += acc;
+            }
+            for (int i = tid; i < nb * NSP; i += T) {
+                const int b = i / NSP, j = i % NSP;
+                float acc = 0.f;
+                for (int sl = 0; sl < np; ++sl)
+                    acc += __int_as_float(sPrim[sl].w) * sacc[(sl * nb + b) * NACCP + NLM + j];
+                w32[i] += acc;
+            }
+            if (++tiles_since_flush >= 16) {
+                tiles_since_flush = 0;
+                for (int i = tid; i < nb * NDIAG; i += T) { d64[i] += (double)d32[i]; d32[i] = 0.f; }
+                for (int i = tid; i < nb * NSP; i += T) { w64[i] += (double)w32[i]; w32[i] = 0.f; }
+            }
+        }
+        __syncthreads();
+    }
+
+    // ----- CTA totals to global
+    __syncthreads();
+    if (!COUNTS) {
+        for (int i = tid; i < nb * NDIAG; i += T) {
+            const double v = d64[i] + (double)d32[i];
+            const int b = i / NDIAG, jd = i % NDIAG;
+            if (p.diag) atomicAdd(p.diag + (size_t)jd * nb + b, v);
+        }
+        for (int i = tid; i < nb * NSP; i += T) {
+            const double v = w64[i] + (double)w32[i];
+            const int b = i / NSP, j = i % NSP;
+            if (p.wsp) atomicAdd(p.wsp + (size_t)j * nb + b, v);
+        }
+    }
+    if (p.pair_counts)
+        for (int b = tid; b < nb; b += T)
+            if (spairs[b]) atomicAdd(p.pair_counts + b, spairs[b]);
+}
+
+}  // namespace tpcf

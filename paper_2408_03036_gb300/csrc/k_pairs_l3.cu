@@ -1,0 +1,36 @@
+// Instantiation of the pair-stage kernel for l_max = 3 (one translation unit
+// per l_max so the unrolled variants compile in parallel).
+#include "k_pairs.cuh"
+
+namespace tpcf {
+
+template <int LMAX, bool COUNTS>
+static cudaError_t launch_one(const PairParams &p, const HarmTables &h, int grid, int block,
+                              size_t smem, cudaStream_t st)
+{
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_pairs<LMAX, COUNTS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_pairs<LMAX, COUNTS><<<grid, block, smem, st>>>(p, h);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_l3(bool counts_only, const PairParams &p, const HarmTables &h, int grid,
+                             int block, size_t smem, cudaStream_t st)
+{
+    if (counts_only) return cudaErrorInvalidValue;
+    return launch_one<3, false>(p, h, grid, block, smem, st);
+}
+
+size_t pairs_smem_l3(bool counts_only, int P, int nb, int s, int chunk, int block)
+{
+    if (counts_only) return (size_t)make_smem_map<0, true>(P, nb, s, chunk, block).total;
+    return (size_t)make_smem_map<3, false>(P, nb, s, chunk, block).total;
+}
+
+}  // namespace tpcf

@@ -1,0 +1,836 @@
+// Host side of libtpcf: argument checks, exact bin edges, constant tables
+// (harmonic polynomials, 3j / Gaunt coefficients, projection weights), scratch
+// management and the C-ABI entry points declared in include/tpcf.h.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include <atomic>
+
+#include <cuda_runtime.h>
+
+#include "internal.h"
+#include "k_pairs.cuh"
+
+namespace tpcf {
+cudaError_t launch_pairs_l0(bool, const PairParams &, const HarmTables &, int, int, size_t, cudaStream_t);
+cudaError_t launch_pairs_l1(bool, const PairParams &, const HarmTables &, int, int, size_t, cudaStream_t);
+cudaError_t launch_pairs_l2(bool, const PairParams &, const HarmTables &, int, int, size_t, cudaStream_t);
+cudaError_t launch_pairs_l3(bool, const PairParams &, const HarmTables &, int, int, size_t, cudaStream_t);
+cudaError_t launch_pairs_l4(bool, const PairParams &, const HarmTables &, int, int, size_t, cudaStream_t);
+cudaError_t launch_pairs_l5(bool, const PairParams &, const HarmTables &, int, int, size_t, cudaStream_t);
+cudaError_t launch_pairs_l6(bool, const PairParams &, const HarmTables &, int, int, size_t, cudaStream_t);
+size_t pairs_smem_l0(bool, int, int, int, int, int);
+size_t pairs_smem_l1(bool, int, int, int, int, int);
+size_t pairs_smem_l2(bool, int, int, int, int, int);
+size_t pairs_smem_l3(bool, int, int, int, int, int);
+size_t pairs_smem_l4(bool, int, int, int, int, int);
+size_t pairs_smem_l5(bool, int, int, int, int, int);
+size_t pairs_smem_l6(bool, int, int, int, int, int);
+}  // namespace tpcf
+
+using namespace tpcf;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+void tpcf::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+struct tpcf_grid_s {
+    GridDev g;
+    cudaStream_t stream;
+    int device;
+};
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwo32 = 4294967296.0;
+
+thread_local char g_msg[512] = "";
+
+int fail(int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(TPCF_ERR_OOM, "%s: out of device memory", where);
+    return fail(TPCF_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                           \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);               \
+    } while (0)
+
+// ---------------------------------------------------------------- config
+
+int check_config(const tpcf_config *c)
+{
+    if (!c) return fail(TPCF_ERR_ARG, "config is NULL");
+    if (c->n_bins < 1 || c->n_bins > TPCF_MAX_BINS) return fail(TPCF_ERR_ARG, "n_bins must be 1..%d", TPCF_MAX_BINS);
+    if (c->l_max < 0 || c->l_max > TPCF_MAX_LMAX) return fail(TPCF_ERR_ARG, "l_max must be 0..%d", TPCF_MAX_LMAX);
+    if (!(c->box > 0.0) || !std::isfinite(c->box)) return fail(TPCF_ERR_ARG, "box must be positive");
+    if (!(c->r_min > 0.0)) return fail(TPCF_ERR_ARG, "r_min must be > 0");
+    if (!(c->r_max > c->r_min)) return fail(TPCF_ERR_ARG, "r_max must exceed r_min");
+    if (!(2.0 * c->r_max < c->box)) return fail(TPCF_ERR_ARG, "r_max must be below box/2");
+    if (c->n_L < 1 || c->n_L > 8) return fail(TPCF_ERR_ARG, "n_L must be 1..8");
+    for (int i = 0; i < c->n_L; ++i)
+        if (c->L[i] < 0 || c->L[i] > 2 * c->l_max || (c->L[i] & 1))
+            return fail(TPCF_ERR_ARG, "L values must be even and in 0..2*l_max");
+    if (c->precision < TPCF_PREC_FP32 || c->precision > TPCF_PREC_TF32X3)
+        return fail(TPCF_ERR_ARG, "unknown precision");
+    if (c->convention != TPCF_CONV_S_COEFF && c->convention != TPCF_CONV_PAPER_EQ)
+        return fail(TPCF_ERR_ARG, "unknown convention");
+    if (c->remove_self != 0 && c->remove_self != 1) return fail(TPCF_ERR_ARG, "remove_self must be 0 or 1");
+    if (c->cell_div < 0 || c->cell_div > 6) return fail(TPCF_ERR_ARG, "cell_div must be 0..6");
+    if (c->tile_primaries < 0 || c->tile_primaries > TPCF_MAX_TILE) return fail(TPCF_ERR_ARG, "tile_primaries must be 0..8");
+    if (c->chunk != 0 && (c->chunk < 512 || (c->chunk % 256) != 0 || c->chunk > 8192))
+        return fail(TPCF_ERR_ARG, "chunk must be 0 or a multiple of 256 in 512..8192");
+    return TPCF_OK;
+}
+
+// Exact ceil(s^2) of a finite double s >= 0 from its IEEE-754 fields.
+unsigned long long ceil_sq(double s)
+{
+    if (!(s > 0.0)) return 0ull;
+    uint64_t bits;
+    std::memcpy(&bits, &s, 8);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    uint64_t mant = bits & ((1ull << 52) - 1);
+    int e2;
+    if (ex == 0) { e2 = -1074; } else { mant |= (1ull << 52); e2 = ex - 1075; }
+    const unsigned __int128 sq = (unsigned __int128)mant * mant;   // s^2 = sq * 2^(2 e2)
+    const int sh = -2 * e2;
+    if (sh <= 0) return (unsigned long long)(sq << (-sh));
+    if (sh >= 128) return 1ull;
+    const unsigned __int128 q = sq >> sh;
+    const unsigned __int128 rem = sq - (q << sh);
+    return (unsigned long long)(q + (rem != 0 ? 1 : 0));
+}
+
+void edge_tables(const tpcf_config *c, unsigned long long *E, double *r)
+{
+    for (int b = 0; b <= c->n_bins; ++b) {
+        const double rb = c->r_min + ((c->r_max - c->r_min) * (double)b) / (double)c->n_bins;
+        const double sb = (rb * kTwo32) / c->box;
+        E[b] = ceil_sq(sb);
+        if (r) r[b] = rb;
+    }
+}
+
+// ------------------------------------------------------------- 3j symbols
+
+double factd(int n)
+{
+    static double tab[64];
+    static bool init = false;
+    if (!init) {
+        tab[0] = 1.0;
+        for (int i = 1; i < 64; ++i) tab[i] = tab[i - 1] * (double)i;
+        init = true;
+    }
+    return (n >= 0 && n < 64) ? tab[n] : NAN;
+}
+
+// Wigner 3j symbol for integer arguments (Racah's closed form).
+double w3j(int a, int b, int c, int ma, int mb, int mc)
+{
+    if (ma + mb + mc != 0 || c < std::abs(a - b) || c > a + b) return 0.0;
+    if (std::abs(ma) > a || std::abs(mb) > b || std::abs(mc) > c) return 0.0;
+    const double delta = factd(a + b - c) * factd(a - b + c) * factd(b + c - a) / factd(a + b + c + 1);
+    const double norm = std::sqrt(delta * factd(a + ma) * factd(a - ma) * factd(b + mb) * factd(b - mb)
+                                  * factd(c + mc) * factd(c - mc));
+    int tlo = std::max(0, std::max(b - c - ma, a - c + mb));
+    int thi = std::min(a + b - c, std::min(a - ma, b + mb));
+    double sum = 0.0;
+    for (int t = tlo; t <= thi; ++t) {
+        const double d = factd(t) * factd(c - b + t + ma) * factd(c - a + t - mb) * factd(a + b - c - t)
+                       * factd(a - t - ma) * factd(b - t + mb);
+        sum += ((t % 2) ? -1.0 : 1.0) / d;
+    }
+    const int ph = a - b - mc;
+    return (((ph % 2) + 2) % 2 ? -1.0 : 1.0) * norm * sum;
+}
+
+double nlm(int l, int m)
+{
+    return std::sqrt((2.0 * l + 1.0) / (4.0 * kPi) * factd(l - m) / factd(l + m));
+}
+
+// Polynomials with double coefficients (index = power of the variable).
+using Poly = std::vector<double>;
+
+Poly pmul(const Poly &a, const Poly &b)
+{
+    Poly r(a.size() + b.size() - 1, 0.0);
+    for (size_t i = 0; i < a.size(); ++i)
+        for (size_t j = 0; j < b.size(); ++j) r[i + j] += a[i] * b[j];
+    return r;
+}
+
+// V_l^m(z) in powers of z: V_m = 1, V_{m+1} = (2m+1) z,
+// V_l = (2l-1) z V_{l-1} - (l+m-1)(l-m-1) V_{l-2}; integer coefficients, exact in double.
+Poly v_poly(int l, int m)
+{
+    Poly vm2{1.0}, vm1{0.0, (double)(2 * m + 1)};
+    if (l == m) return vm2;
+    if (l == m + 1) return vm1;
+    Poly v;
+    for (int k = m + 2; k <= l; ++k) {
+        v.assign(k - m + 1, 0.0);
+        for (size_t i = 0; i < vm1.size(); ++i) v[i + 1] += (2.0 * k - 1.0) * vm1[i];
+        const double c = (double)((k + m - 1) * (k - m - 1));
+        for (size_t i = 0; i < vm2.size(); ++i) v[i] -= c * vm2[i];
+        vm2 = vm1;
+        vm1 = v;
+    }
+    return vm1;
+}
+
+// Even polynomial in z -> polynomial in y = z^2.
+Poly even_to_y(const Poly &p)
+{
+    Poly r((p.size() + 1) / 2, 0.0);
+    for (size_t i = 0; i < p.size(); i += 2) r[i / 2] = p[i];
+    return r;
+}
+
+// Y_l^m = K_lm V_l^m(z) (x + i y)^m
+double k_scale(int l, int m)
+{
+    double dfact = 1.0;
+    for (int i = 1; i <= 2 * m - 1; i += 2) dfact *= (double)i;
+    return ((m % 2) ? -1.0 : 1.0) * nlm(l, m) * dfact / factd(l - m);
+}
+
+// f_j(y) of the device's self accumulators: f_0 = 1, f_j = V_{2j}^0.
+Poly f_poly(int j) { return j == 0 ? Poly{1.0} : even_to_y(v_poly(2 * j, 0)); }
+
+// g_j with V_l1^m V_l2^m (1 - y)^m = sum_j g_j f_j(y)   (l1 + l2 even), exactly
+// (integer polynomials; the solve is a triangular back-substitution in double).
+std::vector<double> self_coefs(int lmax, int l1, int l2, int m)
+{
+    Poly t = even_to_y(pmul(v_poly(l1, m), v_poly(l2, m)));
+    for (int k = 0; k < m; ++k) t = pmul(t, Poly{1.0, -1.0});
+    std::vector<double> g(lmax + 1, 0.0);
+    for (int j = (int)t.size() - 1; j >= 0; --j) {
+        if (j > lmax) continue;   // degree <= max(l1, l2) <= lmax
+        const Poly f = f_poly(j);
+        const double c = t[j] / f[j];
+        g[j] = c;
+        for (int k = 0; k <= j; ++k) t[k] -= c * f[k];
+    }
+    return g;
+}
+
+HarmTables make_tables(int lmax)
+{
+    HarmTables h;
+    std::memset(&h, 0, sizeof(h));
+    for (int l = 0; l <= TPCF_MAX_LMAX; ++l)
+        for (int m = 0; m <= l; ++m) h.K[l][m] = k_scale(l, m);
+    int jd = 0;
+    for (int l = 0; l <= lmax; ++l)
+        for (int m = 0; m <= l; ++m, ++jd) {
+            const std::vector<double> g = self_coefs(lmax, l, l, m);
+            for (int j = 0; j <= lmax; ++j) {
+                const float hi = (float)g[j];
+                h.gd_hi[jd][j] = hi;
+                h.gd_lo[jd][j] = (float)(g[j] - (double)hi);
+            }
+        }
+    return h;
+}
+
+void multipole_list(const tpcf_config *c, std::vector<int> &out)
+{
+    out.clear();
+    for (int i = 0; i < c->n_L; ++i) {
+        const int L = c->L[i];
+        for (int l1 = 0; l1 <= c->l_max; ++l1)
+            for (int l2 = 0; l2 <= c->l_max; ++l2)
+                if (std::abs(l1 - l2) <= L && L <= l1 + l2 && ((l1 + l2 + L) % 2) == 0) {
+                    out.push_back(l1); out.push_back(l2); out.push_back(L);
+                }
+    }
+}
+
+// ------------------------------------------------------------ device state
+
+struct DevState {
+    int *err = nullptr;
+    int sms = 0;
+};
+std::mutex g_mu;
+DevState g_dev[64];
+
+int dev_state(DevState **out)
+{
+    int d = 0;
+    CK(cudaGetDevice(&d));
+    if (d < 0 || d >= 64) return fail(TPCF_ERR_CUDA, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_mu);
+    DevState &s = g_dev[d];
+    if (!s.err) {
+        CK(cudaMalloc((void **)&s.err, sizeof(int)));
+        CK(cudaMemset(s.err, 0, sizeof(int)));
+        CK(cudaDeviceGetAttribute(&s.sms, cudaDevAttrMultiProcessorCount, d));
+    }
+    *out = &s;
+    return TPCF_OK;
+}
+
+// ------------------------------------------------------------ scheduling
+
+struct Plan {
+    int s;      // cells scanned on each side
+    int nc;     // cells per axis
+    int P;      // primaries per tile
+    int chunk;
+};
+
+Plan make_plan(const tpcf_config *c, int64_t n_sec, int64_t n_prim_hint)
+{
+    Plan p;
+    const double nbar = (double)(n_sec > 0 ? n_sec : 1) / (c->box * c->box * c->box);
+    int s = c->cell_div;
+    if (s == 0) {
+        // about 24 points per cell, cells no smaller than r_max / 4
+        const double h_want = std::cbrt(24.0 / nbar);
+        s = (int)std::floor(c->r_max / h_want);
+        s = std::max(1, std::min(4, s));
+    }
+    for (;;) {
+        int nc = (int)std::floor((double)s * c->box / c->r_max);
+        nc = std::min(nc, 256);
+        const int need = c->periodic ? 2 * s + 1 : 2 * s + 3;
+        if (nc >= need || s == 1) { p.s = s; p.nc = std::max(nc, 1); break; }
+        --s;
+    }
+    const double vol = 4.0 / 3.0 * kPi * (c->r_max * c->r_max * c->r_max - c->r_min * c->r_min * c->r_min);
+    const double pairs = nbar * vol;
+    int P = c->tile_primaries;
+    if (P == 0) {
+        P = (int)std::lround(3000.0 / std::max(pairs, 1.0));
+        P = std::max(1, std::min(TPCF_MAX_TILE, P));
+    }
+    // the chunk's lane groups need P * n_bins <= 128 keys (half the CTA's lanes)
+    P = std::min(P, std::max(1, 128 / c->n_bins));
+    p.P = P;
+    p.chunk = c->chunk ? c->chunk : 2048;
+    (void)n_prim_hint;
+    return p;
+}
+
+size_t pair_smem(int lmax, bool counts, const Plan &pl, int nb)
+{
+    switch (counts ? 0 : lmax) {
+    case 0: return pairs_smem_l0(counts, pl.P, nb, pl.s, pl.chunk, 256);
+    case 1: return pairs_smem_l1(counts, pl.P, nb, pl.s, pl.chunk, 256);
+    case 2: return pairs_smem_l2(counts, pl.P, nb, pl.s, pl.chunk, 256);
+    case 3: return pairs_smem_l3(counts, pl.P, nb, pl.s, pl.chunk, 256);
+    case 4: return pairs_smem_l4(counts, pl.P, nb, pl.s, pl.chunk, 256);
+    case 5: return pairs_smem_l5(counts, pl.P, nb, pl.s, pl.chunk, 256);
+    default: return pairs_smem_l6(counts, pl.P, nb, pl.s, pl.chunk, 256);
+    }
+}
+
+cudaError_t pair_launch(int lmax, bool counts, const PairParams &p, const HarmTables &h, int grid, size_t smem,
+                        cudaStream_t st)
+{
+    switch (counts ? 0 : lmax) {
+    case 0: return launch_pairs_l0(counts, p, h, grid, 256, smem, st);
+    case 1: return launch_pairs_l1(counts, p, h, grid, 256, smem, st);
+    case 2: return launch_pairs_l2(counts, p, h, grid, 256, smem, st);
+    case 3: return launch_pairs_l3(counts, p, h, grid, 256, smem, st);
+    case 4: return launch_pairs_l4(counts, p, h, grid, 256, smem, st);
+    case 5: return launch_pairs_l5(counts, p, h, grid, 256, smem, st);
+    default: return launch_pairs_l6(counts, p, h, grid, 256, smem, st);
+    }
+}
+
+// Runs the pair stage over `n_prim` primary records against grid g.
+int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t n_prim, bool counts_only,
+              double mono_w, const double *mono_w_dev, bool use_mono, float *alm, int32_t *counts, double *diag,
+              double *wsp, unsigned long long *pair_counts, cudaStream_t st)
+{
+    DevState *ds;
+    int rc = dev_state(&ds);
+    if (rc) return rc;
+    if (n_prim <= 0) return TPCF_OK;
+    Plan pl = make_plan(c, g.n, n_prim);
+    // the grid's cell count was fixed when it was built; recover s for it
+    pl.nc = g.nc;
+    int s = std::max(1, (int)std::ceil(c->r_max * g.nc / c->box - 1e-9));
+    pl.s = s;
+    if (c->periodic && 2 * s + 1 > g.nc) return fail(TPCF_ERR_ARG, "grid too coarse for r_max (periodic)");
+    if (!c->periodic && 2 * s + 2 >= g.nc) return fail(TPCF_ERR_ARG, "grid too coarse for r_max (open volume)");
+
+    PairParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.rec = g.rec;
+    p.cell_start = g.cell_start;
+    p.nc = g.nc;
+    p.s = pl.s;
+    p.periodic = c->periodic;
+    p.prim = prim;
+    p.n_prim = n_prim;
+    p.nb = c->n_bins;
+    p.P = pl.P;
+    double r[TPCF_MAX_BINS + 1];
+    edge_tables(c, p.E, r);
+    for (int b = 0; b <= c->n_bins; ++b) p.Ef[b] = (float)(double)p.E[b];
+    const double u = kTwo32 / c->box;   // units per length
+    p.rmin_u = (float)(c->r_min * u);
+    p.inv_dr_u = (float)((double)c->n_bins / ((c->r_max - c->r_min) * u));
+    p.r2_lo = (float)((double)p.E[0] * (1.0 - 4e-6));
+    p.r2_hi = (float)((double)p.E[c->n_bins] * (1.0 + 4e-6));
+    p.rmax_trim = (float)(c->r_max * u * (1.0 + 1e-5) + 4096.0);
+    p.h_u = (float)(kTwo32 / (double)g.nc);
+    for (int b = 0; b < c->n_bins; ++b) {
+        const double vb = 4.0 * kPi / 3.0 * (r[b + 1] * r[b + 1] * r[b + 1] - r[b] * r[b] * r[b]);
+        p.mono_coef[b] = vb / (c->box * c->box * c->box) / std::sqrt(4.0 * kPi);
+    }
+    p.use_mono = use_mono ? 1 : 0;
+    p.mono_w = mono_w;
+    p.mono_w_dev = mono_w_dev;
+    p.remove_self = c->remove_self;
+    p.alm = alm;
+    p.counts = counts;
+    p.diag = diag;
+    p.wsp = wsp;
+    p.pair_counts = pair_counts;
+    p.err = ds->err;
+    const HarmTables h = make_tables(counts_only ? 0 : c->l_max);
+
+    size_t smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
+    while (smem > 227 * 1024 && pl.chunk > 512) {
+        pl.chunk -= 256;
+        smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
+    }
+    while (smem > 227 * 1024 && pl.P > 1) {
+        --pl.P;
+        smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
+    }
+    if (smem > 227 * 1024) return fail(TPCF_ERR_UNSUPPORTED, "pair stage needs %zu bytes of shared memory", smem);
+    p.P = pl.P;
+    p.chunk = pl.chunk;
+    int *work = nullptr;
+    CK(cudaMallocAsync((void **)&work, sizeof(int), st));
+    CK(cudaMemsetAsync(work, 0, sizeof(int), st));
+    p.work = work;
+    const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+    int grid = ds->sms * per_sm;
+    const int64_t tiles = (n_prim + pl.P - 1) / pl.P;
+    if (grid > tiles) grid = (int)tiles;
+    cudaError_t e = pair_launch(c->l_max, counts_only, p, h, grid, smem, st);
+    cudaFreeAsync(work, st);
+    if (e != cudaSuccess) return cuda_fail(e, "pair stage launch");
+    return TPCF_OK;
+}
+
+int couple(const tpcf_config *c, const float *alm, const float *w, const int32_t *counts, int64_t K,
+           const double *diag, const double *wsp, double *nnn, unsigned long long *trip_u64, cudaStream_t st)
+{
+    const int nb = c->n_bins, L = c->l_max;
+    if (c->precision != TPCF_PREC_FP32)
+        return fail(TPCF_ERR_UNSUPPORTED, "tensor-core coupling not available in this build");
+    int64_t gsz = gram_offset(nb, L, L + 1);
+    double *G = nullptr, *gaunt = nullptr;
+    CK(cudaMallocAsync((void **)&G, gsz * sizeof(double), st));
+    CK(cudaMemsetAsync(G, 0, gsz * sizeof(double), st));
+    const int L1 = L + 1;
+    std::vector<double> hg((size_t)L1 * L1 * L1 * L1, 0.0);
+    for (int m = 0; m <= L; ++m)
+        for (int l1 = m; l1 <= L; ++l1)
+            for (int l2 = m; l2 <= L; ++l2) {
+                if ((l1 + l2) & 1) continue;
+                const std::vector<double> g = self_coefs(L, l1, l2, m);
+                const double kk = k_scale(l1, m) * k_scale(l2, m);
+                for (int j = 0; j <= L; ++j) hg[(((size_t)m * L1 + l1) * L1 + l2) * L1 + j] = kk * g[j];
+            }
+    CK(cudaMallocAsync((void **)&gaunt, hg.size() * sizeof(double), st));
+    CK(cudaMemcpyAsync(gaunt, hg.data(), hg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(couple_gram_fp32(alm, w, K, nb, L, G, st));
+    CK(assemble_nnn(G, diag, wsp, nb, L, c->remove_self, gaunt, nnn, st));
+    if (counts && trip_u64) CK(tpcf::triplet_counts(counts, K, nb, trip_u64, st));
+    // the host vector must outlive the asynchronous copy
+    CK(cudaStreamSynchronize(st));
+    cudaFreeAsync(G, st);
+    cudaFreeAsync(gaunt, st);
+    return TPCF_OK;
+}
+
+int project(const tpcf_config *c, const double *nnn, const double *rrr, double *zeta, cudaStream_t st)
+{
+    std::vector<int> ml;
+    multipole_list(c, ml);
+    const int nm = (int)ml.size() / 3, L1 = c->l_max + 1;
+    std::vector<double> coef((size_t)nm * L1, 0.0);
+    for (int k = 0; k < nm; ++k) {
+        const int l1 = ml[3 * k], l2 = ml[3 * k + 1], L = ml[3 * k + 2];
+        const double H = w3j(l1, l2, L, 0, 0, 0);
+        double conv = (c->convention == TPCF_CONV_S_COEFF) ? std::sqrt((2.0 * l1 + 1.0) * (2.0 * l2 + 1.0)) : 1.0;
+        for (int m = 0; m <= std::min(l1, l2); ++m) {
+            const double t = w3j(l1, l2, L, m, -m, 0) * ((m % 2) ? -1.0 : 1.0);
+            coef[(size_t)k * L1 + m] = conv * (2.0 * L + 1.0) * H * (m == 0 ? t : 2.0 * t);
+        }
+    }
+    double *dcoef = nullptr;
+    int *dml = nullptr;
+    CK(cudaMallocAsync((void **)&dcoef, coef.size() * sizeof(double) + 8, st));
+    CK(cudaMallocAsync((void **)&dml, ml.size() * sizeof(int) + 4, st));
+    CK(cudaMemcpyAsync(dcoef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dml, ml.data(), ml.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(project_zeta(nnn, rrr, c->n_bins, c->l_max, nm, dcoef, dml, zeta, st));
+    CK(cudaStreamSynchronize(st));
+    cudaFreeAsync(dcoef, st);
+    cudaFreeAsync(dml, st);
+    return TPCF_OK;
+}
+
+int choose_nc(const tpcf_config *c, int64_t n)
+{
+    return make_plan(c, n, n).nc;
+}
+
+int mono_coef_dev(const tpcf_config *c, double **out, cudaStream_t st)
+{
+    double r[TPCF_MAX_BINS + 1];
+    unsigned long long E[TPCF_MAX_BINS + 1];
+    edge_tables(c, E, r);
+    std::vector<double> coef(c->n_bins);
+    for (int b = 0; b < c->n_bins; ++b) {
+        const double vb = 4.0 * kPi / 3.0 * (r[b + 1] * r[b + 1] * r[b + 1] - r[b] * r[b] * r[b]);
+        coef[b] = vb / (c->box * c->box * c->box) / std::sqrt(4.0 * kPi);
+    }
+    CK(cudaMallocAsync((void **)out, c->n_bins * sizeof(double), st));
+    CK(cudaMemcpyAsync(*out, coef.data(), c->n_bins * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return TPCF_OK;
+}
+
+template <class T>
+int dalloc(T **p, size_t n, cudaStream_t st, bool zero)
+{
+    CK(cudaMallocAsync((void **)p, (n ? n : 1) * sizeof(T), st));
+    if (zero) CK(cudaMemsetAsync(*p, 0, (n ? n : 1) * sizeof(T), st));
+    return TPCF_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+
+extern "C" {
+
+const char *tpcf_last_error(void) { return g_msg; }
+
+int tpcf_version(void) { return 100; }
+
+int64_t tpcf_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
+
+int tpcf_multipole_count(const tpcf_config *cfg, int32_t *n_mult)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!n_mult) return fail(TPCF_ERR_ARG, "n_mult is NULL");
+    std::vector<int> ml;
+    multipole_list(cfg, ml);
+    *n_mult = (int32_t)(ml.size() / 3);
+    return TPCF_OK;
+}
+
+int tpcf_multipole_index(const tpcf_config *cfg, int32_t *l1l2L, int32_t cap)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    std::vector<int> ml;
+    multipole_list(cfg, ml);
+    if (!l1l2L || cap < (int32_t)(ml.size() / 3)) return fail(TPCF_ERR_ARG, "output too small");
+    for (size_t i = 0; i < ml.size(); ++i) l1l2L[i] = ml[i];
+    return TPCF_OK;
+}
+
+int tpcf_bin_edges(const tpcf_config *cfg, uint64_t *E)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!E) return fail(TPCF_ERR_ARG, "E is NULL");
+    unsigned long long e[TPCF_MAX_BINS + 1];
+    edge_tables(cfg, e, nullptr);
+    for (int b = 0; b <= cfg->n_bins; ++b) E[b] = e[b];
+    return TPCF_OK;
+}
+
+int tpcf_build_grid(const uint32_t *xyz, const float *w, int64_t n, const tpcf_config *cfg, tpcf_grid *out,
+                    void *stream)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!out) return fail(TPCF_ERR_ARG, "out is NULL");
+    if (n < 0 || n > (int64_t)2000000000) return fail(TPCF_ERR_ARG, "n out of range");
+    if (n > 0 && !xyz) return fail(TPCF_ERR_ARG, "xyz is NULL");
+    DevState *ds;
+    if ((rc = dev_state(&ds))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    tpcf_grid g = new tpcf_grid_s();
+    g->stream = st;
+    cudaGetDevice(&g->device);
+    cudaError_t e = build_grid_dev(xyz, w, n, nullptr, nullptr, 0, nullptr, choose_nc(cfg, n), g->g, ds->err, st);
+    if (e != cudaSuccess) {
+        free_grid_dev(g->g, st);
+        delete g;
+        return cuda_fail(e, "build_grid");
+    }
+    *out = g;
+    return TPCF_OK;
+}
+
+int tpcf_grid_destroy(tpcf_grid grid)
+{
+    if (!grid) return TPCF_OK;
+    free_grid_dev(grid->g, grid->stream);
+    cudaError_t e = cudaStreamSynchronize(grid->stream);
+    delete grid;
+    if (e != cudaSuccess) return cuda_fail(e, "grid_destroy");
+    return TPCF_OK;
+}
+
+int tpcf_grid_info(tpcf_grid grid, int64_t *n_points, int32_t *cells_per_axis)
+{
+    if (!grid) return fail(TPCF_ERR_ARG, "grid is NULL");
+    if (n_points) *n_points = grid->g.n;
+    if (cells_per_axis) *cells_per_axis = grid->g.nc;
+    return TPCF_OK;
+}
+
+int tpcf_grid_points(tpcf_grid grid, uint32_t *xyz, float *w, int64_t *order, void *stream)
+{
+    if (!grid) return fail(TPCF_ERR_ARG, "grid is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = grid->g.n;
+    if (n == 0) return TPCF_OK;
+    if (xyz) CK(cudaMemcpy2DAsync(xyz, 12, grid->g.rec, 16, 12, n, cudaMemcpyDeviceToDevice, st));
+    if (w) CK(cudaMemcpy2DAsync(w, 4, (const char *)grid->g.rec + 12, 16, 4, n, cudaMemcpyDeviceToDevice, st));
+    if (order) CK(cudaMemcpyAsync(order, grid->g.order, n * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    return TPCF_OK;
+}
+
+int tpcf_accumulate_alm(tpcf_grid grid, const uint32_t *prim_xyz, const float *prim_w, int64_t n_prim,
+                        const tpcf_config *cfg, double monopole_weight, float *alm, int32_t *counts, double *diag,
+                        double *wsp, int64_t *pair_counts, void *stream)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!grid) return fail(TPCF_ERR_ARG, "grid is NULL");
+    if (n_prim < 0) return fail(TPCF_ERR_ARG, "n_prim < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevState *ds;
+    if ((rc = dev_state(&ds))) return rc;
+    const int4 *prim = grid->g.rec;
+    int4 *packed = nullptr;
+    if (prim_xyz) {
+        if ((rc = dalloc(&packed, (size_t)n_prim, st, false))) return rc;
+        CK(pack_records(prim_xyz, prim_w, n_prim, packed, ds->err, st));
+        prim = packed;
+    } else if (n_prim != grid->g.n) {
+        return fail(TPCF_ERR_ARG, "n_prim must equal the grid size when prim_xyz is NULL");
+    }
+    rc = run_pairs(cfg, grid->g, prim, n_prim, false, monopole_weight, nullptr, monopole_weight >= 0.0, alm, counts,
+                   diag, wsp, (unsigned long long *)pair_counts, st);
+    if (packed) cudaFreeAsync(packed, st);
+    return rc;
+}
+
+int tpcf_couple_multipoles(const float *alm, const float *prim_w, const int32_t *counts, int64_t n_prim,
+                           const tpcf_config *cfg, const double *diag, const double *wsp, double *nnn,
+                           int64_t *triplet_counts, void *stream)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!alm || !diag || !wsp || !nnn) return fail(TPCF_ERR_ARG, "alm, diag, wsp and nnn are required");
+    if (n_prim < 0) return fail(TPCF_ERR_ARG, "n_prim < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = cfg->n_bins;
+    unsigned long long *T = nullptr;
+    if (triplet_counts && counts) {
+        if ((rc = dalloc(&T, (size_t)nb * nb, st, true))) return rc;
+    }
+    rc = couple(cfg, alm, prim_w, counts, n_prim, diag, wsp, nnn, T, st);
+    if (!rc && T) {
+        cudaError_t e = i64_from_u64(T, triplet_counts, nb * nb, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "triplet counts");
+    }
+    if (T) cudaFreeAsync(T, st);
+    return rc;
+}
+
+int tpcf_project(const tpcf_config *cfg, const double *nnn, const double *rrr, double *zeta, void *stream)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!nnn || !rrr || !zeta) return fail(TPCF_ERR_ARG, "nnn, rrr and zeta are required");
+    return project(cfg, nnn, rrr, zeta, (cudaStream_t)stream);
+}
+
+int tpcf_estimate_3pcf(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                       const uint32_t *r_xyz, const float *r_w, int64_t nr, double *zeta, double *nnn_out,
+                       double *rrr_out, int64_t *pair_counts, int64_t *triplet_counts, void *stream)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!zeta) return fail(TPCF_ERR_ARG, "zeta is required");
+    if (nd < 1 || !d_xyz) return fail(TPCF_ERR_ARG, "need at least one data point");
+    if (nr < 0 || (nr > 0 && !r_xyz)) return fail(TPCF_ERR_ARG, "bad randoms");
+    const bool analytic = (nr == 0);
+    if (analytic && !cfg->periodic) return fail(TPCF_ERR_ARG, "analytic randoms need a periodic box");
+    if (nd + nr > (int64_t)2000000000) return fail(TPCF_ERR_ARG, "catalogue too large");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevState *ds;
+    if ((rc = dev_state(&ds))) return rc;
+    const int nb = cfg->n_bins, L = cfg->l_max;
+    const int nlm = (L + 1) * (L + 1), ndiag = (L + 1) * (L + 2) / 2;
+    const int L1 = L + 1;
+
+    double *wsums = nullptr, *diag = nullptr, *wsp = nullptr, *nnn = nnn_out, *rrr = rrr_out, *mono = nullptr;
+    float *alm = nullptr;
+    int32_t *cnt = nullptr, *cnt_r = nullptr;
+    unsigned long long *pairs = nullptr, *T = nullptr, *TR = nullptr;
+    GridDev gf, gr;
+    if ((rc = dalloc(&wsums, 2, st, true))) return rc;
+    CK(weight_sums(d_w, nd, r_w, nr, wsums, st));
+    const int64_t K = nd + nr;
+    // neighbour field grid: D, or D - (W_D/W_R) R
+    CK(build_grid_dev(d_xyz, d_w, nd, r_xyz, r_w, nr, analytic ? nullptr : wsums, choose_nc(cfg, K), gf, ds->err, st));
+    if ((rc = dalloc(&alm, (size_t)K * nb * nlm, st, false))) return rc;
+    if ((rc = dalloc(&cnt, (size_t)K * nb, st, false))) return rc;
+    if ((rc = dalloc(&diag, (size_t)ndiag * nb, st, true))) return rc;
+    if ((rc = dalloc(&wsp, (size_t)L1 * nb, st, true))) return rc;
+    if ((rc = dalloc(&pairs, (size_t)nb, st, true))) return rc;
+    if ((rc = dalloc(&T, (size_t)nb * nb, st, true))) return rc;
+    if (!nnn && (rc = dalloc(&nnn, (size_t)L1 * L1 * L1 * nb * nb, st, false))) return rc;
+    if (!rrr && (rc = dalloc(&rrr, (size_t)nb * nb, st, false))) return rc;
+    rc = run_pairs(cfg, gf, gf.rec, K, false, 0.0, analytic ? wsums : nullptr, analytic, alm, cnt, diag, wsp, pairs,
+                   st);
+    if (rc) return rc;
+    // primary weights in grid order are the records' w fields: pass them through a strided copy
+    float *wprim = nullptr;
+    if ((rc = dalloc(&wprim, (size_t)K, st, false))) return rc;
+    CK(cudaMemcpy2DAsync(wprim, 4, (const char *)gf.rec + 12, 16, 4, K, cudaMemcpyDeviceToDevice, st));
+    if ((rc = couple(cfg, alm, wprim, cnt, K, diag, wsp, nnn, T, st))) return rc;
+    if (analytic) {
+        if ((rc = mono_coef_dev(cfg, &mono, st))) return rc;
+        CK(rrr_analytic(wsums, mono, nb, rrr, st));
+    } else {
+        CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
+        if ((rc = dalloc(&cnt_r, (size_t)nr * nb, st, false))) return rc;
+        if ((rc = dalloc(&TR, (size_t)nb * nb, st, true))) return rc;
+        rc = run_pairs(cfg, gr, gr.rec, nr, true, 0.0, nullptr, false, nullptr, cnt_r, nullptr, nullptr, nullptr, st);
+        if (rc) return rc;
+        CK(tpcf::triplet_counts(cnt_r, nr, nb, TR, st));
+        CK(rrr_from_counts(TR, wsums, nb, rrr, st));
+    }
+    if ((rc = project(cfg, nnn, rrr, zeta, st))) return rc;
+    if (pair_counts) CK(i64_from_u64(pairs, pair_counts, nb, st));
+    if (triplet_counts) CK(i64_from_u64(T, triplet_counts, nb * nb, st));
+    free_grid_dev(gf, st);
+    free_grid_dev(gr, st);
+    cudaFreeAsync(wsums, st);
+    cudaFreeAsync(alm, st);
+    cudaFreeAsync(cnt, st);
+    cudaFreeAsync(diag, st);
+    cudaFreeAsync(wsp, st);
+    cudaFreeAsync(pairs, st);
+    cudaFreeAsync(T, st);
+    cudaFreeAsync(wprim, st);
+    if (mono) cudaFreeAsync(mono, st);
+    if (cnt_r) cudaFreeAsync(cnt_r, st);
+    if (TR) cudaFreeAsync(TR, st);
+    if (!nnn_out) cudaFreeAsync(nnn, st);
+    if (!rrr_out) cudaFreeAsync(rrr, st);
+    CK(cudaGetLastError());
+    return TPCF_OK;
+}
+
+int tpcf_estimate_3pcf_host(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                            const uint32_t *r_xyz, const float *r_w, int64_t nr, double *zeta, double *nnn,
+                            double *rrr, int64_t *pair_counts, int64_t *triplet_counts, void *stream)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!zeta || !d_xyz || nd < 1) return fail(TPCF_ERR_ARG, "zeta and data are required");
+    if (nr < 0 || (nr > 0 && !r_xyz)) return fail(TPCF_ERR_ARG, "bad randoms");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t nm = 0;
+    tpcf_multipole_count(cfg, &nm);
+    const int nb = cfg->n_bins, L1 = cfg->l_max + 1;
+    uint32_t *dx = nullptr, *rx = nullptr;
+    float *dw = nullptr, *rw = nullptr;
+    double *z = nullptr, *n3 = nullptr, *r3 = nullptr;
+    int64_t *pc = nullptr, *tc = nullptr;
+    if ((rc = dalloc(&dx, (size_t)nd * 3, st, false))) return rc;
+    CK(cudaMemcpyAsync(dx, d_xyz, (size_t)nd * 12, cudaMemcpyHostToDevice, st));
+    if (d_w) {
+        if ((rc = dalloc(&dw, (size_t)nd, st, false))) return rc;
+        CK(cudaMemcpyAsync(dw, d_w, (size_t)nd * 4, cudaMemcpyHostToDevice, st));
+    }
+    if (nr > 0) {
+        if ((rc = dalloc(&rx, (size_t)nr * 3, st, false))) return rc;
+        CK(cudaMemcpyAsync(rx, r_xyz, (size_t)nr * 12, cudaMemcpyHostToDevice, st));
+        if (r_w) {
+            if ((rc = dalloc(&rw, (size_t)nr, st, false))) return rc;
+            CK(cudaMemcpyAsync(rw, r_w, (size_t)nr * 4, cudaMemcpyHostToDevice, st));
+        }
+    }
+    if ((rc = dalloc(&z, (size_t)nm * nb * nb, st, false))) return rc;
+    if (nnn && (rc = dalloc(&n3, (size_t)L1 * L1 * L1 * nb * nb, st, false))) return rc;
+    if (rrr && (rc = dalloc(&r3, (size_t)nb * nb, st, false))) return rc;
+    if (pair_counts && (rc = dalloc(&pc, (size_t)nb, st, false))) return rc;
+    if (triplet_counts && (rc = dalloc(&tc, (size_t)nb * nb, st, false))) return rc;
+    rc = tpcf_estimate_3pcf(cfg, dx, dw, nd, rx, rw, nr, z, n3, r3, pc, tc, stream);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(zeta, z, (size_t)nm * nb * nb * 8, cudaMemcpyDeviceToHost, st));
+    if (nnn) CK(cudaMemcpyAsync(nnn, n3, (size_t)L1 * L1 * L1 * nb * nb * 8, cudaMemcpyDeviceToHost, st));
+    if (rrr) CK(cudaMemcpyAsync(rrr, r3, (size_t)nb * nb * 8, cudaMemcpyDeviceToHost, st));
+    if (pair_counts) CK(cudaMemcpyAsync(pair_counts, pc, (size_t)nb * 8, cudaMemcpyDeviceToHost, st));
+    if (triplet_counts) CK(cudaMemcpyAsync(triplet_counts, tc, (size_t)nb * nb * 8, cudaMemcpyDeviceToHost, st));
+    for (void *p : {(void *)dx, (void *)rx, (void *)dw, (void *)rw, (void *)z, (void *)n3, (void *)r3, (void *)pc,
+                    (void *)tc})
+        if (p) cudaFreeAsync(p, st);
+    CK(cudaStreamSynchronize(st));
+    return tpcf_stream_status(stream);
+}
+
+int tpcf_stream_status(void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    DevState *ds;
+    int rc = dev_state(&ds);
+    if (rc) return rc;
+    int h = 0;
+    CK(cudaMemcpy(&h, ds->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        CK(cudaMemset(ds->err, 0, sizeof(int)));
+        if (h == DEV_ERR_DATA) return fail(TPCF_ERR_DATA, "non-finite weight in the input");
+        if (h == DEV_ERR_TIMEOUT) return fail(TPCF_ERR_TIMEOUT, "a bounded device wait ran out");
+        return fail(TPCF_ERR_CUDA, "device error code %d", h);
+    }
+    return TPCF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+"""Thin ctypes binding of libtpcf (include/tpcf.h), same names as the C ABI.
+
+Argument marshalling only: every step of the estimator runs in the library's
+CUDA kernels.  PyTorch supplies device memory (tensor.data_ptr()) and streams.
+Importing this module does not need a GPU; calling into the library does, and
+a missing library raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtpcf.so")
+
+TPCF_OK = 0
+STATUS = {0: "TPCF_OK", -1: "TPCF_ERR_ARG", -2: "TPCF_ERR_OOM", -3: "TPCF_ERR_CUDA",
+          -4: "TPCF_ERR_TIMEOUT", -5: "TPCF_ERR_UNSUPPORTED", -6: "TPCF_ERR_DATA"}
+PREC = {"fp32": 0, "bf16x3": 1, "tf32x3": 2}
+CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
+
+# Names of every entry point include/tpcf.h declares (checked by the tests).
+EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
+           "tpcf_bin_edges", "tpcf_build_grid", "tpcf_grid_destroy", "tpcf_grid_info", "tpcf_grid_points",
+           "tpcf_accumulate_alm", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
+           "tpcf_estimate_3pcf_host", "tpcf_stream_status"]
+
+
+class TpcfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class tpcf_config(ctypes.Structure):
+    _fields_ = [("r_min", ctypes.c_double), ("r_max", ctypes.c_double),
+                ("n_bins", ctypes.c_int32), ("l_max", ctypes.c_int32),
+                ("n_L", ctypes.c_int32), ("L", ctypes.c_int32 * 8),
+                ("periodic", ctypes.c_int32), ("box", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("remove_self", ctypes.c_int32),
+                ("convention", ctypes.c_int32), ("cell_div", ctypes.c_int32),
+                ("tile_primaries", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+
+
+@dataclass
+class Config:
+    """Estimator configuration (mirrors tpcf_config)."""
+    r_min: float
+    r_max: float
+    n_bins: int
+    l_max: int
+    Ls: tuple = (0, 2, 4)
+    periodic: bool = True
+    box: float = 500.0
+    precision: str = "fp32"
+    remove_self: bool = True
+    convention: str = "S_COEFF"
+    cell_div: int = 0
+    tile_primaries: int = 0
+    chunk: int = 0
+
+    def c(self) -> tpcf_config:
+        arr = (ctypes.c_int32 * 8)(*(list(self.Ls) + [0] * (8 - len(self.Ls))))
+        return tpcf_config(self.r_min, self.r_max, self.n_bins, self.l_max, len(self.Ls), arr,
+                           int(self.periodic), self.box, PREC[self.precision], int(self.remove_self),
+                           CONV[self.convention], self.cell_div, self.tile_primaries, self.chunk)
+
+
+_lib = None
+P = ctypes.c_void_p
+I64 = ctypes.c_int64
+CFG = ctypes.POINTER(tpcf_config)
+
+
+def lib():
+    """Loads libtpcf.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtpcf.so is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+        L = ctypes.CDLL(LIB_PATH)
+        sig = {
+            "tpcf_last_error": ([], ctypes.c_char_p),
+            "tpcf_version": ([], ctypes.c_int),
+            "tpcf_kernel_launches": ([], ctypes.c_int64),
+            "tpcf_multipole_count": ([CFG, P], ctypes.c_int),
+            "tpcf_multipole_index": ([CFG, P, ctypes.c_int32], ctypes.c_int),
+            "tpcf_bin_edges": ([CFG, P], ctypes.c_int),
+            "tpcf_build_grid": ([P, P, I64, CFG, P, P], ctypes.c_int),
+            "tpcf_grid_destroy": ([P], ctypes.c_int),
+            "tpcf_grid_info": ([P, P, P], ctypes.c_int),
+            "tpcf_grid_points": ([P, P, P, P, P], ctypes.c_int),
+            "tpcf_accumulate_alm": ([P, P, P, I64, CFG, ctypes.c_double, P, P, P, P, P, P], ctypes.c_int),
+            "tpcf_couple_multipoles": ([P, P, P, I64, CFG, P, P, P, P, P], ctypes.c_int),
+            "tpcf_project": ([CFG, P, P, P, P], ctypes.c_int),
+            "tpcf_estimate_3pcf": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
+            "tpcf_estimate_3pcf_host": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
+            "tpcf_stream_status": ([P], ctypes.c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != TPCF_OK:
+        raise TpcfError(rc, lib().tpcf_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensors passed to libtpcf must be contiguous")
+        return t.data_ptr()
+    return t.ctypes.data  # numpy (host) array
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def multipole_index(cfg: Config):
+    c = cfg.c()
+    n = ctypes.c_int32(0)
+    _check(lib().tpcf_multipole_count(ctypes.byref(c), ctypes.addressof(n)))
+    arr = (ctypes.c_int32 * (3 * n.value))()
+    _check(lib().tpcf_multipole_index(ctypes.byref(c), ctypes.addressof(arr), n.value))
+    return [tuple(arr[3 * k:3 * k + 3]) for k in range(n.value)]
+
+
+def bin_edges(cfg: Config):
+    c = cfg.c()
+    arr = (ctypes.c_uint64 * (cfg.n_bins + 1))()
+    _check(lib().tpcf_bin_edges(ctypes.byref(c), ctypes.addressof(arr)))
+    return [int(v) for v in arr]
+
+
+def _as_dev_xyz(xyz, device):
+    """uint32 numpy [n,3] or int32 tensor [n,3] -> contiguous int32 device tensor."""
+    if isinstance(xyz, torch.Tensor):
+        return xyz.to(device=device, dtype=torch.int32).contiguous()
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(xyz, dtype=np.uint32).view(np.int32)).to(device)
+
+
+def _as_dev_w(w, device):
+    if w is None:
+        return None
+    if isinstance(w, torch.Tensor):
+        return w.to(device=device, dtype=torch.float32).contiguous()
+    return torch.as_tensor(w, dtype=torch.float32).to(device).contiguous()
+
+
+@dataclass
+class Result:
+    zeta: torch.Tensor
+    mults: list
+    nnn: torch.Tensor | None = None
+    rrr: torch.Tensor | None = None
+    pair_counts: torch.Tensor | None = None
+    triplet_counts: torch.Tensor | None = None
+    extra: dict = field(default_factory=dict)
+
+
+def estimate_3pcf(cfg: Config, d_xyz, d_w=None, r_xyz=None, r_w=None, stream=None, want_all=True,
+                  device="cuda") -> Result:
+    """tpcf_estimate_3pcf on device tensors (numpy inputs are copied to the device first)."""
+    dx = _as_dev_xyz(d_xyz, device)
+    dw = _as_dev_w(d_w, device)
+    rx = _as_dev_xyz(r_xyz, device) if r_xyz is not None else None
+    rw = _as_dev_w(r_w, device) if r_xyz is not None else None
+    nd = dx.shape[0]
+    nr = rx.shape[0] if rx is not None else 0
+    mults = multipole_index(cfg)
+    nb, L1 = cfg.n_bins, cfg.l_max + 1
+    z = torch.empty((len(mults), nb, nb), dtype=torch.float64, device=device)
+    nnn = rrr = pc = tc = None
+    if want_all:
+        nnn = torch.empty((L1, L1, L1, nb, nb), dtype=torch.float64, device=device)
+        rrr = torch.empty((nb, nb), dtype=torch.float64, device=device)
+        pc = torch.empty(nb, dtype=torch.int64, device=device)
+        tc = torch.empty((nb, nb), dtype=torch.int64, device=device)
+    c = cfg.c()
+    _check(lib().tpcf_estimate_3pcf(ctypes.byref(c), _ptr(dx), _ptr(dw), nd, _ptr(rx), _ptr(rw), nr,
+                                    _ptr(z), _ptr(nnn), _ptr(rrr), _ptr(pc), _ptr(tc), _stream(stream)))
+    return Result(z, mults, nnn, rrr, pc, tc)
+
+
+def estimate_3pcf_host(cfg: Config, d_xyz, d_w=None, r_xyz=None, r_w=None, stream=None):
+    """tpcf_estimate_3pcf_host: host (numpy, ideally pinned) buffers in and out."""
+    import numpy as np
+    mults = multipole_index(cfg)
+    nb, L1 = cfg.n_bins, cfg.l_max + 1
+    dx = np.ascontiguousarray(d_xyz, dtype=np.uint32)
+    dw = None if d_w is None else np.ascontiguousarray(d_w, dtype=np.float32)
+    rx = None if r_xyz is None else np.ascontiguousarray(r_xyz, dtype=np.uint32)
+    rw = None if r_w is None else np.ascontiguousarray(r_w, dtype=np.float32)
+    z = np.empty((len(mults), nb, nb))
+    nnn = np.empty((L1, L1, L1, nb, nb))
+    rrr = np.empty((nb, nb))
+    pc = np.empty(nb, dtype=np.int64)
+    tc = np.empty((nb, nb), dtype=np.int64)
+    c = cfg.c()
+    _check(lib().tpcf_estimate_3pcf_host(ctypes.byref(c), _ptr(dx), _ptr(dw), dx.shape[0], _ptr(rx), _ptr(rw),
+                                         0 if rx is None else rx.shape[0], _ptr(z), _ptr(nnn), _ptr(rrr),
+                                         _ptr(pc), _ptr(tc), _stream(stream)))
+    return Result(z, mults, nnn, rrr, pc, tc)
+
+
+class Grid:
+    """tpcf_build_grid / tpcf_grid_destroy."""
+
+    def __init__(self, cfg: Config, xyz, w=None, stream=None, device="cuda"):
+        self.cfg = cfg
+        self.xyz = _as_dev_xyz(xyz, device)
+        self.w = _as_dev_w(w, device)
+        self.handle = ctypes.c_void_p()
+        c = cfg.c()
+        _check(lib().tpcf_build_grid(_ptr(self.xyz), _ptr(self.w), self.xyz.shape[0], ctypes.byref(c),
+                                     ctypes.addressof(self.handle), _stream(stream)))
+
+    def info(self):
+        n = ctypes.c_int64(0)
+        nc = ctypes.c_int32(0)
+        _check(lib().tpcf_grid_info(self.handle, ctypes.addressof(n), ctypes.addressof(nc)))
+        return n.value, nc.value
+
+    def points(self, stream=None):
+        n, _ = self.info()
+        dev = self.xyz.device
+        xyz = torch.empty((n, 3), dtype=torch.int32, device=dev)
+        w = torch.empty(n, dtype=torch.float32, device=dev)
+        order = torch.empty(n, dtype=torch.int64, device=dev)
+        _check(lib().tpcf_grid_points(self.handle, _ptr(xyz), _ptr(w), _ptr(order), _stream(stream)))
+        return xyz, w, order
+
+    def close(self):
+        if self.handle:
+            _check(lib().tpcf_grid_destroy(self.handle))
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def accumulate_alm(grid: Grid, cfg: Config, prim_xyz=None, prim_w=None, monopole_weight=-1.0, stream=None):
+    """tpcf_accumulate_alm; returns (alm, counts, diag, wsp, pair_counts) device tensors."""
+    dev = grid.xyz.device
+    if prim_xyz is None:
+        n = grid.info()[0]
+        px = pw = None
+    else:
+        px = _as_dev_xyz(prim_xyz, dev)
+        pw = _as_dev_w(prim_w, dev)
+        n = px.shape[0]
+    nb, L1 = cfg.n_bins, cfg.l_max + 1
+    alm = torch.empty((n, nb, L1 * L1), dtype=torch.float32, device=dev)
+    counts = torch.empty((n, nb), dtype=torch.int32, device=dev)
+    diag = torch.zeros((L1 * (L1 + 1) // 2, nb), dtype=torch.float64, device=dev)
+    wsp = torch.zeros((L1, nb), dtype=torch.float64, device=dev)
+    pc = torch.zeros(nb, dtype=torch.int64, device=dev)
+    c = cfg.c()
+    _check(lib().tpcf_accumulate_alm(grid.handle, _ptr(px), _ptr(pw), n, ctypes.byref(c), float(monopole_weight),
+                                     _ptr(alm), _ptr(counts), _ptr(diag), _ptr(wsp), _ptr(pc), _stream(stream)))
+    return alm, counts, diag, wsp, pc
+
+
+def couple_multipoles(cfg: Config, alm, prim_w, counts, diag, wsp, stream=None):
+    """tpcf_couple_multipoles; returns (nnn, triplet_counts)."""
+    dev = alm.device
+    nb, L1 = cfg.n_bins, cfg.l_max + 1
+    nnn = torch.empty((L1, L1, L1, nb, nb), dtype=torch.float64, device=dev)
+    tc = torch.empty((nb, nb), dtype=torch.int64, device=dev) if counts is not None else None
+    c = cfg.c()
+    _check(lib().tpcf_couple_multipoles(_ptr(alm), _ptr(prim_w), _ptr(counts), alm.shape[0], ctypes.byref(c),
+                                        _ptr(diag), _ptr(wsp), _ptr(nnn), _ptr(tc), _stream(stream)))
+    return nnn, tc
+
+
+def project(cfg: Config, nnn, rrr, stream=None):
+    mults = multipole_index(cfg)
+    z = torch.empty((len(mults), cfg.n_bins, cfg.n_bins), dtype=torch.float64, device=nnn.device)
+    c = cfg.c()
+    _check(lib().tpcf_project(ctypes.byref(c), _ptr(nnn), _ptr(rrr), _ptr(z), _stream(stream)))
+    return z
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libtpcf in this process so far."""
+    return int(lib().tpcf_kernel_launches())
+
+
+def stream_status(stream=None):
+    _check(lib().tpcf_stream_status(_stream(stream)))

@@ -1,0 +1,85 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point
+include/tpcf.h declares; host-only entry points agree with the oracle.
+No GPU is needed: nothing here launches a kernel."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2408_03036_gb300 import build as B
+from paper_2408_03036_gb300 import tpcf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return tpcf.lib()
+
+
+def declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(tpcf_\w+)\s*\(", txt))
+    return sorted(names)
+
+
+def test_exports_every_declared_symbol(lib):
+    decl = declared_symbols()
+    assert len(decl) >= 15
+    for name in decl:
+        assert hasattr(lib, name), name
+    assert set(decl) <= set(tpcf.EXPORTS) | set(decl)
+    for name in tpcf.EXPORTS:
+        assert name in decl, name
+
+
+def test_version_and_error_string(lib):
+    assert lib.tpcf_version() >= 100
+    cfg = tpcf.Config(20.0, 10.0, 10, 4)
+    with pytest.raises(tpcf.TpcfError) as ei:
+        tpcf.multipole_index(cfg)
+    assert ei.value.code == -1 and "r_max" in str(ei.value)
+
+
+@pytest.mark.parametrize("lmax,Ls", [(4, (0, 2, 4)), (6, (0, 2, 4, 6)), (4, (0, 2)), (2, (0,))])
+def test_multipole_list_matches_oracle(lib, ora, lmax, Ls):
+    cfg = tpcf.Config(20.0, 120.0, 10, lmax, Ls)
+    assert tpcf.multipole_index(cfg) == ora.multipoles(lmax, Ls)
+
+
+def test_counts_of_multipoles(lib):
+    assert len(tpcf.multipole_index(tpcf.Config(20.0, 120.0, 10, 4, (0, 2, 4)))) == 24
+    assert len(tpcf.multipole_index(tpcf.Config(5.0, 155.0, 30, 6, (0, 2, 4, 6)))) == 58
+    assert len(tpcf.multipole_index(tpcf.Config(10.0, 150.0, 20, 4, (0, 2)))) == 15
+
+
+@pytest.mark.parametrize("rmin,rmax,nb,box", [(20.0, 120.0, 10, 500.0), (10.0, 150.0, 20, 1000.0),
+                                              (5.0, 155.0, 30, 500.0), (0.3, 7.7, 7, 33.3)])
+def test_bin_edges_match_oracle(lib, ora, rmin, rmax, nb, box):
+    cfg = tpcf.Config(rmin, rmax, nb, 2, (0,), box=box)
+    ocfg = ora.Config(rmin, rmax, nb, 2, (0,), box=box)
+    E, _ = ora.edges(ocfg)
+    assert tpcf.bin_edges(cfg) == [int(e) for e in E]
+
+
+@pytest.mark.parametrize("bad", [dict(n_bins=0), dict(n_bins=33), dict(l_max=7), dict(r_min=0.0),
+                                 dict(r_max=300.0), dict(Ls=(1,)), dict(Ls=(10,)), dict(precision="fp16"),
+                                 dict(chunk=100), dict(chunk=256), dict(tile_primaries=9)])
+def test_config_validation(lib, bad):
+    kw = dict(r_min=20.0, r_max=120.0, n_bins=10, l_max=4, Ls=(0, 2, 4), box=500.0)
+    if bad.get("precision") == "fp16":
+        cfg = tpcf.Config(**kw)
+        c = cfg.c()
+        c.precision = 9
+        n = ctypes.c_int32(0)
+        assert lib.tpcf_multipole_count(ctypes.byref(c), ctypes.addressof(n)) == -1
+        return
+    kw.update(bad)
+    with pytest.raises(tpcf.TpcfError):
+        tpcf.multipole_index(tpcf.Config(**kw))

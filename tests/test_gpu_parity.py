@@ -1,0 +1,201 @@
+"""CUDA path vs the FP64 oracle, element by element, on the same seeded inputs.
+
+Bar (the benchmark spec's tolerance): per multipole,
+    max_{b1,b2} |zeta_gpu - zeta_oracle| / max_{b1,b2} |zeta_oracle| <= 1e-5
+for the FP32 path, and pair / triplet counts bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2408_03036_gb300 import synth
+from paper_2408_03036_gb300 import tpcf
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_03036_gb300 import build as B
+    B.build()
+    tpcf.lib()
+    return torch
+
+
+def cfg_pair(ora, **kw):
+    """The same configuration for the CUDA path and the oracle."""
+    g = tpcf.Config(**kw)
+    o = ora.Config(kw["r_min"], kw["r_max"], kw["n_bins"], kw["l_max"], kw.get("Ls", (0, 2, 4)),
+                   kw.get("periodic", True), kw.get("box", 500.0), kw.get("remove_self", True),
+                   kw.get("convention", "S_COEFF"))
+    return g, o
+
+
+def per_mult_err(zg, zo):
+    out = []
+    for k in range(zo.shape[0]):
+        den = np.abs(zo[k]).max()
+        num = np.abs(zg[k] - zo[k]).max()
+        out.append(num / den if den > 0 else num)
+    return np.array(out)
+
+
+def nnn_err(ng, no, lmax):
+    """Worst normalised error over the (m, l1, l2) blocks with l1 + l2 even."""
+    worst = 0.0
+    for m in range(lmax + 1):
+        for l1 in range(m, lmax + 1):
+            for l2 in range(m, lmax + 1):
+                if (l1 + l2) % 2:
+                    continue
+                ref = no[m + lmax, l1, l2].real
+                den = np.abs(ref).max()
+                if den == 0:
+                    continue
+                worst = max(worst, np.abs(ng[m, l1, l2] - ref).max() / den)
+    return worst
+
+
+def compare(gpu, gcfg, ocfg, ora, d_xyz, d_w, r_xyz=None, r_w=None, tol=TOL_FP32):
+    res = tpcf.estimate_3pcf(gcfg, d_xyz, d_w, r_xyz, r_w)
+    tpcf.stream_status()
+    est = ora.estimate(ocfg, d_xyz, d_w, r_xyz, r_w)
+    assert res.mults == est.mults
+    zg = res.zeta.cpu().numpy()
+    err = per_mult_err(zg, est.zeta)
+    assert np.array_equal(res.pair_counts.cpu().numpy(), est.pair_counts)
+    assert np.array_equal(res.triplet_counts.cpu().numpy(), est.trip_counts)
+    assert np.allclose(res.rrr.cpu().numpy(), est.rrr, rtol=1e-12, atol=0)
+    assert err.max() <= tol, dict(zip(map(str, est.mults), err))
+    assert nnn_err(res.nnn.cpu().numpy(), est.nnn, gcfg.l_max) <= tol
+    return err
+
+
+def test_small_periodic(gpu, ora):
+    g, o = cfg_pair(ora, r_min=10.0, r_max=60.0, n_bins=5, l_max=2, Ls=(0, 2), box=250.0)
+    xyz, w = synth.poisson(3000, 5)
+    compare(gpu, g, o, ora, xyz, w)
+
+
+def test_config1_poisson_periodic(gpu, ora):
+    """Plain estimator workload: N = 20,000 uniform points, periodic L = 500,
+    10 bins 20-120, l <= 4, L in {0, 2, 4}, analytic randoms."""
+    g, o = cfg_pair(ora, r_min=20.0, r_max=120.0, n_bins=10, l_max=4, Ls=(0, 2, 4), box=500.0)
+    xyz, w = synth.poisson(20000, 1)
+    compare(gpu, g, o, ora, xyz, w)
+
+
+def test_paper_eq_convention(gpu, ora):
+    g, o = cfg_pair(ora, r_min=20.0, r_max=120.0, n_bins=6, l_max=3, Ls=(0, 2), box=500.0,
+                    convention="PAPER_EQ")
+    xyz, w = synth.poisson(8000, 2)
+    compare(gpu, g, o, ora, xyz, w)
+
+
+def test_open_volume_data_minus_randoms(gpu, ora):
+    """Clustered lognormal data with 3x uniform randoms in an open (non-periodic) cube."""
+    g, o = cfg_pair(ora, r_min=10.0, r_max=100.0, n_bins=9, l_max=4, Ls=(0, 2, 4), box=600.0, periodic=False)
+    d, dw = synth.lognormal(8000, 600.0, 3, mesh=64)
+    r, rw = synth.randoms(24000, 4)
+    compare(gpu, g, o, ora, d, dw, r, rw)
+
+
+@pytest.mark.parametrize("tile,chunk,div", [(1, 512, 1), (3, 768, 2), (8, 2048, 3), (2, 4096, 4)])
+def test_schedules_agree(gpu, ora, tile, chunk, div):
+    """Every tiling / staging / cell-size choice gives the same answer."""
+    g, o = cfg_pair(ora, r_min=15.0, r_max=90.0, n_bins=8, l_max=4, Ls=(0, 2, 4), box=400.0,
+                    tile_primaries=tile, chunk=chunk, cell_div=div)
+    xyz, w = synth.poisson(9001, 6)   # ragged: not a multiple of any tile
+    compare(gpu, g, o, ora, xyz, w)
+
+
+def test_signed_weights_and_clustering(gpu, ora):
+    """Non-unit signed weights and strong clustering (many points per cell)."""
+    g, o = cfg_pair(ora, r_min=5.0, r_max=60.0, n_bins=11, l_max=3, Ls=(0, 2), box=300.0)
+    d, _ = synth.lognormal(6000, 300.0, 8, mesh=64, sigma_g=1.6)
+    rng = np.random.default_rng(9)
+    w = rng.uniform(0.5, 2.0, size=d.shape[0]).astype(np.float32)
+    w[::4] *= -1
+    compare(gpu, g, o, ora, d, w)
+
+
+def test_lmax6_thirty_bins(gpu, ora):
+    """l <= 6, 30 bins 5-155 on a Poisson catalogue in a periodic L = 500 box
+    (the precision workload's shape, at 6000 points so the oracle stays quick)."""
+    g, o = cfg_pair(ora, r_min=5.0, r_max=155.0, n_bins=30, l_max=6, Ls=(0, 2, 4, 6), box=500.0)
+    xyz, w = synth.poisson(6000, 1)
+    compare(gpu, g, o, ora, xyz, w)
+
+
+def test_single_point_and_tiny(gpu, ora):
+    g, o = cfg_pair(ora, r_min=10.0, r_max=60.0, n_bins=5, l_max=2, Ls=(0, 2), box=250.0)
+    for n in (1, 2, 7):
+        xyz, w = synth.poisson(n, 40 + n)
+        res = tpcf.estimate_3pcf(g, xyz, w)
+        tpcf.stream_status()
+        est = ora.estimate(o, xyz, w)
+        assert np.array_equal(res.pair_counts.cpu().numpy(), est.pair_counts)
+        assert np.array_equal(res.triplet_counts.cpu().numpy(), est.trip_counts)
+        zg = res.zeta.cpu().numpy()
+        if n == 1:   # no pairs and W - 1 = 0: 0/0 on both sides
+            assert np.isnan(zg).all() and np.isnan(est.zeta).all()
+        else:
+            # a handful of points: several multipoles are exact cancellations (zero in
+            # FP64), so the error is measured against the largest multipole value
+            assert np.abs(zg - est.zeta).max() <= TOL_FP32 * np.abs(est.zeta).max()
+
+
+def test_per_primary_alm_explicit_primaries(gpu, ora):
+    """tpcf_accumulate_alm with explicit primaries reproduces the oracle's a_l^m
+    per primary (real and imaginary parts, m >= 0)."""
+    import torch
+    g, o = cfg_pair(ora, r_min=20.0, r_max=120.0, n_bins=10, l_max=4, Ls=(0, 2, 4), box=500.0)
+    xyz, w = synth.poisson(20000, 1)
+    prim = np.arange(0, 20000, 97)
+    grid = tpcf.Grid(g, xyz, w)
+    alm, counts, diag, wsp, pc = tpcf.accumulate_alm(grid, g, xyz[prim], w[prim], monopole_weight=-1.0)
+    tpcf.stream_status()
+    ro = ora.run(o, xyz, w, prim=prim, want_alm=True)
+    assert np.array_equal(counts.cpu().numpy(), ro.cnt)
+    a = alm.cpu().numpy().astype(np.float64)
+    L = 4
+    for l in range(L + 1):
+        for m in range(l + 1):
+            ref = ro.alm[:, :, l * l + l + m]
+            if m == 0:
+                got = a[:, :, l * l]
+                assert np.abs(got - ref.real).max() <= 2e-6 * max(1.0, np.abs(ref).max())
+            else:
+                gre, gim = a[:, :, l * l + 2 * m - 1], a[:, :, l * l + 2 * m]
+                assert np.abs(gre - ref.real).max() <= 2e-6 * max(1.0, np.abs(ref).max())
+                assert np.abs(gim - ref.imag).max() <= 2e-6 * max(1.0, np.abs(ref).max())
+    grid.close()
+    del torch
+
+
+def test_host_entry_point_matches_device(gpu, ora):
+    g, o = cfg_pair(ora, r_min=20.0, r_max=120.0, n_bins=10, l_max=4, Ls=(0, 2, 4), box=500.0)
+    xyz, w = synth.poisson(20000, 1)
+    a = tpcf.estimate_3pcf(g, xyz, w)
+    b = tpcf.estimate_3pcf_host(g, xyz, w)
+    assert np.array_equal(a.triplet_counts.cpu().numpy(), b.triplet_counts)
+    # same inputs, same kernels; only the order of floating-point atomics differs
+    assert per_mult_err(b.zeta, a.zeta.cpu().numpy()).max() <= 1e-6
+
+
+def test_bad_weights_are_reported(gpu):
+    g = tpcf.Config(r_min=10.0, r_max=60.0, n_bins=5, l_max=2, Ls=(0, 2), box=250.0)
+    xyz, w = synth.poisson(500, 3)
+    w = w.copy()
+    w[7] = np.nan
+    tpcf.estimate_3pcf(g, xyz, w)
+    with pytest.raises(tpcf.TpcfError) as ei:
+        tpcf.stream_status()
+    assert ei.value.code == -6
+    tpcf.stream_status()   # latch cleared
