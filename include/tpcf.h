@@ -166,6 +166,27 @@ int tpcf_couple_multipoles(const float *alm, const float *prim_w, const int32_t 
                            const tpcf_config *cfg, const double *diag, const double *wsp,
                            double *nnn, int64_t *triplet_counts, void *stream);
 
+/* The paper has no counterpart to this entry point: it exists for callers that
+ * must not allocate GPU memory while they run (an application whose device
+ * memory is fully reserved by its own pool, a process that may not grow its
+ * footprint after start-up, or code running where calls into the CUDA
+ * allocator are not allowed).  Same arguments, results and output layout as
+ * tpcf_couple_multipoles with cfg->precision = TPCF_PREC_FP32, but its scratch
+ * (the FP64 Gram blocks, a tile table, the triplet-count accumulator and the
+ * j = k coefficient tables) lives in one fixed block of device memory that the
+ * library declares, about 560 KiB held by every GPU that loads the library
+ * until the process exits; it makes no allocation of any kind on the device.
+ * Limit: the packed Gram blocks, sum over m of (n_bins (l_max - m + 1))^2, must
+ * fit in 65,536 doubles (l_max <= 4 with up to 32 bins; l_max = 6 with up to 21
+ * bins); larger requests return TPCF_ERR_ARG.  The first call on each device
+ * sets the block up with a synchronous copy, so make it before any stream
+ * capture.  All calls on a device share the block (the parts that must start
+ * at zero are cleared by each call): calls whose work overlaps on the GPU race
+ * and must be serialised by the caller. */
+int tpcf_couple_multipoles_static(const float *alm, const float *prim_w, const int32_t *counts, int64_t n_prim,
+                                  const tpcf_config *cfg, const double *diag, const double *wsp,
+                                  double *nnn, int64_t *triplet_counts, void *stream);
+
 /* TripoSH projection (Eq. slep2sugy) of dev nnn (layout as above) divided bin
  * by bin by dev rrr[n_bins][n_bins]; writes dev zeta[n_mult][n_bins][n_bins]. */
 int tpcf_project(const tpcf_config *cfg, const double *nnn, const double *rrr, double *zeta, void *stream);

@@ -79,6 +79,15 @@ cudaError_t couple_gram_fp32(const float *alm, const float *w, int64_t K, int nb
                              double *G, cudaStream_t st);
 cudaError_t triplet_counts(const int32_t *counts, int64_t K, int nb, unsigned long long *T,
                            cudaStream_t st);
+int gram_tile_count(int nb, int lmax);
+cudaError_t couple_gram_fp32_tiles(const float *alm, const float *w, int64_t K, int nb, int lmax, int *d_tiles,
+                                   double *G, cudaStream_t st);
+// j = k coefficients of the off-diagonal (l1 != l2) entries, [m][l1][l2][j] for one l_max
+// (the same table tpcf_couple_multipoles uploads), written to host memory.
+void self_term_table(int lmax, double *out);
+// Host-side argument and configuration checks shared by the entry points.
+int check_config_public(const tpcf_config *c);
+int set_error(int code, const char *msg);
 cudaError_t assemble_nnn(const double *G, const double *diag, const double *wsp, int nb, int lmax,
                          int remove_self, const double *gaunt, double *nnn, cudaStream_t st);
 cudaError_t project_zeta(const double *nnn, const double *rrr, int nb, int lmax, int n_mult,

@@ -193,6 +193,25 @@ __global__ void k_rrr_counts(const unsigned long long *__restrict__ T, const dou
     rrr[i] = a * a * a * (double)T[i] / (4.0 * 3.14159265358979323846);
 }
 
+// Fills the (m, tr, tc) tile table of the Gram blocks on the device.
+__global__ void k_gram_tiles(int nb, int lmax, int *tiles, int ntiles)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    int rem = t;
+    for (int m = 0; m <= lmax; ++m) {
+        const int n_m = nb * (lmax - m + 1);
+        const int tm = (n_m + GT - 1) / GT;
+        if (rem < tm * tm) {
+            tiles[3 * t] = m;
+            tiles[3 * t + 1] = rem / tm;
+            tiles[3 * t + 2] = rem % tm;
+            return;
+        }
+        rem -= tm * tm;
+    }
+}
+
 __global__ void k_u64_to_i64(const unsigned long long *src, int64_t *dst, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -234,6 +253,35 @@ cudaError_t couple_gram_fp32(const float *alm, const float *w, int64_t K, int nb
     e = cudaGetLastError();
     cudaFreeAsync(d, st);
     return e;
+}
+
+int gram_tile_count(int nb, int lmax)
+{
+    int nt = 0;
+    for (int m = 0; m <= lmax; ++m) {
+        const int t = (nb * (lmax - m + 1) + GT - 1) / GT;
+        nt += t * t;
+    }
+    return nt;
+}
+
+// The FP32 Gram with a caller-provided device tile table (filled here) and no
+// allocation of its own.
+cudaError_t couple_gram_fp32_tiles(const float *alm, const float *w, int64_t K, int nb, int lmax, int *d_tiles,
+                                   double *G, cudaStream_t st)
+{
+    const int nt = gram_tile_count(nb, lmax);
+    k_gram_tiles<<<(nt + 127) / 128, 128, 0, st>>>(nb, lmax, d_tiles, nt);
+    note_launch();
+    int64_t ks = (152 * 8 + nt - 1) / nt;
+    const int64_t maxks = (K + 1023) / 1024;
+    if (ks > maxks) ks = maxks;
+    if (ks < 1) ks = 1;
+    if (K > 0) {
+        k_gram_fp32<<<dim3(nt, (unsigned)ks), 256, 0, st>>>(alm, w, K, nb, lmax, d_tiles, nt, G);
+        note_launch();
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t triplet_counts(const int32_t *counts, int64_t K, int nb, unsigned long long *T, cudaStream_t st)

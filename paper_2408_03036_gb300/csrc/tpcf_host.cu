@@ -532,6 +532,24 @@ int dalloc(T **p, size_t n, cudaStream_t st, bool zero)
 
 }  // namespace
 
+void tpcf::self_term_table(int lmax, double *out)
+{
+    const int L1 = lmax + 1;
+    for (int i = 0; i < L1 * L1 * L1 * L1; ++i) out[i] = 0.0;
+    for (int m = 0; m <= lmax; ++m)
+        for (int l1 = m; l1 <= lmax; ++l1)
+            for (int l2 = m; l2 <= lmax; ++l2) {
+                if ((l1 + l2) & 1) continue;
+                const std::vector<double> g = self_coefs(lmax, l1, l2, m);
+                const double kk = k_scale(l1, m) * k_scale(l2, m);
+                for (int j = 0; j <= lmax; ++j) out[(((size_t)m * L1 + l1) * L1 + l2) * L1 + j] = kk * g[j];
+            }
+}
+
+int tpcf::check_config_public(const tpcf_config *c) { return check_config(c); }
+
+int tpcf::set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 // ===================================================================== C ABI
 
 extern "C" {

@@ -26,7 +26,7 @@ CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
 EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
            "tpcf_bin_edges", "tpcf_build_grid", "tpcf_grid_destroy", "tpcf_grid_info", "tpcf_grid_points",
            "tpcf_accumulate_alm", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
-           "tpcf_estimate_3pcf_host", "tpcf_stream_status"]
+           "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static"]
 
 
 class TpcfError(RuntimeError):
@@ -99,6 +99,7 @@ def lib():
             "tpcf_estimate_3pcf": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_estimate_3pcf_host": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_stream_status": ([P], ctypes.c_int),
+            "tpcf_couple_multipoles_static": ([P, P, P, I64, CFG, P, P, P, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -287,6 +288,20 @@ def couple_multipoles(cfg: Config, alm, prim_w, counts, diag, wsp, stream=None):
     c = cfg.c()
     _check(lib().tpcf_couple_multipoles(_ptr(alm), _ptr(prim_w), _ptr(counts), alm.shape[0], ctypes.byref(c),
                                         _ptr(diag), _ptr(wsp), _ptr(nnn), _ptr(tc), _stream(stream)))
+    return nnn, tc
+
+
+def couple_multipoles_static(cfg: Config, alm, prim_w, counts, diag, wsp, stream=None):
+    """tpcf_couple_multipoles_static: the coupling step with no device allocation
+    (fixed library scratch; see include/tpcf.h for the size limit and sharing rules)."""
+    dev = alm.device
+    nb, L1 = cfg.n_bins, cfg.l_max + 1
+    nnn = torch.empty((L1, L1, L1, nb, nb), dtype=torch.float64, device=dev)
+    tc = torch.empty((nb, nb), dtype=torch.int64, device=dev) if counts is not None else None
+    c = cfg.c()
+    _check(lib().tpcf_couple_multipoles_static(_ptr(alm), _ptr(prim_w), _ptr(counts), alm.shape[0],
+                                               ctypes.byref(c), _ptr(diag), _ptr(wsp), _ptr(nnn), _ptr(tc),
+                                               _stream(stream)))
     return nnn, tc
 
 
