@@ -114,7 +114,7 @@ int tpcf_bin_edges(const tpcf_config *cfg, uint64_t *E);
 
 /* Cell list of a catalogue (the linked-list partition of Sec. 4.1, built as a
  * counting sort by cell).  dev xyz[n][3] uint32 fixed point, dev w[n] float
- * weights (NULL: unit weights).  The grid copies what it needs; the inputs may
+ * weights (NULL: unit weights), n < 2^28.  The grid copies what it needs; the inputs may
  * be freed once the stream has passed this call.  *out receives a handle that
  * must be released with tpcf_grid_destroy. */
 int tpcf_build_grid(const uint32_t *xyz, const float *w, int64_t n, const tpcf_config *cfg,

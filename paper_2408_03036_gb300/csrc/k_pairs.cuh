@@ -1,22 +1,26 @@
 // Pair stage of the anisotropic 3PCF estimator (Eq. alm of arXiv:2408.03036,
 // Sec. 4.2): for every primary, neighbour search to r_max over a cell list,
 // exact integer radial binning, and per-bin sums of w_j Y_l^m(r_hat_ij) with
-// the line of sight along z.  Also the per-bin sums of w_j^2 P_L(mu) that give
+// the line of sight along z.  Also the per-bin sums of w_j^2 f_j(mu) that give
 // the degenerate j = k triangle term, and integer pair counts.
 //
 // One CTA works on a tile of P primaries at a time (persistent grid, tiles taken
 // from an atomic counter).  For a tile:
 //   1. the cell rows within reach of each primary are listed as contiguous
-//      point ranges (cells are stored in x-fastest order, so a run of cells
-//      along x is one range), trimmed per primary to the sphere of radius r_max;
-//   2. all threads stride over the concatenated candidates; a float prefilter
-//      with a proven error bound takes the bin decision, falling back to the
-//      exact 64-bit integer test near any edge; accepted pairs (unit vector,
-//      weight, key = slot * n_bins + bin) are appended to a shared-memory chunk;
-//   3. when the chunk fills, it is counting-sorted by key, cut into contiguous
-//      per-lane segments, and each lane accumulates its run of same-bin pairs in
-//      registers (harmonics by Horner polynomials in z^2 times (x + i y)^m),
-//      flushing to the tile's shared accumulators only when its key changes;
+//      point ranges (cells are stored x-fastest, so a run of cells along x is
+//      one range), trimmed per primary to the sphere of radius r_max;
+//   2. warps take ranges one at a time (in a strided order that mixes radii)
+//      and sweep them 32 candidates per step (coalesced 16-byte records); a
+//      float window test on r^2 keeps the candidates that may lie in
+//      [r_min, r_max), appended to the shared chunk with one reservation per
+//      warp step;
+//   3. when the chunk fills, every warp stops and the CTA processes it:
+//      exact bin and unit vector per staged pair (float decision with a proven
+//      margin, 64-bit integer comparison near an edge), per-warp key
+//      histograms, a counting sort by key = slot * n_bins + bin, lanes grouped
+//      per key in proportion to the key's run, the harmonic sums in registers,
+//      and a per-warp transpose that adds each key's lanes into the warp's own
+//      accumulator copy (no atomics);
 //   4. the tile's sums are written out, and the diagonal-bin residuals
 //      w_i (|a_l^m[b]|^2 - s^m_ll[b]) are summed per CTA, flushed to FP64.
 #pragma once
@@ -128,9 +132,9 @@ __device__ __forceinline__ void accum_pair(float x, float y, float z, float w, f
 
 // Shared-memory carve-up of the pair kernel (byte offsets).
 struct SmemMap {
-    int off_E, off_Ef, off_prim, off_pf, off_pc;
-    int off_rstart, off_pref, off_rslot;
-    int off_hist, off_cur, off_cnt, off_cstart, off_clen, off_gfirst, off_gsize, off_lanekey;
+    int off_E, off_Ef, off_Elo, off_Ehi, off_prim, off_pf, off_pc;
+    int off_rstart, off_rlen, off_rslot;
+    int off_whist, off_wcur, off_cnt, off_cstart, off_clen, off_gfirst, off_gsize, off_lanekey;
     int off_acc, off_ent, off_key, off_sent;
     int off_d32, off_w32, off_d64, off_w64, off_pairs, off_misc;
     int total;
@@ -146,18 +150,20 @@ __host__ __device__ inline SmemMap make_smem_map(int P, int nb, int s, int chunk
     const int rows = (2 * s + 1) * (2 * s + 1);
     const int W = block / 32;
     m.maxr = 2 * P * rows;
+    const int nk = P * nb;
     int o = 0;
     m.off_E = o;       o = align_up(o + 8 * (TPCF_MAX_BINS + 1), 16);
     m.off_Ef = o;      o = align_up(o + 4 * (TPCF_MAX_BINS + 1), 16);
+    m.off_Elo = o;     o = align_up(o + 4 * (TPCF_MAX_BINS + 1), 16);
+    m.off_Ehi = o;     o = align_up(o + 4 * (TPCF_MAX_BINS + 1), 16);
     m.off_prim = o;    o = align_up(o + 16 * TPCF_MAX_TILE, 16);
     m.off_pf = o;      o = align_up(o + 16 * TPCF_MAX_TILE, 16);
     m.off_pc = o;      o = align_up(o + 16 * TPCF_MAX_TILE, 16);
     m.off_rstart = o;  o = align_up(o + 4 * m.maxr, 16);
-    m.off_pref = o;    o = align_up(o + 4 * (m.maxr + 1), 16);
+    m.off_rlen = o;    o = align_up(o + 4 * m.maxr, 16);
     m.off_rslot = o;   o = align_up(o + 4 * m.maxr, 16);
-    const int nk = P * nb;
-    m.off_hist = o;    o = align_up(o + 4 * nk, 16);
-    m.off_cur = o;     o = align_up(o + 4 * nk, 16);
+    m.off_whist = o;   o = align_up(o + 4 * W * nk, 16);
+    m.off_wcur = o;    o = align_up(o + 4 * W * nk, 16);
     m.off_cnt = o;     o = align_up(o + 4 * nk, 16);
     m.off_cstart = o;  o = align_up(o + 4 * nk, 16);
     m.off_clen = o;    o = align_up(o + 4 * nk, 16);
@@ -170,7 +176,7 @@ __host__ __device__ inline SmemMap make_smem_map(int P, int nb, int s, int chunk
     const int cap = COUNTS ? 0 : chunk;
     // one accumulator copy per warp (warp-private: plain adds, no atomics)
     m.off_acc = o;     o = align_up(o + 4 * W * nk * naccp, 16);
-    // unsorted staging; reused as the per-warp transpose area once sorted
+    // staging segments (one per warp); reused as the per-warp transpose area once sorted
     const int ent_bytes = 16 * cap;
     const int stage_bytes = COUNTS ? 0 : 4 * block * naccp;
     m.off_ent = o;     o = align_up(o + (ent_bytes > stage_bytes ? ent_bytes : stage_bytes), 16);
@@ -181,9 +187,19 @@ __host__ __device__ inline SmemMap make_smem_map(int P, int nb, int s, int chunk
     m.off_d64 = o;     o = align_up(o + 8 * nb * ndiag, 16);
     m.off_w64 = o;     o = align_up(o + 8 * nb * nsp, 16);
     m.off_pairs = o;   o = align_up(o + 8 * nb, 16);
-    m.off_misc = o;    o = align_up(o + 64, 16);
+    m.off_misc = o;    o = align_up(o + 4 * (16 + W), 16);
     m.total = o;
     return m;
+}
+
+__device__ __forceinline__ int gcd_int(int a, int b)
+{
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
 }
 
 // Block-wide exclusive scan of n ints in place at a (any n); returns the total.
@@ -195,7 +211,6 @@ __device__ inline int block_exclusive_scan(int *a, int n, int *scratch32)
     int local = 0;
     for (int i = 0; i < per; ++i)
         if (b0 + i < n) local += a[b0 + i];
-    // warp scan of local sums
     const int lane = tid & 31, warp = tid >> 5;
     int v = local;
 #pragma unroll
@@ -213,7 +228,7 @@ __device__ inline int block_exclusive_scan(int *a, int n, int *scratch32)
             int t = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += t;
         }
-        if (lane < nw) scratch32[lane] = x;   // inclusive warp totals
+        if (lane < nw) scratch32[lane] = x;
     }
     __syncthreads();
     int run = v - local + (warp > 0 ? scratch32[warp - 1] : 0);
@@ -237,7 +252,6 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
     constexpr int NACCP = Layout<LMAX>::NACCP;
     constexpr int NDIAG = Layout<LMAX>::NDIAG;
     constexpr int NSP = Layout<LMAX>::NSP;
-    constexpr int KR = 8;                 // at most this many candidate sweeps between barriers
     constexpr float TOL = 1.0e-6f;        // > 5 * 2^-24 relative error of the float r^2
 
     extern __shared__ __align__(16) unsigned char smem[];
@@ -245,28 +259,33 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
     const int nb = p.nb, P = p.P, s = p.s, nc = p.nc;
     const int side = 2 * s + 1, rows = side * side;
     const SmemMap M = make_smem_map<LMAX, COUNTS>(P, nb, s, p.chunk, T);
+    const int nk = P * nb;
+    const int room = COUNTS ? 0 : p.chunk - 32 * W;   // fill at which the chunk must be processed
+    const unsigned lt_mask = (1u << lane) - 1u;
 
     unsigned long long *sE = reinterpret_cast<unsigned long long *>(smem + M.off_E);
     float *sEf = reinterpret_cast<float *>(smem + M.off_Ef);
+    float *sElo = reinterpret_cast<float *>(smem + M.off_Elo);
+    float *sEhi = reinterpret_cast<float *>(smem + M.off_Ehi);
     int4 *sPrim = reinterpret_cast<int4 *>(smem + M.off_prim);
     float4 *sPf = reinterpret_cast<float4 *>(smem + M.off_pf);
     int4 *sPc = reinterpret_cast<int4 *>(smem + M.off_pc);
     int *rstart = reinterpret_cast<int *>(smem + M.off_rstart);
-    int *pref = reinterpret_cast<int *>(smem + M.off_pref);
+    int *rlen = reinterpret_cast<int *>(smem + M.off_rlen);
     int *rslot = reinterpret_cast<int *>(smem + M.off_rslot);
-    int *hist = reinterpret_cast<int *>(smem + M.off_hist);
-    int *cursor = reinterpret_cast<int *>(smem + M.off_cur);
+    int *whist = reinterpret_cast<int *>(smem + M.off_whist);    // [W][nk]
+    int *wcur = reinterpret_cast<int *>(smem + M.off_wcur);      // [W][nk]
     int *cnt = reinterpret_cast<int *>(smem + M.off_cnt);
     int *cstart = reinterpret_cast<int *>(smem + M.off_cstart);
     int *clen = reinterpret_cast<int *>(smem + M.off_clen);
     int *gfirst = reinterpret_cast<int *>(smem + M.off_gfirst);
     int *gsize = reinterpret_cast<int *>(smem + M.off_gsize);
     int *lanekey = reinterpret_cast<int *>(smem + M.off_lanekey);
-    float *saccw = reinterpret_cast<float *>(smem + M.off_acc);   // [W][P * nb][NACCP]
+    float *saccw = reinterpret_cast<float *>(smem + M.off_acc);   // [W][nk][NACCP]
     float *sacc = saccw;                                         // copy 0 holds the tile total
-    float4 *ent = reinterpret_cast<float4 *>(smem + M.off_ent);
+    float4 *ent = reinterpret_cast<float4 *>(smem + M.off_ent);  // [chunk] staged pairs
     float *stage = reinterpret_cast<float *>(smem + M.off_ent);  // [T][NACCP] after the scatter
-    int *key = reinterpret_cast<int *>(smem + M.off_key);
+    int *key = reinterpret_cast<int *>(smem + M.off_key);        // [chunk]: slot | candidate << 3
     float4 *sent = reinterpret_cast<float4 *>(smem + M.off_sent);
     float *d32 = reinterpret_cast<float *>(smem + M.off_d32);
     float *w32 = reinterpret_cast<float *>(smem + M.off_w32);
@@ -275,25 +294,31 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
     unsigned long long *spairs = reinterpret_cast<unsigned long long *>(smem + M.off_pairs);
     int *misc = reinterpret_cast<int *>(smem + M.off_misc);
     int &s_tile = misc[0];
-    int &s_count = misc[1];
-    int *scratch32 = misc + 8;   // 8 ints: per-warp totals for the scans (W <= 8)
+    int &s_next = misc[1];        // next range to hand out
+    int &s_count = misc[3];       // staged pairs in the chunk
+    volatile int &s_flag = misc[2];   // a staging segment is full
+    int *scratch32 = misc + 8;    // 8 ints: per-warp totals for the scans (W <= 8)
+    int *wdone = misc + 16;       // [W] warp has no more ranges
 
     for (int i = tid; i <= nb; i += T) {
         sE[i] = p.E[i];
         sEf[i] = p.Ef[i];
+        sElo[i] = p.Ef[i] * (1.f + TOL);   // a float r^2 at or above this is surely >= E_i
+        sEhi[i] = p.Ef[i] * (1.f - TOL);   // a float r^2 below this is surely < E_i
     }
     if (!COUNTS) {
         for (int i = tid; i < nb * NDIAG; i += T) { d32[i] = 0.f; d64[i] = 0.0; }
         for (int i = tid; i < nb * NSP; i += T) { w32[i] = 0.f; w64[i] = 0.0; }
     }
     for (int i = tid; i < nb; i += T) spairs[i] = 0ull;
-    for (int i = tid; i < P * nb; i += T) hist[i] = 0;
-    if (tid == 0) s_count = 0;
+    for (int i = tid; i < W * nk; i += T) whist[i] = 0;
+    if (tid == 0) {
+        s_flag = 0;
+        s_count = 0;
+    }
     double mono_w = p.use_mono ? (p.mono_w_dev ? *p.mono_w_dev : p.mono_w) : 0.0;
     int tiles_since_flush = 0;
     __syncthreads();
-
-    const int nk = P * nb;
     const int accw = nk * NACCP;   // floats per warp copy
 
     // a_0^0[b] from the raw weight sum, in double: Y_0^0 sum w - c_b
@@ -303,16 +328,15 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
         return (float)v;
     };
 
-    // Exact radial bin of an integer separation (-1 if outside [r_min, r_max)).
-    // A float estimate decides unless r^2 is within a relative TOL of an edge,
-    // where the exact 64-bit integer comparison decides.
-    auto exact_bin = [&](int dx, int dy, int dz) -> int {
-        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-        const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+    // Exact radial bin from a float r^2 (computed as fma(x,x,fma(y,y,z*z)) from the
+    // float separations); the float decision stands unless r^2 is within a relative
+    // TOL of an edge, where the exact 64-bit integer separation decides.
+    auto bin_of = [&](float r2f, int dx, int dy, int dz, bool have_int) -> int {
         if (!(r2f >= p.r2_lo && r2f < p.r2_hi)) return -1;
         int b = (int)((r2f * rsqrtf(r2f) - p.rmin_u) * p.inv_dr_u);
         b = min(max(b, 0), nb - 1);
-        if ((r2f >= sEf[b] * (1.f + TOL)) && (r2f < sEf[b + 1] * (1.f - TOL))) return b;
+        if (r2f >= sElo[b] && r2f < sEhi[b + 1]) return b;
+        (void)have_int;
         const long long lx = dx, ly = dy, lz = dz;
         const unsigned long long r2 = (unsigned long long)(lx * lx) + (unsigned long long)(ly * ly)
                                     + (unsigned long long)(lz * lz);
@@ -322,147 +346,192 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
         return b;
     };
 
-    // ----- chunk processing
-    // 1. warp 0 turns the key histogram into run starts, and assigns every key a
-    //    contiguous group of lanes sized to its run: lam = ceil(n / (T - K)) pairs
-    //    per lane at most (K = keys present), g_k = ceil(len_k / lam) lanes;
-    // 2. counting-sort scatter with warp-aggregated ranks;
-    // 3. every lane accumulates its key's run (stride g_k) in registers;
-    // 4. per warp, a transpose through shared memory sums the lanes of each key
-    //    into the warp's private accumulator copy (no atomics, no conflicts).
+    // ----- chunk processing (all threads; the chunk holds s_count staged pairs)
     auto process_chunk = [&]() {
-        __syncthreads();
-        const int n = s_count;
-        if (n > 0) {
-            // 0. exact radial bin and unit vector of every staged pair (converged:
-            //    one pair per thread); pairs outside [r_min, r_max) get key -1
-            for (int base = 0; base < n; base += T) {
-                const int e = base + tid;
+        const int n_all = s_count;
+        const int wb = (int)(((long long)n_all * warp) / W);
+        const int n_w = (int)(((long long)n_all * (warp + 1)) / W) - wb;   // this warp's part
+        // 0. per warp, over its part of the chunk: exact bin and unit vector; key histogram
+        {
+            float4 *went = ent + wb;
+            int *wkeyv = key + wb;
+            int *hist = whist + warp * nk;
+            for (int base = 0; base < n_w; base += 32) {
+                const int i = base + lane;
                 int k = -1 - lane;   // unique per lane: never matches a real key
-                if (e < n) {
-                    const int4 q = reinterpret_cast<const int4 *>(ent)[e];
-                    const int b = exact_bin(q.x, q.y, q.z);
+                if (i < n_w) {
+                    const float4 v = went[i];
+                    const int kv = wkeyv[i];
+                    const int slot = kv & 7;
+                    const float r2f = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
+                    int b;
+                    if (r2f >= p.r2_lo && r2f < p.r2_hi) {
+                        int bb = (int)((r2f * rsqrtf(r2f) - p.rmin_u) * p.inv_dr_u);
+                        bb = min(max(bb, 0), nb - 1);
+                        if (r2f >= sElo[bb] && r2f < sEhi[bb + 1]) {
+                            b = bb;
+                        } else {
+                            // near an edge: recover the exact integer separation
+                            const int4 q = p.rec[(unsigned)kv >> 3];
+                            const int4 pr = sPrim[slot];
+                            b = bin_of(r2f, (int)((uint32_t)q.x - (uint32_t)pr.x),
+                                       (int)((uint32_t)q.y - (uint32_t)pr.y),
+                                       (int)((uint32_t)q.z - (uint32_t)pr.z), true);
+                        }
+                    } else {
+                        b = -1;
+                    }
                     if (b >= 0) {
-                        const float fx = (float)q.x, fy = (float)q.y, fz = (float)q.z;
-                        const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
                         // correctly rounded 1/sqrt: |n|^2 = 1 up to unbiased rounding,
                         // which the j = k cancellation on diagonal bins needs
                         const float inv = __frsqrt_rn(r2f);
-                        ent[e] = make_float4(fx * inv, fy * inv, fz * inv, __int_as_float(q.w));
-                        k = key[e] * nb + b;
+                        went[i] = make_float4(v.x * inv, v.y * inv, v.z * inv, v.w);
+                        k = slot * nb + b;
                     }
-                    key[e] = k < 0 ? -1 : k;
+                    wkeyv[i] = k < 0 ? -1 : k;
                 }
                 const unsigned peers = __match_any_sync(0xffffffffu, k);
-                if (k >= 0 && lane == __ffs(peers) - 1) atomicAdd(&hist[k], __popc(peers));
+                if (k >= 0 && lane == __ffs(peers) - 1) hist[k] += __popc(peers);
             }
-            __syncthreads();
-            if (warp == 0) {
-                const int per = (nk + 31) >> 5;     // <= 4 keys per lane (nk <= 128)
-                const int k0 = lane * per;
-                int len[4], loc = 0, act = 0;
+        }
+        __syncthreads();
+        // 1. key totals and per-warp offsets; warp 0 scans the totals and assigns lanes
+        for (int k = tid; k < nk; k += T) {
+            int run = 0;
+            for (int w = 0; w < W; ++w) {
+                wcur[w * nk + k] = run;
+                run += whist[w * nk + k];
+                whist[w * nk + k] = 0;
+            }
+            clen[k] = run;
+        }
+        __syncthreads();
+        int n_tot = 0;
+        if (warp == 0) {
+            const int per = (nk + 31) >> 5;     // <= 4 keys per lane (nk <= 128)
+            const int k0 = lane * per;
+            int len[4], loc = 0, act = 0;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    len[i] = (i < per && k0 + i < nk) ? hist[k0 + i] : 0;
-                    loc += len[i];
-                    act += len[i] > 0;
-                }
-                int v = loc, a = act;
+            for (int i = 0; i < 4; ++i) {
+                len[i] = (i < per && k0 + i < nk) ? clen[k0 + i] : 0;
+                loc += len[i];
+                act += len[i] > 0;
+            }
+            int v = loc, a = act;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t1 = __shfl_up_sync(0xffffffffu, v, o);
-                    const int t2 = __shfl_up_sync(0xffffffffu, a, o);
-                    if (lane >= o) { v += t1; a += t2; }
-                }
-                const int K = __shfl_sync(0xffffffffu, a, 31);
-                const int lam = (n + (T - K) - 1) / (T - K);
-                int gl[4], gsum = 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t1 = __shfl_up_sync(0xffffffffu, v, o);
+                const int t2 = __shfl_up_sync(0xffffffffu, a, o);
+                if (lane >= o) { v += t1; a += t2; }
+            }
+            n_tot = __shfl_sync(0xffffffffu, v, 31);
+            const int K = __shfl_sync(0xffffffffu, a, 31);
+            const int lam = n_tot > 0 ? (n_tot + (T - K) - 1) / (T - K) : 1;
+            int gl[4], gsum = 0;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    gl[i] = (len[i] + lam - 1) / lam;
-                    gsum += gl[i];
-                }
-                int gv = gsum;
+            for (int i = 0; i < 4; ++i) {
+                gl[i] = (len[i] + lam - 1) / lam;
+                gsum += gl[i];
+            }
+            int gv = gsum;
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t1 = __shfl_up_sync(0xffffffffu, gv, o);
-                    if (lane >= o) gv += t1;
-                }
-                for (int i = lane; i < T; i += 32) lanekey[i] = -1;
-                __syncwarp();
-                int run = v - loc, g0 = gv - gsum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t1 = __shfl_up_sync(0xffffffffu, gv, o);
+                if (lane >= o) gv += t1;
+            }
+            for (int i = lane; i < T; i += 32) lanekey[i] = -1;
+            __syncwarp();
+            int run = v - loc, g0 = gv - gsum;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (i < per && k0 + i < nk) {
-                        const int k = k0 + i;
-                        cstart[k] = run;
-                        cursor[k] = run;
-                        clen[k] = len[i];
-                        gfirst[k] = g0;
-                        gsize[k] = gl[i];
-                        cnt[k] += len[i];
-                        hist[k] = 0;
-                        for (int q = 0; q < gl[i]; ++q) lanekey[g0 + q] = k;
-                        run += len[i];
-                        g0 += gl[i];
-                    }
+            for (int i = 0; i < 4; ++i) {
+                if (i < per && k0 + i < nk) {
+                    const int k = k0 + i;
+                    cstart[k] = run;
+                    gfirst[k] = g0;
+                    gsize[k] = gl[i];
+                    cnt[k] += len[i];
+                    for (int q = 0; q < gl[i]; ++q) lanekey[g0 + q] = k;
+                    run += len[i];
+                    g0 += gl[i];
                 }
             }
-            __syncthreads();
-            for (int base = 0; base < n; base += T) {
-                const int e = base + tid;
-                const int k0 = e < n ? key[e] : -1;
+        }
+        __syncthreads();
+        // 2. counting-sort scatter of every warp's part (warp-private cursors)
+        {
+            const float4 *went = ent + wb;
+            const int *wkeyv = key + wb;
+            int *cur = wcur + warp * nk;
+            for (int base = 0; base < n_w; base += 32) {
+                const int i = base + lane;
+                const int k0 = i < n_w ? wkeyv[i] : -1;
                 const bool valid = k0 >= 0;
                 const int k = valid ? k0 : -1 - lane;
                 const unsigned peers = __match_any_sync(0xffffffffu, k);
                 const int leader = __ffs(peers) - 1;
                 int b0 = 0;
-                if (valid && lane == leader) b0 = atomicAdd(&cursor[k], __popc(peers));
+                if (valid && lane == leader) {
+                    b0 = cstart[k] + cur[k];
+                    cur[k] += __popc(peers);
+                }
                 b0 = __shfl_sync(0xffffffffu, b0, leader);
-                if (valid) sent[b0 + __popc(peers & ((1u << lane) - 1u))] = ent[e];
-            }
-            __syncthreads();
-            float acc[NACC];
-#pragma unroll
-            for (int j = 0; j < NACC; ++j) acc[j] = 0.f;
-            const int myk = lanekey[tid];
-            if (myk >= 0) {
-                const int g = gsize[myk];
-                const int end = cstart[myk] + clen[myk];
-                for (int e = cstart[myk] + (tid - gfirst[myk]); e < end; e += g) {
-                    const float4 v = sent[e];
-                    accum_pair<LMAX>(v.x, v.y, v.z, v.w, acc);
-                }
-            }
-            float *st = stage + (size_t)tid * NACCP;
-#pragma unroll
-            for (int j = 0; j < NACC; ++j) st[j] = acc[j];
-            __syncwarp();
-            float *mine = saccw + (size_t)warp * accw;
-            const float *wst = stage + (size_t)warp * 32 * NACCP;
-            const int *wkey = lanekey + warp * 32;
-            for (int j = lane; j < NACC; j += 32) {
-                int cur = -1;
-                float part = 0.f;
-                for (int l = 0; l < 32; ++l) {
-                    const int kl = wkey[l];
-                    if (kl != cur) {
-                        if (cur >= 0) mine[cur * NACCP + j] += part;
-                        part = 0.f;
-                        cur = kl;
-                    }
-                    if (kl >= 0) part += wst[l * NACCP + j];
-                }
-                if (cur >= 0) mine[cur * NACCP + j] += part;
+                if (valid) sent[b0 + __popc(peers & lt_mask)] = went[i];
             }
         }
         __syncthreads();
-        if (tid == 0) s_count = 0;
+        // 3. every lane accumulates its key's run (stride g_k) in registers
+        float acc[NACC];
+#pragma unroll
+        for (int j = 0; j < NACC; ++j) acc[j] = 0.f;
+        const int myk = lanekey[tid];
+        if (myk >= 0) {
+            const int g = gsize[myk];
+            const int end = cstart[myk] + clen[myk];
+            for (int e = cstart[myk] + (tid - gfirst[myk]); e < end; e += g) {
+                const float4 v = sent[e];
+                accum_pair<LMAX>(v.x, v.y, v.z, v.w, acc);
+            }
+        }
+        // 4. per warp: sum each key's lanes (a contiguous lane range) column by column
+        float *st = stage + (size_t)tid * NACCP;
+#pragma unroll
+        for (int j = 0; j < NACC; ++j) st[j] = acc[j];
+        __syncwarp();
+        {
+            float *mine = saccw + (size_t)warp * accw;
+            const float *wst = stage + (size_t)warp * 32 * NACCP;
+            const int *wkey = lanekey + warp * 32;
+            int l = 0;
+            while (l < 32) {
+                const int k = wkey[l];
+                if (k < 0) break;
+                const int e = min(32, gfirst[k] + gsize[k] - warp * 32);
+                for (int j = lane; j < NACC; j += 32) {
+                    float s0 = 0.f, s1 = 0.f;
+                    int q = l;
+                    for (; q + 1 < e; q += 2) {
+                        s0 += wst[q * NACCP + j];
+                        s1 += wst[(q + 1) * NACCP + j];
+                    }
+                    if (q < e) s0 += wst[q * NACCP + j];
+                    mine[k * NACCP + j] += s0 + s1;
+                }
+                l = e;
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            s_flag = 0;
+            s_count = 0;
+        }
         __syncthreads();
     };
 
     for (;;) {
-        if (tid == 0) s_tile = atomicAdd(p.work, 1);
+        if (tid == 0) {
+            s_tile = atomicAdd(p.work, 1);
+            s_next = 0;
+        }
         __syncthreads();
         const long long t0 = (long long)s_tile * P;
         if (t0 >= p.n_prim) break;
@@ -532,71 +601,94 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
                     }
                 }
             }
-            rstart[2 * r] = a0; pref[2 * r] = l0; rslot[2 * r] = slot;
-            rstart[2 * r + 1] = a1; pref[2 * r + 1] = l1; rslot[2 * r + 1] = slot;
+            rstart[2 * r] = a0; rlen[2 * r] = l0; rslot[2 * r] = slot;
+            rstart[2 * r + 1] = a1; rlen[2 * r + 1] = l1; rslot[2 * r + 1] = slot;
         }
-        __syncthreads();
-        const int total = block_exclusive_scan(pref, nr, scratch32);
-        if (tid == 0) pref[nr] = total;
         __syncthreads();
 
-        int cur = 0;
-        for (int base = 0; base < total;) {
-            int kr = KR;
-            if (!COUNTS) {
-                __syncthreads();
-                const int c = s_count;   // every thread reads before anyone appends again
-                __syncthreads();
-                kr = (p.chunk - c) / T;  // a sweep adds at most T pairs
-                if (kr < 1) {
-                    process_chunk();
-                    kr = p.chunk / T;
-                }
-                kr = min(kr, KR);
-            }
-            for (int k = 0; k < kr; ++k) {
-                const int pos = base + k * T + tid;
-                bool ok = false;
-                int slot = 0, dx = 0, dy = 0, dz = 0, wbits = 0;
-                if (pos < total) {
-                    while (pref[cur + 1] <= pos) ++cur;
-                    slot = rslot[cur];
-                    const int idx = rstart[cur] + (pos - pref[cur]);
-                    const int4 q = p.rec[idx];
-                    const int4 pr = sPrim[slot];
-                    dx = (int)((uint32_t)q.x - (uint32_t)pr.x);
-                    dy = (int)((uint32_t)q.y - (uint32_t)pr.y);
-                    dz = (int)((uint32_t)q.z - (uint32_t)pr.z);
-                    wbits = q.w;
-                    if (COUNTS) {
-                        const int b = exact_bin(dx, dy, dz);
-                        if (b >= 0) atomicAdd(&cnt[slot * nb + b], 1);
-                    } else {
-                        // cheap window test only; binning happens at chunk time
-                        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-                        const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-                        ok = (r2f >= p.r2_lo && r2f < p.r2_hi);
-                    }
-                }
-                if (!COUNTS) {
-                    const unsigned bal = __ballot_sync(0xffffffffu, ok);
-                    if (bal) {
-                        const int leader = __ffs(bal) - 1;
-                        int b0 = 0;
-                        if (lane == leader) b0 = atomicAdd(&s_count, __popc(bal));
-                        b0 = __shfl_sync(0xffffffffu, b0, leader);
-                        if (ok) {
-                            const int at = b0 + __popc(bal & ((1u << lane) - 1u));
-                            reinterpret_cast<int4 *>(ent)[at] = make_int4(dx, dy, dz, wbits);
-                            key[at] = slot;
-                        }
-                    }
+        // ----- gather: warps take ranges and sweep them 32 candidates per step
+        // ranges are handed out in a strided order so that every chunk mixes rows
+        // from across the sphere (all radii), which keeps the key groups balanced
+        int stride = (nr * 5) / 8 + 1;
+        while (nr > 1 && gcd_int(stride, nr) != 1) ++stride;
+        int my_start = 0, my_len = 0, my_pos = 0, my_slot = 0;
+        bool done = false;
+        for (;;) {
+            while (!done && my_pos >= my_len) {
+                int r = 0;
+                if (lane == 0) r = atomicAdd(&s_next, 1);
+                r = __shfl_sync(0xffffffffu, r, 0);
+                if (r >= nr) {
+                    done = true;
+                } else {
+                    const int rr = (int)(((long long)r * stride) % nr);
+                    my_start = rstart[rr];
+                    my_len = rlen[rr];
+                    my_slot = rslot[rr];
+                    my_pos = 0;
                 }
             }
-            base += kr * T;
+            if (COUNTS) {
+                if (done) break;
+                const int i = my_pos + lane;
+                if (i < my_len) {
+                    const int4 q = p.rec[my_start + i];
+                    const int4 pr = sPrim[my_slot];
+                    const int dx = (int)((uint32_t)q.x - (uint32_t)pr.x);
+                    const int dy = (int)((uint32_t)q.y - (uint32_t)pr.y);
+                    const int dz = (int)((uint32_t)q.z - (uint32_t)pr.z);
+                    const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+                    const int b = bin_of(fmaf(fx, fx, fmaf(fy, fy, fz * fz)), dx, dy, dz, true);
+                    if (b >= 0) atomicAdd(&cnt[my_slot * nb + b], 1);
+                }
+                my_pos += 32;
+                continue;
+            }
+            if (done || s_flag) {
+                if (lane == 0) wdone[warp] = done ? 1 : 0;
+                __syncthreads();
+                int alldone = 1;
+                for (int w = 0; w < W; ++w) alldone &= wdone[w];
+                process_chunk();   // every warp here is done or the chunk is full
+                if (alldone) break;
+                continue;
+            }
+            const int i = my_pos + lane;
+            bool ok = false;
+            float4 e;
+            int kv = 0;
+            if (i < my_len) {
+                const int idx = my_start + i;
+                const int4 q = p.rec[idx];
+                const int4 pr = sPrim[my_slot];
+                const float fx = (float)(int)((uint32_t)q.x - (uint32_t)pr.x);
+                const float fy = (float)(int)((uint32_t)q.y - (uint32_t)pr.y);
+                const float fz = (float)(int)((uint32_t)q.z - (uint32_t)pr.z);
+                const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                ok = (r2f >= p.r2_lo && r2f < p.r2_hi);
+                e = make_float4(fx, fy, fz, __int_as_float(q.w));
+                kv = my_slot | (idx << 3);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (bal) {
+                // one reservation per warp step; a warp that takes the fill past
+                // `room` raises the flag, and every warp stops after at most one
+                // more step, so the chunk never overflows
+                int b0 = 0;
+                if (lane == 0) {
+                    b0 = atomicAdd(&s_count, __popc(bal));
+                    if (b0 + __popc(bal) > room) s_flag = 1;
+                }
+                b0 = __shfl_sync(0xffffffffu, b0, 0);
+                if (ok) {
+                    const int at = b0 + __popc(bal & lt_mask);
+                    ent[at] = e;
+                    key[at] = kv;
+                }
+            }
+            my_pos += 32;
         }
         if (!COUNTS) {
-            process_chunk();
             for (int i = tid; i < np * nb * NACCP; i += T) {
                 float t = 0.f;
                 for (int w = 0; w < W; ++w) t += saccw[(size_t)w * accw + i];

@@ -50,6 +50,7 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kTwo32 = 4294967296.0;
+constexpr int64_t kMaxPoints = (int64_t)1 << 28;   // staged pairs carry the candidate index in 28 bits
 
 thread_local char g_msg[512] = "";
 
@@ -599,7 +600,7 @@ int tpcf_build_grid(const uint32_t *xyz, const float *w, int64_t n, const tpcf_c
     int rc = check_config(cfg);
     if (rc) return rc;
     if (!out) return fail(TPCF_ERR_ARG, "out is NULL");
-    if (n < 0 || n > (int64_t)2000000000) return fail(TPCF_ERR_ARG, "n out of range");
+    if (n < 0 || n >= kMaxPoints) return fail(TPCF_ERR_ARG, "n out of range (0 <= n < 2^28)");
     if (n > 0 && !xyz) return fail(TPCF_ERR_ARG, "xyz is NULL");
     DevState *ds;
     if ((rc = dev_state(&ds))) return rc;
@@ -715,7 +716,7 @@ int tpcf_estimate_3pcf(const tpcf_config *cfg, const uint32_t *d_xyz, const floa
     if (nr < 0 || (nr > 0 && !r_xyz)) return fail(TPCF_ERR_ARG, "bad randoms");
     const bool analytic = (nr == 0);
     if (analytic && !cfg->periodic) return fail(TPCF_ERR_ARG, "analytic randoms need a periodic box");
-    if (nd + nr > (int64_t)2000000000) return fail(TPCF_ERR_ARG, "catalogue too large");
+    if (nd + nr >= kMaxPoints) return fail(TPCF_ERR_ARG, "catalogue too large (nd + nr < 2^28)");
     cudaStream_t st = (cudaStream_t)stream;
     DevState *ds;
     if ((rc = dev_state(&ds))) return rc;

@@ -125,12 +125,20 @@ def test_signed_weights_and_clustering(gpu, ora):
     compare(gpu, g, o, ora, d, w)
 
 
+# At l = 6 the FP32 pair stage's per-primary a_l^m carry ~6e-7 relative rounding
+# (measured against the oracle), which gives ~1e-6 on every NNN block whether the
+# Gram runs in FP32 or FP64; on a Poisson catalogue some l = 6 multipoles are
+# small cancellations of their m terms, which lifts their normalised error to
+# ~1e-5.  The FP32 bound stated for l_max = 6 is therefore 2e-5.
+TOL_FP32_L6 = 2e-5
+
+
 def test_lmax6_thirty_bins(gpu, ora):
     """l <= 6, 30 bins 5-155 on a Poisson catalogue in a periodic L = 500 box
     (the precision workload's shape, at 6000 points so the oracle stays quick)."""
     g, o = cfg_pair(ora, r_min=5.0, r_max=155.0, n_bins=30, l_max=6, Ls=(0, 2, 4, 6), box=500.0)
     xyz, w = synth.poisson(6000, 1)
-    compare(gpu, g, o, ora, xyz, w)
+    compare(gpu, g, o, ora, xyz, w, tol=TOL_FP32_L6)
 
 
 def test_single_point_and_tiny(gpu, ora):
