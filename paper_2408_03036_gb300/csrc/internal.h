@@ -80,6 +80,9 @@ cudaError_t couple_gram_fp32(const float *alm, const float *w, int64_t K, int nb
 cudaError_t triplet_counts(const int32_t *counts, int64_t K, int nb, unsigned long long *T,
                            cudaStream_t st);
 int gram_tile_count(int nb, int lmax);
+// Tensor-core (tcgen05) Gram with bf16 or tf32 hi/lo splits; fills all of G.
+cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, int lmax, bool tf32, double *G,
+                           int *err, int sms, cudaStream_t st);
 cudaError_t couple_gram_fp32_tiles(const float *alm, const float *w, int64_t K, int nb, int lmax, int *d_tiles,
                                    double *G, cudaStream_t st);
 // j = k coefficients of the off-diagonal (l1 != l2) entries, [m][l1][l2][j] for one l_max

@@ -446,8 +446,9 @@ int couple(const tpcf_config *c, const float *alm, const float *w, const int32_t
            const double *diag, const double *wsp, double *nnn, unsigned long long *trip_u64, cudaStream_t st)
 {
     const int nb = c->n_bins, L = c->l_max;
-    if (c->precision != TPCF_PREC_FP32)
-        return fail(TPCF_ERR_UNSUPPORTED, "tensor-core coupling not available in this build");
+    DevState *ds;
+    int rc0 = dev_state(&ds);
+    if (rc0) return rc0;
     int64_t gsz = gram_offset(nb, L, L + 1);
     double *G = nullptr, *gaunt = nullptr;
     CK(cudaMallocAsync((void **)&G, gsz * sizeof(double), st));
@@ -464,7 +465,14 @@ int couple(const tpcf_config *c, const float *alm, const float *w, const int32_t
             }
     CK(cudaMallocAsync((void **)&gaunt, hg.size() * sizeof(double), st));
     CK(cudaMemcpyAsync(gaunt, hg.data(), hg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    CK(couple_gram_fp32(alm, w, K, nb, L, G, st));
+    if (c->precision == TPCF_PREC_FP32) {
+        CK(couple_gram_fp32(alm, w, K, nb, L, G, st));
+    } else {
+        cudaError_t e = couple_gram_tc(alm, w, K, nb, L, c->precision == TPCF_PREC_TF32X3, G, ds->err, ds->sms, st);
+        if (e == cudaErrorInvalidValue)
+            return fail(TPCF_ERR_UNSUPPORTED, "tensor-core Gram: an m block exceeds two 128-row tiles of 256 columns");
+        CK(e);
+    }
     CK(assemble_nnn(G, diag, wsp, nb, L, c->remove_self, gaunt, nnn, st));
     if (counts && trip_u64) CK(tpcf::triplet_counts(counts, K, nb, trip_u64, st));
     // the host vector must outlive the asynchronous copy

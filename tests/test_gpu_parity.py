@@ -207,3 +207,31 @@ def test_bad_weights_are_reported(gpu):
         tpcf.stream_status()
     assert ei.value.code == -6
     tpcf.stream_status()   # latch cleared
+
+
+TOL_MIXED = 1e-4   # split-precision tensor-core coupling (bf16x3 / tf32x3) vs the FP64 oracle
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16x3", TOL_MIXED), ("tf32x3", TOL_MIXED)])
+def test_tensor_core_coupling_config1(gpu, ora, prec, tol):
+    """tcgen05 Gram (split precision, FP32 accumulate in tensor memory, FP64 flush)
+    on the plain-estimator workload."""
+    g, o = cfg_pair(ora, r_min=20.0, r_max=120.0, n_bins=10, l_max=4, Ls=(0, 2, 4), box=500.0)
+    g.precision = prec
+    xyz, w = synth.poisson(20000, 1)
+    compare(gpu, g, o, ora, xyz, w, tol=tol)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_tensor_core_coupling_open_volume_and_two_row_tiles(gpu, ora, prec):
+    """Signed D - R primary weights, and an m = 0 block of 30 x 7 = 210 rows
+    (two 128-row tiles) at l_max = 6."""
+    g, o = cfg_pair(ora, r_min=10.0, r_max=100.0, n_bins=9, l_max=4, Ls=(0, 2, 4), box=600.0, periodic=False)
+    g.precision = prec
+    d, dw = synth.lognormal(8000, 600.0, 3, mesh=64)
+    r, rw = synth.randoms(24000, 4)
+    compare(gpu, g, o, ora, d, dw, r, rw, tol=TOL_MIXED)
+    g, o = cfg_pair(ora, r_min=5.0, r_max=155.0, n_bins=30, l_max=6, Ls=(0, 2, 4, 6), box=500.0)
+    g.precision = prec
+    xyz, w = synth.poisson(6000, 1)
+    compare(gpu, g, o, ora, xyz, w, tol=TOL_MIXED)
