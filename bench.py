@@ -37,12 +37,21 @@ WORKLOAD = ("clustered lognormal halos N_D=400000 (512^3 mesh, P~k^-1.5 exp(-(k/
             "LOS shift f=0.8) + N_R=1200000 randoms, open cube L=1000 Mpc/h, 20 bins 10-150 Mpc/h, "
             "l_max=4, L={0,2,4}")
 FLOP_PER_PAIR = 4 * 25 + 15   # algorithmic FP32 work per accepted pair at l_max = 4
+# covariance batch: lognormal mocks (same field recipe, 256^3 mesh) in a periodic
+# cube of side 1000 Mpc/h, sizes uniform in [100k, 400k], analytic randoms
+N_MOCKS, MOCK_LO, MOCK_HI, MOCK_MESH, SEED_MOCKS = 256, 100_000, 400_000, 256, 77
 
 
 def config(precision="fp32"):
     from paper_2408_03036_gb300 import tpcf
     return tpcf.Config(r_min=10.0, r_max=150.0, n_bins=20, l_max=4, Ls=(0, 2, 4), periodic=False,
                        box=BOX, precision=precision)
+
+
+def mock_config(precision="fp32", **kw):
+    from paper_2408_03036_gb300 import tpcf
+    return tpcf.Config(r_min=10.0, r_max=150.0, n_bins=20, l_max=4, Ls=(0, 2, 4), periodic=True,
+                       box=BOX, precision=precision, **kw)
 
 
 def make_inputs(rank=0):
@@ -243,6 +252,10 @@ def run_ours(args):
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = end_to_end(cfg, d, dw, r, rw, args, stream, tpcf)
 
+    del dx, dwt, rx, rwt
+    torch.cuda.empty_cache()   # the batch sizes its groups from the free device memory
+    mocks = batch_mocks(args, dev, stream, tpcf, flush, rank) if args.mocks > 0 else None
+
     if rank != 0:
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -252,12 +265,89 @@ def run_ours(args):
                        "primaries_per_step": prim_per_step, "pairs_per_step": pairs_per_step,
                        "l2": "flushed between timed steps (256 MB write, outside the events)"},
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof, "e2e": e2e}
+    if mocks is not None:
+        line["mocks_per_hour"] = mocks
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def batch_mocks(args, dev, stream, tpcf, flush, rank=0):
+    """Mocks per hour for the covariance batch: one graph-captured batch run per
+    step (all mocks' pair stages in one persistent launch per group), plain FP32
+    coupling against the bf16x3 tensor-core coupling, plus one-catalogue calls
+    on a sample of the same mocks as the unbatched comparison."""
+    import numpy as np
+    import torch
+    from paper_2408_03036_gb300 import synth
+    n_mocks = args.mocks
+    sizes = synth.mock_sizes(n_mocks, MOCK_LO, MOCK_HI, SEED_MOCKS + 1000 * rank)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    xyz = torch.empty((int(off[-1]), 3), dtype=torch.int32, device=dev)
+    for k, n in enumerate(sizes):
+        x, _ = synth.lognormal_device(int(n), BOX, SEED_MOCKS + 1000 * rank + 1 + k, mesh=MOCK_MESH, device=dev)
+        xyz[off[k]:off[k + 1]] = x
+        del x
+    w = torch.ones(int(off[-1]), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    # tile shapes for this density from the autotuner (one primary per tile in a batch)
+    tuned = tpcf.autotune(mock_config("fp32", tile_primaries=1), xyz[:int(off[1])], w[:int(off[1])],
+                          stream=stream, device=dev)
+    out = {"mocks": n_mocks, "points": int(off[-1]), "sizes": [int(sizes.min()), int(sizes.max())],
+           "tuned": {"cell_div": tuned.cell_div, "chunk": tuned.chunk}}
+    zs = {}
+    for prec in ("fp32", "bf16x3"):
+        cfg = mock_config(prec, cell_div=tuned.cell_div, chunk=tuned.chunk, tile_primaries=1)
+        b = tpcf.Batch(cfg, off)
+        z = b.zeta_buffer(dev)
+        b.run_graph(xyz, w, z, stream=stream)          # eager run + capture (warm-up)
+        b.run_graph(xyz, w, z, stream=stream)          # first graph launch (warm-up)
+        torch.cuda.synchronize(dev)
+        tpcf.stream_status(stream)
+        ms = 0.0
+        for _ in range(args.batch_steps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            b.run_graph(xyz, w, z, stream=stream)
+            e.record(stream)
+            torch.cuda.synchronize(dev)
+            ms += s.elapsed_time(e)
+        tpcf.stream_status(stream)
+        groups, nc = b.info()
+        out[prec] = {"mocks_per_hour": n_mocks * args.batch_steps / (ms / 1000.0) * 3600.0,
+                     "s_per_batch": ms / 1000.0 / args.batch_steps, "groups": groups, "cells_per_axis": nc}
+        zs[prec] = z.cpu().numpy()
+        b.close()
+        del z
+    # mixed against plain: worst over mocks and multipoles of max|diff| / max|plain|
+    zf, zb = zs["fp32"], zs["bf16x3"]
+    den = np.abs(zf).max(axis=(2, 3))
+    num = np.abs(zb - zf).max(axis=(2, 3))
+    out["bf16x3_vs_fp32_max_rel_err"] = float((num / np.where(den > 0, den, 1.0)).max())
+    out["mixed_over_plain"] = out["bf16x3"]["mocks_per_hour"] / out["fp32"]["mocks_per_hour"]
+    # unbatched: one tpcf_estimate_3pcf per mock, a sample of the same mocks
+    ns = min(n_mocks, 32)
+    cfg = mock_config("fp32")
+    for k in range(2):
+        tpcf.estimate_3pcf(cfg, xyz[off[k]:off[k + 1]], w[off[k]:off[k + 1]], stream=stream, device=dev,
+                           want_all=False)
+    torch.cuda.synchronize(dev)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for k in range(ns):
+        tpcf.estimate_3pcf(cfg, xyz[off[k]:off[k + 1]], w[off[k]:off[k + 1]], stream=stream, device=dev,
+                           want_all=False)
+    e.record(stream)
+    torch.cuda.synchronize(dev)
+    t = s.elapsed_time(e) / 1000.0
+    pts = int(off[ns] - off[0])
+    out["sequential_fp32"] = {"mocks_per_hour": pts / t / (off[-1] / n_mocks) * 3600.0, "sample_mocks": ns,
+                              "note": "per-mock calls on the first mocks, scaled by the batch's mean mock size"}
+    return out
 
 
 def fp32_peak_tflops(dev):
@@ -328,6 +418,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "bf16x3", "tf32x3"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mocks", type=int, default=N_MOCKS, help="mocks in the covariance batch (0: skip)")
+    ap.add_argument("--batch-steps", type=int, default=1, help="timed graph launches of the batch")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
     if args.impl == "reference":

@@ -214,6 +214,58 @@ int tpcf_estimate_3pcf_host(const tpcf_config *cfg,
                             double *zeta, double *nnn, double *rrr,
                             int64_t *pair_counts, int64_t *triplet_counts, void *stream);
 
+/* ----------------------------------------------------------------- batches
+ * Many periodic catalogues of uneven sizes (mocks for a covariance matrix, the
+ * use Sec. 4.3 motivates), each estimated with analytic randoms.  The points of
+ * all mocks are concatenated: mock k is points [offsets[k], offsets[k+1]).  The
+ * pair stage of a whole group of mocks is one persistent launch whose tiles may
+ * come from any mock; all mocks fit one group unless the per-point buffers
+ * would take more than half of the free device memory. */
+typedef struct tpcf_batch_s *tpcf_batch;
+
+/* Plans a batch: host offsets[n_mocks + 1] (offsets[0] = 0, non-decreasing,
+ * total < 2^28), cfg->periodic = 1.  group_points > 0 caps the points of one
+ * group (0: the memory rule above); a single mock larger than the cap is an
+ * error.  Allocates every buffer and uploads every table now, so
+ * tpcf_batch_run only enqueues device work. */
+int tpcf_batch_create(const tpcf_config *cfg, const int64_t *offsets, int32_t n_mocks, int64_t group_points,
+                      tpcf_batch *out);
+
+/* Number of groups (persistent pair-stage launches per run) and cells per axis. */
+int tpcf_batch_info(tpcf_batch batch, int32_t *n_groups, int32_t *cells_per_axis);
+
+/* Runs the batch: dev xyz[total][3], dev w[total] (NULL: unit weights);
+ * writes dev zeta[n_mocks][n_mult][n_bins][n_bins] and, if not NULL, dev
+ * triplet_counts[n_mocks][n_bins][n_bins].  Makes no host synchronisation and no
+ * host-to-device copy, so it can be captured into a CUDA graph (its scratch
+ * comes from stream-ordered allocations, which capture as graph memory nodes). */
+int tpcf_batch_run(tpcf_batch batch, const uint32_t *xyz, const float *w, double *zeta, int64_t *triplet_counts,
+                   void *stream);
+
+/* Same work as tpcf_batch_run, as one CUDA graph launch.  The first call with a
+ * given set of buffers runs the batch eagerly on `stream` and captures the same
+ * work (on a private stream, thread-local capture mode) into a graph kept in the
+ * batch; later calls with the same four pointers launch that graph on `stream`.
+ * New pointers replace the graph.  Calls on one batch must not overlap. */
+int tpcf_batch_run_graph(tpcf_batch batch, const uint32_t *xyz, const float *w, double *zeta,
+                         int64_t *triplet_counts, void *stream);
+
+/* Releases a batch (synchronises the device first). NULL is accepted. */
+int tpcf_batch_destroy(tpcf_batch batch);
+
+/* create + run + tpcf_stream_status + destroy. */
+int tpcf_estimate_3pcf_batched(const tpcf_config *cfg, const uint32_t *xyz, const float *w, const int64_t *offsets,
+                               int32_t n_mocks, double *zeta, int64_t *triplet_counts, void *stream);
+
+/* Chooses cell_div (2..5), tile_primaries (1, 2, 4) and chunk (1536, 2048,
+ * 3072) for a catalogue like this one by timing the pair stage on a strided
+ * sample of at most 6144 of its primaries (dev xyz[n][3], dev w[n] or NULL) for
+ * every valid combination; *tuned = *cfg with the fastest choice.  A nonzero
+ * cfg->tile_primaries is kept fixed (batches run one primary per tile).
+ * Synchronises the stream. */
+int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, int64_t n, void *stream,
+                  tpcf_config *tuned);
+
 /* Synchronises the stream and reports any latched device-side error
  * (TPCF_ERR_DATA, TPCF_ERR_TIMEOUT) or CUDA error; clears the latch. */
 int tpcf_stream_status(void *stream);

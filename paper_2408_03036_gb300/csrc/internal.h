@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/tpcf.h is).
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -58,7 +59,22 @@ struct PairParams {
     unsigned long long *pair_counts;
     int *work;                // tile counter (zeroed before launch)
     int *err;                 // device error latch
+    // Batches of catalogues (null prim_mock: one catalogue).  Primary i belongs to
+    // mock prim_mock[i]; its cells start at mock * ncell_mock in cell_start, its
+    // W is mono_w_mock[mock], and its diag / wsp / pair_counts go to that mock's
+    // slice of the outputs.  Requires one primary per tile (P = 1).
+    const int *prim_mock;
+    int64_t ncell_mock;
+    const double *mono_w_mock;
 };
+
+// Bit of the current device in a per-device "done" mask (one-time attribute set-up).
+inline unsigned long long device_bit()
+{
+    int d = 0;
+    cudaGetDevice(&d);
+    return 1ull << (d & 63);
+}
 
 // Counts kernel launches made by the library (reported by tpcf_kernel_launches).
 void note_launch(int n = 1);
@@ -68,6 +84,11 @@ cudaError_t build_grid_dev(const uint32_t *xyz, const float *w, int64_t n,
                            const uint32_t *xyz2, const float *w2, int64_t n2, const double *wsums,
                            int nc, GridDev &g, int *err, cudaStream_t st);
 void free_grid_dev(GridDev &g, cudaStream_t st);
+// One grid over many catalogues: points [offsets[k], offsets[k+1]) form mock k,
+// whose cells are k * nc^3 ... (k+1) * nc^3 - 1; rec_mock[i] = mock of record i.
+cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t n, const int64_t *d_offsets,
+                                   int n_mocks, int nc, GridDev &g, int32_t *rec_mock, int *err, cudaStream_t st);
+cudaError_t weight_sums_mocks(const float *w, const int64_t *d_offsets, int n_mocks, double *out, cudaStream_t st);
 
 cudaError_t pack_records(const uint32_t *xyz, const float *w, int64_t n, int4 *out, int *err,
                          cudaStream_t st);

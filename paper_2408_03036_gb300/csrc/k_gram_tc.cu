@@ -424,18 +424,20 @@ cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, 
     p.n_slices = slices;
     p.err = err;
     const int64_t per = partial_offset(nb, lmax, lmax + 1);
-    cudaError_t e = cudaMallocAsync((void **)&p.partial, (size_t)slices * per * sizeof(double), st);
-    if (e != cudaSuccess) return e;
     // at least 116 KB so that one CTA owns an SM: tensor-memory allocations never wait
     size_t smem = gram_tc_smem(nb, lmax);
     if (smem < 116 * 1024) smem = 116 * 1024;
-    static bool attr[2] = {false, false};
-    if (!attr[tf32]) {
+    static std::atomic<unsigned long long> attr_done[2];   // devices whose attribute is set
+    const unsigned long long bit = device_bit();
+    cudaError_t e;
+    if (!(attr_done[tf32].load(std::memory_order_acquire) & bit)) {
         e = cudaFuncSetAttribute(tf32 ? k_gram_tc<true> : k_gram_tc<false>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
-        attr[tf32] = true;
+        attr_done[tf32].fetch_or(bit, std::memory_order_acq_rel);
     }
+    e = cudaMallocAsync((void **)&p.partial, (size_t)slices * per * sizeof(double), st);
+    if (e != cudaSuccess) return e;
     const dim3 grid(lmax + 1, slices);
     if (tf32) k_gram_tc<true><<<grid, kThreads, smem, st>>>(p);
     else k_gram_tc<false><<<grid, kThreads, smem, st>>>(p);

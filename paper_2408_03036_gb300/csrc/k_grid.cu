@@ -180,6 +180,58 @@ __global__ void k_wsum(const float *__restrict__ w1, int64_t n1, const float *__
     }
 }
 
+// Mock of every point from the offsets (binary search), cell index offset by
+// mock * ncell, histogram; weights copied as given.
+__global__ void k_cell_hist_batched(const uint32_t *__restrict__ xyz, const float *__restrict__ w, int64_t n,
+                                    const int64_t *__restrict__ offsets, int n_mocks, int nc, int64_t ncell,
+                                    int32_t *__restrict__ cid, int32_t *__restrict__ mock_of,
+                                    int32_t *__restrict__ hist, int4 *__restrict__ tmp, int *err)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_mocks - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (offsets[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        const uint32_t x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        const float wt = w ? w[i] : 1.0f;
+        if (!(wt == wt) || isinf(wt)) atomicCAS(err, 0, DEV_ERR_DATA);
+        const int64_t c = (int64_t)lo * ncell + (cell1(z, nc) * nc + cell1(y, nc)) * nc + cell1(x, nc);
+        cid[i] = (int32_t)c;
+        mock_of[i] = lo;
+        tmp[i] = make_int4((int)x, (int)y, (int)z, __float_as_int(wt));
+        atomicAdd(&hist[c], 1);
+    }
+}
+
+// Mock id of every record in grid order.
+__global__ void k_mock_of_rec(const int64_t *__restrict__ order, const int32_t *__restrict__ mock_of, int64_t n,
+                              int32_t *__restrict__ out)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = mock_of[order[i]];
+}
+
+// W per mock: one block per mock.
+__global__ void k_wsum_mocks(const float *__restrict__ w, const int64_t *__restrict__ offsets, double *out)
+{
+    __shared__ double red[32];
+    const int mk = blockIdx.x;
+    double s = 0.0;
+    for (int64_t i = offsets[mk] + threadIdx.x; i < offsets[mk + 1]; i += blockDim.x) s += w ? (double)w[i] : 1.0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (warp == 0) {
+        s = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) out[mk] = s;
+    }
+}
+
 int grid_blocks(int64_t n, int block)
 {
     int64_t b = (n + block - 1) / block;
@@ -232,6 +284,62 @@ cudaError_t build_grid_dev(const uint32_t *xyz, const float *w, int64_t n,
     cudaFreeAsync(hist, st);
     cudaFreeAsync(cursor, st);
     return e;
+}
+
+cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t n, const int64_t *d_offsets,
+                                   int n_mocks, int nc, GridDev &g, int32_t *rec_mock, int *err, cudaStream_t st)
+{
+    const int64_t ncell1 = (int64_t)nc * nc * nc;
+    const int64_t ncell = ncell1 * n_mocks;
+    g.n = n;
+    g.nc = nc;
+    g.ncell = ncell;
+    cudaError_t e;
+    int32_t *cid = nullptr, *hist = nullptr, *cursor = nullptr, *mock_of = nullptr;
+    int4 *tmp = nullptr;
+    int64_t *scratch = nullptr;
+    const int64_t alloc_n = n > 0 ? n : 1;
+    if ((e = cudaMallocAsync((void **)&g.rec, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&g.order, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&g.cell_start, (ncell + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&cid, alloc_n * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&mock_of, alloc_n * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&tmp, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&scratch, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&hist, ncell * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMallocAsync((void **)&cursor, ncell * sizeof(int32_t), st)) != cudaSuccess) return e;
+    cudaMemsetAsync(hist, 0, ncell * sizeof(int32_t), st);
+    const int B = 256;
+    if (n > 0) {
+        k_cell_hist_batched<<<grid_blocks(n, B), B, 0, st>>>(xyz, w, n, d_offsets, n_mocks, nc, ncell1, cid, mock_of,
+                                                            hist, tmp, err);
+        note_launch();
+    }
+    k_scan_cells<<<1, 1024, 0, st>>>(hist, ncell, g.cell_start, cursor);
+    note_launch();
+    if (n > 0) {
+        k_scatter_idx<<<grid_blocks(n, B), B, 0, st>>>(cid, n, cursor, g.order);
+        k_sort_cells<<<grid_blocks(ncell * 32, B), B, 0, st>>>(g.cell_start, ncell, g.order, tmp, g.rec, scratch);
+        k_mock_of_rec<<<grid_blocks(n, B), B, 0, st>>>(g.order, mock_of, n, rec_mock);
+        note_launch(3);
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(cid, st);
+    cudaFreeAsync(mock_of, st);
+    cudaFreeAsync(tmp, st);
+    cudaFreeAsync(scratch, st);
+    cudaFreeAsync(hist, st);
+    cudaFreeAsync(cursor, st);
+    return e;
+}
+
+cudaError_t weight_sums_mocks(const float *w, const int64_t *d_offsets, int n_mocks, double *out, cudaStream_t st)
+{
+    if (n_mocks > 0) {
+        k_wsum_mocks<<<n_mocks, 256, 0, st>>>(w, d_offsets, out);
+        note_launch();
+    }
+    return cudaGetLastError();
 }
 
 void free_grid_dev(GridDev &g, cudaStream_t st)

@@ -318,6 +318,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
     }
     double mono_w = p.use_mono ? (p.mono_w_dev ? *p.mono_w_dev : p.mono_w) : 0.0;
     int tiles_since_flush = 0;
+    int cta_mock = -1;            // catalogue whose sums the CTA is accumulating
     __syncthreads();
     const int accw = nk * NACCP;   // floats per warp copy
 
@@ -527,6 +528,34 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
         __syncthreads();
     };
 
+    // adds the CTA's FP64 diagonal / self / pair-count sums to catalogue `mk`'s
+    // slice of the outputs and clears them (all threads)
+    auto flush_cta = [&](int mk) {
+        __syncthreads();
+        if (!COUNTS) {
+            for (int i = tid; i < nb * NDIAG; i += T) {
+                const double v = d64[i] + (double)d32[i];
+                const int b = i / NDIAG, jd = i % NDIAG;
+                if (p.diag && v != 0.0) atomicAdd(p.diag + ((size_t)mk * NDIAG + jd) * nb + b, v);
+                d64[i] = 0.0;
+                d32[i] = 0.f;
+            }
+            for (int i = tid; i < nb * NSP; i += T) {
+                const double v = w64[i] + (double)w32[i];
+                const int b = i / NSP, j = i % NSP;
+                if (p.wsp && v != 0.0) atomicAdd(p.wsp + ((size_t)mk * NSP + j) * nb + b, v);
+                w64[i] = 0.0;
+                w32[i] = 0.f;
+            }
+        }
+        for (int b = tid; b < nb; b += T) {
+            if (p.pair_counts && spairs[b]) atomicAdd(p.pair_counts + (size_t)mk * nb + b, spairs[b]);
+            spairs[b] = 0ull;
+        }
+        tiles_since_flush = 0;
+        __syncthreads();
+    };
+
     for (;;) {
         if (tid == 0) {
             s_tile = atomicAdd(p.work, 1);
@@ -536,6 +565,13 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
         const long long t0 = (long long)s_tile * P;
         if (t0 >= p.n_prim) break;
         const int np = (int)min((long long)P, p.n_prim - t0);
+        const int mock = p.prim_mock ? p.prim_mock[t0] : 0;
+        if (mock != cta_mock) {
+            if (cta_mock >= 0) flush_cta(cta_mock);
+            cta_mock = mock;
+            if (p.prim_mock && p.use_mono) mono_w = p.mono_w_mock[mock];
+        }
+        const long long mock_cells = (long long)mock * p.ncell_mock;
 
         // primaries of the tile
         if (tid < np) {
@@ -587,7 +623,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
                     x1 = min(x1, nc - 1);
                 }
                 if (x1 >= x0) {
-                    const long long base = ((long long)wz * nc + wy) * nc;
+                    const long long base = mock_cells + ((long long)wz * nc + wy) * nc;
                     int sa = x0, sb = x1, ta = 1, tb = 0;   // second run empty
                     if (p.periodic) {
                         if (x0 < 0) { sa = x0 + nc; sb = nc - 1; ta = 0; tb = x1; }
@@ -772,22 +808,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
     }
 
     // ----- CTA totals to global
-    __syncthreads();
-    if (!COUNTS) {
-        for (int i = tid; i < nb * NDIAG; i += T) {
-            const double v = d64[i] + (double)d32[i];
-            const int b = i / NDIAG, jd = i % NDIAG;
-            if (p.diag) atomicAdd(p.diag + (size_t)jd * nb + b, v);
-        }
-        for (int i = tid; i < nb * NSP; i += T) {
-            const double v = w64[i] + (double)w32[i];
-            const int b = i / NSP, j = i % NSP;
-            if (p.wsp) atomicAdd(p.wsp + (size_t)j * nb + b, v);
-        }
-    }
-    if (p.pair_counts)
-        for (int b = tid; b < nb; b += T)
-            if (spairs[b]) atomicAdd(p.pair_counts + b, spairs[b]);
+    if (cta_mock >= 0) flush_cta(cta_mock);
 }
 
 }  // namespace tpcf

@@ -8,12 +8,13 @@ template <int LMAX, bool COUNTS>
 static cudaError_t launch_one(const PairParams &p, const HarmTables &h, int grid, int block,
                               size_t smem, cudaStream_t st)
 {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
+    const unsigned long long bit = device_bit();
+    if (!(attr_done.load(std::memory_order_acquire) & bit)) {
         cudaError_t e = cudaFuncSetAttribute(k_pairs<LMAX, COUNTS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        attr_done.fetch_or(bit, std::memory_order_acq_rel);
     }
     k_pairs<LMAX, COUNTS><<<grid, block, smem, st>>>(p, h);
     note_launch();

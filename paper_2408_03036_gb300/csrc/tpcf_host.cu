@@ -46,6 +46,34 @@ struct tpcf_grid_s {
     int device;
 };
 
+// A planned batch of periodic catalogues (analytic randoms): device tables and
+// every buffer are made at creation, so a run only enqueues kernels, copies and
+// stream-ordered allocations (it can be captured in a CUDA graph).
+struct tpcf_batch_s {
+    tpcf_config cfg;
+    int n_mocks = 0;
+    std::vector<int64_t> off;            // host offsets [n_mocks + 1]
+    std::vector<int> group;              // first mock of every group, then n_mocks
+    int device = 0;
+    int nc = 0;
+    int64_t max_group_points = 0;
+    int n_mult = 0;
+    // device tables and buffers
+    int64_t *d_off = nullptr;            // [n_mocks + 1]
+    int64_t *d_goff = nullptr;           // rebased offsets per group (concatenated)
+    double *d_gaunt = nullptr, *d_coef = nullptr, *d_mono = nullptr;
+    int *d_mults = nullptr, *d_tiles = nullptr;
+    int32_t *rec_mock = nullptr;
+    float *alm = nullptr, *wprim = nullptr;
+    int32_t *counts = nullptr;
+    double *wsum = nullptr, *diag = nullptr, *wsp = nullptr, *G = nullptr, *nnn = nullptr, *rrr = nullptr;
+    unsigned long long *pairs = nullptr, *T = nullptr;
+    // graph of one run, captured for the buffers in gp
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *gp[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
@@ -363,9 +391,15 @@ cudaError_t pair_launch(int lmax, bool counts, const PairParams &p, const HarmTa
 }
 
 // Runs the pair stage over `n_prim` primary records against grid g.
+struct BatchInfo {
+    const int *prim_mock;       // mock of every primary
+    int64_t ncell_mock;         // cells per mock
+    const double *mono_w_mock;  // W per mock
+};
+
 int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t n_prim, bool counts_only,
               double mono_w, const double *mono_w_dev, bool use_mono, float *alm, int32_t *counts, double *diag,
-              double *wsp, unsigned long long *pair_counts, cudaStream_t st)
+              double *wsp, unsigned long long *pair_counts, cudaStream_t st, const BatchInfo *bi = nullptr)
 {
     DevState *ds;
     int rc = dev_state(&ds);
@@ -426,6 +460,13 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
         smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
     }
     if (smem > 227 * 1024) return fail(TPCF_ERR_UNSUPPORTED, "pair stage needs %zu bytes of shared memory", smem);
+    if (bi) {
+        pl.P = 1;   // one primary per tile: a tile never straddles two catalogues
+        smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
+        p.prim_mock = bi->prim_mock;
+        p.ncell_mock = bi->ncell_mock;
+        p.mono_w_mock = bi->mono_w_mock;
+    }
     p.P = pl.P;
     p.chunk = pl.chunk;
     int *work = nullptr;
@@ -480,6 +521,22 @@ int couple(const tpcf_config *c, const float *alm, const float *w, const int32_t
     cudaFreeAsync(G, st);
     cudaFreeAsync(gaunt, st);
     return TPCF_OK;
+}
+
+void projection_tables(const tpcf_config *c, std::vector<double> &coef, std::vector<int> &ml)
+{
+    multipole_list(c, ml);
+    const int nm = (int)ml.size() / 3, L1 = c->l_max + 1;
+    coef.assign((size_t)nm * L1, 0.0);
+    for (int k = 0; k < nm; ++k) {
+        const int l1 = ml[3 * k], l2 = ml[3 * k + 1], L = ml[3 * k + 2];
+        const double H = w3j(l1, l2, L, 0, 0, 0);
+        const double conv = (c->convention == TPCF_CONV_S_COEFF) ? std::sqrt((2.0 * l1 + 1.0) * (2.0 * l2 + 1.0)) : 1.0;
+        for (int m = 0; m <= std::min(l1, l2); ++m) {
+            const double t = w3j(l1, l2, L, m, -m, 0) * ((m % 2) ? -1.0 : 1.0);
+            coef[(size_t)k * L1 + m] = conv * (2.0 * L + 1.0) * H * (m == 0 ? t : 2.0 * t);
+        }
+    }
 }
 
 int project(const tpcf_config *c, const double *nnn, const double *rrr, double *zeta, cudaStream_t st)
@@ -839,6 +896,318 @@ int tpcf_estimate_3pcf_host(const tpcf_config *cfg, const uint32_t *d_xyz, const
         if (p) cudaFreeAsync(p, st);
     CK(cudaStreamSynchronize(st));
     return tpcf_stream_status(stream);
+}
+
+int tpcf_batch_create(const tpcf_config *cfg, const int64_t *offsets, int32_t n_mocks, int64_t group_points,
+                      tpcf_batch *out)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!out || !offsets || n_mocks < 1) return fail(TPCF_ERR_ARG, "need offsets and at least one mock");
+    if (!cfg->periodic) return fail(TPCF_ERR_UNSUPPORTED, "batches use periodic boxes with analytic randoms");
+    for (int k = 0; k < n_mocks; ++k)
+        if (offsets[k + 1] < offsets[k] || offsets[0] != 0) return fail(TPCF_ERR_ARG, "offsets must start at 0 and not decrease");
+    const int64_t n_total = offsets[n_mocks];
+    if (n_total >= kMaxPoints) return fail(TPCF_ERR_ARG, "batch too large (total points < 2^28)");
+    if (group_points < 0) return fail(TPCF_ERR_ARG, "group_points < 0");
+    DevState *ds;
+    if ((rc = dev_state(&ds))) return rc;
+    tpcf_batch b = new tpcf_batch_s();
+    b->cfg = *cfg;
+    b->n_mocks = n_mocks;
+    b->off.assign(offsets, offsets + n_mocks + 1);
+    cudaGetDevice(&b->device);
+    b->nc = choose_nc(cfg, std::max<int64_t>(1, n_total / n_mocks));
+    const int nb = cfg->n_bins, L = cfg->l_max, L1 = L + 1;
+    const int nlm = L1 * L1, ndiag = L1 * (L1 + 1) / 2;
+    const int64_t ncell1 = (int64_t)b->nc * b->nc * b->nc;
+    // groups of whole mocks: the per-point buffers of one group use at most half the free memory
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const double per_point = (double)nb * nlm * 4 + nb * 4 + 4 + 4 + 64 * 2;
+    int64_t cap = (int64_t)(0.5 * (double)free_b / per_point);
+    if (group_points > 0) cap = std::min(cap, group_points);
+    cap = std::max<int64_t>(cap, 1);
+    b->group.push_back(0);
+    int64_t gstart = 0;
+    for (int k = 0; k < n_mocks; ++k) {
+        const int64_t nk = offsets[k + 1] - offsets[k];
+        if (nk > cap) {
+            delete b;
+            if (group_points > 0 && nk > group_points) return fail(TPCF_ERR_ARG, "mock %d exceeds group_points", k);
+            return fail(TPCF_ERR_OOM, "mock %d does not fit in device memory", k);
+        }
+        if (offsets[k + 1] - gstart > cap || (int64_t)(k - b->group.back() + 1) * ncell1 >= ((int64_t)1 << 31)) {
+            b->group.push_back(k);
+            gstart = offsets[k];
+        }
+    }
+    b->group.push_back(n_mocks);
+    for (size_t g = 0; g + 1 < b->group.size(); ++g)
+        b->max_group_points = std::max(b->max_group_points, offsets[b->group[g + 1]] - offsets[b->group[g]]);
+    std::vector<int64_t> goff;
+    for (size_t g = 0; g + 1 < b->group.size(); ++g)
+        for (int k = b->group[g]; k <= b->group[g + 1]; ++k) goff.push_back(offsets[k] - offsets[b->group[g]]);
+    std::vector<double> coef;
+    std::vector<int> ml;
+    projection_tables(cfg, coef, ml);
+    b->n_mult = (int)ml.size() / 3;
+    std::vector<double> gaunt((size_t)L1 * L1 * L1 * L1);
+    self_term_table(L, gaunt.data());
+    double r[TPCF_MAX_BINS + 1];
+    unsigned long long E[TPCF_MAX_BINS + 1];
+    edge_tables(cfg, E, r);
+    std::vector<double> mono(nb);
+    for (int q = 0; q < nb; ++q)
+        mono[q] = 4.0 * kPi / 3.0 * (r[q + 1] * r[q + 1] * r[q + 1] - r[q] * r[q] * r[q]) / (cfg->box * cfg->box * cfg->box)
+                  / std::sqrt(4.0 * kPi);
+    const int64_t P = b->max_group_points;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](void **ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes ? bytes : 8);
+    };
+    A((void **)&b->d_off, (n_mocks + 1) * sizeof(int64_t));
+    A((void **)&b->d_goff, goff.size() * sizeof(int64_t));
+    A((void **)&b->d_gaunt, gaunt.size() * sizeof(double));
+    A((void **)&b->d_coef, coef.size() * sizeof(double));
+    A((void **)&b->d_mults, ml.size() * sizeof(int));
+    A((void **)&b->d_mono, nb * sizeof(double));
+    A((void **)&b->d_tiles, 3 * (size_t)gram_tile_count(nb, L) * sizeof(int));
+    A((void **)&b->rec_mock, P * sizeof(int32_t));
+    A((void **)&b->alm, (size_t)P * nb * nlm * sizeof(float));
+    A((void **)&b->wprim, P * sizeof(float));
+    A((void **)&b->counts, (size_t)P * nb * sizeof(int32_t));
+    A((void **)&b->wsum, n_mocks * sizeof(double));
+    A((void **)&b->diag, (size_t)n_mocks * ndiag * nb * sizeof(double));
+    A((void **)&b->wsp, (size_t)n_mocks * L1 * nb * sizeof(double));
+    A((void **)&b->G, gram_offset(nb, L, L + 1) * sizeof(double));
+    A((void **)&b->nnn, (size_t)L1 * L1 * L1 * nb * nb * sizeof(double));
+    A((void **)&b->rrr, (size_t)nb * nb * sizeof(double));
+    A((void **)&b->pairs, (size_t)n_mocks * nb * sizeof(unsigned long long));
+    A((void **)&b->T, (size_t)n_mocks * nb * nb * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_off, offsets, (n_mocks + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_goff, goff.data(), goff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_gaunt, gaunt.data(), gaunt.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_mults, ml.data(), ml.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_mono, mono.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        tpcf_batch_destroy(b);
+        return cuda_fail(e, "batch buffers");
+    }
+    *out = b;
+    return TPCF_OK;
+}
+
+int tpcf_batch_destroy(tpcf_batch b)
+{
+    if (!b) return TPCF_OK;
+    cudaDeviceSynchronize();
+    for (void *ptr : {(void *)b->d_off, (void *)b->d_goff, (void *)b->d_gaunt, (void *)b->d_coef, (void *)b->d_mults,
+                      (void *)b->d_mono, (void *)b->d_tiles, (void *)b->rec_mock, (void *)b->alm, (void *)b->wprim,
+                      (void *)b->counts, (void *)b->wsum, (void *)b->diag, (void *)b->wsp, (void *)b->G,
+                      (void *)b->nnn, (void *)b->rrr, (void *)b->pairs, (void *)b->T})
+        if (ptr) cudaFree(ptr);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+    return TPCF_OK;
+}
+
+int tpcf_batch_info(tpcf_batch b, int32_t *n_groups, int32_t *cells_per_axis)
+{
+    if (!b) return fail(TPCF_ERR_ARG, "batch is NULL");
+    if (n_groups) *n_groups = (int32_t)b->group.size() - 1;
+    if (cells_per_axis) *cells_per_axis = b->nc;
+    return TPCF_OK;
+}
+
+int tpcf_batch_run(tpcf_batch b, const uint32_t *xyz, const float *w, double *zeta, int64_t *triplet_counts,
+                   void *stream)
+{
+    if (!b) return fail(TPCF_ERR_ARG, "batch is NULL");
+    if (!xyz || !zeta) return fail(TPCF_ERR_ARG, "xyz and zeta are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevState *ds;
+    int rc = dev_state(&ds);
+    if (rc) return rc;
+    const tpcf_config *c = &b->cfg;
+    const int nb = c->n_bins, L = c->l_max, L1 = L + 1;
+    const int nlm = L1 * L1, ndiag = L1 * (L1 + 1) / 2;
+    const int64_t ncell1 = (int64_t)b->nc * b->nc * b->nc;
+    const int64_t gsz = gram_offset(nb, L, L + 1);
+    CK(cudaMemsetAsync(b->diag, 0, (size_t)b->n_mocks * ndiag * nb * sizeof(double), st));
+    CK(cudaMemsetAsync(b->wsp, 0, (size_t)b->n_mocks * L1 * nb * sizeof(double), st));
+    CK(cudaMemsetAsync(b->pairs, 0, (size_t)b->n_mocks * nb * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(b->T, 0, (size_t)b->n_mocks * nb * nb * sizeof(unsigned long long), st));
+    size_t goff_at = 0;
+    for (size_t g = 0; g + 1 < b->group.size(); ++g) {
+        const int m0 = b->group[g], m1 = b->group[g + 1], nm = m1 - m0;
+        const int64_t p0 = b->off[m0], np = b->off[m1] - p0;
+        const int64_t *d_goff = b->d_goff + goff_at;
+        goff_at += (size_t)nm + 1;
+        const float *wg = w ? w + p0 : nullptr;
+        CK(weight_sums_mocks(wg, d_goff, nm, b->wsum + m0, st));
+        GridDev grid;
+        CK(build_grid_batched_dev(xyz + 3 * p0, wg, np, d_goff, nm, b->nc, grid, b->rec_mock, ds->err, st));
+        BatchInfo bi{b->rec_mock, ncell1, b->wsum + m0};
+        rc = run_pairs(c, grid, grid.rec, np, false, 0.0, nullptr, true, b->alm, b->counts,
+                       b->diag + (size_t)m0 * ndiag * nb, b->wsp + (size_t)m0 * L1 * nb, b->pairs + (size_t)m0 * nb,
+                       st, &bi);
+        if (rc) return rc;
+        if (np > 0)
+            CK(cudaMemcpy2DAsync(b->wprim, 4, (const char *)grid.rec + 12, 16, 4, np, cudaMemcpyDeviceToDevice, st));
+        for (int k = m0; k < m1; ++k) {
+            const int64_t r0 = b->off[k] - p0, K = b->off[k + 1] - b->off[k];
+            const float *alm_k = b->alm + (size_t)r0 * nb * nlm;
+            if (c->precision == TPCF_PREC_FP32) {
+                CK(cudaMemsetAsync(b->G, 0, gsz * sizeof(double), st));
+                CK(couple_gram_fp32_tiles(alm_k, b->wprim + r0, K, nb, L, b->d_tiles, b->G, st));
+            } else {
+                cudaError_t e = couple_gram_tc(alm_k, b->wprim + r0, K, nb, L, c->precision == TPCF_PREC_TF32X3, b->G,
+                                               ds->err, ds->sms, st);
+                if (e == cudaErrorInvalidValue)
+                    return fail(TPCF_ERR_UNSUPPORTED, "tensor-core Gram: an m block exceeds two 128-row tiles");
+                CK(e);
+            }
+            CK(assemble_nnn(b->G, b->diag + (size_t)k * ndiag * nb, b->wsp + (size_t)k * L1 * nb, nb, L,
+                            c->remove_self, b->d_gaunt, b->nnn, st));
+            CK(tpcf::triplet_counts(b->counts + (size_t)r0 * nb, K, nb, b->T + (size_t)k * nb * nb, st));
+            CK(rrr_analytic(b->wsum + k, b->d_mono, nb, b->rrr, st));
+            CK(project_zeta(b->nnn, b->rrr, nb, L, b->n_mult, b->d_coef, b->d_mults,
+                            zeta + (size_t)k * b->n_mult * nb * nb, st));
+        }
+        free_grid_dev(grid, st);
+    }
+    if (triplet_counts) CK(i64_from_u64(b->T, triplet_counts, b->n_mocks * nb * nb, st));
+    return TPCF_OK;
+}
+
+int tpcf_batch_run_graph(tpcf_batch b, const uint32_t *xyz, const float *w, double *zeta, int64_t *triplet_counts,
+                         void *stream)
+{
+    if (!b) return fail(TPCF_ERR_ARG, "batch is NULL");
+    const void *key[4] = {xyz, w, zeta, triplet_counts};
+    if (b->exec && std::memcmp(key, b->gp, sizeof(key)) == 0) {
+        CK(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+        return TPCF_OK;
+    }
+    // first use with these buffers: run eagerly (this also finishes every one-time
+    // set-up), then record the same work on a private stream
+    int rc = tpcf_batch_run(b, xyz, w, zeta, triplet_counts, stream);
+    if (rc) return rc;
+    if (b->exec) {
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
+    if (!b->cap) CK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    rc = tpcf_batch_run(b, xyz, w, zeta, triplet_counts, b->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &graph);
+    if (rc) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "batch capture");
+    const cudaError_t e2 = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) {
+        b->exec = nullptr;
+        return cuda_fail(e2, "batch graph instantiation");
+    }
+    std::memcpy(b->gp, key, sizeof(key));
+    return TPCF_OK;
+}
+
+int tpcf_estimate_3pcf_batched(const tpcf_config *cfg, const uint32_t *xyz, const float *w, const int64_t *offsets,
+                               int32_t n_mocks, double *zeta, int64_t *triplet_counts, void *stream)
+{
+    tpcf_batch b = nullptr;
+    int rc = tpcf_batch_create(cfg, offsets, n_mocks, 0, &b);
+    if (rc) return rc;
+    rc = tpcf_batch_run(b, xyz, w, zeta, triplet_counts, stream);
+    if (!rc) rc = tpcf_stream_status(stream);
+    tpcf_batch_destroy(b);
+    return rc;
+}
+
+int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, int64_t n, void *stream,
+                  tpcf_config *tuned)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!tuned || !xyz || n < 1 || n >= kMaxPoints) return fail(TPCF_ERR_ARG, "autotune needs a catalogue and an output");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevState *ds;
+    if ((rc = dev_state(&ds))) return rc;
+    *tuned = *cfg;
+    const int nb = cfg->n_bins, L1 = cfg->l_max + 1;
+    const int64_t ns = std::min<int64_t>(n, 6144);       // sampled primaries per trial
+    const int64_t stride = std::max<int64_t>(1, n / ns);
+    float *alm = nullptr;
+    int32_t *cnt = nullptr;
+    double *diag = nullptr, *wsp = nullptr;
+    unsigned long long *pc = nullptr;
+    int4 *prim = nullptr;
+    CK(cudaMalloc((void **)&alm, (size_t)ns * nb * L1 * L1 * sizeof(float)));
+    CK(cudaMalloc((void **)&cnt, (size_t)ns * nb * sizeof(int32_t)));
+    CK(cudaMalloc((void **)&diag, (size_t)L1 * (L1 + 1) / 2 * nb * sizeof(double)));
+    CK(cudaMalloc((void **)&wsp, (size_t)L1 * nb * sizeof(double)));
+    CK(cudaMalloc((void **)&pc, nb * sizeof(unsigned long long)));
+    CK(cudaMalloc((void **)&prim, ns * sizeof(int4)));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    const int divs[] = {2, 3, 4, 5};
+    const int tiles_all[] = {1, 2, 4};
+    const int tiles_fixed[] = {cfg->tile_primaries};
+    const bool fixed_tile = cfg->tile_primaries > 0;   // a batch runs one primary per tile
+    const int chunks[] = {1536, 2048, 3072};
+    for (int dv : divs) {
+        tpcf_config t = *cfg;
+        t.cell_div = dv;
+        const Plan pl = make_plan(&t, n, n);
+        if (pl.s != dv) continue;   // the box cannot hold this many cells per r_max
+        GridDev g;
+        CK(build_grid_dev(xyz, w, n, nullptr, nullptr, 0, nullptr, pl.nc, g, ds->err, st));
+        CK(cudaMemcpy2DAsync(prim, 16, g.rec, 16 * stride, 16, ns, cudaMemcpyDeviceToDevice, st));
+        for (int ti = 0; ti < (fixed_tile ? 1 : 3); ++ti) {
+            const int tp = fixed_tile ? tiles_fixed[0] : tiles_all[ti];
+            if (tp * nb > 128) continue;
+            for (int ch : chunks) {
+                t.tile_primaries = tp;
+                t.chunk = ch;
+                float ms = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaEventRecord(e0, st);
+                    rc = run_pairs(&t, g, prim, ns, false, -1.0, nullptr, false, alm, cnt, diag, wsp, pc, st);
+                    cudaEventRecord(e1, st);
+                    if (rc) break;
+                    cudaEventSynchronize(e1);
+                    float x = 0.f;
+                    cudaEventElapsedTime(&x, e0, e1);
+                    if (rep > 0) ms = std::min(ms, x);
+                }
+                if (rc) break;
+                if (ms < best) {
+                    best = ms;
+                    tuned->cell_div = dv;
+                    tuned->tile_primaries = tp;
+                    tuned->chunk = ch;
+                }
+            }
+            if (rc) break;
+        }
+        free_grid_dev(g, st);
+        if (rc) break;
+    }
+    cudaStreamSynchronize(st);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (void *ptr : {(void *)alm, (void *)cnt, (void *)diag, (void *)wsp, (void *)pc, (void *)prim}) cudaFree(ptr);
+    return rc;
 }
 
 int tpcf_stream_status(void *stream)

@@ -26,7 +26,9 @@ CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
 EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
            "tpcf_bin_edges", "tpcf_build_grid", "tpcf_grid_destroy", "tpcf_grid_info", "tpcf_grid_points",
            "tpcf_accumulate_alm", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
-           "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static"]
+           "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
+           "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
+           "tpcf_estimate_3pcf_batched", "tpcf_autotune"]
 
 
 class TpcfError(RuntimeError):
@@ -100,6 +102,13 @@ def lib():
             "tpcf_estimate_3pcf_host": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_stream_status": ([P], ctypes.c_int),
             "tpcf_couple_multipoles_static": ([P, P, P, I64, CFG, P, P, P, P, P], ctypes.c_int),
+            "tpcf_batch_create": ([CFG, P, ctypes.c_int32, I64, P], ctypes.c_int),
+            "tpcf_batch_info": ([P, P, P], ctypes.c_int),
+            "tpcf_batch_run": ([P, P, P, P, P, P], ctypes.c_int),
+            "tpcf_batch_run_graph": ([P, P, P, P, P, P], ctypes.c_int),
+            "tpcf_batch_destroy": ([P], ctypes.c_int),
+            "tpcf_estimate_3pcf_batched": ([CFG, P, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
+            "tpcf_autotune": ([CFG, P, P, I64, P, CFG], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -311,6 +320,82 @@ def project(cfg: Config, nnn, rrr, stream=None):
     c = cfg.c()
     _check(lib().tpcf_project(ctypes.byref(c), _ptr(nnn), _ptr(rrr), _ptr(z), _stream(stream)))
     return z
+
+
+class Batch:
+    """tpcf_batch_create / run / destroy: many periodic catalogues of uneven sizes,
+    concatenated; mock k is rows offsets[k]:offsets[k+1] of the point arrays."""
+
+    def __init__(self, cfg: Config, offsets, group_points: int = 0):
+        import numpy as np
+        self.cfg = cfg
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        self.n_mocks = len(self.offsets) - 1
+        self.mults = multipole_index(cfg)
+        self.handle = ctypes.c_void_p()
+        c = cfg.c()
+        _check(lib().tpcf_batch_create(ctypes.byref(c), _ptr(self.offsets), self.n_mocks, int(group_points),
+                                       ctypes.addressof(self.handle)))
+
+    def info(self):
+        ng = ctypes.c_int32(0)
+        nc = ctypes.c_int32(0)
+        _check(lib().tpcf_batch_info(self.handle, ctypes.addressof(ng), ctypes.addressof(nc)))
+        return ng.value, nc.value
+
+    def zeta_buffer(self, device="cuda"):
+        nb = self.cfg.n_bins
+        return torch.empty((self.n_mocks, len(self.mults), nb, nb), dtype=torch.float64, device=device)
+
+    def run(self, xyz, w, zeta, triplet_counts=None, stream=None):
+        """Enqueues the whole batch on the stream (no host synchronisation)."""
+        _check(lib().tpcf_batch_run(self.handle, _ptr(xyz), _ptr(w), _ptr(zeta), _ptr(triplet_counts),
+                                    _stream(stream)))
+
+    def run_graph(self, xyz, w, zeta, triplet_counts=None, stream=None):
+        """tpcf_batch_run_graph: eager run + capture on first use of these buffers,
+        one graph launch afterwards."""
+        _check(lib().tpcf_batch_run_graph(self.handle, _ptr(xyz), _ptr(w), _ptr(zeta), _ptr(triplet_counts),
+                                          _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            _check(lib().tpcf_batch_destroy(self.handle))
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def estimate_3pcf_batched(cfg: Config, xyz, w, offsets, stream=None, device="cuda", want_counts=True):
+    """tpcf_estimate_3pcf_batched; returns (zeta [n_mocks, n_mult, nb, nb], triplet counts or None)."""
+    import numpy as np
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    dx = _as_dev_xyz(xyz, device)
+    dw = _as_dev_w(w, device)
+    nm = len(off) - 1
+    nb = cfg.n_bins
+    z = torch.empty((nm, len(multipole_index(cfg)), nb, nb), dtype=torch.float64, device=device)
+    tc = torch.empty((nm, nb, nb), dtype=torch.int64, device=device) if want_counts else None
+    c = cfg.c()
+    _check(lib().tpcf_estimate_3pcf_batched(ctypes.byref(c), _ptr(dx), _ptr(dw), _ptr(off), nm, _ptr(z),
+                                            _ptr(tc), _stream(stream)))
+    return z, tc
+
+
+def autotune(cfg: Config, xyz, w=None, stream=None, device="cuda") -> Config:
+    """tpcf_autotune: the fastest (cell_div, tile_primaries, chunk) for catalogues like this one."""
+    import dataclasses
+    dx = _as_dev_xyz(xyz, device)
+    dw = _as_dev_w(w, device)
+    c = cfg.c()
+    out = tpcf_config()
+    _check(lib().tpcf_autotune(ctypes.byref(c), _ptr(dx), _ptr(dw), dx.shape[0], _stream(stream),
+                               ctypes.byref(out)))
+    return dataclasses.replace(cfg, cell_div=out.cell_div, tile_primaries=out.tile_primaries, chunk=out.chunk)
 
 
 def kernel_launches() -> int:
