@@ -85,7 +85,8 @@ typedef struct {
     int32_t cell_div;       /* cells per r_max along an axis, 1..6; 0 = automatic */
     int32_t tile_primaries; /* primaries processed together by one CTA, 1..8 (capped so that
                                tile_primaries * n_bins <= 128); 0 = automatic */
-    int32_t chunk;          /* staged pairs per CTA chunk (multiple of 256, 512..8192); 0 = automatic */
+    int32_t chunk;          /* staged pairs per CTA (multiple of 256, 512..12288, above 32 per bin);
+                               0 = automatic (6144 up to l_max 4, else 12288) */
 } tpcf_config;
 
 typedef struct tpcf_grid_s *tpcf_grid;   /* library-owned cell list (opaque) */
@@ -257,8 +258,8 @@ int tpcf_batch_destroy(tpcf_batch batch);
 int tpcf_estimate_3pcf_batched(const tpcf_config *cfg, const uint32_t *xyz, const float *w, const int64_t *offsets,
                                int32_t n_mocks, double *zeta, int64_t *triplet_counts, void *stream);
 
-/* Chooses cell_div (2..5), tile_primaries (1, 2, 4) and chunk (1536, 2048,
- * 3072) for a catalogue like this one by timing the pair stage on a strided
+/* Chooses cell_div (2..5), tile_primaries (1, 2, 4) and chunk (3072, 4096,
+ * 6144) for a catalogue like this one by timing the pair stage on a strided
  * sample of at most 6144 of its primaries (dev xyz[n][3], dev w[n] or NULL) for
  * every valid combination; *tuned = *cfg with the fastest choice.  A nonzero
  * cfg->tile_primaries is kept fixed (batches run one primary per tile).

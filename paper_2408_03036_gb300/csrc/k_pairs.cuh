@@ -811,4 +811,508 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs(const PairPa
     if (cta_mock >= 0) flush_cta(cta_mock);
 }
 
+
+// ---------------------------------------------------------------------------
+// Queued pair stage (harmonic sums).  Same tile / range / window scheme as
+// k_pairs, but the CTA keeps one lane assignment for the whole tile:
+//   * every key (slot, bin) of the tile owns g_k lanes and a queue of cap_k
+//     entries in shared memory, both in proportion to the key's expected share
+//     of the pairs (a per-CTA running histogram over bins, seeded with the
+//     shell volumes);
+//   * gathering warps compute the exact bin of every candidate that passes the
+//     window test and append it to its key's queue (one shared atomic per
+//     entry); an entry that finds its queue full stays in the lane and raises
+//     the flag;
+//   * when the flag is up (or every warp is out of ranges) the CTA drains the
+//     queues: each lane sums its key's entries, strided by g_k, into registers
+//     that it keeps for the whole tile; queue counters are double-buffered, so
+//     a drain costs two barriers;
+//   * at the end of the tile the g_k lanes of every key are added through one
+//     shared-memory transpose.
+// Compared with k_pairs there is no per-chunk sort, key histogram or per-chunk
+// reduction, and staged pairs are written and read once.
+struct QMap {
+    int off_E, off_Ef, off_Elo, off_Ehi, off_prim, off_pf, off_pc;
+    int off_rstart, off_rlen, off_rslot;
+    int off_qbase, off_qcap, off_qcnt, off_cnt, off_gfirst, off_gsize, off_lanekey, off_hist;
+    int off_sacc, off_queue;
+    int off_d32, off_w32, off_d64, off_w64, off_pairs, off_misc;
+    int total;
+    int maxr;
+};
+
+template <int LMAX>
+__host__ __device__ inline QMap make_qmap(int P, int nb, int s, int chunk, int block)
+{
+    QMap m;
+    const int rows = (2 * s + 1) * (2 * s + 1);
+    const int W = block / 32;
+    m.maxr = 2 * P * rows;
+    const int nk = P * nb;
+    constexpr int naccp = Layout<LMAX>::NACCP;
+    int o = 0;
+    m.off_E = o;       o = align_up(o + 8 * (TPCF_MAX_BINS + 1), 16);
+    m.off_Ef = o;      o = align_up(o + 4 * (TPCF_MAX_BINS + 1), 16);
+    m.off_Elo = o;     o = align_up(o + 4 * (TPCF_MAX_BINS + 1), 16);
+    m.off_Ehi = o;     o = align_up(o + 4 * (TPCF_MAX_BINS + 1), 16);
+    m.off_prim = o;    o = align_up(o + 16 * TPCF_MAX_TILE, 16);
+    m.off_pf = o;      o = align_up(o + 16 * TPCF_MAX_TILE, 16);
+    m.off_pc = o;      o = align_up(o + 16 * TPCF_MAX_TILE, 16);
+    m.off_rstart = o;  o = align_up(o + 4 * m.maxr, 16);
+    m.off_rlen = o;    o = align_up(o + 4 * m.maxr, 16);
+    m.off_rslot = o;   o = align_up(o + 4 * m.maxr, 16);
+    m.off_qbase = o;   o = align_up(o + 4 * nk, 16);
+    m.off_qcap = o;    o = align_up(o + 4 * nk, 16);
+    m.off_qcnt = o;    o = align_up(o + 4 * 2 * nk, 16);
+    m.off_cnt = o;     o = align_up(o + 4 * nk, 16);
+    m.off_gfirst = o;  o = align_up(o + 4 * nk, 16);
+    m.off_gsize = o;   o = align_up(o + 4 * nk, 16);
+    m.off_lanekey = o; o = align_up(o + 4 * block, 16);
+    m.off_hist = o;    o = align_up(o + 4 * TPCF_MAX_BINS, 16);
+    m.off_sacc = o;    o = align_up(o + 4 * nk * naccp, 16);
+    // the queues; reused as the [block][NACCP] transpose area at the end of a tile
+    const int qbytes = 16 * chunk, stage = 4 * block * naccp;
+    m.off_queue = o;   o = align_up(o + (qbytes > stage ? qbytes : stage), 16);
+    m.off_d32 = o;     o = align_up(o + 4 * nb * Layout<LMAX>::NDIAG, 16);
+    m.off_w32 = o;     o = align_up(o + 4 * nb * Layout<LMAX>::NSP, 16);
+    m.off_d64 = o;     o = align_up(o + 8 * nb * Layout<LMAX>::NDIAG, 16);
+    m.off_w64 = o;     o = align_up(o + 8 * nb * Layout<LMAX>::NSP, 16);
+    m.off_pairs = o;   o = align_up(o + 8 * nb, 16);
+    m.off_misc = o;    o = align_up(o + 4 * (16 + W), 16);
+    m.total = o;
+    return m;
+}
+
+template <int LMAX>
+__global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const PairParams p, const HarmTables H)
+{
+    constexpr int NLM = Layout<LMAX>::NLM;
+    constexpr int NACC = Layout<LMAX>::NACC;
+    constexpr int NACCP = Layout<LMAX>::NACCP;
+    constexpr int NDIAG = Layout<LMAX>::NDIAG;
+    constexpr int NSP = Layout<LMAX>::NSP;
+    constexpr float TOL = 1.0e-6f;        // > 5 * 2^-24 relative error of the float r^2
+    constexpr unsigned FULL = 0xffffffffu;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = T >> 5;
+    const int nb = p.nb, P = p.P, s = p.s, nc = p.nc, C = p.chunk;
+    const int side = 2 * s + 1, rows = side * side;
+    const QMap M = make_qmap<LMAX>(P, nb, s, C, T);
+    const int nkmax = P * nb;
+
+    unsigned long long *sE = reinterpret_cast<unsigned long long *>(smem + M.off_E);
+    float *sEf = reinterpret_cast<float *>(smem + M.off_Ef);
+    float *sElo = reinterpret_cast<float *>(smem + M.off_Elo);
+    float *sEhi = reinterpret_cast<float *>(smem + M.off_Ehi);
+    int4 *sPrim = reinterpret_cast<int4 *>(smem + M.off_prim);
+    float4 *sPf = reinterpret_cast<float4 *>(smem + M.off_pf);
+    int4 *sPc = reinterpret_cast<int4 *>(smem + M.off_pc);
+    int *rstart = reinterpret_cast<int *>(smem + M.off_rstart);
+    int *rlen = reinterpret_cast<int *>(smem + M.off_rlen);
+    int *rslot = reinterpret_cast<int *>(smem + M.off_rslot);
+    int *qbase = reinterpret_cast<int *>(smem + M.off_qbase);
+    int *qcap = reinterpret_cast<int *>(smem + M.off_qcap);
+    int *qcnt = reinterpret_cast<int *>(smem + M.off_qcnt);      // [2][nkmax]
+    int *cnt = reinterpret_cast<int *>(smem + M.off_cnt);
+    int *gfirst = reinterpret_cast<int *>(smem + M.off_gfirst);
+    int *gsize = reinterpret_cast<int *>(smem + M.off_gsize);
+    int *lanekey = reinterpret_cast<int *>(smem + M.off_lanekey);
+    float *hist = reinterpret_cast<float *>(smem + M.off_hist);  // expected share of every bin
+    float *sacc = reinterpret_cast<float *>(smem + M.off_sacc);  // [nk][NACCP] tile sums
+    float4 *queue = reinterpret_cast<float4 *>(smem + M.off_queue);
+    float *stage = reinterpret_cast<float *>(smem + M.off_queue);
+    float *d32 = reinterpret_cast<float *>(smem + M.off_d32);
+    float *w32 = reinterpret_cast<float *>(smem + M.off_w32);
+    double *d64 = reinterpret_cast<double *>(smem + M.off_d64);
+    double *w64 = reinterpret_cast<double *>(smem + M.off_w64);
+    unsigned long long *spairs = reinterpret_cast<unsigned long long *>(smem + M.off_pairs);
+    int *misc = reinterpret_cast<int *>(smem + M.off_misc);
+    int &s_tile = misc[0];
+    int &s_next = misc[1];
+    volatile int &s_flag = misc[2];   // a queue is full
+    int *wdone = misc + 16;           // [W] warp has no more ranges and nothing pending
+
+    for (int i = tid; i <= nb; i += T) {
+        sE[i] = p.E[i];
+        sEf[i] = p.Ef[i];
+        sElo[i] = p.Ef[i] * (1.f + TOL);
+        sEhi[i] = p.Ef[i] * (1.f - TOL);
+    }
+    for (int i = tid; i < nb * NDIAG; i += T) { d32[i] = 0.f; d64[i] = 0.0; }
+    for (int i = tid; i < nb * NSP; i += T) { w32[i] = 0.f; w64[i] = 0.0; }
+    for (int i = tid; i < nb; i += T) spairs[i] = 0ull;
+    for (int i = tid; i < 2 * nkmax; i += T) qcnt[i] = 0;
+    if (tid < nb) {
+        // seed: the shell volumes, r^3 in units of the bin edges' squares
+        const float a = sqrtf(p.Ef[tid]), b = sqrtf(p.Ef[tid + 1]);
+        hist[tid] = b * b * b - a * a * a;
+    }
+    if (tid == 0) s_flag = 0;
+    double mono_w = p.use_mono ? (p.mono_w_dev ? *p.mono_w_dev : p.mono_w) : 0.0;
+    int tiles_since_flush = 0;
+    int cta_mock = -1;
+    int par = 0;                      // live half of the double-buffered queue counters
+    __syncthreads();
+
+    auto a00 = [&](float wsum, int b) -> float {
+        double v = (double)wsum * H.K[0][0];
+        if (p.use_mono) v -= (mono_w - 1.0) * p.mono_coef[b];
+        return (float)v;
+    };
+
+    auto flush_cta = [&](int mk) {
+        __syncthreads();
+        for (int i = tid; i < nb * NDIAG; i += T) {
+            const double v = d64[i] + (double)d32[i];
+            const int b = i / NDIAG, jd = i % NDIAG;
+            if (p.diag && v != 0.0) atomicAdd(p.diag + ((size_t)mk * NDIAG + jd) * nb + b, v);
+            d64[i] = 0.0;
+            d32[i] = 0.f;
+        }
+        for (int i = tid; i < nb * NSP; i += T) {
+            const double v = w64[i] + (double)w32[i];
+            const int b = i / NSP, j = i % NSP;
+            if (p.wsp && v != 0.0) atomicAdd(p.wsp + ((size_t)mk * NSP + j) * nb + b, v);
+            w64[i] = 0.0;
+            w32[i] = 0.f;
+        }
+        for (int b = tid; b < nb; b += T) {
+            if (p.pair_counts && spairs[b]) atomicAdd(p.pair_counts + (size_t)mk * nb + b, spairs[b]);
+            spairs[b] = 0ull;
+        }
+        tiles_since_flush = 0;
+        __syncthreads();
+    };
+
+    for (;;) {
+        if (tid == 0) {
+            s_tile = atomicAdd(p.work, 1);
+            s_next = 0;
+        }
+        __syncthreads();
+        const long long t0 = (long long)s_tile * P;
+        if (t0 >= p.n_prim) break;
+        const int np = (int)min((long long)P, p.n_prim - t0);
+        const int nk = np * nb;
+        const int mock = p.prim_mock ? p.prim_mock[t0] : 0;
+        if (mock != cta_mock) {
+            if (cta_mock >= 0) flush_cta(cta_mock);
+            cta_mock = mock;
+            if (p.prim_mock && p.use_mono) mono_w = p.mono_w_mock[mock];
+        }
+        const long long mock_cells = (long long)mock * p.ncell_mock;
+
+        if (tid < np) {
+            const int4 q = p.prim[t0 + tid];
+            sPrim[tid] = q;
+            const uint32_t ux = (uint32_t)q.x, uy = (uint32_t)q.y, uz = (uint32_t)q.z;
+            sPf[tid] = make_float4((float)ux, (float)uy, (float)uz, __int_as_float(q.w));
+            sPc[tid] = make_int4((int)(((unsigned long long)ux * nc) >> 32),
+                                 (int)(((unsigned long long)uy * nc) >> 32),
+                                 (int)(((unsigned long long)uz * nc) >> 32), 0);
+            const float wq = __int_as_float(q.w);
+            if (!(wq == wq) || isinf(wq)) latch_error(p.err, DEV_ERR_DATA);
+        }
+        // tile plan (warp 0): queue capacities and lane groups in proportion to the
+        // expected share e_b / np of every key; at least 32 entries and one lane each
+        if (warp == 0) {
+            float e = lane < nb ? hist[lane] : 0.f;
+            float tot = e;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
+            e = lane < nb ? 0.999f * e / (tot * (float)np) : 0.f;   // sum over keys < 1
+            const int capb = lane < nb ? 32 + (int)((float)(C - 32 * nk) * e) : 0;
+            const int gb = lane < nb ? 1 + (int)((float)(T - nk) * e) : 0;
+            int cs = capb, gs = gb;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t1 = __shfl_up_sync(FULL, cs, o);
+                const int t2 = __shfl_up_sync(FULL, gs, o);
+                if (lane >= o) { cs += t1; gs += t2; }
+            }
+            const int ctot = __shfl_sync(FULL, cs, 31), gtot = __shfl_sync(FULL, gs, 31);
+            for (int i = lane; i < T; i += 32) lanekey[i] = -1;
+            __syncwarp();
+            if (lane < nb) {
+                for (int sl = 0; sl < np; ++sl) {
+                    const int k = sl * nb + lane;
+                    qbase[k] = sl * ctot + cs - capb;
+                    qcap[k] = capb;
+                    const int g0 = sl * gtot + gs - gb;
+                    gfirst[k] = g0;
+                    gsize[k] = gb;
+                    cnt[k] = 0;
+                    for (int q = 0; q < gb; ++q) lanekey[g0 + q] = k;
+                }
+            }
+        }
+        __syncthreads();
+
+        // candidate ranges (as in k_pairs)
+        const int nr = 2 * np * rows;
+        for (int r = tid; r < np * rows; r += T) {
+            const int slot = r / rows, row = r % rows;
+            const int dz = row / side - s, dy = row % side - s;
+            const int4 pc = sPc[slot];
+            const float4 pf = sPf[slot];
+            const int cy = pc.y + dy, cz = pc.z + dz;
+            int a0 = 0, l0 = 0, a1 = 0, l1 = 0;
+            const float ylo = (float)cy * p.h_u, zlo = (float)cz * p.h_u;
+            const float dyv = fmaxf(0.f, fmaxf(ylo - pf.y, pf.y - (ylo + p.h_u)));
+            const float dzv = fmaxf(0.f, fmaxf(zlo - pf.z, pf.z - (zlo + p.h_u)));
+            const float rr = p.rmax_trim;
+            const float d2 = dyv * dyv + dzv * dzv;
+            bool row_ok = d2 <= rr * rr;
+            int wy = cy, wz = cz;
+            if (p.periodic) {
+                wy = (cy % nc + nc) % nc;
+                wz = (cz % nc + nc) % nc;
+            } else if (cy < 0 || cz < 0 || cy >= nc || cz >= nc) {
+                row_ok = false;
+            }
+            if (row_ok) {
+                const float wx = sqrtf(fmaxf(rr * rr - d2, 0.f)) * 1.0001f + 4096.f;
+                int x0 = (int)floorf((pf.x - wx) / p.h_u);
+                int x1 = (int)floorf((pf.x + wx) / p.h_u);
+                x0 = max(x0, pc.x - s);
+                x1 = min(x1, pc.x + s);
+                if (!p.periodic) {
+                    x0 = max(x0, 0);
+                    x1 = min(x1, nc - 1);
+                }
+                if (x1 >= x0) {
+                    const long long base = mock_cells + ((long long)wz * nc + wy) * nc;
+                    int sa = x0, sb = x1, ta = 1, tb = 0;
+                    if (p.periodic) {
+                        if (x0 < 0) { sa = x0 + nc; sb = nc - 1; ta = 0; tb = x1; }
+                        else if (x1 >= nc) { sa = x0; sb = nc - 1; ta = 0; tb = x1 - nc; }
+                    }
+                    a0 = p.cell_start[base + sa];
+                    l0 = p.cell_start[base + sb + 1] - a0;
+                    if (tb >= ta) {
+                        a1 = p.cell_start[base + ta];
+                        l1 = p.cell_start[base + tb + 1] - a1;
+                    }
+                }
+            }
+            rstart[2 * r] = a0; rlen[2 * r] = l0; rslot[2 * r] = slot;
+            rstart[2 * r + 1] = a1; rlen[2 * r + 1] = l1; rslot[2 * r + 1] = slot;
+        }
+        __syncthreads();
+
+        const int myk = lanekey[tid];
+        const int myg = myk >= 0 ? gsize[myk] : 1;
+        const int myr = myk >= 0 ? tid - gfirst[myk] : 0;
+        const int myq = myk >= 0 ? qbase[myk] : 0;
+        const int mycap = myk >= 0 ? qcap[myk] : 0;
+        float acc[NACC];
+#pragma unroll
+        for (int j = 0; j < NACC; ++j) acc[j] = 0.f;
+
+        // drains the queues (all threads); returns whether every warp has finished
+        auto drain = [&]() -> bool {
+            __syncthreads();                                   // (A) appends are visible
+            int alldone = 1;
+            for (int w = 0; w < W; ++w) alldone &= wdone[w];
+            const int *live = qcnt + par * nkmax;
+            if (tid < nk) cnt[tid] += min(live[tid], qcap[tid]);
+            if (tid < nkmax) qcnt[(par ^ 1) * nkmax + tid] = 0;   // the other half: free since the last drain
+            if (tid == 0) s_flag = 0;
+            if (myk >= 0) {
+                const int n = min(live[myk], mycap);
+                const float4 *qq = queue + myq;
+                for (int e = myr; e < n; e += myg) {
+                    const float4 v = qq[e];
+                    const float r2f = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
+                    // correctly rounded 1/sqrt: |n|^2 = 1 up to unbiased rounding,
+                    // which the j = k cancellation on diagonal bins needs
+                    const float inv = __frsqrt_rn(r2f);
+                    accum_pair<LMAX>(v.x * inv, v.y * inv, v.z * inv, v.w, acc);
+                }
+            }
+            __syncthreads();                                   // (B) queues consumed
+            par ^= 1;
+            return alldone != 0;
+        };
+
+        // ----- gather: warps take ranges (strided order) and sweep them 32 candidates per step
+        int stride = (nr * 5) / 8 + 1;
+        while (nr > 1 && gcd_int(stride, nr) != 1) ++stride;
+        int my_start = 0, my_len = 0, my_pos = 0, my_slot = 0;
+        bool done = false, have = false;
+        float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
+        int ek = 0;
+        for (;;) {
+            if (!__any_sync(FULL, have)) {
+                while (!done && my_pos >= my_len) {
+                    int r = 0;
+                    if (lane == 0) r = atomicAdd(&s_next, 1);
+                    r = __shfl_sync(FULL, r, 0);
+                    if (r >= nr) {
+                        done = true;
+                    } else {
+                        const int rr = (int)(((long long)r * stride) % nr);
+                        my_start = rstart[rr];
+                        my_len = rlen[rr];
+                        my_slot = rslot[rr];
+                        my_pos = 0;
+                    }
+                }
+                if (!done) {
+                    const int i = my_pos + lane;
+                    my_pos += 32;
+                    if (i < my_len) {
+                        const int4 q = p.rec[my_start + i];
+                        const int4 pr = sPrim[my_slot];
+                        const int dx = (int)((uint32_t)q.x - (uint32_t)pr.x);
+                        const int dy = (int)((uint32_t)q.y - (uint32_t)pr.y);
+                        const int dz = (int)((uint32_t)q.z - (uint32_t)pr.z);
+                        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+                        const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                        if (r2f >= p.r2_lo && r2f < p.r2_hi) {
+                            int b = (int)((r2f * rsqrtf(r2f) - p.rmin_u) * p.inv_dr_u);
+                            b = min(max(b, 0), nb - 1);
+                            if (!(r2f >= sElo[b] && r2f < sEhi[b + 1])) {
+                                // near an edge: the exact 64-bit integer separation decides
+                                const long long lx = dx, ly = dy, lz = dz;
+                                const unsigned long long r2 = (unsigned long long)(lx * lx)
+                                                            + (unsigned long long)(ly * ly)
+                                                            + (unsigned long long)(lz * lz);
+                                if (r2 < sE[0] || r2 >= sE[nb]) {
+                                    b = -1;
+                                } else {
+                                    while (b > 0 && r2 < sE[b]) --b;
+                                    while (b < nb - 1 && r2 >= sE[b + 1]) ++b;
+                                }
+                            }
+                            if (b >= 0) {
+                                have = true;
+                                ent = make_float4(fx, fy, fz, __int_as_float(q.w));
+                                ek = my_slot * nb + b;
+                            }
+                        }
+                    }
+                }
+            }
+            const bool fin = done && !__any_sync(FULL, have);
+            if (__any_sync(FULL, fin || s_flag)) {
+                if (lane == 0) wdone[warp] = fin ? 1 : 0;
+                if (drain()) break;
+                continue;
+            }
+            if (have) {
+                const int pos = atomicAdd(&qcnt[par * nkmax + ek], 1);
+                if (pos < qcap[ek]) {
+                    queue[qbase[ek] + pos] = ent;
+                    have = false;
+                } else {
+                    s_flag = 1;   // stays pending until the queues are drained
+                }
+            }
+        }
+
+        // ----- tile sums: every key's lanes added through one transpose
+        {
+            float *st = stage + (size_t)tid * NACCP;
+#pragma unroll
+            for (int j = 0; j < NACC; ++j) st[j] = acc[j];
+        }
+        __syncthreads();
+        for (int i = tid; i < nk * NACC; i += T) {
+            const int k = i / NACC, j = i % NACC;
+            const int g0 = gfirst[k], g = gsize[k];
+            float t = 0.f;
+            for (int q = 0; q < g; ++q) t += stage[(g0 + q) * NACCP + j];
+            sacc[k * NACCP + j] = t;
+        }
+        __syncthreads();
+
+        // ----- tile outputs (as in k_pairs)
+        const long long g0 = t0;
+        if (p.alm) {
+            for (int i = tid; i < np * nb * NLM; i += T) {
+                const int slot = i / (nb * NLM), rem = i % (nb * NLM);
+                const int b = rem / NLM, k = rem % NLM;
+                const float raw = sacc[(slot * nb + b) * NACCP + k];
+                float v;
+                if (k == 0) {
+                    v = a00(raw, b);
+                } else {
+                    int l = 1;
+                    while ((l + 1) * (l + 1) <= k) ++l;
+                    const int m = (k - l * l + 1) >> 1;
+                    v = (float)((double)raw * H.K[l][m]);
+                }
+                p.alm[(g0 + slot) * nb * NLM + rem] = v;
+            }
+        }
+        if (p.counts)
+            for (int i = tid; i < np * nb; i += T) p.counts[g0 * nb + i] = cnt[i];
+        for (int b = tid; b < nb; b += T) {
+            unsigned long long t = 0;
+            for (int sl = 0; sl < np; ++sl) t += (unsigned long long)cnt[sl * nb + b];
+            spairs[b] += t;
+        }
+        for (int i = tid; i < nb * NDIAG; i += T) {
+            const int b = i / NDIAG, jd = i % NDIAG;
+            int l = 0;
+            while ((l + 1) * (l + 2) / 2 <= jd) ++l;
+            const int m = jd - l * (l + 1) / 2;
+            float acc2 = 0.f;
+            const float k2 = (float)(H.K[l][m] * H.K[l][m]);
+            for (int sl = 0; sl < np; ++sl) {
+                const float *a = sacc + (sl * nb + b) * NACCP;
+                float self = 0.f;
+                if (p.remove_self)
+                    for (int j = 0; j <= LMAX; ++j) {
+                        self = fmaf(H.gd_hi[jd][j], a[NLM + j], self);
+                        self = fmaf(H.gd_lo[jd][j], a[NLM + j], self);
+                    }
+                float d;
+                if (l == 0) {
+                    const float re = a00(a[0], b);
+                    d = fmaf(re, re, -k2 * self);
+                } else {
+                    const float re = a[l * l + (m ? 2 * m - 1 : 0)];
+                    const float im = m ? a[l * l + 2 * m] : 0.f;
+                    d = k2 * (fmaf(re, re, im * im) - self);
+                }
+                acc2 += __int_as_float(sPrim[sl].w) * d;
+            }
+            d32[i] += acc2;
+        }
+        for (int i = tid; i < nb * NSP; i += T) {
+            const int b = i / NSP, j = i % NSP;
+            float acc2 = 0.f;
+            for (int sl = 0; sl < np; ++sl)
+                acc2 += __int_as_float(sPrim[sl].w) * sacc[(sl * nb + b) * NACCP + NLM + j];
+            w32[i] += acc2;
+        }
+        if (++tiles_since_flush >= 16) {
+            tiles_since_flush = 0;
+            for (int i = tid; i < nb * NDIAG; i += T) { d64[i] += (double)d32[i]; d32[i] = 0.f; }
+            for (int i = tid; i < nb * NSP; i += T) { w64[i] += (double)w32[i]; w32[i] = 0.f; }
+        }
+        // the bin shares for the next tile: half the old estimate, half this tile's counts
+        if (warp == 0) {
+            int c = 0;
+            if (lane < nb)
+                for (int sl = 0; sl < np; ++sl) c += cnt[sl * nb + lane];
+            const float h = lane < nb ? hist[lane] : 0.f;
+            int ct = c;
+            float ht = h;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ct += __shfl_xor_sync(FULL, ct, o);
+                ht += __shfl_xor_sync(FULL, ht, o);
+            }
+            if (lane < nb && ct > 0) hist[lane] = 0.5f * h / ht + 0.5f * (float)c / (float)ct + 1e-4f;
+        }
+        __syncthreads();
+    }
+
+    if (cta_mock >= 0) flush_cta(cta_mock);
+}
+
 }  // namespace tpcf

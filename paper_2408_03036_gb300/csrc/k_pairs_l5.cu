@@ -4,6 +4,7 @@
 
 namespace tpcf {
 
+// COUNTS: integer pair counts only (k_pairs); otherwise the queued harmonic kernel.
 template <int LMAX, bool COUNTS>
 static cudaError_t launch_one(const PairParams &p, const HarmTables &h, int grid, int block,
                               size_t smem, cudaStream_t st)
@@ -11,12 +12,16 @@ static cudaError_t launch_one(const PairParams &p, const HarmTables &h, int grid
     static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
     const unsigned long long bit = device_bit();
     if (!(attr_done.load(std::memory_order_acquire) & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(k_pairs<LMAX, COUNTS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaError_t e;
+        if constexpr (COUNTS)
+            e = cudaFuncSetAttribute(k_pairs<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        else
+            e = cudaFuncSetAttribute(k_pairs_q<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         attr_done.fetch_or(bit, std::memory_order_acq_rel);
     }
-    k_pairs<LMAX, COUNTS><<<grid, block, smem, st>>>(p, h);
+    if constexpr (COUNTS) k_pairs<0, true><<<grid, block, smem, st>>>(p, h);
+    else k_pairs_q<LMAX><<<grid, block, smem, st>>>(p, h);
     note_launch();
     return cudaGetLastError();
 }
@@ -31,7 +36,7 @@ cudaError_t launch_pairs_l5(bool counts_only, const PairParams &p, const HarmTab
 size_t pairs_smem_l5(bool counts_only, int P, int nb, int s, int chunk, int block)
 {
     if (counts_only) return (size_t)make_smem_map<0, true>(P, nb, s, chunk, block).total;
-    return (size_t)make_smem_map<5, false>(P, nb, s, chunk, block).total;
+    return (size_t)make_qmap<5>(P, nb, s, chunk, block).total;
 }
 
 }  // namespace tpcf

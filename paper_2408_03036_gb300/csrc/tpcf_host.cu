@@ -125,8 +125,8 @@ int check_config(const tpcf_config *c)
     if (c->remove_self != 0 && c->remove_self != 1) return fail(TPCF_ERR_ARG, "remove_self must be 0 or 1");
     if (c->cell_div < 0 || c->cell_div > 6) return fail(TPCF_ERR_ARG, "cell_div must be 0..6");
     if (c->tile_primaries < 0 || c->tile_primaries > TPCF_MAX_TILE) return fail(TPCF_ERR_ARG, "tile_primaries must be 0..8");
-    if (c->chunk != 0 && (c->chunk < 512 || (c->chunk % 256) != 0 || c->chunk > 8192))
-        return fail(TPCF_ERR_ARG, "chunk must be 0 or a multiple of 256 in 512..8192");
+    if (c->chunk != 0 && (c->chunk < 512 || (c->chunk % 256) != 0 || c->chunk > 12288))
+        return fail(TPCF_ERR_ARG, "chunk must be 0 or a multiple of 256 in 512..12288");
     return TPCF_OK;
 }
 
@@ -358,7 +358,8 @@ Plan make_plan(const tpcf_config *c, int64_t n_sec, int64_t n_prim_hint)
     // the chunk's lane groups need P * n_bins <= 128 keys (half the CTA's lanes)
     P = std::min(P, std::max(1, 128 / c->n_bins));
     p.P = P;
-    p.chunk = c->chunk ? c->chunk : 2048;
+    // queue entries per CTA: two CTAs per SM up to l_max 4, one above
+    p.chunk = c->chunk ? c->chunk : (c->l_max <= 4 ? 6144 : 12288);
     (void)n_prim_hint;
     return p;
 }
@@ -460,6 +461,13 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
         smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
     }
     if (smem > 227 * 1024) return fail(TPCF_ERR_UNSUPPORTED, "pair stage needs %zu bytes of shared memory", smem);
+    if (!counts_only) {
+        // the harmonic kernel gives every key at least 32 queue entries
+        while (pl.P > 1 && pl.chunk < 32 * (pl.P * c->n_bins + 1)) --pl.P;
+        if (pl.chunk < 32 * (pl.P * c->n_bins + 1))
+            return fail(TPCF_ERR_ARG, "chunk %d is below 32 entries per bin (%d bins)", pl.chunk, c->n_bins);
+        smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
+    }
     if (bi) {
         pl.P = 1;   // one primary per tile: a tile never straddles two catalogues
         smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
@@ -1164,7 +1172,7 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
     const int tiles_all[] = {1, 2, 4};
     const int tiles_fixed[] = {cfg->tile_primaries};
     const bool fixed_tile = cfg->tile_primaries > 0;   // a batch runs one primary per tile
-    const int chunks[] = {1536, 2048, 3072};
+    const int chunks[] = {3072, 4096, 6144};
     for (int dv : divs) {
         tpcf_config t = *cfg;
         t.cell_div = dv;
