@@ -45,6 +45,8 @@ struct PairParams {
     float Ef[TPCF_MAX_BINS + 1];
     float rmin_u, inv_dr_u;   // float bin estimate b = (sqrt(r2) - rmin_u) * inv_dr_u
     float r2_lo, r2_hi;       // float prefilter window (conservative)
+    float t_off, tdelta;      // t = sqrt(r2) * inv_dr_u + t_off is the bin coordinate; a float t
+                              // within tdelta of an integer is decided in exact arithmetic
     float rmax_trim;          // conservative r_max (units) for row trimming
     float h_u;                // cell side in units (2^32 / nc)
     double mono_coef[TPCF_MAX_BINS];  // c_b = (W - 1) * mono_coef[b]

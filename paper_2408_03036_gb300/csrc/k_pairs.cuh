@@ -931,6 +931,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
     int &s_tile = misc[0];
     int &s_next = misc[1];
     volatile int &s_flag = misc[2];   // a queue is full
+    int &s_nr = misc[3];              // non-empty candidate ranges of the tile
     int *wdone = misc + 16;           // [W] warp has no more ranges and nothing pending
 
     for (int i = tid; i <= nb; i += T) {
@@ -989,6 +990,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         if (tid == 0) {
             s_tile = atomicAdd(p.work, 1);
             s_next = 0;
+            s_nr = 0;
         }
         __syncthreads();
         const long long t0 = (long long)s_tile * P;
@@ -1049,8 +1051,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         }
         __syncthreads();
 
-        // candidate ranges (as in k_pairs)
-        const int nr = 2 * np * rows;
+        // candidate ranges (as in k_pairs), non-empty ones listed in any order
         for (int r = tid; r < np * rows; r += T) {
             const int slot = r / rows, row = r % rows;
             const int dz = row / side - s, dy = row % side - s;
@@ -1096,10 +1097,17 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                     }
                 }
             }
-            rstart[2 * r] = a0; rlen[2 * r] = l0; rslot[2 * r] = slot;
-            rstart[2 * r + 1] = a1; rlen[2 * r + 1] = l1; rslot[2 * r + 1] = slot;
+            if (l0 > 0) {
+                const int at = atomicAdd(&s_nr, 1);
+                rstart[at] = a0; rlen[at] = l0; rslot[at] = slot;
+            }
+            if (l1 > 0) {
+                const int at = atomicAdd(&s_nr, 1);
+                rstart[at] = a1; rlen[at] = l1; rslot[at] = slot;
+            }
         }
         __syncthreads();
+        const int nr = s_nr;
 
         const int myk = lanekey[tid];
         const int myg = myk >= 0 ? gsize[myk] : 1;
@@ -1136,70 +1144,78 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
             return alldone != 0;
         };
 
-        // ----- gather: warps take ranges (strided order) and sweep them 32 candidates per step
+        // ----- gather: warps take ranges (in a strided order that mixes radii, so the
+        // queues fill evenly) and sweep them 32 candidates per step
         int stride = (nr * 5) / 8 + 1;
         while (nr > 1 && gcd_int(stride, nr) != 1) ++stride;
-        int my_start = 0, my_len = 0, my_pos = 0, my_slot = 0;
+        int my_start = 0, my_len = 0, my_pos = 0, kb = 0;
+        uint32_t px = 0, py = 0, pz = 0;
         bool done = false, have = false;
         float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
         int ek = 0;
         for (;;) {
-            if (!__any_sync(FULL, have)) {
-                while (!done && my_pos >= my_len) {
+            // bit 0: an entry of the warp waits for room; bit 1: a queue is full
+            const unsigned st = __reduce_or_sync(FULL, (have ? 1u : 0u) | (s_flag ? 2u : 0u));
+            const bool fin = done && !(st & 1u);
+            if ((st & 2u) || fin) {
+                if (lane == 0) wdone[warp] = fin ? 1 : 0;
+                if (drain()) break;
+                continue;
+            }
+            if (!(st & 1u)) {
+                if (my_pos >= my_len) {   // ranges are never empty
                     int r = 0;
                     if (lane == 0) r = atomicAdd(&s_next, 1);
                     r = __shfl_sync(FULL, r, 0);
                     if (r >= nr) {
                         done = true;
-                    } else {
-                        const int rr = (int)(((long long)r * stride) % nr);
-                        my_start = rstart[rr];
-                        my_len = rlen[rr];
-                        my_slot = rslot[rr];
-                        my_pos = 0;
+                        continue;
+                    }
+                    const int rr = (int)(((unsigned)r * (unsigned)stride) % (unsigned)nr);
+                    my_start = rstart[rr];
+                    my_len = rlen[rr];
+                    const int sl = rslot[rr];
+                    const int4 pr = sPrim[sl];
+                    px = (uint32_t)pr.x;
+                    py = (uint32_t)pr.y;
+                    pz = (uint32_t)pr.z;
+                    kb = sl * nb;
+                    my_pos = 0;
+                }
+                const int i = my_pos + lane;
+                my_pos += 32;
+                const bool valid = i < my_len;
+                const int4 q = p.rec[my_start + min(i, my_len - 1)];
+                const int dx = (int)((uint32_t)q.x - px);
+                const int dy = (int)((uint32_t)q.y - py);
+                const int dz = (int)((uint32_t)q.z - pz);
+                const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
+                const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+                // bin coordinate t = (r - r_min) / dr; its integer part is the bin unless
+                // t is within tdelta of an integer, where the 64-bit separation decides
+                const float rg = fmaxf(r2f, 1.f);
+                const float t = fmaf(rg * rsqrtf(rg), p.inv_dr_u, p.t_off);
+                const float tf = floorf(t);
+                int b = (int)tf;
+                const float fr = t - tf;
+                const bool sure = fr > p.tdelta && fr < 1.f - p.tdelta;
+                bool ok = valid && sure && b >= 0 && b < nb;
+                const bool unsure = valid && !sure && t > -1.f && t < (float)(nb + 1);
+                if (__any_sync(FULL, unsure)) {
+                    if (unsure) {
+                        const long long lx = dx, ly = dy, lz = dz;
+                        const unsigned long long r2 = (unsigned long long)(lx * lx)
+                                                    + (unsigned long long)(ly * ly)
+                                                    + (unsigned long long)(lz * lz);
+                        ok = r2 >= sE[0] && r2 < sE[nb];
+                        b = min(max(b, 0), nb - 1);
+                        while (b > 0 && r2 < sE[b]) --b;
+                        while (b < nb - 1 && r2 >= sE[b + 1]) ++b;
                     }
                 }
-                if (!done) {
-                    const int i = my_pos + lane;
-                    my_pos += 32;
-                    if (i < my_len) {
-                        const int4 q = p.rec[my_start + i];
-                        const int4 pr = sPrim[my_slot];
-                        const int dx = (int)((uint32_t)q.x - (uint32_t)pr.x);
-                        const int dy = (int)((uint32_t)q.y - (uint32_t)pr.y);
-                        const int dz = (int)((uint32_t)q.z - (uint32_t)pr.z);
-                        const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-                        const float r2f = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
-                        if (r2f >= p.r2_lo && r2f < p.r2_hi) {
-                            int b = (int)((r2f * rsqrtf(r2f) - p.rmin_u) * p.inv_dr_u);
-                            b = min(max(b, 0), nb - 1);
-                            if (!(r2f >= sElo[b] && r2f < sEhi[b + 1])) {
-                                // near an edge: the exact 64-bit integer separation decides
-                                const long long lx = dx, ly = dy, lz = dz;
-                                const unsigned long long r2 = (unsigned long long)(lx * lx)
-                                                            + (unsigned long long)(ly * ly)
-                                                            + (unsigned long long)(lz * lz);
-                                if (r2 < sE[0] || r2 >= sE[nb]) {
-                                    b = -1;
-                                } else {
-                                    while (b > 0 && r2 < sE[b]) --b;
-                                    while (b < nb - 1 && r2 >= sE[b + 1]) ++b;
-                                }
-                            }
-                            if (b >= 0) {
-                                have = true;
-                                ent = make_float4(fx, fy, fz, __int_as_float(q.w));
-                                ek = my_slot * nb + b;
-                            }
-                        }
-                    }
-                }
-            }
-            const bool fin = done && !__any_sync(FULL, have);
-            if (__any_sync(FULL, fin || s_flag)) {
-                if (lane == 0) wdone[warp] = fin ? 1 : 0;
-                if (drain()) break;
-                continue;
+                have = ok;
+                ent = make_float4(fx, fy, fz, __int_as_float(q.w));
+                ek = kb + b;
             }
             if (have) {
                 const int pos = atomicAdd(&qcnt[par * nkmax + ek], 1);

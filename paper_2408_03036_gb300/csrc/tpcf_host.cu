@@ -431,6 +431,15 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
     const double u = kTwo32 / c->box;   // units per length
     p.rmin_u = (float)(c->r_min * u);
     p.inv_dr_u = (float)((double)c->n_bins / ((c->r_max - c->r_min) * u));
+    {
+        // float bin coordinate t = (r - r_min) / dr from the float r^2: relative error of r
+        // below 5.1e-7 (r^2 from rounded separations 3e-7, rsqrt 2.4e-7, products), of the
+        // constants below 6e-8; a margin of four times the resulting bound
+        const double dr = (c->r_max - c->r_min) / c->n_bins;
+        p.t_off = (float)(-(double)p.rmin_u * (double)p.inv_dr_u);
+        p.tdelta = (float)(4.0 * (((c->r_max + dr) / dr) * 5.1e-7 + (c->r_min / dr) * 6e-8
+                                  + (c->n_bins + 1.0) * 6e-8));
+    }
     p.r2_lo = (float)((double)p.E[0] * (1.0 - 4e-6));
     p.r2_hi = (float)((double)p.E[c->n_bins] * (1.0 + 4e-6));
     p.rmax_trim = (float)(c->r_max * u * (1.0 + 1e-5) + 4096.0);
