@@ -267,6 +267,8 @@ def run_ours(args):
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof, "e2e": e2e}
     if mocks is not None:
         line["mocks_per_hour"] = mocks
+    if not args.no_precision:
+        line["precision_vs_oracle"] = precision_report(dev, stream, tpcf)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -350,6 +352,85 @@ def batch_mocks(args, dev, stream, tpcf, flush, rank=0):
     return out
 
 
+def gram_flop_per_primary(nb, lmax):
+    """Algorithmic FLOP of the Gram coupling per primary: for every m, the block of
+    n_b (l_max - m + 1) rows, real part only at m = 0, real and imaginary above."""
+    macs = sum((1 if m == 0 else 2) * (nb * (lmax - m + 1)) ** 2 for m in range(lmax + 1))
+    return 2 * macs
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "of measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "of fallback"
+
+
+def coupling_report(cfg, alm, wprim, counts, diag, wsp, dev, stream, tpcf, reps=3):
+    """The coupling step alone on the workload's per-primary a_lm: plain FP32 Gram
+    against the bf16x3 and tf32x3 tensor-core Grams (three MMAs per useful MAC)."""
+    import dataclasses
+    import torch
+    peaks, which = measured_peaks()
+    K = alm.shape[0]
+    flop = gram_flop_per_primary(cfg.n_bins, cfg.l_max) * K
+    out = {"primaries": K, "algorithmic_flop": flop}
+    for prec in ("fp32", "bf16x3", "tf32x3"):
+        c = dataclasses.replace(cfg, precision=prec)
+        tpcf.couple_multipoles(c, alm, wprim, counts, diag, wsp, stream=stream)
+        torch.cuda.synchronize(dev)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(reps):
+            s.record(stream)
+            tpcf.couple_multipoles(c, alm, wprim, counts, diag, wsp, stream=stream)
+            e.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(s.elapsed_time(e))
+        t = statistics.median(ms) / 1000.0
+        r = {"ms": t * 1000.0, "algorithmic_tflops": flop / t / 1e12}
+        if prec != "fp32":
+            # tensor-pipe work is three MMAs per useful MAC; tf32 runs at half the bf16 rate
+            peak = peaks["bf16_tflops"] * (1.0 if prec == "bf16x3" else 0.5)
+            r["tensor_tflops"] = 3 * flop / t / 1e12
+            r["tensor_peak_tflops"] = peak
+            r["tensor_frac"] = r["tensor_tflops"] / peak
+            r["peak_note"] = which + (" bf16" if prec == "bf16x3" else " bf16 x 0.5 (nominal tf32/bf16 ratio)")
+        out[prec] = r
+    return out
+
+
+def precision_report(dev, stream, tpcf):
+    """Per-multipole error against the FP64 oracle on the precision workload:
+    Poisson N=20,000 in a periodic cube L=500, l_max 6, 30 bins 5-155, L in
+    {0,2,4,6}, for the plain FP32 coupling and the two tensor-core splits."""
+    import numpy as np
+    from oracle import oracle as ora
+    from paper_2408_03036_gb300 import synth
+    x, w = synth.poisson(20_000, 5)
+    o = ora.Config(5.0, 155.0, 30, 6, (0, 2, 4, 6), True, 500.0)
+    t = time.perf_counter()
+    est = ora.estimate(o, x, w)
+    out = {"workload": "Poisson N=20000, periodic L=500, 30 bins 5-155, l_max=6, L={0,2,4,6}",
+           "oracle_s": time.perf_counter() - t, "n_mult": len(est.mults)}
+    for prec in ("fp32", "bf16x3", "tf32x3"):
+        cfg = tpcf.Config(r_min=5.0, r_max=155.0, n_bins=30, l_max=6, Ls=(0, 2, 4, 6), periodic=True, box=500.0,
+                          precision=prec)
+        res = tpcf.estimate_3pcf(cfg, x, w, stream=stream, device=dev)
+        tpcf.stream_status(stream)
+        zg = res.zeta.cpu().numpy()
+        err = []
+        for k in range(len(est.mults)):
+            den = np.abs(est.zeta[k]).max()
+            err.append(float(np.abs(zg[k] - est.zeta[k]).max() / den) if den > 0 else 0.0)
+        err = np.array(err)
+        out[prec] = {"max_rel_err": float(err.max()), "median_rel_err": float(np.median(err)),
+                     "worst": "%d%d%d" % tuple(est.mults[int(err.argmax())]),
+                     "counts_exact": bool(np.array_equal(res.triplet_counts.cpu().numpy(), est.trip_counts))}
+    return out
+
+
 def fp32_peak_tflops(dev):
     import torch
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -369,6 +450,9 @@ def roofline(cfg, d, dw, r, rw, dev, stream, tpcf, reps=3):
         out = tpcf.accumulate_alm(grid, cfg, stream=stream)
     torch.cuda.synchronize(dev)
     pairs = int(out[4].sum().item())
+    n_grid = grid.info()[0]
+    _, gw, _ = grid.points(stream=stream)   # primary weights in grid order
+    coupling = coupling_report(cfg, out[0], gw, out[1], out[2], out[3], dev, stream, tpcf)
     s = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
     ms = []
@@ -384,8 +468,10 @@ def roofline(cfg, d, dw, r, rw, dev, stream, tpcf, reps=3):
     peak = fp32_peak_tflops(dev)
     return {"bound": "alu", "kernel": "k_pairs (pair stage, D-R field)", "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "per_launch": {"pairs": pairs, "flop_per_pair": FLOP_PER_PAIR, "ms": t * 1000.0},
-            "peak_note": "FP32 FMA pipe: 2 x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)"}
+            "per_launch": {"pairs": pairs, "flop_per_pair": FLOP_PER_PAIR, "ms": t * 1000.0,
+                           "primaries": n_grid},
+            "peak_note": "FP32 FMA pipe: 2 x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)",
+            "coupling": coupling}
 
 
 def end_to_end(cfg, d, dw, r, rw, args, stream, tpcf):
@@ -419,6 +505,7 @@ def main():
     ap.add_argument("--precision", choices=["fp32", "bf16x3", "tf32x3"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mocks", type=int, default=N_MOCKS, help="mocks in the covariance batch (0: skip)")
+    ap.add_argument("--no-precision", action="store_true", help="skip the per-multipole precision report")
     ap.add_argument("--batch-steps", type=int, default=1, help="timed graph launches of the batch")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
