@@ -353,10 +353,10 @@ def batch_mocks(args, dev, stream, tpcf, flush, rank=0):
 
 
 def gram_flop_per_primary(nb, lmax):
-    """Algorithmic FLOP of the Gram coupling per primary: for every m, the block of
-    n_b (l_max - m + 1) rows, real part only at m = 0, real and imaginary above."""
-    macs = sum((1 if m == 0 else 2) * (nb * (lmax - m + 1)) ** 2 for m in range(lmax + 1))
-    return 2 * macs
+    """Algorithmic FLOP of the Gram coupling per primary: for every m, the
+    symmetric block of n_m = n_b (l_max - m + 1) rows (real part only at m = 0,
+    real and imaginary above), 2 FLOP per multiply-add over the upper triangle."""
+    return sum((1 if m == 0 else 2) * (nb * (lmax - m + 1)) ** 2 for m in range(lmax + 1))
 
 
 def measured_peaks():
@@ -391,9 +391,10 @@ def coupling_report(cfg, alm, wprim, counts, diag, wsp, dev, stream, tpcf, reps=
         t = statistics.median(ms) / 1000.0
         r = {"ms": t * 1000.0, "algorithmic_tflops": flop / t / 1e12}
         if prec != "fp32":
-            # tensor-pipe work is three MMAs per useful MAC; tf32 runs at half the bf16 rate
+            # tensor-pipe work: three MMAs over the full square blocks (twice the
+            # upper-triangle count); tf32 runs at half the bf16 rate
             peak = peaks["bf16_tflops"] * (1.0 if prec == "bf16x3" else 0.5)
-            r["tensor_tflops"] = 3 * flop / t / 1e12
+            r["tensor_tflops"] = 6 * flop / t / 1e12
             r["tensor_peak_tflops"] = peak
             r["tensor_frac"] = r["tensor_tflops"] / peak
             r["peak_note"] = which + (" bf16" if prec == "bf16x3" else " bf16 x 0.5 (nominal tf32/bf16 ratio)")
