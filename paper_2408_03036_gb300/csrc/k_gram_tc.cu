@@ -11,15 +11,20 @@
 // tensor memory; the dropped lo_A lo_B term is below 2^-16 (bf16) or 2^-22 (tf32)
 // of each product.  Partial sums are moved to FP64 every kFlushK K-rows.
 //
-// One CTA owns one m block (one or two 128-row tiles of D, N = n_m padded to a
-// multiple of 16 columns) for one slice of primaries.  Operand tiles of 16 K
-// entries (bf16) or 8 (tf32) are staged in shared memory in the canonical
-// no-swizzle K-major layout (core matrices of 8 rows x 16 bytes; core matrices
-// adjacent in K are 128 bytes apart, adjacent 8-row groups 256 bytes apart),
-// double-buffered; one elected thread issues the MMAs and commits them to an
-// mbarrier per stage.  Every wait is bounded; a timeout latches an error flag,
-// releases tensor memory and returns.
+// The m blocks are packed into 128-row tiles (blocks above 128 rows take two
+// units of 128 rows against all their rows) and the tiles into CTA groups of at
+// most 512 TMEM columns; one CTA covers its group for one slice of primaries, so
+// a primary's row of a_l^m is read once per group.  A stage holds 16 primaries
+// (8 for tf32) x (real, imaginary part) of every staged row, written as 16-byte
+// core-matrix rows of the canonical no-swizzle K-major layout (core matrices
+// adjacent in K 128 bytes apart, 8-row groups KS/8 x 128 bytes apart), and is
+// double-buffered: threads stage one buffer while the tensor cores read the
+// other.  One elected thread issues the MMAs and commits them to an mbarrier
+// per buffer.  Every wait is bounded; a timeout latches an error flag, waits for
+// the MMAs in flight, releases tensor memory and returns.
+#include <algorithm>
 #include <cstdint>
+#include <cstring>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -29,7 +34,7 @@ namespace tpcf {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kRowTile = 128;                 // M of every MMA (TMEM lanes)
 constexpr int kStageBytesRow = 32;            // one K step = 32 bytes per operand row
 constexpr long long kWaitLimit = 1ll << 26;   // polls of an mbarrier before giving up
@@ -134,6 +139,17 @@ __device__ __forceinline__ void split_bf16(float x, uint16_t &hi, uint16_t &lo)
     lo = __bfloat16_as_ushort(l);
 }
 
+// Two values at once: hi = bf16x2(a, b) rounded to nearest, lo = bf16x2 of the
+// exact FP32 remainders; element a in the low half (lower K index).
+__device__ __forceinline__ void split_bf16x2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
 __device__ __forceinline__ uint32_t to_tf32(float x)
 {
     uint32_t r;
@@ -147,14 +163,37 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo)
     lo = to_tf32(x - __uint_as_float(hi));
 }
 
-// Byte offset of element (row, k) of a staged tile (k < 16 for bf16, < 8 for tf32).
-template <bool TF32>
-__device__ __forceinline__ uint32_t tile_off(int row, int k)
-{
-    const int per = TF32 ? 4 : 8;   // elements per 16-byte core-matrix row
-    const int esz = TF32 ? 4 : 2;
-    return (uint32_t)(((row >> 3) * 2 + k / per) * 128 + (row & 7) * 16 + (k % per) * esz);
-}
+constexpr int kMaxM = TPCF_MAX_LMAX + 1;
+constexpr int kMaxUnits = 2 * kMaxM;
+constexpr int kMaxRows = 384;                 // staged operand rows per CTA (two stages fit)
+
+// One MMA target: D[128 x n] at TMEM column tmem_col = A rows a_row.. (128) times
+// B rows b_row.. (n), both in the CTA's staged rows; part_off locates the unit's
+// [128][n] FP64 block in every slice's partial sums.
+struct TcUnit {
+    int a_row, b_row, n, tmem_col;
+    long long part_off;
+};
+// Staged rows row .. row + rows - 1 hold the m block (rows = n_b (l_max - m + 1)).
+struct TcSeg {
+    int row, m, rows;
+};
+struct TcGroup {
+    int unit0, n_units, seg0, n_segs, rows_alloc, tmem_alloc;
+};
+// G_m[i][j] = D_{unit_lo}[off + i][off + j] (one tile) or, for blocks above 128
+// rows, D_{unit_lo}[i][j] for i < 128 and D_{unit_hi}[i - 128][j].
+struct TcMap {
+    int unit_lo, unit_hi, off;
+};
+struct TcPlan {
+    int n_groups, n_units, n_segs;
+    TcGroup g[kMaxM];
+    TcUnit u[kMaxUnits];
+    TcSeg s[kMaxM];
+    TcMap map[kMaxM];
+    long long slice_size;   // doubles of partial sums per slice
+};
 
 struct TcParams {
     const float *alm;
@@ -163,58 +202,154 @@ struct TcParams {
     int nb, lmax;
     int64_t per_slice;    // primaries per slice
     int n_slices;
-    double *partial;      // [n_slices][sum over m of rt_m * 128 * N_m]
+    double *partial;      // [n_slices][slice_size], zeroed before the launch
     int *err;
+    TcPlan plan;
 };
-
-__device__ __forceinline__ int harm_index(int l, int m, int part)
-{
-    return l * l + (m == 0 ? 0 : 2 * m - 1 + part);
-}
 
 __host__ __device__ inline int pad16(int n) { return (n + 15) / 16 * 16; }
 
-__host__ __device__ inline int64_t partial_offset(int nb, int lmax, int m)
+// Packs the m blocks into CTA groups.  Blocks above 128 rows take two 128-row
+// units against all their rows; smaller blocks share 128-row tiles (first fit,
+// largest first), whose unit computes the tile's full square (cross-block entries
+// are not used).  A group holds at most 512 TMEM columns and kMaxRows staged rows.
+bool make_tc_plan(int nb, int lmax, TcPlan &P)
 {
-    int64_t off = 0;
-    for (int k = 0; k < m; ++k) {
-        const int n = nb * (lmax - k + 1);
-        off += (int64_t)((n + kRowTile - 1) / kRowTile) * kRowTile * pad16(n);
+    std::memset(&P, 0, sizeof(P));
+    struct Item { int rows, cols; bool big; int ms[kMaxM], mo[kMaxM], nm; };
+    Item items[kMaxM];
+    int ni = 0;
+    int order[kMaxM];
+    for (int m = 0; m <= lmax; ++m) order[m] = m;   // n_m decreases with m
+    for (int k = 0; k <= lmax; ++k) {
+        const int m = order[k];
+        const int n = nb * (lmax - m + 1);
+        if (n > 256) return false;
+        if (n > 128) {
+            Item &it = items[ni++];
+            it.rows = n; it.cols = 2 * pad16(n); it.big = true; it.nm = 1; it.ms[0] = m; it.mo[0] = 0;
+            continue;
+        }
+        int t = -1;
+        for (int q = 0; q < ni; ++q)
+            if (!items[q].big && items[q].rows + n <= 128) { t = q; break; }
+        if (t < 0) {
+            t = ni++;
+            items[t].rows = 0; items[t].big = false; items[t].nm = 0;
+        }
+        Item &it = items[t];
+        it.ms[it.nm] = m; it.mo[it.nm] = it.rows; ++it.nm;
+        it.rows += n;
+        it.cols = pad16(it.rows);
     }
-    return off;
+    // groups: first fit in item order (largest first)
+    int grp_of[kMaxM], g_cols[kMaxM], g_rows[kMaxM], g_alloc[kMaxM];
+    int ng = 0;
+    for (int q = 0; q < ni; ++q) {
+        const Item &it = items[q];
+        const int r8 = (it.rows + 7) / 8 * 8;
+        int g = -1;
+        for (int h = 0; h < ng; ++h) {
+            const int start = g_rows[h];
+            const int need = std::max(g_alloc[h], std::max(start + r8, start + (it.big ? 256 : 128)));
+            if (g_cols[h] + it.cols <= 512 && need <= kMaxRows) { g = h; break; }
+        }
+        if (g < 0) {
+            g = ng++;
+            g_cols[g] = 0; g_rows[g] = 0; g_alloc[g] = 0;
+        }
+        const int start = g_rows[g];
+        g_alloc[g] = std::max(g_alloc[g], std::max(start + r8, start + (it.big ? 256 : 128)));
+        if (g_alloc[g] > kMaxRows) return false;
+        g_rows[g] = start + r8;
+        g_cols[g] += it.cols;
+        grp_of[q] = g;
+    }
+    // units and segments, group by group
+    long long part = 0;
+    for (int g = 0; g < ng; ++g) {
+        TcGroup &G = P.g[g];
+        G.unit0 = P.n_units; G.seg0 = P.n_segs;
+        int row = 0, col = 0;
+        for (int q = 0; q < ni; ++q) {
+            if (grp_of[q] != g) continue;
+            const Item &it = items[q];
+            const int n = pad16(it.rows);
+            if (it.big) {
+                const int m = it.ms[0];
+                P.map[m] = {P.n_units, P.n_units + 1, 0};
+                P.u[P.n_units++] = {row, row, n, col, part};
+                part += 128LL * n;
+                P.u[P.n_units++] = {row + 128, row, n, col + n, part};
+                part += 128LL * n;
+                col += 2 * n;
+                P.s[P.n_segs++] = {row, m, it.rows};
+            } else {
+                for (int j = 0; j < it.nm; ++j) {
+                    P.map[it.ms[j]] = {P.n_units, -1, it.mo[j]};
+                    P.s[P.n_segs++] = {row + it.mo[j], it.ms[j], nb * (lmax - it.ms[j] + 1)};
+                }
+                P.u[P.n_units++] = {row, row, n, col, part};
+                part += 128LL * n;
+                col += n;
+            }
+            row += (it.rows + 7) / 8 * 8;
+        }
+        G.n_units = P.n_units - G.unit0;
+        G.n_segs = P.n_segs - G.seg0;
+        G.rows_alloc = g_alloc[g];
+        int alloc = 32;
+        while (alloc < col) alloc <<= 1;
+        G.tmem_alloc = alloc;
+    }
+    P.n_groups = ng;
+    P.slice_size = part;
+    return true;
 }
 
 template <bool TF32>
 __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const TcParams p)
 {
+    constexpr int KP = TF32 ? 8 : 16;          // primaries per stage
+    constexpr int KS = 2 * KP;                 // K entries per stage (real and imaginary part)
+    constexpr int ESZ = TF32 ? 4 : 2;
+    constexpr int KSTEP = TF32 ? 8 : 16;       // K per MMA
+    constexpr int NKS = KS / KSTEP;
+    constexpr int PER_CM = 16 / ESZ;           // elements per 16-byte core-matrix row
+    constexpr uint32_t SBO = (KS / PER_CM) * 128;   // bytes between 8-row groups
+    constexpr int FLUSH_P = 512;               // primaries (1024 K rows) per FP32 accumulation run
+
     extern __shared__ __align__(128) unsigned char smem[];
-    const int m = blockIdx.x;
+    const TcGroup G = p.plan.g[blockIdx.x];
     const int slice = blockIdx.y;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int nb = p.nb, lmax = p.lmax;
-    const int nlm = (lmax + 1) * (lmax + 1);
-    const int n_m = nb * (lmax - m + 1);
-    const int RT = (n_m + kRowTile - 1) / kRowTile;   // row tiles (1 or 2)
-    const int N = pad16(n_m);
-    const int parts = m == 0 ? 1 : 2;
-    const int KS = TF32 ? 8 : 16;                      // K entries per MMA step
-    const int64_t i0 = (int64_t)slice * p.per_slice;
-    const int64_t i1 = min(p.K, i0 + p.per_slice);
-    const int64_t krows = (i1 > i0) ? (i1 - i0) * parts : 0;
-    const int64_t nsteps = (krows + KS - 1) / KS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nb = p.nb, nlm = (p.lmax + 1) * (p.lmax + 1);
+    const int R = G.rows_alloc;
+    const uint32_t op_bytes = (uint32_t)R * KS * ESZ;
+    const uint32_t stage_bytes = 4 * op_bytes;        // A_hi, A_lo, B_hi, B_lo
+    int4 *rowinfo = reinterpret_cast<int4 *>(smem + 2 * stage_bytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes + 16 * R);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * stage_bytes + 16 * R + 16);
+    volatile int *s_abort = reinterpret_cast<int *>(smem + 2 * stage_bytes + 16 * R + 20);
 
-    // stage layout: A_hi, A_lo (RT*128 rows), B_hi, B_lo (N rows); 32 bytes per row
-    const uint32_t a_bytes = (uint32_t)RT * kRowTile * kStageBytesRow;
-    const uint32_t b_bytes = (uint32_t)N * kStageBytesRow;
-    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
-    unsigned char *stage0 = smem;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);   // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * stage_bytes + 16);
-    int *s_abort = reinterpret_cast<int *>(smem + 2 * stage_bytes + 20);
+    const int64_t i_beg = (int64_t)slice * p.per_slice;
+    const int64_t i_end = min(p.K, i_beg + p.per_slice);
+    const int64_t nst = i_end > i_beg ? (i_end - i_beg + KP - 1) / KP : 0;
 
-    uint32_t ncols = 32;
-    while (ncols < (uint32_t)(RT * N)) ncols <<= 1;
-
+    // row table; unused rows stay zero in both stages for the whole launch
+    for (int r = tid; r < R; r += kThreads) {
+        int4 ri = make_int4(0, -1, 0, 0);
+        for (int q = 0; q < G.n_segs; ++q) {
+            const TcSeg sg = p.plan.s[G.seg0 + q];
+            if (r >= sg.row && r < sg.row + sg.rows) {
+                const int within = r - sg.row, l = sg.m + within / nb;
+                ri = make_int4(l * l + (sg.m ? 2 * sg.m - 1 : 0), sg.m ? l * l + 2 * sg.m : -1, within % nb, 1);
+            }
+        }
+        rowinfo[r] = ri;
+    }
+    for (uint32_t q = tid; q < 2 * stage_bytes / 16; q += kThreads)
+        reinterpret_cast<uint4 *>(smem)[q] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) {
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
@@ -223,153 +358,198 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const TcParams p)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(ncols));
+                     "r"(G.tmem_alloc));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, kRowTile, N);
-    double *part_out = p.partial + (int64_t)slice * partial_offset(nb, lmax, lmax + 1) + partial_offset(nb, lmax, m);
+    double *part = p.partial + (int64_t)slice * p.plan.slice_size;
 
     uint32_t phase[2] = {0u, 0u};
     bool used[2] = {false, false};
-    bool ok = true;
-    int64_t since_flush = 0;
-    bool acc_on = false;
+    bool acc_on = false, ok = true;
+    int since = 0;
 
-    // FP32 tensor-memory partials -> this slice's FP64 partial block, then restart accumulation
-    auto flush = [&](bool first) {
-        // all MMAs committed so far must have landed
-        for (int s = 0; s < 2; ++s)
-            if (used[s]) {
-                if (tid == 0 && !mbar_wait(&bars[s], phase[s] ^ 1u)) *s_abort = 1;
-            }
+    // TMEM (FP32) -> this slice's FP64 partial sums (all threads)
+    auto flush = [&]() {
+        if (tid == 0)
+            for (int s = 0; s < 2; ++s)
+                if (used[s] && !mbar_wait(&bars[s], phase[s] ^ 1u)) *s_abort = 1;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        used[0] = used[1] = false;
         if (*s_abort) return;
-        if (warp < 4) {
-            const int lane_base = 32 * warp;
-            const int row_in_tile = lane_base + (tid & 31);
-            for (int rt = 0; rt < RT; ++rt) {
-                for (int c0 = 0; c0 < N; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(rt * N + c0), v);
-                    double *dst = part_out + ((int64_t)(rt * kRowTile + row_in_tile)) * N + c0;
+        // warp w reads TMEM lanes 32 (w % 4) ..; the warps sharing a lane quarter split the columns
+        constexpr int NSETS = kThreads / 128;
+        const int quarter = warp & 3, set = warp >> 2;
+        const int row = 32 * quarter + lane;
+        for (int q = 0; q < G.n_units; ++q) {
+            const TcUnit u = p.plan.u[G.unit0 + q];
+            double *dst = part + u.part_off + (int64_t)row * u.n;
+            for (int c0 = 16 * set; c0 < u.n; c0 += 16 * NSETS) {
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(u.tmem_col + c0), v);
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) dst[q] = first ? (double)v[q] : dst[q] + (double)v[q];
-                }
+                for (int j = 0; j < 16; ++j) dst[c0 + j] += (double)v[j];
             }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        acc_on = false;
     };
 
-    bool first_flush = true;
-    for (int64_t st = 0; st < nsteps && ok; ++st) {
-        const int s = (int)(st & 1);
-        unsigned char *stg = stage0 + s * stage_bytes;
-        // the MMAs that last read this stage must be done before it is rewritten
-        if (used[s]) {
-            if (tid == 0 && !mbar_wait(&bars[s], phase[s] ^ 1u)) *s_abort = 1;
+    // software pipeline: the values of stage st + 1 are loaded into registers while
+    // stage st is written to shared memory and its MMAs are issued.  A thread's
+    // items (octet o of row r) are the same in every stage: their source columns
+    // and destination offsets are computed once.
+    constexpr int OCT = KP / 4;                                  // octets per row and stage
+    constexpr int MAXI = (kMaxRows * OCT + kThreads - 1) / kThreads;
+    const int n_items = R * OCT;
+    const int64_t RL = (int64_t)nb * nlm;                        // floats per primary
+    int it_col[MAXI], it_dsin[MAXI], it_o[MAXI];
+    uint32_t it_off[MAXI];
+    bool it_on[MAXI];
+#pragma unroll
+    for (int it = 0; it < MAXI; ++it) {
+        const int item = tid + it * kThreads;
+        const int r = item % R, o = item / R;
+        const int4 ri = item < n_items ? rowinfo[r] : make_int4(0, -1, 0, 0);
+        it_on[it] = item < n_items && ri.w;
+        it_col[it] = ri.z * nlm + ri.x;
+        it_dsin[it] = ri.y >= 0 ? ri.y - ri.x : -1;
+        it_o[it] = o;
+        it_off[it] = TF32 ? (uint32_t)(((r >> 3) * (KS / 4) + (8 * o) / 4) * 128 + (r & 7) * 16)
+                          : (uint32_t)(((r >> 3) * (KS / 8) + o) * 128 + (r & 7) * 16);
+    }
+    float xv[MAXI][8], wq[MAXI][4];
+    auto load_stage = [&](int64_t st) {
+        const int64_t i0 = i_beg + st * KP;
+#pragma unroll
+        for (int it = 0; it < MAXI; ++it) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int64_t i = i0 + 4 * it_o[it] + q;
+                float xc = 0.f, xs = 0.f, wi = 0.f;
+                if (it_on[it] && i < i_end) {
+                    const float *src = p.alm + i * RL + it_col[it];
+                    xc = __ldg(src);
+                    xs = it_dsin[it] >= 0 ? __ldg(src + it_dsin[it]) : 0.f;
+                    wi = p.w ? __ldg(p.w + i) : 1.f;
+                }
+                xv[it][2 * q] = xc;
+                xv[it][2 * q + 1] = xs;
+                wq[it][q] = wi;
+            }
         }
+    };
+    if (nst > 0) load_stage(0);
+
+    for (int64_t st = 0; st < nst; ++st) {
+        const int s = (int)(st & 1);
+        unsigned char *stg = smem + s * stage_bytes;
+        // the MMAs that last read this stage must have completed
+        if (tid == 0 && used[s] && !mbar_wait(&bars[s], phase[s] ^ 1u)) *s_abort = 1;
         __syncthreads();
         if (*s_abort) { ok = false; break; }
-        // stage KS K-entries: element (row, k) for rows < RT*128 (A) and < N (B)
-        const int64_t k0 = st * KS;
-        const int rows_a = RT * kRowTile;
-        for (int e = tid; e < rows_a * KS; e += kThreads) {
-            const int row = e / KS, k = e % KS;
-            const int64_t kk = k0 + k;
-            float x = 0.f, wx = 0.f;
-            if (row < n_m && kk < krows) {
-                const int64_t i = i0 + kk / parts;
-                const int part = (int)(kk % parts);
-                const int l = m + row / nb, b = row % nb;
-                x = p.alm[(i * nb + b) * nlm + harm_index(l, m, part)];
-                wx = p.w ? p.w[i] * x : x;
+        // stage: item (octet o, row r) = 8 K entries (4 primaries x real/imaginary) of row r
+#pragma unroll
+        for (int it = 0; it < MAXI; ++it) {
+            if (!it_on[it]) continue;
+            float wv[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                wv[2 * q] = wq[it][q] * xv[it][2 * q];
+                wv[2 * q + 1] = wq[it][q] * xv[it][2 * q + 1];
             }
-            const uint32_t off = tile_off<TF32>(row, k);
+            const uint32_t off = it_off[it];
             if (TF32) {
-                uint32_t h, lo;
-                split_tf32(wx, h, lo);
-                *reinterpret_cast<uint32_t *>(stg + off) = h;
-                *reinterpret_cast<uint32_t *>(stg + a_bytes + off) = lo;
-                if (row < N) {
-                    split_tf32(x, h, lo);
-                    *reinterpret_cast<uint32_t *>(stg + 2 * a_bytes + off) = h;
-                    *reinterpret_cast<uint32_t *>(stg + 2 * a_bytes + b_bytes + off) = lo;
+                uint32_t bh[8], bl[8], ah[8], al[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    split_tf32(xv[it][j], bh[j], bl[j]);
+                    split_tf32(wv[j], ah[j], al[j]);
+                }
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    const uint32_t o2 = off + 128u * half;   // the next core matrix along K
+                    const int j0 = 4 * half;
+                    *reinterpret_cast<uint4 *>(stg + o2) = make_uint4(ah[j0], ah[j0 + 1], ah[j0 + 2], ah[j0 + 3]);
+                    *reinterpret_cast<uint4 *>(stg + op_bytes + o2) = make_uint4(al[j0], al[j0 + 1], al[j0 + 2], al[j0 + 3]);
+                    *reinterpret_cast<uint4 *>(stg + 2 * op_bytes + o2) = make_uint4(bh[j0], bh[j0 + 1], bh[j0 + 2], bh[j0 + 3]);
+                    *reinterpret_cast<uint4 *>(stg + 3 * op_bytes + o2) = make_uint4(bl[j0], bl[j0 + 1], bl[j0 + 2], bl[j0 + 3]);
                 }
             } else {
-                uint16_t h, lo;
-                split_bf16(wx, h, lo);
-                *reinterpret_cast<uint16_t *>(stg + off) = h;
-                *reinterpret_cast<uint16_t *>(stg + a_bytes + off) = lo;
-                if (row < N) {
-                    split_bf16(x, h, lo);
-                    *reinterpret_cast<uint16_t *>(stg + 2 * a_bytes + off) = h;
-                    *reinterpret_cast<uint16_t *>(stg + 2 * a_bytes + b_bytes + off) = lo;
+                uint32_t bh[4], bl[4], ah[4], al[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    split_bf16x2(xv[it][2 * j], xv[it][2 * j + 1], bh[j], bl[j]);
+                    split_bf16x2(wv[2 * j], wv[2 * j + 1], ah[j], al[j]);
                 }
+                *reinterpret_cast<uint4 *>(stg + off) = make_uint4(ah[0], ah[1], ah[2], ah[3]);
+                *reinterpret_cast<uint4 *>(stg + op_bytes + off) = make_uint4(al[0], al[1], al[2], al[3]);
+                *reinterpret_cast<uint4 *>(stg + 2 * op_bytes + off) = make_uint4(bh[0], bh[1], bh[2], bh[3]);
+                *reinterpret_cast<uint4 *>(stg + 3 * op_bytes + off) = make_uint4(bl[0], bl[1], bl[2], bl[3]);
             }
         }
+        if (st + 1 < nst) load_stage(st + 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t base = smem_u32(stg);
-            const uint64_t bhi = make_desc(base + 2 * a_bytes, 128, 256);
-            const uint64_t blo = make_desc(base + 2 * a_bytes + b_bytes, 128, 256);
-            for (int rt = 0; rt < RT; ++rt) {
-                const uint32_t aoff = (uint32_t)rt * kRowTile * kStageBytesRow;
-                const uint64_t ahi = make_desc(base + aoff, 128, 256);
-                const uint64_t alo = make_desc(base + a_bytes + aoff, 128, 256);
-                const uint32_t d = tmem + (uint32_t)(rt * N);
-                mma_issue<TF32>(d, ahi, bhi, idesc, acc_on ? 1u : 0u);
-                mma_issue<TF32>(d, ahi, blo, idesc, 1u);
-                mma_issue<TF32>(d, alo, bhi, idesc, 1u);
+            for (int q = 0; q < G.n_units; ++q) {
+                const TcUnit u = p.plan.u[G.unit0 + q];
+                const uint32_t idesc = make_idesc(TF32 ? 2u : 1u, kRowTile, u.n);
+                const uint32_t d = tmem + (uint32_t)u.tmem_col;
+                const uint32_t aoff = (uint32_t)(u.a_row >> 3) * SBO, boff = (uint32_t)(u.b_row >> 3) * SBO;
+#pragma unroll
+                for (int ks = 0; ks < NKS; ++ks) {
+                    const uint32_t kb = 256u * ks;
+                    const uint64_t ahi = make_desc(base + aoff + kb, 128, SBO);
+                    const uint64_t alo = make_desc(base + op_bytes + aoff + kb, 128, SBO);
+                    const uint64_t bhi = make_desc(base + 2 * op_bytes + boff + kb, 128, SBO);
+                    const uint64_t blo = make_desc(base + 3 * op_bytes + boff + kb, 128, SBO);
+                    mma_issue<TF32>(d, ahi, bhi, idesc, (acc_on || ks > 0) ? 1u : 0u);
+                    mma_issue<TF32>(d, ahi, blo, idesc, 1u);
+                    mma_issue<TF32>(d, alo, bhi, idesc, 1u);
+                }
             }
             mma_commit(&bars[s]);
         }
         used[s] = true;
         phase[s] ^= 1u;
         acc_on = true;
-        since_flush += KS;
-        if (since_flush >= kFlushK) {
-            flush(first_flush);
-            first_flush = false;
-            since_flush = 0;
-            acc_on = false;
-            used[0] = used[1] = false;
+        since += KP;
+        if (since >= FLUSH_P) {
+            flush();
+            since = 0;
             if (*s_abort) { ok = false; break; }
         }
     }
-    if (ok && acc_on) {
-        flush(first_flush);
-        first_flush = false;
-    }
-    if (first_flush && ok) {   // empty slice: the partial block must still read as zero
-        for (int64_t q = tid; q < (int64_t)RT * kRowTile * N; q += kThreads) part_out[q] = 0.0;
-    }
+    if (ok && acc_on) flush();
     if (*s_abort || !ok) {
-        if (tid == 0) atomicCAS(p.err, 0, DEV_ERR_TIMEOUT);
-        // wait (bounded) for anything still in flight before releasing TMEM
-        for (int s = 0; s < 2; ++s)
-            if (used[s] && tid == 0) mbar_wait(&bars[s], phase[s] ^ 1u);
+        if (tid == 0) {
+            atomicCAS(p.err, 0, DEV_ERR_TIMEOUT);
+            // wait (bounded) for anything still in flight before releasing TMEM
+            for (int s = 0; s < 2; ++s)
+                if (used[s]) mbar_wait(&bars[s], phase[s] ^ 1u);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.tmem_alloc));
 }
 
-// G_m[row][col] = sum over slices of the partial blocks (rows/cols < n_m).
-__global__ void k_gram_tc_reduce(const double *partial, int n_slices, int nb, int lmax, double *G)
+// G_m[i][j] = sum over slices of the unit entries that hold it.
+__global__ void k_gram_tc_reduce(const double *partial, int n_slices, long long slice_size, int nb, int lmax,
+                                 TcPlan plan, double *G)
 {
-    const int64_t per_slice = partial_offset(nb, lmax, lmax + 1);
     const int64_t total = gram_offset(nb, lmax, lmax + 1);
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
@@ -377,44 +557,36 @@ __global__ void k_gram_tc_reduce(const double *partial, int n_slices, int nb, in
         while (m < lmax && idx >= gram_offset(nb, lmax, m + 1)) ++m;
         const int n_m = nb * (lmax - m + 1);
         const int64_t r = idx - gram_offset(nb, lmax, m);
-        const int row = (int)(r / n_m), col = (int)(r % n_m);
-        const int64_t src = partial_offset(nb, lmax, m) + (int64_t)row * pad16(n_m) + col;
+        const int i = (int)(r / n_m), j = (int)(r % n_m);
+        const TcMap mp = plan.map[m];
+        int unit = mp.unit_lo, ri = mp.off + i;
+        const int cj = mp.off + j;
+        if (mp.unit_hi >= 0 && i >= 128) {
+            unit = mp.unit_hi;
+            ri = i - 128;
+        }
+        const TcUnit u = plan.u[unit];
+        const int64_t src = u.part_off + (int64_t)ri * u.n + cj;
         double s = 0.0;
-        for (int sl = 0; sl < n_slices; ++sl) s += partial[sl * per_slice + src];
+        for (int sl = 0; sl < n_slices; ++sl) s += partial[sl * slice_size + src];
         G[idx] = s;
     }
 }
 
 }  // namespace
 
-size_t gram_tc_smem(int nb, int lmax)
-{
-    size_t best = 0;
-    for (int m = 0; m <= lmax; ++m) {
-        const int n_m = nb * (lmax - m + 1);
-        const int RT = (n_m + kRowTile - 1) / kRowTile;
-        const size_t stage = 2 * (size_t)RT * kRowTile * kStageBytesRow + 2 * (size_t)pad16(n_m) * kStageBytesRow;
-        best = stage > best ? stage : best;
-    }
-    return 2 * best + 64;
-}
-
 cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, int lmax, bool tf32, double *G,
                            int *err, int sms, cudaStream_t st)
 {
-    // TMEM columns: RT * N per CTA must fit 512; two 128-row tiles of N <= 256
-    for (int m = 0; m <= lmax; ++m) {
-        const int n_m = nb * (lmax - m + 1);
-        const int RT = (n_m + kRowTile - 1) / kRowTile;
-        if (RT > 2 || RT * pad16(n_m) > 512 || pad16(n_m) > 256) return cudaErrorInvalidValue;
-    }
+    TcParams p;
+    if (!make_tc_plan(nb, lmax, p.plan)) return cudaErrorInvalidValue;
     if (K <= 0) return cudaMemsetAsync(G, 0, gram_offset(nb, lmax, lmax + 1) * sizeof(double), st);
-    int slices = (sms + lmax) / (lmax + 1);
+    const int ng = p.plan.n_groups;
+    int slices = sms / ng;
     if (slices < 1) slices = 1;
     const int64_t min_per = 1024;
     if ((K + slices - 1) / slices < min_per) slices = (int)((K + min_per - 1) / min_per);
     if (slices < 1) slices = 1;
-    TcParams p;
     p.alm = alm;
     p.w = w;
     p.K = K;
@@ -423,10 +595,14 @@ cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, 
     p.per_slice = (K + slices - 1) / slices;
     p.n_slices = slices;
     p.err = err;
-    const int64_t per = partial_offset(nb, lmax, lmax + 1);
-    // at least 116 KB so that one CTA owns an SM: tensor-memory allocations never wait
-    size_t smem = gram_tc_smem(nb, lmax);
+    int rmax = 0;
+    for (int g = 0; g < ng; ++g) rmax = std::max(rmax, p.plan.g[g].rows_alloc);
+    const int ks = tf32 ? 16 : 32, esz = tf32 ? 4 : 2;
+    // two stages of four operands, the row table, barriers; at least 116 KB so that
+    // one CTA owns an SM and tensor-memory allocations never wait
+    size_t smem = 2 * 4 * (size_t)rmax * ks * esz + 16 * (size_t)rmax + 64;
     if (smem < 116 * 1024) smem = 116 * 1024;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     static std::atomic<unsigned long long> attr_done[2];   // devices whose attribute is set
     const unsigned long long bit = device_bit();
     cudaError_t e;
@@ -436,18 +612,22 @@ cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, 
         if (e != cudaSuccess) return e;
         attr_done[tf32].fetch_or(bit, std::memory_order_acq_rel);
     }
-    e = cudaMallocAsync((void **)&p.partial, (size_t)slices * per * sizeof(double), st);
+    const size_t pbytes = (size_t)slices * p.plan.slice_size * sizeof(double);
+    e = cudaMallocAsync((void **)&p.partial, pbytes, st);
     if (e != cudaSuccess) return e;
-    const dim3 grid(lmax + 1, slices);
-    if (tf32) k_gram_tc<true><<<grid, kThreads, smem, st>>>(p);
-    else k_gram_tc<false><<<grid, kThreads, smem, st>>>(p);
-    note_launch();
-    e = cudaGetLastError();
+    e = cudaMemsetAsync(p.partial, 0, pbytes, st);
+    if (e == cudaSuccess) {
+        const dim3 grid(ng, slices);
+        if (tf32) k_gram_tc<true><<<grid, kThreads, smem, st>>>(p);
+        else k_gram_tc<false><<<grid, kThreads, smem, st>>>(p);
+        note_launch();
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
         const int64_t tot = gram_offset(nb, lmax, lmax + 1);
         int g = (int)((tot + 255) / 256);
         if (g > 4096) g = 4096;
-        k_gram_tc_reduce<<<g, 256, 0, st>>>(p.partial, slices, nb, lmax, G);
+        k_gram_tc_reduce<<<g, 256, 0, st>>>(p.partial, slices, p.plan.slice_size, nb, lmax, p.plan, G);
         note_launch();
         e = cudaGetLastError();
     }

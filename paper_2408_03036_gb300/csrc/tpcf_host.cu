@@ -528,7 +528,7 @@ int couple(const tpcf_config *c, const float *alm, const float *w, const int32_t
     } else {
         cudaError_t e = couple_gram_tc(alm, w, K, nb, L, c->precision == TPCF_PREC_TF32X3, G, ds->err, ds->sms, st);
         if (e == cudaErrorInvalidValue)
-            return fail(TPCF_ERR_UNSUPPORTED, "tensor-core Gram: an m block exceeds two 128-row tiles of 256 columns");
+            return fail(TPCF_ERR_UNSUPPORTED, "tensor-core Gram: no tile plan for this shape");
         CK(e);
     }
     CK(assemble_nnn(G, diag, wsp, nb, L, c->remove_self, gaunt, nnn, st));
@@ -1084,7 +1084,7 @@ int tpcf_batch_run(tpcf_batch b, const uint32_t *xyz, const float *w, double *ze
                 cudaError_t e = couple_gram_tc(alm_k, b->wprim + r0, K, nb, L, c->precision == TPCF_PREC_TF32X3, b->G,
                                                ds->err, ds->sms, st);
                 if (e == cudaErrorInvalidValue)
-                    return fail(TPCF_ERR_UNSUPPORTED, "tensor-core Gram: an m block exceeds two 128-row tiles");
+                    return fail(TPCF_ERR_UNSUPPORTED, "tensor-core Gram: no tile plan for this shape");
                 CK(e);
             }
             CK(assemble_nnn(b->G, b->diag + (size_t)k * ndiag * nb, b->wsp + (size_t)k * L1 * nb, nb, L,

@@ -235,3 +235,33 @@ def test_tensor_core_coupling_open_volume_and_two_row_tiles(gpu, ora, prec):
     g.precision = prec
     xyz, w = synth.poisson(6000, 1)
     compare(gpu, g, o, ora, xyz, w, tol=TOL_MIXED)
+
+
+@pytest.mark.parametrize("nb,lmax", [(32, 4), (25, 4), (7, 6), (1, 0), (3, 2), (32, 6), (13, 5)])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_tensor_core_tile_plans_match_fp32_gram(gpu, prec, nb, lmax):
+    """Every packing of the m blocks into tensor-core tiles and CTA groups (blocks
+    above 128 rows, shared tiles, several groups) against the FP32 Gram on the
+    same per-primary sums, block by block."""
+    import dataclasses
+    import torch
+    cfg = tpcf.Config(r_min=10.0, r_max=90.0, n_bins=nb, l_max=lmax, Ls=(0,), box=400.0)
+    xyz, w = synth.lognormal(5000, 400.0, 21, mesh=64)
+    wt = np.random.default_rng(3).uniform(-1.0, 2.0, size=w.shape[0]).astype(np.float32)
+    grid = tpcf.Grid(cfg, xyz, wt)
+    alm, counts, diag, wsp, _ = tpcf.accumulate_alm(grid, cfg, prim_xyz=xyz, prim_w=wt)
+    pw = torch.from_numpy(wt).cuda()
+    ref, tref = tpcf.couple_multipoles(cfg, alm, pw, counts, diag, wsp)
+    got, tgot = tpcf.couple_multipoles(dataclasses.replace(cfg, precision=prec), alm, pw, counts, diag, wsp)
+    tpcf.stream_status()
+    assert torch.equal(tref, tgot)
+    ref, got = ref.cpu().numpy(), got.cpu().numpy()
+    worst = 0.0
+    for m in range(lmax + 1):
+        for l1 in range(m, lmax + 1):
+            for l2 in range(m, lmax + 1):
+                den = np.abs(ref[m, l1, l2]).max()
+                if den > 0:
+                    worst = max(worst, np.abs(got[m, l1, l2] - ref[m, l1, l2]).max() / den)
+    assert worst <= 1e-4, worst
+    grid.close()
