@@ -28,7 +28,10 @@ EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_mult
            "tpcf_accumulate_alm", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
            "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
-           "tpcf_estimate_3pcf_batched", "tpcf_autotune"]
+           "tpcf_estimate_3pcf_batched", "tpcf_autotune",
+           "tpcf_emu_create", "tpcf_emu_destroy", "tpcf_emu_param_count", "tpcf_emu_set_input_box",
+           "tpcf_emu_fit_output_scaling", "tpcf_emu_train_step", "tpcf_emu_gradients", "tpcf_emu_predict",
+           "tpcf_emu_get_params", "tpcf_emu_set_params", "tpcf_emu_get_output_scaling"]
 
 
 class TpcfError(RuntimeError):
@@ -109,6 +112,17 @@ def lib():
             "tpcf_batch_destroy": ([P], ctypes.c_int),
             "tpcf_estimate_3pcf_batched": ([CFG, P, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
             "tpcf_autotune": ([CFG, P, P, I64, P, CFG], ctypes.c_int),
+            "tpcf_emu_create": ([P, ctypes.c_int32, ctypes.c_uint64, P], ctypes.c_int),
+            "tpcf_emu_destroy": ([P], ctypes.c_int),
+            "tpcf_emu_param_count": ([P, P], ctypes.c_int),
+            "tpcf_emu_set_input_box": ([P, P, P], ctypes.c_int),
+            "tpcf_emu_fit_output_scaling": ([P, P, I64, P], ctypes.c_int),
+            "tpcf_emu_train_step": ([P, P, P, I64, ctypes.c_float, P, P], ctypes.c_int),
+            "tpcf_emu_gradients": ([P, P, P, I64, P, P, P], ctypes.c_int),
+            "tpcf_emu_predict": ([P, P, I64, P, P], ctypes.c_int),
+            "tpcf_emu_get_params": ([P, P, P], ctypes.c_int),
+            "tpcf_emu_set_params": ([P, P, P], ctypes.c_int),
+            "tpcf_emu_get_output_scaling": ([P, P, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -396,6 +410,77 @@ def autotune(cfg: Config, xyz, w=None, stream=None, device="cuda") -> Config:
     _check(lib().tpcf_autotune(ctypes.byref(c), _ptr(dx), _ptr(dw), dx.shape[0], _stream(stream),
                                ctypes.byref(out)))
     return dataclasses.replace(cfg, cell_div=out.cell_div, tile_primaries=out.tile_primaries, chunk=out.chunk)
+
+
+class Emulator:
+    """tpcf_emu_*: the MLP emulator of the tree-level 3PCF multipoles
+    (BF16 weights, FP32 accumulation, own forward / backward / Adam kernels)."""
+
+    def __init__(self, widths, seed=0, device="cuda"):
+        import numpy as np
+        self.widths = [int(w) for w in widths]
+        self.device = device
+        arr = np.ascontiguousarray(self.widths, dtype=np.int32)
+        self.handle = ctypes.c_void_p()
+        _check(lib().tpcf_emu_create(_ptr(arr), len(self.widths) - 1, ctypes.c_uint64(seed),
+                                     ctypes.addressof(self.handle)))
+        n = ctypes.c_int64(0)
+        _check(lib().tpcf_emu_param_count(self.handle, ctypes.addressof(n)))
+        self.n_params = n.value
+        self.loss_buf = torch.zeros(1, dtype=torch.float64, device=device)
+
+    def set_input_box(self, lo, hi):
+        import numpy as np
+        lo = np.ascontiguousarray(lo, dtype=np.float32)
+        hi = np.ascontiguousarray(hi, dtype=np.float32)
+        _check(lib().tpcf_emu_set_input_box(self.handle, _ptr(lo), _ptr(hi)))
+
+    def fit_output_scaling(self, y, stream=None):
+        _check(lib().tpcf_emu_fit_output_scaling(self.handle, _ptr(y), y.shape[0], _stream(stream)))
+
+    def output_scaling(self):
+        import numpy as np
+        mu = np.empty(self.widths[-1], dtype=np.float32)
+        sd = np.empty(self.widths[-1], dtype=np.float32)
+        _check(lib().tpcf_emu_get_output_scaling(self.handle, _ptr(mu), _ptr(sd)))
+        return mu, sd
+
+    def train_step(self, x, y, lr, loss=None, stream=None):
+        """One Adam step; the batch loss (before the update) goes to `loss` (a
+        one-element float64 device tensor) when given."""
+        _check(lib().tpcf_emu_train_step(self.handle, _ptr(x), _ptr(y), x.shape[0], ctypes.c_float(lr),
+                                         _ptr(loss), _stream(stream)))
+
+    def gradients(self, x, y, stream=None):
+        g = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        _check(lib().tpcf_emu_gradients(self.handle, _ptr(x), _ptr(y), x.shape[0], _ptr(g), _ptr(self.loss_buf),
+                                        _stream(stream)))
+        return g, self.loss_buf
+
+    def predict(self, x, out=None, stream=None):
+        if out is None:
+            out = torch.empty((x.shape[0], self.widths[-1]), dtype=torch.float32, device=self.device)
+        _check(lib().tpcf_emu_predict(self.handle, _ptr(x), x.shape[0], _ptr(out), _stream(stream)))
+        return out
+
+    def get_params(self, stream=None):
+        p = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        _check(lib().tpcf_emu_get_params(self.handle, _ptr(p), _stream(stream)))
+        return p
+
+    def set_params(self, p, stream=None):
+        _check(lib().tpcf_emu_set_params(self.handle, _ptr(p), _stream(stream)))
+
+    def close(self):
+        if self.handle:
+            _check(lib().tpcf_emu_destroy(self.handle))
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kernel_launches() -> int:
