@@ -269,6 +269,8 @@ def run_ours(args):
         line["mocks_per_hour"] = mocks
     if not args.no_precision:
         line["precision_vs_oracle"] = precision_report(dev, stream, tpcf)
+    if not args.no_emulator:
+        line["emulator"] = emulator_report(dev, stream, tpcf, with_cpu=not args.no_cpu_baseline)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -432,6 +434,64 @@ def precision_report(dev, stream, tpcf):
     return out
 
 
+EMU_WIDTHS = [6, 256, 256, 256, 256, 3150]   # theta -> 15 multipoles x 210 (r1 <= r2) of 20 bins
+
+
+def emulator_report(dev, stream, tpcf, with_cpu=True, steps=2000, batch=512):
+    """The MLP emulator of the tree-level multipoles: training and inference
+    throughput of the project's own kernels (timing only: random parameters in
+    the prior box and synthetic targets), and the plain model's evaluation time
+    per parameter vector on the host cores as its CPU baseline."""
+    import numpy as np
+    import torch
+    lo = np.array([0.5, 1.0, -1.0, 0.6, 0.95, -0.05], np.float32)
+    hi = np.array([1.0, 3.0, 2.0, 1.0, 1.05, 0.05], np.float32)
+    n = 200_000
+    g = torch.Generator(device=dev).manual_seed(3)
+    x = torch.from_numpy(lo).to(dev) + torch.rand((n, 6), device=dev, generator=g) * torch.from_numpy(hi - lo).to(dev)
+    y = torch.randn((n, EMU_WIDTHS[-1]), device=dev, generator=g)
+    emu = tpcf.Emulator(EMU_WIDTHS, seed=1, device=dev)
+    emu.set_input_box(lo, hi)
+    emu.fit_output_scaling(y, stream=stream)
+    batches = [torch.randint(0, n, (batch,), device=dev, generator=g) for _ in range(16)]
+    xb = [x[i].contiguous() for i in batches]
+    yb = [y[i].contiguous() for i in batches]
+    for k in range(20):
+        emu.train_step(xb[k % 16], yb[k % 16], 1e-3, stream=stream)
+    torch.cuda.synchronize(dev)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record(stream)
+    for k in range(steps):
+        emu.train_step(xb[k % 16], yb[k % 16], 1e-3, stream=stream)
+    e.record(stream)
+    torch.cuda.synchronize(dev)
+    t_train = s.elapsed_time(e) / 1000.0
+    out = torch.empty((n, EMU_WIDTHS[-1]), device=dev)
+    emu.predict(x, out=out, stream=stream)
+    torch.cuda.synchronize(dev)
+    s.record(stream)
+    emu.predict(x, out=out, stream=stream)
+    e.record(stream)
+    torch.cuda.synchronize(dev)
+    t_inf = s.elapsed_time(e) / 1000.0
+    tpcf.stream_status(stream)
+    emu.close()
+    per_sample_flop = 2 * sum(a * b for a, b in zip(EMU_WIDTHS[:-1], EMU_WIDTHS[1:]))
+    rep = {"widths": EMU_WIDTHS, "train_samples_per_s": steps * batch / t_train, "batch": batch,
+           "train_tflops": 3 * per_sample_flop * steps * batch / t_train / 1e12,
+           "infer_theta_per_s": n / t_inf, "infer_tflops": per_sample_flop * n / t_inf / 1e12,
+           "note": "BF16 weights, FP32 accumulation, SIMT GEMM kernels; accuracy against the plain model is "
+                   "checked by the emulator tests"}
+    if with_cpu:
+        from oracle import treelevel as T
+        setup = T.ModelSetup()
+        t0 = time.perf_counter()
+        T.model_direct(setup, (0.86, 2.7, 0.8, 0.828, 1.0, 0.0))
+        rep["cpu_baseline"] = {"kind": "plain tree-level model (oracle)", "s_per_theta": time.perf_counter() - t0,
+                               "cores": 1}
+    return rep
+
+
 def fp32_peak_tflops(dev):
     import torch
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -507,6 +567,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mocks", type=int, default=N_MOCKS, help="mocks in the covariance batch (0: skip)")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-multipole precision report")
+    ap.add_argument("--no-emulator", action="store_true", help="skip the emulator throughput report")
     ap.add_argument("--batch-steps", type=int, default=1, help="timed graph launches of the batch")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least three untimed warm-up steps
