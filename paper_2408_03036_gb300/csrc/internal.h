@@ -42,9 +42,8 @@ struct PairParams {
     int P;              // primaries per tile
     int chunk;          // staged pairs per chunk
     unsigned long long E[TPCF_MAX_BINS + 1];
-    float Ef[TPCF_MAX_BINS + 1];
+    float Ef[TPCF_MAX_BINS + 1];  // edges as floats (seed of the bin-share estimate)
     float rmin_u, inv_dr_u;   // float bin estimate b = (sqrt(r2) - rmin_u) * inv_dr_u
-    float r2_lo, r2_hi;       // float prefilter window (conservative)
     float t_off, tdelta;      // t = sqrt(r2) * inv_dr_u + t_off is the bin coordinate; a float t
                               // within tdelta of an integer is decided in exact arithmetic
     float rmax_trim;          // conservative r_max (units) for row trimming

@@ -4,7 +4,7 @@
 
 namespace tpcf {
 
-// COUNTS: integer pair counts only (k_pairs); otherwise the queued harmonic kernel.
+// COUNTS: integer pair counts only (k_counts); otherwise the queued harmonic kernel.
 template <int LMAX, bool COUNTS>
 static cudaError_t launch_one(const PairParams &p, const HarmTables &h, int grid, int block,
                               size_t smem, cudaStream_t st)
@@ -14,13 +14,13 @@ static cudaError_t launch_one(const PairParams &p, const HarmTables &h, int grid
     if (!(attr_done.load(std::memory_order_acquire) & bit)) {
         cudaError_t e;
         if constexpr (COUNTS)
-            e = cudaFuncSetAttribute(k_pairs<0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            e = cudaFuncSetAttribute(k_counts<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         else
             e = cudaFuncSetAttribute(k_pairs_q<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         attr_done.fetch_or(bit, std::memory_order_acq_rel);
     }
-    if constexpr (COUNTS) k_pairs<0, true><<<grid, block, smem, st>>>(p, h);
+    if constexpr (COUNTS) k_counts<0><<<grid, block, smem, st>>>(p);
     else k_pairs_q<LMAX><<<grid, block, smem, st>>>(p, h);
     note_launch();
     return cudaGetLastError();
@@ -35,7 +35,7 @@ cudaError_t launch_pairs_l1(bool counts_only, const PairParams &p, const HarmTab
 
 size_t pairs_smem_l1(bool counts_only, int P, int nb, int s, int chunk, int block)
 {
-    if (counts_only) return (size_t)make_smem_map<0, true>(P, nb, s, chunk, block).total;
+    if (counts_only) return (size_t)make_cmap(P, nb, s).total;
     return (size_t)make_qmap<1>(P, nb, s, chunk, block).total;
 }
 

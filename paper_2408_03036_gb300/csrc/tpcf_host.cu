@@ -440,8 +440,6 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
         p.tdelta = (float)(4.0 * (((c->r_max + dr) / dr) * 5.1e-7 + (c->r_min / dr) * 6e-8
                                   + (c->n_bins + 1.0) * 6e-8));
     }
-    p.r2_lo = (float)((double)p.E[0] * (1.0 - 4e-6));
-    p.r2_hi = (float)((double)p.E[c->n_bins] * (1.0 + 4e-6));
     p.rmax_trim = (float)(c->r_max * u * (1.0 + 1e-5) + 4096.0);
     p.h_u = (float)(kTwo32 / (double)g.nc);
     for (int b = 0; b < c->n_bins; ++b) {
@@ -490,7 +488,8 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
     CK(cudaMallocAsync((void **)&work, sizeof(int), st));
     CK(cudaMemsetAsync(work, 0, sizeof(int), st));
     p.work = work;
-    const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+    // the count kernel is small (about 50 registers, a few KB of shared memory): four CTAs per SM
+    const int per_sm = counts_only ? 4 : (smem <= 110 * 1024 ? 2 : 1);
     int grid = ds->sms * per_sm;
     const int64_t tiles = (n_prim + pl.P - 1) / pl.P;
     if (grid > tiles) grid = (int)tiles;
