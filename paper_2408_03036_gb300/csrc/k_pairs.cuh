@@ -325,17 +325,21 @@ __global__ void __launch_bounds__(256, 2) k_counts(const PairParams p)
             const int rr = (int)(((unsigned)r * (unsigned)stride) % (unsigned)nr);
             const int start = rstart[rr], len = rlen[rr], sl = rslot[rr];
             const int4 pr = sPrim[sl];
-            for (int pos = 0; pos < len; pos += 32) {
-                const int i = pos + lane;
-                const bool valid = i < len;
-                const int4 q = p.rec[start + min(i, len - 1)];
-                const int dx = (int)((uint32_t)q.x - (uint32_t)pr.x);
-                const int dy = (int)((uint32_t)q.y - (uint32_t)pr.y);
-                const int dz = (int)((uint32_t)q.z - (uint32_t)pr.z);
-                const int b = cand_bin(p, sE, nb, valid, dx, dy, dz, (float)dx, (float)dy, (float)dz);
-                const int key = b >= 0 ? sl * nb + b : -1 - lane;   // unique for lanes without a pair
-                const unsigned peers = __match_any_sync(FULL, key);
-                if (b >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[key], __popc(peers));
+            for (int pos = 0; pos < len; pos += 64) {
+                const int i0 = pos + lane, i1 = i0 + 32;
+                const int4 q0 = p.rec[start + min(i0, len - 1)];
+                const int4 q1 = p.rec[start + min(i1, len - 1)];
+                const int dx0 = (int)((uint32_t)q0.x - (uint32_t)pr.x), dx1 = (int)((uint32_t)q1.x - (uint32_t)pr.x);
+                const int dy0 = (int)((uint32_t)q0.y - (uint32_t)pr.y), dy1 = (int)((uint32_t)q1.y - (uint32_t)pr.y);
+                const int dz0 = (int)((uint32_t)q0.z - (uint32_t)pr.z), dz1 = (int)((uint32_t)q1.z - (uint32_t)pr.z);
+                const int b0 = cand_bin(p, sE, nb, i0 < len, dx0, dy0, dz0, (float)dx0, (float)dy0, (float)dz0);
+                const int b1 = cand_bin(p, sE, nb, i1 < len, dx1, dy1, dz1, (float)dx1, (float)dy1, (float)dz1);
+                // keys of both candidates; lanes without a pair get keys no other lane has
+                const int k0 = b0 >= 0 ? sl * nb + b0 : -1 - lane, k1 = b1 >= 0 ? sl * nb + b1 : -33 - lane;
+                const unsigned p0 = __match_any_sync(FULL, k0);
+                if (b0 >= 0 && lane == __ffs(p0) - 1) atomicAdd(&cnt[k0], __popc(p0));
+                const unsigned p1 = __match_any_sync(FULL, k1);
+                if (b1 >= 0 && lane == __ffs(p1) - 1) atomicAdd(&cnt[k1], __popc(p1));
             }
         }
         __syncthreads();
@@ -624,12 +628,24 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         while (nr > 1 && gcd_int(stride, nr) != 1) ++stride;
         int my_start = 0, my_len = 0, my_pos = 0, kb = 0;
         uint32_t px = 0, py = 0, pz = 0;
-        bool done = false, have = false;
-        float4 ent = make_float4(0.f, 0.f, 0.f, 0.f);
-        int ek = 0;
+        // two candidates per lane and step (i and i + 32): independent loads and bins
+        bool done = false, have0 = false, have1 = false;
+        float4 ent0 = make_float4(0.f, 0.f, 0.f, 0.f), ent1 = ent0;
+        int ek0 = 0, ek1 = 0;
+        // appends a pending entry; false if its queue is full (it stays pending)
+        auto append = [&](bool &have, const float4 &ent, int ek) {
+            if (!have) return;
+            const int pos = atomicAdd(&qcnt[par * nkmax + ek], 1);
+            if (pos < qcap[ek]) {
+                queue[qbase[ek] + pos] = ent;
+                have = false;
+            } else {
+                s_flag = 1;   // stays pending until the queues are drained
+            }
+        };
         for (;;) {
             // bit 0: an entry of the warp waits for room; bit 1: a queue is full
-            const unsigned st = __reduce_or_sync(FULL, (have ? 1u : 0u) | (s_flag ? 2u : 0u));
+            const unsigned st = __reduce_or_sync(FULL, (have0 || have1 ? 1u : 0u) | (s_flag ? 2u : 0u));
             const bool fin = done && !(st & 1u);
             if ((st & 2u) || fin) {
                 if (lane == 0) wdone[warp] = fin ? 1 : 0;
@@ -656,29 +672,27 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                     kb = sl * nb;
                     my_pos = 0;
                 }
-                const int i = my_pos + lane;
-                my_pos += 32;
-                const bool valid = i < my_len;
-                const int4 q = p.rec[my_start + min(i, my_len - 1)];
-                const int dx = (int)((uint32_t)q.x - px);
-                const int dy = (int)((uint32_t)q.y - py);
-                const int dz = (int)((uint32_t)q.z - pz);
-                const float fx = (float)dx, fy = (float)dy, fz = (float)dz;
-                const int b = cand_bin(p, sE, nb, valid, dx, dy, dz, fx, fy, fz);
-                const bool ok = b >= 0;
-                have = ok;
-                ent = make_float4(fx, fy, fz, __int_as_float(q.w));
-                ek = kb + b;
+                const int i0 = my_pos + lane, i1 = i0 + 32;
+                my_pos += 64;
+                const bool v0 = i0 < my_len, v1 = i1 < my_len;
+                const int4 q0 = p.rec[my_start + min(i0, my_len - 1)];
+                const int4 q1 = p.rec[my_start + min(i1, my_len - 1)];
+                const int dx0 = (int)((uint32_t)q0.x - px), dx1 = (int)((uint32_t)q1.x - px);
+                const int dy0 = (int)((uint32_t)q0.y - py), dy1 = (int)((uint32_t)q1.y - py);
+                const int dz0 = (int)((uint32_t)q0.z - pz), dz1 = (int)((uint32_t)q1.z - pz);
+                const float fx0 = (float)dx0, fy0 = (float)dy0, fz0 = (float)dz0;
+                const float fx1 = (float)dx1, fy1 = (float)dy1, fz1 = (float)dz1;
+                const int b0 = cand_bin(p, sE, nb, v0, dx0, dy0, dz0, fx0, fy0, fz0);
+                const int b1 = cand_bin(p, sE, nb, v1, dx1, dy1, dz1, fx1, fy1, fz1);
+                have0 = b0 >= 0;
+                have1 = b1 >= 0;
+                ent0 = make_float4(fx0, fy0, fz0, __int_as_float(q0.w));
+                ent1 = make_float4(fx1, fy1, fz1, __int_as_float(q1.w));
+                ek0 = kb + b0;
+                ek1 = kb + b1;
             }
-            if (have) {
-                const int pos = atomicAdd(&qcnt[par * nkmax + ek], 1);
-                if (pos < qcap[ek]) {
-                    queue[qbase[ek] + pos] = ent;
-                    have = false;
-                } else {
-                    s_flag = 1;   // stays pending until the queues are drained
-                }
-            }
+            append(have0, ent0, ek0);
+            append(have1, ent1, ek1);
         }
 
         // ----- tile sums: every key's lanes added through one transpose

@@ -336,10 +336,10 @@ Plan make_plan(const tpcf_config *c, int64_t n_sec, int64_t n_prim_hint)
     const double nbar = (double)(n_sec > 0 ? n_sec : 1) / (c->box * c->box * c->box);
     int s = c->cell_div;
     if (s == 0) {
-        // about 24 points per cell, cells no smaller than r_max / 4
+        // about 24 points per cell, cells no smaller than r_max / 6
         const double h_want = std::cbrt(24.0 / nbar);
         s = (int)std::floor(c->r_max / h_want);
-        s = std::max(1, std::min(4, s));
+        s = std::max(1, std::min(6, s));
     }
     for (;;) {
         int nc = (int)std::floor((double)s * c->box / c->r_max);
