@@ -227,8 +227,7 @@ __device__ __forceinline__ int cand_bin(const PairParams &p, const unsigned long
 
 // ---------------------------------------------------------------------------
 // Integer pair counts only (the random-only RRR pass): the same tiles, ranges
-// and exact binning, with counts per (slot, bin) added by one shared atomic per
-// group of lanes with equal keys.
+// and exact binning, with one shared atomic per pair on the (slot, bin) counts.
 struct CMap {
     int off_E, off_prim, off_pf, off_pc, off_rstart, off_rlen, off_rslot, off_cnt, off_pairs, off_misc;
     int total;
@@ -334,12 +333,8 @@ __global__ void __launch_bounds__(256, 2) k_counts(const PairParams p)
                 const int dz0 = (int)((uint32_t)q0.z - (uint32_t)pr.z), dz1 = (int)((uint32_t)q1.z - (uint32_t)pr.z);
                 const int b0 = cand_bin(p, sE, nb, i0 < len, dx0, dy0, dz0, (float)dx0, (float)dy0, (float)dz0);
                 const int b1 = cand_bin(p, sE, nb, i1 < len, dx1, dy1, dz1, (float)dx1, (float)dy1, (float)dz1);
-                // keys of both candidates; lanes without a pair get keys no other lane has
-                const int k0 = b0 >= 0 ? sl * nb + b0 : -1 - lane, k1 = b1 >= 0 ? sl * nb + b1 : -33 - lane;
-                const unsigned p0 = __match_any_sync(FULL, k0);
-                if (b0 >= 0 && lane == __ffs(p0) - 1) atomicAdd(&cnt[k0], __popc(p0));
-                const unsigned p1 = __match_any_sync(FULL, k1);
-                if (b1 >= 0 && lane == __ffs(p1) - 1) atomicAdd(&cnt[k1], __popc(p1));
+                if (b0 >= 0) atomicAdd(&cnt[sl * nb + b0], 1);
+                if (b1 >= 0) atomicAdd(&cnt[sl * nb + b1], 1);
             }
         }
         __syncthreads();
@@ -377,7 +372,7 @@ __global__ void __launch_bounds__(256, 2) k_counts(const PairParams p)
 struct QMap {
     int off_E, off_prim, off_pf, off_pc;
     int off_rstart, off_rlen, off_rslot;
-    int off_qbase, off_qcap, off_qcnt, off_cnt, off_gfirst, off_gsize, off_lanekey, off_hist;
+    int off_qinfo, off_qcnt, off_cnt, off_gfirst, off_gsize, off_lanekey, off_hist;
     int off_sacc, off_queue;
     int off_d32, off_w32, off_d64, off_w64, off_pairs, off_misc;
     int total;
@@ -401,8 +396,7 @@ __host__ __device__ inline QMap make_qmap(int P, int nb, int s, int chunk, int b
     m.off_rstart = o;  o = align_up(o + 4 * m.maxr, 16);
     m.off_rlen = o;    o = align_up(o + 4 * m.maxr, 16);
     m.off_rslot = o;   o = align_up(o + 4 * m.maxr, 16);
-    m.off_qbase = o;   o = align_up(o + 4 * nk, 16);
-    m.off_qcap = o;    o = align_up(o + 4 * nk, 16);
+    m.off_qinfo = o;   o = align_up(o + 8 * nk, 16);
     m.off_qcnt = o;    o = align_up(o + 4 * 2 * nk, 16);
     m.off_cnt = o;     o = align_up(o + 4 * nk, 16);
     m.off_gfirst = o;  o = align_up(o + 4 * nk, 16);
@@ -446,8 +440,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
     int *rstart = reinterpret_cast<int *>(smem + M.off_rstart);
     int *rlen = reinterpret_cast<int *>(smem + M.off_rlen);
     int *rslot = reinterpret_cast<int *>(smem + M.off_rslot);
-    int *qbase = reinterpret_cast<int *>(smem + M.off_qbase);
-    int *qcap = reinterpret_cast<int *>(smem + M.off_qcap);
+    int2 *qinfo = reinterpret_cast<int2 *>(smem + M.off_qinfo);   // (first entry, capacity) per key
     int *qcnt = reinterpret_cast<int *>(smem + M.off_qcnt);      // [2][nkmax]
     int *cnt = reinterpret_cast<int *>(smem + M.off_cnt);
     int *gfirst = reinterpret_cast<int *>(smem + M.off_gfirst);
@@ -571,8 +564,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
             if (lane < nb) {
                 for (int sl = 0; sl < np; ++sl) {
                     const int k = sl * nb + lane;
-                    qbase[k] = sl * ctot + cs - capb;
-                    qcap[k] = capb;
+                    qinfo[k] = make_int2(sl * ctot + cs - capb, capb);
                     const int g0 = sl * gtot + gs - gb;
                     gfirst[k] = g0;
                     gsize[k] = gb;
@@ -590,8 +582,8 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         const int myk = lanekey[tid];
         const int myg = myk >= 0 ? gsize[myk] : 1;
         const int myr = myk >= 0 ? tid - gfirst[myk] : 0;
-        const int myq = myk >= 0 ? qbase[myk] : 0;
-        const int mycap = myk >= 0 ? qcap[myk] : 0;
+        const int myq = myk >= 0 ? qinfo[myk].x : 0;
+        const int mycap = myk >= 0 ? qinfo[myk].y : 0;
         float acc[NACC];
 #pragma unroll
         for (int j = 0; j < NACC; ++j) acc[j] = 0.f;
@@ -602,7 +594,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
             int alldone = 1;
             for (int w = 0; w < W; ++w) alldone &= wdone[w];
             const int *live = qcnt + par * nkmax;
-            if (tid < nk) cnt[tid] += min(live[tid], qcap[tid]);
+            if (tid < nk) cnt[tid] += min(live[tid], qinfo[tid].y);
             if (tid < nkmax) qcnt[(par ^ 1) * nkmax + tid] = 0;   // the other half: free since the last drain
             if (tid == 0) s_flag = 0;
             if (myk >= 0) {
@@ -632,12 +624,15 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         bool done = false, have0 = false, have1 = false;
         float4 ent0 = make_float4(0.f, 0.f, 0.f, 0.f), ent1 = ent0;
         int ek0 = 0, ek1 = 0;
-        // appends a pending entry; false if its queue is full (it stays pending)
+        // appends a pending entry (one shared atomic); an entry that finds its queue
+        // full stays pending and raises the flag.  (Aggregating equal keys across the
+        // warp with a match instruction measured slower.)
         auto append = [&](bool &have, const float4 &ent, int ek) {
             if (!have) return;
             const int pos = atomicAdd(&qcnt[par * nkmax + ek], 1);
-            if (pos < qcap[ek]) {
-                queue[qbase[ek] + pos] = ent;
+            const int2 qi = qinfo[ek];
+            if (pos < qi.y) {
+                queue[qi.x + pos] = ent;
                 have = false;
             } else {
                 s_flag = 1;   // stays pending until the queues are drained
