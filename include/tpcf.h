@@ -258,7 +258,7 @@ int tpcf_batch_destroy(tpcf_batch batch);
 int tpcf_estimate_3pcf_batched(const tpcf_config *cfg, const uint32_t *xyz, const float *w, const int64_t *offsets,
                                int32_t n_mocks, double *zeta, int64_t *triplet_counts, void *stream);
 
-/* Chooses cell_div (2..5), tile_primaries (1, 2, 4) and chunk (3072, 4096,
+/* Chooses cell_div (2..6), tile_primaries (1, 2, 4) and chunk (3072, 4096,
  * 6144) for a catalogue like this one by timing the pair stage on a strided
  * sample of at most 6144 of its primaries (dev xyz[n][3], dev w[n] or NULL) for
  * every valid combination; *tuned = *cfg with the fastest choice.  A nonzero

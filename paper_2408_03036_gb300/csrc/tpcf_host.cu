@@ -1176,7 +1176,7 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    const int divs[] = {2, 3, 4, 5};
+    const int divs[] = {2, 3, 4, 5, 6};
     const int tiles_all[] = {1, 2, 4};
     const int tiles_fixed[] = {cfg->tile_primaries};
     const bool fixed_tile = cfg->tile_primaries > 0;   // a batch runs one primary per tile
