@@ -37,6 +37,11 @@ WORKLOAD = ("clustered lognormal halos N_D=400000 (512^3 mesh, P~k^-1.5 exp(-(k/
             "LOS shift f=0.8) + N_R=1200000 randoms, open cube L=1000 Mpc/h, 20 bins 10-150 Mpc/h, "
             "l_max=4, L={0,2,4}")
 FLOP_PER_PAIR = 4 * 25 + 15   # algorithmic FP32 work per accepted pair at l_max = 4
+# DRAM bytes (read + write) per primary of the harmonic pair kernel, from one ncu
+# capture of the current kernel at this workload's density (400,000 primaries in
+# a 630 Mpc/h cube: 16.5 MB read + 776.9 MB written, the a_lm output); the
+# traffic grows with the primaries, so a launch moves this times its primaries
+PAIR_DRAM_BYTES_PER_PRIMARY = 1983.0
 # covariance batch: lognormal mocks (same field recipe, 256^3 mesh) in a periodic
 # cube of side 1000 Mpc/h, sizes uniform in [100k, 400k], analytic randoms
 N_MOCKS, MOCK_LO, MOCK_HI, MOCK_MESH, SEED_MOCKS = 256, 100_000, 400_000, 256, 77
@@ -527,8 +532,10 @@ def roofline(cfg, d, dw, r, rw, dev, stream, tpcf, reps=3):
     t = statistics.median(ms) / 1000.0
     achieved = FLOP_PER_PAIR * pairs / t / 1e12
     peak = fp32_peak_tflops(dev)
-    return {"bound": "alu", "kernel": "k_pairs (pair stage, D-R field)", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+    return {"bound": "alu", "kernel": "k_pairs_q (harmonic pair stage, D-R field)", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": PAIR_DRAM_BYTES_PER_PRIMARY * n_grid,
+            "traffic_note": "bytes per launch, scaled by primaries from a capture of 400,000 primaries",
             "per_launch": {"pairs": pairs, "flop_per_pair": FLOP_PER_PAIR, "ms": t * 1000.0,
                            "primaries": n_grid},
             "peak_note": "FP32 FMA pipe: 2 x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)",
