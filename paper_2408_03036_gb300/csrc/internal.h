@@ -103,6 +103,9 @@ cudaError_t triplet_counts(const int32_t *counts, int64_t K, int nb, unsigned lo
                            cudaStream_t st);
 int gram_tile_count(int nb, int lmax);
 // Tensor-core (tcgen05) Gram with bf16 or tf32 hi/lo splits; fills all of G.
+// The plain FP32 Gram on the tensor-core tile plan (SIMT FMAs, FP64 partial sums).
+cudaError_t couple_gram_simt(const float *alm, const float *w, int64_t K, int nb, int lmax, double *G, int sms,
+                             cudaStream_t st);
 cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, int lmax, bool tf32, double *G,
                            int *err, int sms, cudaStream_t st);
 cudaError_t couple_gram_fp32_tiles(const float *alm, const float *w, int64_t K, int nb, int lmax, int *d_tiles,

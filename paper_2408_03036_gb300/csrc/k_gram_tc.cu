@@ -573,6 +573,120 @@ __global__ void k_gram_tc_reduce(const double *partial, int n_slices, long long 
     }
 }
 
+// ---------------------------------------------------------------------------
+// The plain FP32 Gram on the same tile plan: one CTA per (unit, column half,
+// slice of primaries) computes its 128 x (up to 128) block of D with FP32 FMAs,
+// 8 x 8 outputs per thread; the staged operands are FP32 (A = w x, B = x),
+// [K entry][row]; FP32 runs of 256 primaries are added to FP64 partial sums.
+constexpr int kSimtKP = 16;          // primaries per stage (32 K entries)
+constexpr int kSimtFlush = 256;      // primaries per FP32 accumulation run
+
+__global__ void __launch_bounds__(256, 2) k_gram_simt(const TcParams p)
+{
+    __shared__ __align__(16) float sA[2 * kSimtKP][128];
+    __shared__ __align__(16) float sB[2 * kSimtKP][128];
+    __shared__ int4 rowinfoA[128], rowinfoB[128];
+    // work item -> (unit, column half)
+    int item = blockIdx.x, unit = 0, half = 0;
+    for (unit = 0; unit < p.plan.n_units; ++unit) {
+        const int halves = (p.plan.u[unit].n + 127) / 128;
+        if (item < halves) { half = item; break; }
+        item -= halves;
+    }
+    if (unit >= p.plan.n_units) return;
+    const TcUnit U = p.plan.u[unit];
+    int grp = 0;
+    while (grp + 1 < p.plan.n_groups && p.plan.g[grp + 1].unit0 <= unit) ++grp;
+    const TcGroup G = p.plan.g[grp];
+    const int ncols = min(128, U.n - 128 * half);
+    const int brow0 = U.b_row + 128 * half;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int nb = p.nb, nlm = (p.lmax + 1) * (p.lmax + 1);
+    const int64_t RL = (int64_t)nb * nlm;
+    // row tables of the 128 A rows and the ncols B rows (staged-row numbering of the group)
+    for (int r = tid; r < 256; r += blockDim.x) {
+        const int row = r < 128 ? U.a_row + r : brow0 + (r - 128);
+        int4 ri = make_int4(0, -1, 0, 0);
+        if (r < 128 || r - 128 < ncols)
+            for (int q = 0; q < G.n_segs; ++q) {
+                const TcSeg sg = p.plan.s[G.seg0 + q];
+                if (row >= sg.row && row < sg.row + sg.rows) {
+                    const int within = row - sg.row, l = sg.m + within / nb;
+                    ri = make_int4(l * l + (sg.m ? 2 * sg.m - 1 : 0), sg.m ? l * l + 2 * sg.m : -1, within % nb, 1);
+                }
+            }
+        if (r < 128) rowinfoA[r] = ri;
+        else rowinfoB[r - 128] = ri;
+    }
+    const int64_t i_beg = (int64_t)blockIdx.y * p.per_slice;
+    const int64_t i_end = min(p.K, i_beg + p.per_slice);
+    double *part = p.partial + (int64_t)blockIdx.y * p.plan.slice_size + U.part_off;
+    float acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
+    auto flush = [&]() {
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int r = ty * 8 + a;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int c = tx * 8 + b;
+                if (c < ncols) part[(int64_t)r * U.n + 128 * half + c] += (double)acc[a][b];
+                acc[a][b] = 0.f;
+            }
+        }
+    };
+    int since = 0;
+    __syncthreads();
+    for (int64_t i0 = i_beg; i0 < i_end; i0 += kSimtKP) {
+        __syncthreads();
+        // stage: entry k = 2 p + part of primary i0 + p, rows of A (w-scaled) and B
+        for (int e = tid; e < 2 * 128 * kSimtKP; e += blockDim.x) {
+            const int which = e / (128 * kSimtKP);            // 0: A rows, 1: B rows
+            const int rem = e % (128 * kSimtKP);
+            const int pp = rem / 128, r = rem % 128;
+            const int64_t i = i0 + pp;
+            const int4 ri = which ? rowinfoB[r] : rowinfoA[r];
+            float xc = 0.f, xs = 0.f;
+            if (ri.w && i < i_end) {
+                const float *src = p.alm + i * RL + ri.z * nlm;
+                xc = __ldg(src + ri.x);
+                xs = ri.y >= 0 ? __ldg(src + ri.y) : 0.f;
+                if (!which && p.w) {
+                    const float wi = __ldg(p.w + i);
+                    xc *= wi;
+                    xs *= wi;
+                }
+            }
+            float (*dst)[128] = which ? sB : sA;
+            dst[2 * pp][r] = xc;
+            dst[2 * pp + 1][r] = xs;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int k = 0; k < 2 * kSimtKP; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&sA[k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&sA[k][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&sB[k][tx * 8]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&sB[k][tx * 8 + 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+        }
+        since += kSimtKP;
+        if (since >= kSimtFlush) {
+            flush();
+            since = 0;
+        }
+    }
+    if (since > 0) flush();
+}
+
 }  // namespace
 
 cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, int lmax, bool tf32, double *G,
@@ -620,6 +734,47 @@ cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, 
         const dim3 grid(ng, slices);
         if (tf32) k_gram_tc<true><<<grid, kThreads, smem, st>>>(p);
         else k_gram_tc<false><<<grid, kThreads, smem, st>>>(p);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const int64_t tot = gram_offset(nb, lmax, lmax + 1);
+        int g = (int)((tot + 255) / 256);
+        if (g > 4096) g = 4096;
+        k_gram_tc_reduce<<<g, 256, 0, st>>>(p.partial, slices, p.plan.slice_size, nb, lmax, p.plan, G);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(p.partial, st);
+    return e;
+}
+
+cudaError_t couple_gram_simt(const float *alm, const float *w, int64_t K, int nb, int lmax, double *G, int sms,
+                             cudaStream_t st)
+{
+    TcParams p;
+    if (!make_tc_plan(nb, lmax, p.plan)) return cudaErrorInvalidValue;
+    if (K <= 0) return cudaMemsetAsync(G, 0, gram_offset(nb, lmax, lmax + 1) * sizeof(double), st);
+    int items = 0;
+    for (int u = 0; u < p.plan.n_units; ++u) items += (p.plan.u[u].n + 127) / 128;
+    int slices = (2 * sms + items - 1) / items;
+    const int64_t min_per = 2048;
+    if ((K + slices - 1) / slices < min_per) slices = (int)((K + min_per - 1) / min_per);
+    if (slices < 1) slices = 1;
+    p.alm = alm;
+    p.w = w;
+    p.K = K;
+    p.nb = nb;
+    p.lmax = lmax;
+    p.per_slice = (K + slices - 1) / slices;
+    p.n_slices = slices;
+    p.err = nullptr;
+    const size_t pbytes = (size_t)slices * p.plan.slice_size * sizeof(double);
+    cudaError_t e = cudaMallocAsync((void **)&p.partial, pbytes, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p.partial, 0, pbytes, st);
+    if (e == cudaSuccess) {
+        k_gram_simt<<<dim3(items, slices), 256, 0, st>>>(p);
         note_launch();
         e = cudaGetLastError();
     }

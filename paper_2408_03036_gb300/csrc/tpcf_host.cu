@@ -523,7 +523,7 @@ int couple(const tpcf_config *c, const float *alm, const float *w, const int32_t
     CK(cudaMallocAsync((void **)&gaunt, hg.size() * sizeof(double), st));
     CK(cudaMemcpyAsync(gaunt, hg.data(), hg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     if (c->precision == TPCF_PREC_FP32) {
-        CK(couple_gram_fp32(alm, w, K, nb, L, G, st));
+        CK(couple_gram_simt(alm, w, K, nb, L, G, ds->sms, st));
     } else {
         cudaError_t e = couple_gram_tc(alm, w, K, nb, L, c->precision == TPCF_PREC_TF32X3, G, ds->err, ds->sms, st);
         if (e == cudaErrorInvalidValue)
@@ -1051,7 +1051,6 @@ int tpcf_batch_run(tpcf_batch b, const uint32_t *xyz, const float *w, double *ze
     const int nb = c->n_bins, L = c->l_max, L1 = L + 1;
     const int nlm = L1 * L1, ndiag = L1 * (L1 + 1) / 2;
     const int64_t ncell1 = (int64_t)b->nc * b->nc * b->nc;
-    const int64_t gsz = gram_offset(nb, L, L + 1);
     CK(cudaMemsetAsync(b->diag, 0, (size_t)b->n_mocks * ndiag * nb * sizeof(double), st));
     CK(cudaMemsetAsync(b->wsp, 0, (size_t)b->n_mocks * L1 * nb * sizeof(double), st));
     CK(cudaMemsetAsync(b->pairs, 0, (size_t)b->n_mocks * nb * sizeof(unsigned long long), st));
@@ -1077,8 +1076,7 @@ int tpcf_batch_run(tpcf_batch b, const uint32_t *xyz, const float *w, double *ze
             const int64_t r0 = b->off[k] - p0, K = b->off[k + 1] - b->off[k];
             const float *alm_k = b->alm + (size_t)r0 * nb * nlm;
             if (c->precision == TPCF_PREC_FP32) {
-                CK(cudaMemsetAsync(b->G, 0, gsz * sizeof(double), st));
-                CK(couple_gram_fp32_tiles(alm_k, b->wprim + r0, K, nb, L, b->d_tiles, b->G, st));
+                CK(couple_gram_simt(alm_k, b->wprim + r0, K, nb, L, b->G, ds->sms, st));
             } else {
                 cudaError_t e = couple_gram_tc(alm_k, b->wprim + r0, K, nb, L, c->precision == TPCF_PREC_TF32X3, b->G,
                                                ds->err, ds->sms, st);
