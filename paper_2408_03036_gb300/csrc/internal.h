@@ -97,17 +97,16 @@ cudaError_t weight_sums(const float *w1, int64_t n1, const float *w2, int64_t n2
                         cudaStream_t st);
 
 // Coupling (Gram over primaries) and assembly.
-cudaError_t couple_gram_fp32(const float *alm, const float *w, int64_t K, int nb, int lmax,
-                             double *G, cudaStream_t st);
 cudaError_t triplet_counts(const int32_t *counts, int64_t K, int nb, unsigned long long *T,
                            cudaStream_t st);
 int gram_tile_count(int nb, int lmax);
-// Tensor-core (tcgen05) Gram with bf16 or tf32 hi/lo splits; fills all of G.
-// The plain FP32 Gram on the tensor-core tile plan (SIMT FMAs, FP64 partial sums).
+// The plain FP32 Gram on the tensor-core tile plan (SIMT FMAs, FP64 partial sums); fills all of G.
 cudaError_t couple_gram_simt(const float *alm, const float *w, int64_t K, int nb, int lmax, double *G, int sms,
                              cudaStream_t st);
+// Tensor-core (tcgen05) Gram with bf16 or tf32 hi/lo splits; fills all of G.
 cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, int lmax, bool tf32, double *G,
                            int *err, int sms, cudaStream_t st);
+// The FP32 Gram with a caller-provided tile table and no allocation (accumulates into G).
 cudaError_t couple_gram_fp32_tiles(const float *alm, const float *w, int64_t K, int nb, int lmax, int *d_tiles,
                                    double *G, cudaStream_t st);
 // j = k coefficients of the off-diagonal (l1 != l2) entries, [m][l1][l2][j] for one l_max

@@ -220,41 +220,6 @@ __global__ void k_u64_to_i64(const unsigned long long *src, int64_t *dst, int n)
 
 }  // namespace
 
-cudaError_t couple_gram_fp32(const float *alm, const float *w, int64_t K, int nb, int lmax, double *G,
-                             cudaStream_t st)
-{
-    // tile list (m, tr, tc), uploaded through a small stream-ordered buffer
-    int h[3 * 512];
-    int nt = 0;
-    for (int m = 0; m <= lmax; ++m) {
-        const int n_m = nb * (lmax - m + 1);
-        const int t = (n_m + GT - 1) / GT;
-        for (int a = 0; a < t; ++a)
-            for (int b = 0; b < t; ++b) {
-                if (nt >= 512) return cudaErrorInvalidValue;
-                h[3 * nt] = m; h[3 * nt + 1] = a; h[3 * nt + 2] = b;
-                ++nt;
-            }
-    }
-    int *d = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&d, sizeof(int) * 3 * nt, st);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(d, h, sizeof(int) * 3 * nt, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return e;
-    // enough K-slices to fill the GPU a few times over, slices of >= 1024 primaries
-    int64_t ks = (152 * 8 + nt - 1) / nt;
-    const int64_t maxks = (K + 1023) / 1024;
-    if (ks > maxks) ks = maxks;
-    if (ks < 1) ks = 1;
-    if (K > 0) {
-        k_gram_fp32<<<dim3(nt, (unsigned)ks), 256, 0, st>>>(alm, w, K, nb, lmax, d, nt, G);
-        note_launch();
-    }
-    e = cudaGetLastError();
-    cudaFreeAsync(d, st);
-    return e;
-}
-
 int gram_tile_count(int nb, int lmax)
 {
     int nt = 0;
