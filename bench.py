@@ -396,7 +396,10 @@ def coupling_report(cfg, alm, wprim, counts, diag, wsp, dev, stream, tpcf, reps=
             torch.cuda.synchronize(dev)
             ms.append(s.elapsed_time(e))
         t = statistics.median(ms) / 1000.0
-        r = {"ms": t * 1000.0, "algorithmic_tflops": flop / t / 1e12}
+        # the Gram reads every primary's a_lm row (and weight) once: an HBM-bound step
+        nbytes = alm.numel() * 4 + wprim.numel() * 4
+        r = {"ms": t * 1000.0, "algorithmic_tflops": flop / t / 1e12, "hbm_gbs": nbytes / t / 1e9,
+             "hbm_frac": nbytes / t / 1e9 / peaks["hbm_gbs"], "hbm_note": which + " copy bandwidth"}
         if prec != "fp32":
             # tensor-pipe work: three MMAs over the full square blocks (twice the
             # upper-triangle count); tf32 runs at half the bf16 rate
