@@ -24,6 +24,10 @@ Readings of the paper recorded here (the same list is in the design doc):
     c_b = (W - 1)/L^3 V_b Y_0^0 and RRR_00^0[b1][b2] = W c_b1 c_b2;
   * non-periodic volumes use explicit randoms with weights -W_D/W_R, and
     RRR_00^0 from the randoms alone with weights +W_D/W_R;
+  * the 2PCF multipoles (Eq. xi_meas_leg) take P_l(mu) of every pair exactly
+    (the limit of vanishing mu bins), share the 3PCF's radial bins, and use
+    the natural estimator (Eq. xi_natest) on the same D - R field, i.e.
+    (DD - 2DR + RR) / RR with explicit randoms;
   * ``convention="PAPER_EQ"`` is Eq. slep2sugy as printed with orthonormal
     Y; ``"S_COEFF"`` (default) multiplies it by sqrt((2 l1 + 1)(2 l2 + 1)), the
     coefficient of the Schmidt-normalised basis function S_{l1 l2 L} of
@@ -216,29 +220,63 @@ class Estimate:
     extra: dict = field(default_factory=dict)
 
 
-def estimate(cfg: Config, d_xyz, d_w, r_xyz=None, r_w=None, nthreads=0) -> Estimate:
+def m0_sums(alm, w, L, step=2):
+    """S_l[b] = sum_i w_i Re a_l^0[b](x_i) for l = 0, step, ..., L: the weighted
+    pair sums sum_{i != j in b} w_i w_j Y_l^0(r_hat_ij) behind the Legendre
+    multipoles of Eq. xi_meas_leg (Y_l^0 = sqrt((2l+1)/4pi) P_l(mu), mu the
+    cosine to the z line of sight)."""
+    w = np.asarray(w, dtype=np.float64)
+    return np.array([w @ alm[:, :, l * l + l].real for l in range(0, L + 1, step)])
+
+
+def xi_multipoles(S, rr, step=2):
+    """Eq. xi_meas_leg in the limit of vanishing mu bins, with the natural
+    estimator of Eq. xi_natest generalised to the D - R field:
+    xi_l[b] = (2l+1) sum_pairs w w P_l(mu) / RR_b = sqrt(4pi (2l+1)) S_l[b] / RR_b,
+    with RR_b the (isotropic) weighted random pair count of bin b."""
+    out = np.zeros_like(S)
+    for e in range(S.shape[0]):
+        l = step * e
+        out[e] = math.sqrt(4.0 * math.pi * (2 * l + 1)) * S[e] / rr
+    return out
+
+
+def estimate(cfg: Config, d_xyz, d_w, r_xyz=None, r_w=None, nthreads=0, want_xi=False) -> Estimate:
     """Full estimator: (D - R)^3 / R^3 multipoles (Eq. ssest with Eq. slep2sugy).
 
-    Without randoms (periodic only) the analytic-random form is used."""
+    Without randoms (periodic only) the analytic-random form is used.  With
+    want_xi the even 2PCF multipoles xi_l, l = 0, 2, ..., l_max, of the same
+    field and radial bins go to extra["xi"] (their normaliser RR_b to
+    extra["rr"])."""
     d_w = np.asarray(d_w, dtype=np.float64)
     WD = float(d_w.sum())
     if r_xyz is None:
         if not cfg.periodic:
             raise ValueError("analytic randoms need a periodic box")
-        o = run(cfg, d_xyz, d_w, offset_weight=WD, nthreads=nthreads)
+        w = d_w
+        o = run(cfg, d_xyz, d_w, offset_weight=WD, nthreads=nthreads, want_alm=want_xi)
         cb = shell_offsets(cfg, WD)
         rrr = WD * np.outer(cb, cb)
+        # analytic RR_b = W (W - 1) V_b / L^3
+        rr = WD * math.sqrt(4.0 * math.pi) * cb
     else:
         r_w = np.asarray(r_w, dtype=np.float64)
         alpha = WD / float(r_w.sum())
         xyz = np.concatenate([np.asarray(d_xyz, np.uint32), np.asarray(r_xyz, np.uint32)])
         w = np.concatenate([d_w, -alpha * r_w])
-        o = run(cfg, xyz, w, nthreads=nthreads)
-        orr = run(cfg, r_xyz, alpha * r_w, nthreads=nthreads, l_max=0)
+        o = run(cfg, xyz, w, nthreads=nthreads, want_alm=want_xi)
+        orr = run(cfg, r_xyz, alpha * r_w, nthreads=nthreads, l_max=0, want_alm=want_xi)
         rrr = orr.nnn[0, 0, 0].real
+        if want_xi:
+            # sum over ordered random pairs of alpha^2 w_i w_j, from the l = 0 sums
+            rr = math.sqrt(4.0 * math.pi) * m0_sums(orr.alm, alpha * r_w, 0)[0]
     mults = multipoles(cfg.l_max, cfg.Ls)
     zr, zi = project(cfg, o.nnn, rrr, mults)
-    return Estimate(zr, zi, mults, o.nnn, rrr, o.pair_counts, o.trip_counts)
+    est = Estimate(zr, zi, mults, o.nnn, rrr, o.pair_counts, o.trip_counts)
+    if want_xi:
+        est.extra["xi"] = xi_multipoles(m0_sums(o.alm, w, cfg.l_max), rr)
+        est.extra["rr"] = rr
+    return est
 
 
 def max_threads() -> int:

@@ -293,3 +293,60 @@ def test_nonperiodic_rrr_is_integer_triplet_count(ora):
     o = ora.run(cfg, rxyz, alpha * rw.astype(np.float64), l_max=0, nthreads=2)
     ref = alpha ** 3 * o.trip_counts / (4 * math.pi)
     assert np.abs(o.nnn[0, 0, 0].real - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------ 2PCF multipoles
+@pytest.mark.parametrize("periodic", [True, False])
+def test_xi_numerator_vs_brute_force_pairs(ora, periodic):
+    """sum_i w_i a_l^0[b] equals the brute-force pair sum sum w_i w_j Y_l^0(r_ij)
+    (with the analytic-random offset c_b W on l = 0 for the periodic form)."""
+    from scipy.special import eval_legendre
+    box = 150.0
+    xyz, _ = synth.poisson(400, 77)
+    w = np.random.default_rng(3).uniform(0.5, 1.5, 400)
+    cfg = ora.Config(5.0, 40.0, 5, 4, (0,), periodic, box)
+    E = bf.exact_edges(5.0, 40.0, 5, box)
+    off = float(w.sum()) if periodic else -1.0
+    o = ora.run(cfg, xyz, w, offset_weight=off, want_alm=True)
+    S = ora.m0_sums(o.alm, w, 4)
+    ref = np.zeros((3, 5))
+    for i, (js, bins, d) in enumerate(bf.neighbours(xyz, periodic, E)):
+        mu = d[:, 2] / np.sqrt((d * d).sum(1))
+        for e, l in enumerate((0, 2, 4)):
+            np.add.at(ref[e], bins, w[i] * w[js] * math.sqrt((2 * l + 1) / (4 * math.pi)) * eval_legendre(l, mu))
+    if periodic:
+        ref[0] -= float(w.sum()) * ora.shell_offsets(cfg, float(w.sum()))
+    np.testing.assert_allclose(S, ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+
+
+def test_xi_poisson_null(ora):
+    """Uniform points in a periodic box: every 2PCF multipole of the analytic-random
+    form has zero expectation (E[DD_b] = N (N - 1) V_b / L^3 and the separation
+    directions are isotropic), checked against the spread over seeds."""
+    N, seeds = 3000, 24
+    cfg = ora.Config(10.0, 50.0, 4, 2, (0,), True, 200.0)
+    xs = np.array([ora.estimate(cfg, *synth.poisson(N, 2000 + s), nthreads=4, want_xi=True).extra["xi"]
+                   for s in range(seeds)])
+    dev = np.abs(xs.mean(0)) / (xs.std(0, ddof=1) / math.sqrt(seeds))
+    assert dev.max() < 5.0, dev.max()
+
+
+def test_xi_normaliser_is_the_random_pair_sum(ora):
+    """RR_b is alpha^2 times the ordered random pair count for unit random weights,
+    and alpha^2 sum_{i != j} w_i w_j over the random pairs of bin b (brute force)
+    for weighted randoms."""
+    box = 150.0
+    d, dw = synth.poisson(600, 5)
+    r, rw = synth.randoms(1800, 6)
+    cfg = ora.Config(5.0, 40.0, 5, 2, (0,), False, box)
+    est = ora.estimate(cfg, d, dw, r, rw, want_xi=True)
+    alpha = dw.astype(np.float64).sum() / rw.astype(np.float64).sum()
+    pc = ora.run(cfg, r, rw, l_max=0).pair_counts
+    np.testing.assert_allclose(est.extra["rr"], alpha ** 2 * pc, rtol=1e-12)
+    rw2 = np.random.default_rng(7).uniform(0.2, 1.8, r.shape[0])
+    est2 = ora.estimate(cfg, d, dw, r, rw2, want_xi=True)
+    alpha2 = dw.astype(np.float64).sum() / rw2.sum()
+    ref = np.zeros(5)
+    for i, (js, bins, _) in enumerate(bf.neighbours(r, False, bf.exact_edges(5.0, 40.0, 5, box))):
+        np.add.at(ref, bins, alpha2 ** 2 * rw2[i] * rw2[js])
+    np.testing.assert_allclose(est2.extra["rr"], ref, rtol=1e-12)
