@@ -199,12 +199,34 @@ int tpcf_project(const tpcf_config *cfg, const double *nnn, const double *rrr, d
  * Inputs dev d_xyz[nd][3], d_w[nd] (NULL: unit), r_xyz[nr][3], r_w[nr] (NULL: unit).
  * Outputs dev: zeta[n_mult][n_bins][n_bins] (required), and optionally
  *   nnn (as tpcf_couple_multipoles), rrr[n_bins][n_bins], pair_counts[n_bins]
- *   (pairs of the neighbour field), triplet_counts[n_bins][n_bins]. */
+ *   (pairs of the neighbour field), triplet_counts[n_bins][n_bins].
+ * RRR_00^0 with explicit randoms: with unit random weights (r_w NULL or all
+ * ones, checked on the device with one 4-byte read back) it is
+ * (W_D/W_R)^3 T_RR / (4 pi) from the integer random triplet counts T_RR (a
+ * lean count-only pass); otherwise it is (W_D/W_R)^3 times the l = 0 coupling
+ * of the randoms with their own weights (one l = 0 harmonic pass). */
 int tpcf_estimate_3pcf(const tpcf_config *cfg,
                        const uint32_t *d_xyz, const float *d_w, int64_t nd,
                        const uint32_t *r_xyz, const float *r_w, int64_t nr,
                        double *zeta, double *nnn, double *rrr,
                        int64_t *pair_counts, int64_t *triplet_counts, void *stream);
+
+/* tpcf_estimate_3pcf plus the even anisotropic 2PCF multipoles of the same
+ * field and radial bins (Eq. xi_meas_leg with the natural estimator of
+ * Eq. xi_natest, which the D - R field turns into (DD - 2DR + RR) / RR):
+ *   xi[e][b] = (2l + 1) sum_{pairs in b} w_i w_j P_l(mu_ij) / RR_b,  l = 2e,
+ *   e = 0 .. l_max / 2, mu the cosine of the pair separation to the z axis
+ *   (the fixed line of sight), every pair's P_l taken exactly (the limit of
+ *   vanishing mu bins).  RR_b is W_D (W_D - 1) V_b / L^3 with analytic randoms,
+ *   else (W_D/W_R)^2 times the weighted ordered random pair sum of bin b.
+ *   The l = 0 term carries the -1 of Eq. xi_natest through the random
+ *   subtraction.  dev xi[l_max/2 + 1][n_bins] (NULL: as tpcf_estimate_3pcf).
+ *   The sums come from the m = 0 harmonics of the pair stage: no extra pass. */
+int tpcf_estimate_3pcf_xi(const tpcf_config *cfg,
+                          const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                          const uint32_t *r_xyz, const float *r_w, int64_t nr,
+                          double *zeta, double *nnn, double *rrr,
+                          int64_t *pair_counts, int64_t *triplet_counts, double *xi, void *stream);
 
 /* As tpcf_estimate_3pcf, but every pointer is HOST memory (pinned memory gives
  * the fastest copies).  Copies in, runs, copies out, and synchronises the

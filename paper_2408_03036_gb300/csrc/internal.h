@@ -89,6 +89,8 @@ void free_grid_dev(GridDev &g, cudaStream_t st);
 // whose cells are k * nc^3 ... (k+1) * nc^3 - 1; rec_mock[i] = mock of record i.
 cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t n, const int64_t *d_offsets,
                                    int n_mocks, int nc, GridDev &g, int32_t *rec_mock, int *err, cudaStream_t st);
+// *out (zeroed by the caller) += number of w[i] != 1.
+cudaError_t count_not_one(const float *w, int64_t n, int *out, cudaStream_t st);
 cudaError_t weight_sums_mocks(const float *w, const int64_t *d_offsets, int n_mocks, double *out, cudaStream_t st);
 
 cudaError_t pack_records(const uint32_t *xyz, const float *w, int64_t n, int4 *out, int *err,
@@ -120,6 +122,16 @@ cudaError_t assemble_nnn(const double *G, const double *diag, const double *wsp,
 cudaError_t project_zeta(const double *nnn, const double *rrr, int nb, int lmax, int n_mult,
                          const double *coef, const int *mults, double *zeta, cudaStream_t st);
 cudaError_t rrr_analytic(const double *wsum, const double *coef, int nb, double *rrr, cudaStream_t st);
+// RRR_00^0 = alpha^3 nnn0 (nnn0: the l = 0 coupling of the randoms with their own weights).
+cudaError_t rrr_weighted(const double *nnn0, const double *wsums, int nb, double *rrr, cudaStream_t st);
+// out[e][b] += sum_i w_i a_{lstep e}^0[b](i) (out zeroed by the caller; n_ell * nb <= 128).
+cudaError_t m0_sums(const float *alm, const float *w, int64_t K, int nb, int lmax, int n_ell, int lstep, double *out,
+                    cudaStream_t st);
+// 2PCF multipoles from the m = 0 sums S and the pair normaliser (rr_mode 0 analytic,
+// 1 random pair counts pc, 2 weighted random sums s0); rr [nb] is scratch.
+cudaError_t xi_from_sums(int rr_mode, const double *wsums, const double *coef, const unsigned long long *pc,
+                         const double *s0, const double *S, int n_ell, int lstep, int nb, double *rr, double *xi,
+                         cudaStream_t st);
 cudaError_t rrr_from_counts(const unsigned long long *T, const double *wsums, int nb, double *rrr,
                             cudaStream_t st);
 cudaError_t i64_from_u64(const unsigned long long *src, int64_t *dst, int n, cudaStream_t st);

@@ -1,6 +1,7 @@
 // Coupling of the per-primary harmonic sums (Eq. measured_mult of
 // arXiv:2408.03036, summed over primaries as in Sec. 4.2), the integer triplet
-// counts, the assembly of NNN^m and the TripoSH projection (Eq. slep2sugy).
+// counts, the assembly of NNN^m, the TripoSH projection (Eq. slep2sugy), the
+// random normalisers and the 2PCF multipoles of Eq. xi_meas_leg.
 //
 // Gram layout: for every m, the vector v_i of primary i collects
 // a_l^m[b] for l = m..l_max, b = 0..n_b-1 (row (l - m) * n_b + b), real and
@@ -193,6 +194,82 @@ __global__ void k_rrr_counts(const unsigned long long *__restrict__ T, const dou
     rrr[i] = a * a * a * (double)T[i] / (4.0 * 3.14159265358979323846);
 }
 
+// RRR_00^0 = alpha^3 nnn0 with nnn0 the l = 0 coupling of the randoms weighted by w_R
+// (alpha = W_D / W_R): exact for any random weights.
+__global__ void k_rrr_scale(const double *__restrict__ nnn0, const double *__restrict__ wsums, int nb,
+                            double *__restrict__ rrr)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * nb) return;
+    const double a = wsums[0] / wsums[1];
+    rrr[i] = a * a * a * nnn0[i];
+}
+
+// out[e][b] += sum_i w_i a_{lstep e}^0[b](i).  Each warp takes primaries in turn,
+// its lanes the (e, b) outputs (at most 128, four per lane); FP64 sums, reduced
+// in shared memory, then one FP64 atomic per output and CTA.
+__global__ void __launch_bounds__(256) k_m0_sums(const float *__restrict__ alm, const float *__restrict__ w,
+                                                 int64_t K, int nb, int lmax, int n_ell, int lstep,
+                                                 double *__restrict__ out)
+{
+    __shared__ double s[128];
+    const int n_out = n_ell * nb;
+    for (int t = threadIdx.x; t < n_out; t += blockDim.x) s[t] = 0.0;
+    __syncthreads();
+    const int nlm = (lmax + 1) * (lmax + 1);
+    const int lane = threadIdx.x & 31;
+    int off[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int o = lane + 32 * q;
+        const int l = lstep * (o / nb);
+        off[q] = o < n_out ? (o % nb) * nlm + l * l : -1;
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < K; i += nwarp) {
+        const double wi = w ? (double)w[i] : 1.0;
+        const float *a = alm + i * nb * nlm;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (off[q] >= 0) acc[q] += wi * (double)a[off[q]];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (off[q] >= 0 && acc[q] != 0.0) atomicAdd(&s[lane + 32 * q], acc[q]);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n_out; t += blockDim.x)
+        if (s[t] != 0.0) atomicAdd(out + t, s[t]);
+}
+
+// 2PCF multipoles xi_l[b] = sqrt(4 pi (2l + 1)) S_l[b] / RR_b (Eq. xi_meas_leg with
+// exact per-pair Legendre polynomials), l = lstep e.  RR_b by rr_mode:
+//   0: analytic, W (W - 1) V_b / L^3 = W (W - 1) sqrt(4 pi) coef[b];
+//   1: alpha^2 times the ordered random pair count pc[b] (unit random weights);
+//   2: alpha^2 sqrt(4 pi) s0[b], s0 = sum_i w_i a_0^0[b] of the randoms.
+__global__ void k_xi(int rr_mode, const double *__restrict__ wsums, const double *__restrict__ coef,
+                     const unsigned long long *__restrict__ pc, const double *__restrict__ s0,
+                     const double *__restrict__ S, int n_ell, int lstep, int nb, double *__restrict__ rr,
+                     double *__restrict__ xi)
+{
+    const int b = threadIdx.x;
+    if (b >= nb) return;
+    const double sq4pi = 3.5449077018110320546;   // sqrt(4 pi)
+    double r;
+    if (rr_mode == 0) {
+        const double W = wsums[0];
+        r = W * (W - 1.0) * coef[b] * sq4pi;
+    } else {
+        const double a = wsums[0] / wsums[1];
+        r = rr_mode == 1 ? a * a * (double)pc[b] : a * a * sq4pi * s0[b];
+    }
+    rr[b] = r;
+    for (int e = 0; e < n_ell; ++e) {
+        const int l = lstep * e;
+        xi[e * nb + b] = sq4pi * sqrt(2.0 * l + 1.0) * S[e * nb + b] / r;
+    }
+}
+
 // Fills the (m, tr, tc) tile table of the Gram blocks on the device.
 __global__ void k_gram_tiles(int nb, int lmax, int *tiles, int ntiles)
 {
@@ -295,6 +372,34 @@ cudaError_t rrr_analytic(const double *wsum, const double *coef, int nb, double 
 cudaError_t rrr_from_counts(const unsigned long long *T, const double *wsums, int nb, double *rrr, cudaStream_t st)
 {
     k_rrr_counts<<<(nb * nb + 255) / 256, 256, 0, st>>>(T, wsums, nb, rrr);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t rrr_weighted(const double *nnn0, const double *wsums, int nb, double *rrr, cudaStream_t st)
+{
+    k_rrr_scale<<<(nb * nb + 255) / 256, 256, 0, st>>>(nnn0, wsums, nb, rrr);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t m0_sums(const float *alm, const float *w, int64_t K, int nb, int lmax, int n_ell, int lstep, double *out,
+                    cudaStream_t st)
+{
+    if (n_ell * nb > 128 || lstep * (n_ell - 1) > lmax) return cudaErrorInvalidValue;
+    if (K <= 0) return cudaSuccess;
+    int64_t g = (K + 7) / 8;
+    if (g > 152 * 4) g = 152 * 4;
+    k_m0_sums<<<(unsigned)g, 256, 0, st>>>(alm, w, K, nb, lmax, n_ell, lstep, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t xi_from_sums(int rr_mode, const double *wsums, const double *coef, const unsigned long long *pc,
+                         const double *s0, const double *S, int n_ell, int lstep, int nb, double *rr, double *xi,
+                         cudaStream_t st)
+{
+    k_xi<<<1, 32, 0, st>>>(rr_mode, wsums, coef, pc, s0, S, n_ell, lstep, nb, rr, xi);
     note_launch();
     return cudaGetLastError();
 }

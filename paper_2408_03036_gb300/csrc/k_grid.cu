@@ -213,6 +213,16 @@ __global__ void k_mock_of_rec(const int64_t *__restrict__ order, const int32_t *
 }
 
 // W per mock: one block per mock.
+// *out += number of weights that differ from 1.
+__global__ void k_count_not_one(const float *__restrict__ w, int64_t n, int *out)
+{
+    int c = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        c += w[i] != 1.0f;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 __global__ void k_wsum_mocks(const float *__restrict__ w, const int64_t *__restrict__ offsets, double *out)
 {
     __shared__ double red[32];
@@ -331,6 +341,15 @@ cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t 
     cudaFreeAsync(hist, st);
     cudaFreeAsync(cursor, st);
     return e;
+}
+
+cudaError_t count_not_one(const float *w, int64_t n, int *out, cudaStream_t st)
+{
+    if (n > 0) {
+        k_count_not_one<<<grid_blocks(n, 256), 256, 0, st>>>(w, n, out);
+        note_launch();
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t weight_sums_mocks(const float *w, const int64_t *d_offsets, int n_mocks, double *out, cudaStream_t st)

@@ -790,6 +790,15 @@ int tpcf_estimate_3pcf(const tpcf_config *cfg, const uint32_t *d_xyz, const floa
                        const uint32_t *r_xyz, const float *r_w, int64_t nr, double *zeta, double *nnn_out,
                        double *rrr_out, int64_t *pair_counts, int64_t *triplet_counts, void *stream)
 {
+    return tpcf_estimate_3pcf_xi(cfg, d_xyz, d_w, nd, r_xyz, r_w, nr, zeta, nnn_out, rrr_out, pair_counts,
+                                 triplet_counts, nullptr, stream);
+}
+
+int tpcf_estimate_3pcf_xi(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                          const uint32_t *r_xyz, const float *r_w, int64_t nr, double *zeta, double *nnn_out,
+                          double *rrr_out, int64_t *pair_counts, int64_t *triplet_counts, double *xi,
+                          void *stream)
+{
     int rc = check_config(cfg);
     if (rc) return rc;
     if (!zeta) return fail(TPCF_ERR_ARG, "zeta is required");
@@ -804,11 +813,27 @@ int tpcf_estimate_3pcf(const tpcf_config *cfg, const uint32_t *d_xyz, const floa
     const int nb = cfg->n_bins, L = cfg->l_max;
     const int nlm = (L + 1) * (L + 1), ndiag = (L + 1) * (L + 2) / 2;
     const int L1 = L + 1;
+    const int n_ell = L / 2 + 1;   // even multipoles 0, 2, ..., l_max
+    // weighted randoms: RRR_00^0 and the pair normaliser come from the l = 0 harmonic
+    // sums of the randoms; unit randoms (r_w NULL or all ones): from integer counts
+    bool weighted_r = false;
+    if (!analytic && r_w) {
+        int *d_n = nullptr, h_n = 0;
+        if ((rc = dalloc(&d_n, 1, st, true))) return rc;
+        CK(count_not_one(r_w, nr, d_n, st));
+        CK(cudaMemcpyAsync(&h_n, d_n, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        cudaFreeAsync(d_n, st);
+        weighted_r = h_n != 0;
+    }
 
     double *wsums = nullptr, *diag = nullptr, *wsp = nullptr, *nnn = nnn_out, *rrr = rrr_out, *mono = nullptr;
+    double *S = nullptr, *s0 = nullptr, *rr = nullptr;
     float *alm = nullptr;
     int32_t *cnt = nullptr, *cnt_r = nullptr;
-    unsigned long long *pairs = nullptr, *T = nullptr, *TR = nullptr;
+    unsigned long long *pairs = nullptr, *T = nullptr, *TR = nullptr, *pairs_r = nullptr;
+    float *alm_r = nullptr, *wprim_r = nullptr;
+    double *diag_r = nullptr, *wsp_r = nullptr, *nnn_r = nullptr;
     GridDev gf, gr;
     if ((rc = dalloc(&wsums, 2, st, true))) return rc;
     CK(weight_sums(d_w, nd, r_w, nr, wsums, st));
@@ -831,34 +856,60 @@ int tpcf_estimate_3pcf(const tpcf_config *cfg, const uint32_t *d_xyz, const floa
     if ((rc = dalloc(&wprim, (size_t)K, st, false))) return rc;
     CK(cudaMemcpy2DAsync(wprim, 4, (const char *)gf.rec + 12, 16, 4, K, cudaMemcpyDeviceToDevice, st));
     if ((rc = couple(cfg, alm, wprim, cnt, K, diag, wsp, nnn, T, st))) return rc;
+    if (xi) {
+        if ((rc = dalloc(&S, (size_t)n_ell * nb, st, true))) return rc;
+        if ((rc = dalloc(&rr, (size_t)nb, st, false))) return rc;
+        CK(m0_sums(alm, wprim, K, nb, L, n_ell, 2, S, st));
+    }
+    int rr_mode = 0;
     if (analytic) {
         if ((rc = mono_coef_dev(cfg, &mono, st))) return rc;
         CK(rrr_analytic(wsums, mono, nb, rrr, st));
-    } else {
+    } else if (!weighted_r) {
         CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
         if ((rc = dalloc(&cnt_r, (size_t)nr * nb, st, false))) return rc;
         if ((rc = dalloc(&TR, (size_t)nb * nb, st, true))) return rc;
-        rc = run_pairs(cfg, gr, gr.rec, nr, true, 0.0, nullptr, false, nullptr, cnt_r, nullptr, nullptr, nullptr, st);
+        if (xi && (rc = dalloc(&pairs_r, (size_t)nb, st, true))) return rc;
+        rc = run_pairs(cfg, gr, gr.rec, nr, true, 0.0, nullptr, false, nullptr, cnt_r, nullptr, nullptr, pairs_r,
+                       st);
         if (rc) return rc;
         CK(tpcf::triplet_counts(cnt_r, nr, nb, TR, st));
         CK(rrr_from_counts(TR, wsums, nb, rrr, st));
+        rr_mode = 1;
+    } else {
+        // the l = 0 pass over the randoms with their own weights, then its coupling
+        tpcf_config c0 = *cfg;
+        c0.l_max = 0;
+        c0.n_L = 1;
+        c0.L[0] = 0;
+        CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
+        if ((rc = dalloc(&alm_r, (size_t)nr * nb, st, false))) return rc;
+        if ((rc = dalloc(&cnt_r, (size_t)nr * nb, st, false))) return rc;
+        if ((rc = dalloc(&diag_r, (size_t)nb, st, true))) return rc;
+        if ((rc = dalloc(&wsp_r, (size_t)nb, st, true))) return rc;
+        if ((rc = dalloc(&nnn_r, (size_t)nb * nb, st, false))) return rc;
+        if ((rc = dalloc(&wprim_r, (size_t)nr, st, false))) return rc;
+        rc = run_pairs(&c0, gr, gr.rec, nr, false, 0.0, nullptr, false, alm_r, cnt_r, diag_r, wsp_r, nullptr, st);
+        if (rc) return rc;
+        CK(cudaMemcpy2DAsync(wprim_r, 4, (const char *)gr.rec + 12, 16, 4, nr, cudaMemcpyDeviceToDevice, st));
+        if ((rc = couple(&c0, alm_r, wprim_r, nullptr, nr, diag_r, wsp_r, nnn_r, nullptr, st))) return rc;
+        CK(rrr_weighted(nnn_r, wsums, nb, rrr, st));
+        if (xi) {
+            if ((rc = dalloc(&s0, (size_t)nb, st, true))) return rc;
+            CK(m0_sums(alm_r, wprim_r, nr, nb, 0, 1, 2, s0, st));
+        }
+        rr_mode = 2;
     }
     if ((rc = project(cfg, nnn, rrr, zeta, st))) return rc;
+    if (xi) CK(xi_from_sums(rr_mode, wsums, mono, pairs_r, s0, S, n_ell, 2, nb, rr, xi, st));
     if (pair_counts) CK(i64_from_u64(pairs, pair_counts, nb, st));
     if (triplet_counts) CK(i64_from_u64(T, triplet_counts, nb * nb, st));
     free_grid_dev(gf, st);
     free_grid_dev(gr, st);
-    cudaFreeAsync(wsums, st);
-    cudaFreeAsync(alm, st);
-    cudaFreeAsync(cnt, st);
-    cudaFreeAsync(diag, st);
-    cudaFreeAsync(wsp, st);
-    cudaFreeAsync(pairs, st);
-    cudaFreeAsync(T, st);
-    cudaFreeAsync(wprim, st);
-    if (mono) cudaFreeAsync(mono, st);
-    if (cnt_r) cudaFreeAsync(cnt_r, st);
-    if (TR) cudaFreeAsync(TR, st);
+    for (void *q : {(void *)wsums, (void *)alm, (void *)cnt, (void *)diag, (void *)wsp, (void *)pairs, (void *)T,
+                    (void *)wprim, (void *)mono, (void *)cnt_r, (void *)TR, (void *)pairs_r, (void *)alm_r,
+                    (void *)wprim_r, (void *)diag_r, (void *)wsp_r, (void *)nnn_r, (void *)S, (void *)s0, (void *)rr})
+        if (q) cudaFreeAsync(q, st);
     if (!nnn_out) cudaFreeAsync(nnn, st);
     if (!rrr_out) cudaFreeAsync(rrr, st);
     CK(cudaGetLastError());

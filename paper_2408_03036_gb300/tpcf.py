@@ -26,6 +26,7 @@ CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
 EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
            "tpcf_bin_edges", "tpcf_build_grid", "tpcf_grid_destroy", "tpcf_grid_info", "tpcf_grid_points",
            "tpcf_accumulate_alm", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
+           "tpcf_estimate_3pcf_xi",
            "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
            "tpcf_estimate_3pcf_batched", "tpcf_autotune",
@@ -102,6 +103,7 @@ def lib():
             "tpcf_couple_multipoles": ([P, P, P, I64, CFG, P, P, P, P, P], ctypes.c_int),
             "tpcf_project": ([CFG, P, P, P, P], ctypes.c_int),
             "tpcf_estimate_3pcf": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
+            "tpcf_estimate_3pcf_xi": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_estimate_3pcf_host": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_stream_status": ([P], ctypes.c_int),
             "tpcf_couple_multipoles_static": ([P, P, P, I64, CFG, P, P, P, P, P], ctypes.c_int),
@@ -193,12 +195,14 @@ class Result:
     rrr: torch.Tensor | None = None
     pair_counts: torch.Tensor | None = None
     triplet_counts: torch.Tensor | None = None
+    xi: torch.Tensor | None = None      # even 2PCF multipoles [l_max // 2 + 1, n_bins]
     extra: dict = field(default_factory=dict)
 
 
 def estimate_3pcf(cfg: Config, d_xyz, d_w=None, r_xyz=None, r_w=None, stream=None, want_all=True,
-                  device="cuda") -> Result:
-    """tpcf_estimate_3pcf on device tensors (numpy inputs are copied to the device first)."""
+                  device="cuda", want_xi=False) -> Result:
+    """tpcf_estimate_3pcf on device tensors (numpy inputs are copied to the device first);
+    with want_xi, tpcf_estimate_3pcf_xi, which adds the even 2PCF multipoles."""
     dx = _as_dev_xyz(d_xyz, device)
     dw = _as_dev_w(d_w, device)
     rx = _as_dev_xyz(r_xyz, device) if r_xyz is not None else None
@@ -215,6 +219,12 @@ def estimate_3pcf(cfg: Config, d_xyz, d_w=None, r_xyz=None, r_w=None, stream=Non
         pc = torch.empty(nb, dtype=torch.int64, device=device)
         tc = torch.empty((nb, nb), dtype=torch.int64, device=device)
     c = cfg.c()
+    if want_xi:
+        xi = torch.empty((cfg.l_max // 2 + 1, nb), dtype=torch.float64, device=device)
+        _check(lib().tpcf_estimate_3pcf_xi(ctypes.byref(c), _ptr(dx), _ptr(dw), nd, _ptr(rx), _ptr(rw), nr,
+                                           _ptr(z), _ptr(nnn), _ptr(rrr), _ptr(pc), _ptr(tc), _ptr(xi),
+                                           _stream(stream)))
+        return Result(z, mults, nnn, rrr, pc, tc, xi)
     _check(lib().tpcf_estimate_3pcf(ctypes.byref(c), _ptr(dx), _ptr(dw), nd, _ptr(rx), _ptr(rw), nr,
                                     _ptr(z), _ptr(nnn), _ptr(rrr), _ptr(pc), _ptr(tc), _stream(stream)))
     return Result(z, mults, nnn, rrr, pc, tc)
