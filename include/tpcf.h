@@ -289,6 +289,36 @@ int tpcf_estimate_3pcf_batched(const tpcf_config *cfg, const uint32_t *xyz, cons
 int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, int64_t n, void *stream,
                   tpcf_config *tuned);
 
+/* -------------------------------------------------------------- covariance
+ * Covariant errors from mocks (Sec. 4.3).  The data vector of mock k is
+ * d_i^k = src[k * stride + idx[i]], i = 0 .. n_dv-1 (dev idx, or NULL for
+ * d_i^k = src[k * stride + i]); with the batch's zeta array
+ * [n_mocks][n_mult][n_bins][n_bins], stride = n_mult n_bins^2 and idx from
+ * tpcf_data_vector_index select multipoles and triangles in place.
+ * Writes dev mean[n_dv] and dev cov[n_dv][n_dv] (row-major, symmetric):
+ *   cov_ij = sum_k (d_i^k - mean_i)(d_j^k - mean_j) / (n_mocks - 1)
+ * (Eq. covariance), in FP64.  n_mocks >= 2, n_dv <= 2^20.  An idx entry
+ * outside [0, stride) is reported as TPCF_ERR_DATA by tpcf_stream_status and
+ * turns its row and column into NaN. */
+int tpcf_covariance(const double *src, int64_t n_mocks, int64_t stride, const int64_t *idx, int64_t n_dv,
+                    double *mean, double *cov, void *stream);
+
+/* Host arithmetic for a covariance from n_mocks mocks of an n_dv-long data
+ * vector and n_params fitted parameters: *hartlap = (n_mocks - n_dv - 2) /
+ * (n_mocks - 1), the factor on the inverse covariance (Eq. Hartlap), and *m1,
+ * the factor on the parameters' variance (Eqs. Perc1, Perc).  Either output
+ * may be NULL.  Needs n_mocks > n_dv + 4 (TPCF_ERR_ARG otherwise). */
+int tpcf_covariance_factors(int64_t n_mocks, int64_t n_dv, int64_t n_params, double *hartlap, double *m1);
+
+/* Host: flat indices into a zeta array [n_mult][n_bins][n_bins] of cfg (the
+ * order of tpcf_multipole_index) for the n_sel multipoles host
+ * l1l2L[n_sel][3], in that order, each over the triangles b1 <= b2 with
+ * b2 - b1 >= eta (|r1 - r2| >= eta dr, the selection of Sec. 4.3), b1 then b2
+ * ascending.  *n_out = entries needed; host idx (cap entries, may be NULL to
+ * query the count).  A multipole cfg does not measure is TPCF_ERR_ARG. */
+int tpcf_data_vector_index(const tpcf_config *cfg, const int32_t *l1l2L, int32_t n_sel, int32_t eta,
+                           int64_t *idx, int64_t cap, int64_t *n_out);
+
 /* Synchronises the stream and reports any latched device-side error
  * (TPCF_ERR_DATA, TPCF_ERR_TIMEOUT) or CUDA error; clears the latch. */
 int tpcf_stream_status(void *stream);

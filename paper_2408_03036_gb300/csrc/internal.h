@@ -15,7 +15,7 @@
 namespace tpcf {
 
 // Device-side error latch values (first error wins).
-enum : int { DEV_OK = 0, DEV_ERR_DATA = 1, DEV_ERR_TIMEOUT = 2, DEV_ERR_CAPACITY = 3 };
+enum : int { DEV_OK = 0, DEV_ERR_DATA = 1, DEV_ERR_TIMEOUT = 2, DEV_ERR_CAPACITY = 3, DEV_ERR_INDEX = 4 };
 
 // Cell list in device memory.  Records are int4 {x, y, z, float_as_int(w)} with
 // x, y, z uint32 fixed-point bit patterns, sorted by cell index
@@ -134,6 +134,10 @@ cudaError_t xi_from_sums(int rr_mode, const double *wsums, const double *coef, c
                          cudaStream_t st);
 cudaError_t rrr_from_counts(const unsigned long long *T, const double *wsums, int nb, double *rrr,
                             cudaStream_t st);
+// Sample covariance over n mocks of the data vectors d_i^k = src[k * stride + idx[i]]
+// (idx NULL: i): mean [nd], cov [nd][nd] (Eq. covariance); bad indices latch DEV_ERR_INDEX.
+cudaError_t covariance(const double *src, int64_t n, int64_t stride, const int64_t *idx, int64_t nd, double *mean,
+                       double *cov, int *err, cudaStream_t st);
 cudaError_t i64_from_u64(const unsigned long long *src, int64_t *dst, int n, cudaStream_t st);
 
 // Offsets of the per-m Gram blocks in the packed G array: block m is

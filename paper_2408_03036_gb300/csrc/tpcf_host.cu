@@ -1275,6 +1275,65 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
     return rc;
 }
 
+int tpcf_covariance(const double *src, int64_t n_mocks, int64_t stride, const int64_t *idx, int64_t n_dv,
+                    double *mean, double *cov, void *stream)
+{
+    if (!src || !mean || !cov) return fail(TPCF_ERR_ARG, "src, mean and cov are required");
+    if (n_mocks < 2) return fail(TPCF_ERR_ARG, "need at least two mocks (got %lld)", (long long)n_mocks);
+    if (n_dv < 1 || stride < 1) return fail(TPCF_ERR_ARG, "n_dv and stride must be positive");
+    if (!idx && n_dv > stride) return fail(TPCF_ERR_ARG, "without idx, n_dv must not exceed stride");
+    if (n_dv > (int64_t)1 << 20) return fail(TPCF_ERR_ARG, "data vector longer than 2^20");
+    DevState *ds;
+    int rc = dev_state(&ds);
+    if (rc) return rc;
+    CK(covariance(src, n_mocks, stride, idx, n_dv, mean, cov, ds->err, (cudaStream_t)stream));
+    return TPCF_OK;
+}
+
+int tpcf_covariance_factors(int64_t n_mocks, int64_t n_dv, int64_t n_params, double *hartlap, double *m1)
+{
+    if (n_dv < 1 || n_params < 0) return fail(TPCF_ERR_ARG, "n_dv >= 1 and n_params >= 0 required");
+    if (n_mocks <= n_dv + 4)
+        return fail(TPCF_ERR_ARG, "need n_mocks > n_dv + 4 (got %lld mocks for %lld entries)", (long long)n_mocks,
+                    (long long)n_dv);
+    const double nm = (double)n_mocks, nd = (double)n_dv, np = (double)n_params;
+    if (hartlap) *hartlap = (nm - nd - 2.0) / (nm - 1.0);
+    const double q = (nm - nd - 1.0) * (nm - nd - 4.0);
+    const double A = 2.0 / q, B = (nm - nd - 2.0) / q;
+    if (m1) *m1 = (1.0 + B * (nd - np)) / (1.0 + A + B * (np + 1.0));
+    return TPCF_OK;
+}
+
+int tpcf_data_vector_index(const tpcf_config *cfg, const int32_t *l1l2L, int32_t n_sel, int32_t eta, int64_t *idx,
+                           int64_t cap, int64_t *n_out)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (n_sel < 0 || (n_sel > 0 && !l1l2L) || eta < 0 || !n_out)
+        return fail(TPCF_ERR_ARG, "bad selection arguments");
+    std::vector<int> ml;
+    multipole_list(cfg, ml);
+    const int nm = (int)ml.size() / 3, nb = cfg->n_bins;
+    int64_t n = 0;
+    for (int s = 0; s < n_sel; ++s) {
+        int k = -1;
+        for (int q = 0; q < nm; ++q)
+            if (ml[3 * q] == l1l2L[3 * s] && ml[3 * q + 1] == l1l2L[3 * s + 1] && ml[3 * q + 2] == l1l2L[3 * s + 2])
+                k = q;
+        if (k < 0)
+            return fail(TPCF_ERR_ARG, "multipole (%d %d %d) is not measured by this configuration", l1l2L[3 * s],
+                        l1l2L[3 * s + 1], l1l2L[3 * s + 2]);
+        for (int b1 = 0; b1 < nb; ++b1)
+            for (int b2 = b1 + eta; b2 < nb; ++b2) {
+                if (idx && n < cap) idx[n] = ((int64_t)k * nb + b1) * nb + b2;
+                ++n;
+            }
+    }
+    *n_out = n;
+    if (idx && n > cap) return fail(TPCF_ERR_ARG, "idx holds %lld entries, %lld needed", (long long)cap, (long long)n);
+    return TPCF_OK;
+}
+
 int tpcf_stream_status(void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
@@ -1289,6 +1348,7 @@ int tpcf_stream_status(void *stream)
         CK(cudaMemset(ds->err, 0, sizeof(int)));
         if (h == DEV_ERR_DATA) return fail(TPCF_ERR_DATA, "non-finite weight in the input");
         if (h == DEV_ERR_TIMEOUT) return fail(TPCF_ERR_TIMEOUT, "a bounded device wait ran out");
+        if (h == DEV_ERR_INDEX) return fail(TPCF_ERR_DATA, "a data-vector index is outside the source row");
         return fail(TPCF_ERR_CUDA, "device error code %d", h);
     }
     return TPCF_OK;

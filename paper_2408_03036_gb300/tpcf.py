@@ -30,6 +30,7 @@ EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_mult
            "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
            "tpcf_estimate_3pcf_batched", "tpcf_autotune",
+           "tpcf_covariance", "tpcf_covariance_factors", "tpcf_data_vector_index",
            "tpcf_emu_create", "tpcf_emu_destroy", "tpcf_emu_param_count", "tpcf_emu_set_input_box",
            "tpcf_emu_fit_output_scaling", "tpcf_emu_train_step", "tpcf_emu_gradients", "tpcf_emu_predict",
            "tpcf_emu_get_params", "tpcf_emu_set_params", "tpcf_emu_get_output_scaling"]
@@ -114,6 +115,9 @@ def lib():
             "tpcf_batch_destroy": ([P], ctypes.c_int),
             "tpcf_estimate_3pcf_batched": ([CFG, P, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
             "tpcf_autotune": ([CFG, P, P, I64, P, CFG], ctypes.c_int),
+            "tpcf_covariance": ([P, I64, I64, P, I64, P, P, P], ctypes.c_int),
+            "tpcf_covariance_factors": ([I64, I64, I64, P, P], ctypes.c_int),
+            "tpcf_data_vector_index": ([CFG, P, ctypes.c_int32, ctypes.c_int32, P, I64, P], ctypes.c_int),
             "tpcf_emu_create": ([P, ctypes.c_int32, ctypes.c_uint64, P], ctypes.c_int),
             "tpcf_emu_destroy": ([P], ctypes.c_int),
             "tpcf_emu_param_count": ([P, P], ctypes.c_int),
@@ -162,6 +166,49 @@ def multipole_index(cfg: Config):
     arr = (ctypes.c_int32 * (3 * n.value))()
     _check(lib().tpcf_multipole_index(ctypes.byref(c), ctypes.addressof(arr), n.value))
     return [tuple(arr[3 * k:3 * k + 3]) for k in range(n.value)]
+
+
+def data_vector_index(cfg: Config, selected, eta: int):
+    """tpcf_data_vector_index: flat indices (numpy int64) into a [n_mult][nb][nb] zeta
+    array for the selected (l1, l2, L) multipoles over triangles b2 - b1 >= eta."""
+    import numpy as np
+    c = cfg.c()
+    sel = np.ascontiguousarray(np.asarray(selected, dtype=np.int32).reshape(-1, 3))
+    n = ctypes.c_int64(0)
+    _check(lib().tpcf_data_vector_index(ctypes.byref(c), _ptr(sel), sel.shape[0], int(eta), None, 0,
+                                        ctypes.addressof(n)))
+    idx = np.empty(n.value, dtype=np.int64)
+    _check(lib().tpcf_data_vector_index(ctypes.byref(c), _ptr(sel), sel.shape[0], int(eta), _ptr(idx), idx.size,
+                                        ctypes.addressof(n)))
+    return idx
+
+
+def covariance(src, idx=None, n_dv=None, stream=None):
+    """tpcf_covariance over the leading (mock) axis of the device tensor src
+    (FP64, contiguous); idx (int64, host or device) selects entries of each
+    mock's flattened row.  Returns (mean [n_dv], cov [n_dv, n_dv])."""
+    if src.dtype != torch.float64 or not src.is_contiguous():
+        raise ValueError("src must be a contiguous float64 tensor")
+    n_mocks = src.shape[0]
+    stride = src[0].numel()
+    di = None
+    if idx is not None:
+        di = torch.as_tensor(idx, dtype=torch.int64).to(src.device).contiguous()
+        n_dv = di.numel()
+    elif n_dv is None:
+        n_dv = stride
+    mean = torch.empty(n_dv, dtype=torch.float64, device=src.device)
+    cov = torch.empty((n_dv, n_dv), dtype=torch.float64, device=src.device)
+    _check(lib().tpcf_covariance(_ptr(src), n_mocks, stride, _ptr(di), n_dv, _ptr(mean), _ptr(cov),
+                                 _stream(stream)))
+    return mean, cov
+
+
+def covariance_factors(n_mocks: int, n_dv: int, n_params: int):
+    """tpcf_covariance_factors: (Hartlap factor, Percival m1)."""
+    h, m = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(lib().tpcf_covariance_factors(n_mocks, n_dv, n_params, ctypes.addressof(h), ctypes.addressof(m)))
+    return h.value, m.value
 
 
 def bin_edges(cfg: Config):

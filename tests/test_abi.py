@@ -5,6 +5,8 @@ import ctypes
 import os
 import re
 
+import numpy as np
+
 import pytest
 
 from paper_2408_03036_gb300 import build as B
@@ -83,3 +85,25 @@ def test_config_validation(lib, bad):
     kw.update(bad)
     with pytest.raises(tpcf.TpcfError):
         tpcf.multipole_index(tpcf.Config(**kw))
+
+
+@pytest.mark.parametrize("nb,eta,sel", [(12, 3, [(0, 0, 0), (2, 0, 2)]), (20, 0, [(1, 1, 0)]),
+                                        (20, 2, [(0, 0, 0), (1, 1, 0), (2, 2, 0), (2, 0, 2), (1, 1, 2), (3, 1, 2)])])
+def test_data_vector_index_matches_oracle(lib, ora, nb, eta, sel):
+    from oracle import covariance as CV
+    cfg = tpcf.Config(10.0, 130.0, nb, 4, (0, 2, 4))
+    got = tpcf.data_vector_index(cfg, sel, eta)
+    ref = CV.data_vector_index(nb, ora.multipoles(4, (0, 2, 4)), sel, eta)
+    assert np.array_equal(got, ref)
+    with pytest.raises(tpcf.TpcfError):
+        tpcf.data_vector_index(tpcf.Config(10.0, 130.0, nb, 4, (0, 2)), [(1, 3, 4)], eta)
+
+
+@pytest.mark.parametrize("nm,nd,npar", [(3000, 336, 6), (3000, 288, 7), (40, 20, 3)])
+def test_covariance_factors_match_oracle(lib, nm, nd, npar):
+    from oracle import covariance as CV
+    h, m1 = tpcf.covariance_factors(nm, nd, npar)
+    assert abs(h - CV.hartlap(nm, nd)) < 1e-15
+    assert abs(m1 - CV.percival_m1(nm, nd, npar)) < 1e-14
+    with pytest.raises(tpcf.TpcfError):
+        tpcf.covariance_factors(nd + 4, nd, npar)
