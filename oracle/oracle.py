@@ -28,6 +28,11 @@ Readings of the paper recorded here (the same list is in the design doc):
     (the limit of vanishing mu bins), share the 3PCF's radial bins, and use
     the natural estimator (Eq. xi_natest) on the same D - R field, i.e.
     (DD - 2DR + RR) / RR with explicit randoms;
+  * the full edge correction (``edge="full"``, for explicit randoms) solves
+    N = zeta R for zeta on the real, l1 + l2 even coefficients (the ones the
+    L-even multipoles use), dropping the imaginary and odd-parity parts of
+    RRR, which vanish for a random catalogue symmetric under the reflections
+    z -> -z and y -> -y and are shot noise otherwise;
   * ``convention="PAPER_EQ"`` is Eq. slep2sugy as printed with orthonormal
     Y; ``"S_COEFF"`` (default) multiplies it by sqrt((2 l1 + 1)(2 l2 + 1)), the
     coefficient of the Schmidt-normalised basis function S_{l1 l2 L} of
@@ -241,7 +246,8 @@ def xi_multipoles(S, rr, step=2):
     return out
 
 
-def estimate(cfg: Config, d_xyz, d_w, r_xyz=None, r_w=None, nthreads=0, want_xi=False) -> Estimate:
+def estimate(cfg: Config, d_xyz, d_w, r_xyz=None, r_w=None, nthreads=0, want_xi=False,
+             edge="binwise") -> Estimate:
     """Full estimator: (D - R)^3 / R^3 multipoles (Eq. ssest with Eq. slep2sugy).
 
     Without randoms (periodic only) the analytic-random form is used.  With
@@ -271,12 +277,94 @@ def estimate(cfg: Config, d_xyz, d_w, r_xyz=None, r_w=None, nthreads=0, want_xi=
             # sum over ordered random pairs of alpha^2 w_i w_j, from the l = 0 sums
             rr = math.sqrt(4.0 * math.pi) * m0_sums(orr.alm, alpha * r_w, 0)[0]
     mults = multipoles(cfg.l_max, cfg.Ls)
-    zr, zi = project(cfg, o.nnn, rrr, mults)
-    est = Estimate(zr, zi, mults, o.nnn, rrr, o.pair_counts, o.trip_counts)
+    if edge == "full":
+        # the full anisotropic edge correction: RRR^m_{l1 l2} of the randoms at l_max
+        if r_xyz is None:
+            raise ValueError("the full edge correction needs explicit randoms")
+        rfull = run(cfg, r_xyz, alpha * r_w, nthreads=nthreads).nnn
+        zhat = edge_correct(o.nnn, rfull, cfg.l_max)
+        zr, zi = project(cfg, zhat, np.ones_like(rrr), mults)
+        est = Estimate(zr, zi, mults, o.nnn, rrr, o.pair_counts, o.trip_counts)
+        est.extra["rrr_full"] = rfull
+        est.extra["zeta_hat"] = zhat
+    elif edge == "binwise":
+        zr, zi = project(cfg, o.nnn, rrr, mults)
+        est = Estimate(zr, zi, mults, o.nnn, rrr, o.pair_counts, o.trip_counts)
+    else:
+        raise ValueError(edge)
     if want_xi:
         est.extra["xi"] = xi_multipoles(m0_sums(o.alm, w, cfg.l_max), rr)
         est.extra["rr"] = rr
     return est
+
+
+def gaunt(l1: int, m1: int, l2: int, m2: int, l3: int) -> float:
+    """int Y_l1^m1 Y_l2^m2 (Y_l3^(m1+m2))* dOmega, the coefficient of Y_l3^(m1+m2)
+    in the product Y_l1^m1 Y_l2^m2 (real for orthonormal Y)."""
+    m3 = m1 + m2
+    if abs(m1) > l1 or abs(m2) > l2 or abs(m3) > l3:
+        return 0.0
+    pre = math.sqrt((2 * l1 + 1) * (2 * l2 + 1) * (2 * l3 + 1) / (4.0 * math.pi))
+    return pre * wigner3j(l1, l2, l3, 0, 0, 0) * wigner3j(l1, l2, l3, m1, m2, -m3) * (-1.0) ** m3
+
+
+def edge_modes(L: int) -> list:
+    """(l1, l2, m), m >= 0, l1, l2 in [m, L], l1 + l2 even: the real coefficients the
+    edge-correction system is solved for (its unknowns and its equations)."""
+    return [(l1, l2, m) for m in range(L + 1) for l1 in range(m, L + 1) for l2 in range(m, L + 1)
+            if (l1 + l2) % 2 == 0]
+
+
+def edge_matrix(rrr_real, L: int):
+    """The coupling matrix of N = zeta R in the basis Y_l1^m(r1) Y_l2^m*(r2).
+
+    Functions of (r_hat_1, r_hat_2) about the fixed line of sight expand as
+    F = sum_{l1 l2 m} F^m_{l1 l2} Y_l1^m(r_hat_1) Y_l2^m*(r_hat_2); a product
+    couples them through one Gaunt coefficient per angle:
+      (F G)^m_{l1 l2} = sum F^m'_{l1' l2'} G^(m-m')_{l1'' l2''}
+                        gaunt(l1', m', l1'', m-m', l1) gaunt(l2', m', l2'', m-m', l2).
+    The unknowns are real with zeta^-m = zeta^m, so the columns of +m' and -m'
+    are added.  rrr_real[m][l1][l2] (m = -L..L at index m + L) holds Re RRR^m for
+    one bin pair.  The factor 4 pi makes the solution the bin-wise-normalised
+    zeta_hat^m = zeta^m / 4 pi, which equals NNN^m / RRR_00^0 for isotropic R."""
+    modes = edge_modes(L)
+    M = np.zeros((len(modes), len(modes)))
+    for r, (l1, l2, m) in enumerate(modes):
+        for c, (p1, p2, mp) in enumerate(modes):
+            v = 0.0
+            for mq in ((mp, -mp) if mp > 0 else (0,)):
+                mr = m - mq
+                if abs(mr) > L:
+                    continue
+                for q1 in range(abs(mr), L + 1):
+                    for q2 in range(abs(mr), L + 1):
+                        if (q1 + q2) % 2:
+                            continue
+                        g = gaunt(p1, mq, q1, mr, l1) * gaunt(p2, mq, q2, mr, l2)
+                        if g != 0.0:
+                            v += g * rrr_real[mr + L, q1, q2]
+            M[r, c] = 4.0 * math.pi * v
+    return modes, M
+
+
+def edge_correct(nnn, rrr, L: int):
+    """Solves Re NNN^m_{l1 l2} = sum M (zeta_hat) bin pair by bin pair (N = zeta R
+    with the full anisotropic RRR^m_{l1 l2} of the randoms, truncated at l_max)
+    on the real, l1 + l2 even coefficients; returns zeta_hat in the layout of
+    nnn (complex [2L+1][L+1][L+1][nb][nb], zeta_hat^-m = zeta_hat^m, zero
+    outside the solved modes)."""
+    nb = nnn.shape[-1]
+    out = np.zeros(nnn.shape, dtype=np.complex128)
+    rr = rrr.real
+    for b1 in range(nb):
+        for b2 in range(nb):
+            modes, M = edge_matrix(rr[:, :, :, b1, b2], L)
+            rhs = np.array([nnn[m + L, l1, l2, b1, b2].real for (l1, l2, m) in modes])
+            z = np.linalg.solve(M, rhs)
+            for (l1, l2, m), v in zip(modes, z):
+                out[m + L, l1, l2, b1, b2] = v
+                out[-m + L, l1, l2, b1, b2] = v
+    return out
 
 
 def max_threads() -> int:
