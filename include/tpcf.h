@@ -228,6 +228,30 @@ int tpcf_estimate_3pcf_xi(const tpcf_config *cfg,
                           double *zeta, double *nnn, double *rrr,
                           int64_t *pair_counts, int64_t *triplet_counts, double *xi, void *stream);
 
+/* The estimator with the full anisotropic edge correction (explicit randoms,
+ * nr >= 1; any geometry).  Instead of dividing NNN^m bin-wise by RRR_00^0 it
+ * computes every RRR^m_{l1 l2} of the randoms (weights (W_D/W_R) r_w, the
+ * same pair and coupling kernels at l_max) and, for every bin pair, solves
+ * N = zeta R, the product of functions of (r_hat_1, r_hat_2) about the fixed
+ * line of sight expanded in Y_l1^m(r_hat_1) Y_l2^m*(r_hat_2) (Eq. zeta_meas),
+ * whose coefficients couple through one Gaunt integral per direction:
+ *   Re NNN^m_{l1 l2} = sum 4 pi RRR^{m - m'}_{l1'' l2''} G(l1' m', l1'' m-m'; l1)
+ *                      G(l2' m', l2'' m-m'; l2) zeta_hat^m'_{l1' l2'},
+ * truncated at l_max, on the real coefficients with l1 + l2 even (the ones
+ * the L-even multipoles use; the imaginary and odd-parity parts of RRR, zero
+ * for a mirror-symmetric random catalogue, are dropped).  zeta_hat is then
+ * projected with Eq. slep2sugy.  For isotropic randoms it equals the bin-wise
+ * tpcf_estimate_3pcf.  Outputs dev: zeta[n_mult][n_bins][n_bins] (required),
+ * nnn (the D - R field's, as tpcf_couple_multipoles), rrr_multipoles
+ * [l_max+1]^3[n_bins][n_bins] (RRR^m_{l1 l2} in the nnn layout) and
+ * xi[l_max/2 + 1][n_bins] (as tpcf_estimate_3pcf_xi), each optional.  A
+ * singular system (no random triangles in a bin pair) gives NaN there and
+ * TPCF_ERR_DATA from tpcf_stream_status. */
+int tpcf_estimate_3pcf_full_edge(const tpcf_config *cfg,
+                                 const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                                 const uint32_t *r_xyz, const float *r_w, int64_t nr,
+                                 double *zeta, double *nnn, double *rrr_multipoles, double *xi, void *stream);
+
 /* As tpcf_estimate_3pcf, but every pointer is HOST memory (pinned memory gives
  * the fastest copies).  Copies in, runs, copies out, and synchronises the
  * stream before returning. */

@@ -41,6 +41,7 @@ Readings of the paper recorded here (the same list is in the design doc):
 from __future__ import annotations
 
 import ctypes
+import functools
 import math
 import os
 import subprocess
@@ -315,23 +316,14 @@ def edge_modes(L: int) -> list:
             if (l1 + l2) % 2 == 0]
 
 
-def edge_matrix(rrr_real, L: int):
-    """The coupling matrix of N = zeta R in the basis Y_l1^m(r1) Y_l2^m*(r2).
-
-    Functions of (r_hat_1, r_hat_2) about the fixed line of sight expand as
-    F = sum_{l1 l2 m} F^m_{l1 l2} Y_l1^m(r_hat_1) Y_l2^m*(r_hat_2); a product
-    couples them through one Gaunt coefficient per angle:
-      (F G)^m_{l1 l2} = sum F^m'_{l1' l2'} G^(m-m')_{l1'' l2''}
-                        gaunt(l1', m', l1'', m-m', l1) gaunt(l2', m', l2'', m-m', l2).
-    The unknowns are real with zeta^-m = zeta^m, so the columns of +m' and -m'
-    are added.  rrr_real[m][l1][l2] (m = -L..L at index m + L) holds Re RRR^m for
-    one bin pair.  The factor 4 pi makes the solution the bin-wise-normalised
-    zeta_hat^m = zeta^m / 4 pi, which equals NNN^m / RRR_00^0 for isotropic R."""
+@functools.lru_cache(maxsize=None)
+def _edge_terms(L: int):
+    """The nonzero Gaunt products of the coupling matrix (they do not depend on
+    the bins): (row, column, m'', l1'', l2'', gaunt * gaunt)."""
     modes = edge_modes(L)
-    M = np.zeros((len(modes), len(modes)))
+    terms = []
     for r, (l1, l2, m) in enumerate(modes):
         for c, (p1, p2, mp) in enumerate(modes):
-            v = 0.0
             for mq in ((mp, -mp) if mp > 0 else (0,)):
                 mr = m - mq
                 if abs(mr) > L:
@@ -342,9 +334,28 @@ def edge_matrix(rrr_real, L: int):
                             continue
                         g = gaunt(p1, mq, q1, mr, l1) * gaunt(p2, mq, q2, mr, l2)
                         if g != 0.0:
-                            v += g * rrr_real[mr + L, q1, q2]
-            M[r, c] = 4.0 * math.pi * v
-    return modes, M
+                            terms.append((r, c, mr, q1, q2, g))
+    return modes, terms
+
+
+def edge_matrix(rrr_real, L: int):
+    """The coupling matrix of N = zeta R in the basis Y_l1^m(r1) Y_l2^m*(r2).
+
+    Functions of (r_hat_1, r_hat_2) about the fixed line of sight expand as
+    F = sum_{l1 l2 m} F^m_{l1 l2} Y_l1^m(r_hat_1) Y_l2^m*(r_hat_2); a product
+    couples them through one Gaunt coefficient per angle:
+      (F G)^m_{l1 l2} = sum F^m'_{l1' l2'} G^(m-m')_{l1'' l2''}
+                        gaunt(l1', m', l1'', m-m', l1) gaunt(l2', m', l2'', m-m', l2).
+    The unknowns are real with zeta^-m = zeta^m, so the columns of +m' and -m'
+    are added.  rrr_real[m][l1][l2][...] (m = -L..L at index m + L; any trailing
+    bin axes) holds Re RRR^m.  The factor 4 pi makes the solution the
+    bin-wise-normalised zeta_hat^m = zeta^m / 4 pi, which equals
+    NNN^m / RRR_00^0 for isotropic R.  Returns (modes, M[row][col][...])."""
+    modes, terms = _edge_terms(L)
+    M = np.zeros((len(modes), len(modes)) + rrr_real.shape[3:])
+    for r, c, mr, q1, q2, g in terms:
+        M[r, c] += g * rrr_real[mr + L, q1, q2]
+    return modes, 4.0 * math.pi * M
 
 
 def edge_correct(nnn, rrr, L: int):
@@ -355,12 +366,11 @@ def edge_correct(nnn, rrr, L: int):
     outside the solved modes)."""
     nb = nnn.shape[-1]
     out = np.zeros(nnn.shape, dtype=np.complex128)
-    rr = rrr.real
+    modes, M = edge_matrix(rrr.real, L)
     for b1 in range(nb):
         for b2 in range(nb):
-            modes, M = edge_matrix(rr[:, :, :, b1, b2], L)
             rhs = np.array([nnn[m + L, l1, l2, b1, b2].real for (l1, l2, m) in modes])
-            z = np.linalg.solve(M, rhs)
+            z = np.linalg.solve(M[:, :, b1, b2], rhs)
             for (l1, l2, m), v in zip(modes, z):
                 out[m + L, l1, l2, b1, b2] = v
                 out[-m + L, l1, l2, b1, b2] = v

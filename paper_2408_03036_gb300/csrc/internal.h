@@ -122,8 +122,6 @@ cudaError_t assemble_nnn(const double *G, const double *diag, const double *wsp,
 cudaError_t project_zeta(const double *nnn, const double *rrr, int nb, int lmax, int n_mult,
                          const double *coef, const int *mults, double *zeta, cudaStream_t st);
 cudaError_t rrr_analytic(const double *wsum, const double *coef, int nb, double *rrr, cudaStream_t st);
-// RRR_00^0 = alpha^3 nnn0 (nnn0: the l = 0 coupling of the randoms with their own weights).
-cudaError_t rrr_weighted(const double *nnn0, const double *wsums, int nb, double *rrr, cudaStream_t st);
 // out[e][b] += sum_i w_i a_{lstep e}^0[b](i) (out zeroed by the caller; n_ell * nb <= 128).
 cudaError_t m0_sums(const float *alm, const float *w, int64_t K, int nb, int lmax, int n_ell, int lstep, double *out,
                     cudaStream_t st);
@@ -138,6 +136,12 @@ cudaError_t rrr_from_counts(const unsigned long long *T, const double *wsums, in
 // (idx NULL: i): mean [nd], cov [nd][nd] (Eq. covariance); bad indices latch DEV_ERR_INDEX.
 cudaError_t covariance(const double *src, int64_t n, int64_t stride, const int64_t *idx, int64_t nd, double *mean,
                        double *cov, int *err, cudaStream_t st);
+// Full edge correction: per bin pair, solve the Gaunt-coupled system of nu real
+// unknowns (term list built on the host) for zeta_hat [L1][L1][L1][nb][nb].
+cudaError_t edge_solve(const double *nnn, const double *rfull, int nb, int lmax, int nu, const int *modes,
+                       const int *tstart, const int *tridx, const double *tcoef, double *zhat, int *err,
+                       cudaStream_t st);
+cudaError_t scale_alpha3(double *x, int64_t n, const double *wsums, cudaStream_t st);
 cudaError_t i64_from_u64(const unsigned long long *src, int64_t *dst, int n, cudaStream_t st);
 
 // Offsets of the per-m Gram blocks in the packed G array: block m is

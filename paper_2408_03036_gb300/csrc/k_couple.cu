@@ -156,7 +156,7 @@ __global__ void k_assemble(const double *__restrict__ G, const double *__restric
     }
 }
 
-// zeta[k][b1][b2] = sum_m coef[k][m] nnn[m][l1][l2][b1][b2] / rrr[b1][b2]
+// zeta[k][b1][b2] = sum_m coef[k][m] nnn[m][l1][l2][b1][b2] / rrr[b1][b2] (rrr NULL: no division)
 __global__ void k_project(const double *__restrict__ nnn, const double *__restrict__ rrr, int nb, int lmax,
                           int n_mult, const double *__restrict__ coef, const int *__restrict__ mults,
                           double *__restrict__ zeta)
@@ -171,7 +171,7 @@ __global__ void k_project(const double *__restrict__ nnn, const double *__restri
         double s = 0.0;
         for (int m = 0; m <= min(l1, l2); ++m)
             s += coef[k * L1 + m] * nnn[((int64_t)(m * L1 + l1) * L1 + l2) * nb * nb + bb];
-        zeta[idx] = s / rrr[bb];
+        zeta[idx] = rrr ? s / rrr[bb] : s;
     }
 }
 
@@ -192,17 +192,6 @@ __global__ void k_rrr_counts(const unsigned long long *__restrict__ T, const dou
     if (i >= nb * nb) return;
     const double a = wsums[0] / wsums[1];
     rrr[i] = a * a * a * (double)T[i] / (4.0 * 3.14159265358979323846);
-}
-
-// RRR_00^0 = alpha^3 nnn0 with nnn0 the l = 0 coupling of the randoms weighted by w_R
-// (alpha = W_D / W_R): exact for any random weights.
-__global__ void k_rrr_scale(const double *__restrict__ nnn0, const double *__restrict__ wsums, int nb,
-                            double *__restrict__ rrr)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb * nb) return;
-    const double a = wsums[0] / wsums[1];
-    rrr[i] = a * a * a * nnn0[i];
 }
 
 // out[e][b] += sum_i w_i a_{lstep e}^0[b](i).  Each warp takes primaries in turn,
@@ -372,13 +361,6 @@ cudaError_t rrr_analytic(const double *wsum, const double *coef, int nb, double 
 cudaError_t rrr_from_counts(const unsigned long long *T, const double *wsums, int nb, double *rrr, cudaStream_t st)
 {
     k_rrr_counts<<<(nb * nb + 255) / 256, 256, 0, st>>>(T, wsums, nb, rrr);
-    note_launch();
-    return cudaGetLastError();
-}
-
-cudaError_t rrr_weighted(const double *nnn0, const double *wsums, int nb, double *rrr, cudaStream_t st)
-{
-    k_rrr_scale<<<(nb * nb + 255) / 256, 256, 0, st>>>(nnn0, wsums, nb, rrr);
     note_launch();
     return cudaGetLastError();
 }

@@ -555,6 +555,62 @@ void projection_tables(const tpcf_config *c, std::vector<double> &coef, std::vec
     }
 }
 
+// Gaunt coefficient: int Y_l1^m1 Y_l2^m2 (Y_l3^(m1+m2))* dOmega.
+double gaunt(int l1, int m1, int l2, int m2, int l3)
+{
+    const int m3 = m1 + m2;
+    if (std::abs(m1) > l1 || std::abs(m2) > l2 || std::abs(m3) > l3) return 0.0;
+    const double pre = std::sqrt((2.0 * l1 + 1.0) * (2.0 * l2 + 1.0) * (2.0 * l3 + 1.0) / (4.0 * kPi));
+    return pre * w3j(l1, l2, l3, 0, 0, 0) * w3j(l1, l2, l3, m1, m2, -m3) * ((m3 & 1) ? -1.0 : 1.0);
+}
+
+// The unknowns of the edge-correction system and the sparse terms of its matrix:
+// entry (r, c) = sum over t in [tstart[r nu + c], tstart[r nu + c + 1]) of
+// tcoef[t] * RRR block tridx[t] (block (m * L1 + l1) * L1 + l2 of the [m][l1][l2]
+// layout), with the +m' and -m' columns of a real, m-symmetric unknown added.
+struct EdgeTables {
+    std::vector<int> modes, tstart, tridx;
+    std::vector<double> tcoef;
+    int nu = 0;
+};
+
+void edge_corr_tables(int L, EdgeTables &t)
+{
+    const int L1 = L + 1;
+    t.modes.clear();
+    for (int m = 0; m <= L; ++m)
+        for (int l1 = m; l1 <= L; ++l1)
+            for (int l2 = m; l2 <= L; ++l2)
+                if (((l1 + l2) & 1) == 0) {
+                    t.modes.push_back(l1);
+                    t.modes.push_back(l2);
+                    t.modes.push_back(m);
+                }
+    t.nu = (int)t.modes.size() / 3;
+    t.tstart.assign(1, 0);
+    t.tridx.clear();
+    t.tcoef.clear();
+    for (int r = 0; r < t.nu; ++r) {
+        const int l1 = t.modes[3 * r], l2 = t.modes[3 * r + 1], m = t.modes[3 * r + 2];
+        for (int c = 0; c < t.nu; ++c) {
+            const int p1 = t.modes[3 * c], p2 = t.modes[3 * c + 1], mp = t.modes[3 * c + 2];
+            for (int sgn = 0; sgn < (mp > 0 ? 2 : 1); ++sgn) {
+                const int mq = sgn ? -mp : mp, mr = m - mq, ar = std::abs(mr);
+                if (ar > L) continue;
+                for (int q1 = ar; q1 <= L; ++q1)
+                    for (int q2 = ar; q2 <= L; ++q2) {
+                        if ((q1 + q2) & 1) continue;
+                        const double g = gaunt(p1, mq, q1, mr, l1) * gaunt(p2, mq, q2, mr, l2);
+                        if (g == 0.0) continue;
+                        t.tridx.push_back((ar * L1 + q1) * L1 + q2);
+                        t.tcoef.push_back(4.0 * kPi * g);
+                    }
+            }
+            t.tstart.push_back((int)t.tridx.size());
+        }
+    }
+}
+
 int project(const tpcf_config *c, const double *nnn, const double *rrr, double *zeta, cudaStream_t st)
 {
     std::vector<int> ml;
@@ -609,6 +665,156 @@ int dalloc(T **p, size_t n, cudaStream_t st, bool zero)
 {
     CK(cudaMallocAsync((void **)p, (n ? n : 1) * sizeof(T), st));
     if (zero) CK(cudaMemsetAsync(*p, 0, (n ? n : 1) * sizeof(T), st));
+    return TPCF_OK;
+}
+
+int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                  const uint32_t *r_xyz, const float *r_w, int64_t nr, double *zeta, double *nnn_out,
+                  double *rrr_out, int64_t *pair_counts, int64_t *triplet_counts, double *xi, bool edge_full,
+                  double *rfull_out, cudaStream_t st)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!zeta) return fail(TPCF_ERR_ARG, "zeta is required");
+    if (nd < 1 || !d_xyz) return fail(TPCF_ERR_ARG, "need at least one data point");
+    if (nr < 0 || (nr > 0 && !r_xyz)) return fail(TPCF_ERR_ARG, "bad randoms");
+    const bool analytic = (nr == 0);
+    if (analytic && !cfg->periodic) return fail(TPCF_ERR_ARG, "analytic randoms need a periodic box");
+    if (nd + nr >= kMaxPoints) return fail(TPCF_ERR_ARG, "catalogue too large (nd + nr < 2^28)");
+    DevState *ds;
+    if ((rc = dev_state(&ds))) return rc;
+    const int nb = cfg->n_bins, L = cfg->l_max;
+    const int nlm = (L + 1) * (L + 1), ndiag = (L + 1) * (L + 2) / 2;
+    const int L1 = L + 1;
+    const int n_ell = L / 2 + 1;   // even multipoles 0, 2, ..., l_max
+    // weighted randoms: RRR_00^0 and the pair normaliser come from the l = 0 harmonic
+    // sums of the randoms; unit randoms (r_w NULL or all ones): from integer counts
+    bool weighted_r = false;
+    if (!analytic && r_w) {
+        int *d_n = nullptr, h_n = 0;
+        if ((rc = dalloc(&d_n, 1, st, true))) return rc;
+        CK(count_not_one(r_w, nr, d_n, st));
+        CK(cudaMemcpyAsync(&h_n, d_n, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        cudaFreeAsync(d_n, st);
+        weighted_r = h_n != 0;
+    }
+
+    double *wsums = nullptr, *diag = nullptr, *wsp = nullptr, *nnn = nnn_out, *rrr = rrr_out, *mono = nullptr;
+    double *S = nullptr, *s0 = nullptr, *rr = nullptr;
+    float *alm = nullptr;
+    int32_t *cnt = nullptr, *cnt_r = nullptr;
+    unsigned long long *pairs = nullptr, *T = nullptr, *TR = nullptr, *pairs_r = nullptr;
+    float *alm_r = nullptr, *wprim_r = nullptr;
+    double *diag_r = nullptr, *wsp_r = nullptr, *nnn_r = nullptr;
+    GridDev gf, gr;
+    if ((rc = dalloc(&wsums, 2, st, true))) return rc;
+    CK(weight_sums(d_w, nd, r_w, nr, wsums, st));
+    const int64_t K = nd + nr;
+    // neighbour field grid: D, or D - (W_D/W_R) R
+    CK(build_grid_dev(d_xyz, d_w, nd, r_xyz, r_w, nr, analytic ? nullptr : wsums, choose_nc(cfg, K), gf, ds->err, st));
+    if ((rc = dalloc(&alm, (size_t)K * nb * nlm, st, false))) return rc;
+    if ((rc = dalloc(&cnt, (size_t)K * nb, st, false))) return rc;
+    if ((rc = dalloc(&diag, (size_t)ndiag * nb, st, true))) return rc;
+    if ((rc = dalloc(&wsp, (size_t)L1 * nb, st, true))) return rc;
+    if ((rc = dalloc(&pairs, (size_t)nb, st, true))) return rc;
+    if ((rc = dalloc(&T, (size_t)nb * nb, st, true))) return rc;
+    if (!nnn && (rc = dalloc(&nnn, (size_t)L1 * L1 * L1 * nb * nb, st, false))) return rc;
+    if (!rrr && (rc = dalloc(&rrr, (size_t)nb * nb, st, false))) return rc;
+    rc = run_pairs(cfg, gf, gf.rec, K, false, 0.0, analytic ? wsums : nullptr, analytic, alm, cnt, diag, wsp, pairs,
+                   st);
+    if (rc) return rc;
+    // primary weights in grid order are the records' w fields: pass them through a strided copy
+    float *wprim = nullptr;
+    if ((rc = dalloc(&wprim, (size_t)K, st, false))) return rc;
+    CK(cudaMemcpy2DAsync(wprim, 4, (const char *)gf.rec + 12, 16, 4, K, cudaMemcpyDeviceToDevice, st));
+    if ((rc = couple(cfg, alm, wprim, cnt, K, diag, wsp, nnn, T, st))) return rc;
+    if (xi) {
+        if ((rc = dalloc(&S, (size_t)n_ell * nb, st, true))) return rc;
+        if ((rc = dalloc(&rr, (size_t)nb, st, false))) return rc;
+        CK(m0_sums(alm, wprim, K, nb, L, n_ell, 2, S, st));
+    }
+    int rr_mode = 0;
+    if (analytic) {
+        if ((rc = mono_coef_dev(cfg, &mono, st))) return rc;
+        CK(rrr_analytic(wsums, mono, nb, rrr, st));
+    } else if (!weighted_r && !edge_full) {
+        CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
+        if ((rc = dalloc(&cnt_r, (size_t)nr * nb, st, false))) return rc;
+        if ((rc = dalloc(&TR, (size_t)nb * nb, st, true))) return rc;
+        if (xi && (rc = dalloc(&pairs_r, (size_t)nb, st, true))) return rc;
+        rc = run_pairs(cfg, gr, gr.rec, nr, true, 0.0, nullptr, false, nullptr, cnt_r, nullptr, nullptr, pairs_r,
+                       st);
+        if (rc) return rc;
+        CK(tpcf::triplet_counts(cnt_r, nr, nb, TR, st));
+        CK(rrr_from_counts(TR, wsums, nb, rrr, st));
+        rr_mode = 1;
+    } else {
+        // a harmonic pass over the randoms with their own weights, then its coupling:
+        // l = 0 only (RRR_00^0 of weighted randoms) or every l (the full edge correction)
+        tpcf_config cr = *cfg;
+        if (!edge_full) {
+            cr.l_max = 0;
+            cr.n_L = 1;
+            cr.L[0] = 0;
+        }
+        const int Lr = cr.l_max, L1r = Lr + 1;
+        const size_t nfull = (size_t)L1r * L1r * L1r * nb * nb;
+        CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
+        if ((rc = dalloc(&alm_r, (size_t)nr * nb * L1r * L1r, st, false))) return rc;
+        if ((rc = dalloc(&cnt_r, (size_t)nr * nb, st, false))) return rc;
+        if ((rc = dalloc(&diag_r, (size_t)nb * L1r * (Lr + 2) / 2, st, true))) return rc;
+        if ((rc = dalloc(&wsp_r, (size_t)nb * L1r, st, true))) return rc;
+        if (rfull_out) nnn_r = rfull_out;
+        else if ((rc = dalloc(&nnn_r, nfull, st, false))) return rc;
+        if ((rc = dalloc(&wprim_r, (size_t)nr, st, false))) return rc;
+        rc = run_pairs(&cr, gr, gr.rec, nr, false, 0.0, nullptr, false, alm_r, cnt_r, diag_r, wsp_r, nullptr, st);
+        if (rc) return rc;
+        CK(cudaMemcpy2DAsync(wprim_r, 4, (const char *)gr.rec + 12, 16, 4, nr, cudaMemcpyDeviceToDevice, st));
+        if ((rc = couple(&cr, alm_r, wprim_r, nullptr, nr, diag_r, wsp_r, nnn_r, nullptr, st))) return rc;
+        // RRR = alpha^3 times the randoms' own coupling; its m = 0, l1 = l2 = 0 block is RRR_00^0
+        CK(scale_alpha3(nnn_r, (int64_t)nfull, wsums, st));
+        CK(cudaMemcpyAsync(rrr, nnn_r, (size_t)nb * nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (xi) {
+            if ((rc = dalloc(&s0, (size_t)nb, st, true))) return rc;
+            CK(m0_sums(alm_r, wprim_r, nr, nb, Lr, 1, 2, s0, st));
+        }
+        rr_mode = 2;
+    }
+    if (edge_full) {
+        EdgeTables et;
+        edge_corr_tables(L, et);
+        int *d_modes = nullptr, *d_ts = nullptr, *d_ti = nullptr;
+        double *d_tc = nullptr, *zhat = nullptr;
+        if ((rc = dalloc(&d_modes, et.modes.size(), st, false))) return rc;
+        if ((rc = dalloc(&d_ts, et.tstart.size(), st, false))) return rc;
+        if ((rc = dalloc(&d_ti, et.tridx.size() + 1, st, false))) return rc;
+        if ((rc = dalloc(&d_tc, et.tcoef.size() + 1, st, false))) return rc;
+        if ((rc = dalloc(&zhat, (size_t)L1 * L1 * L1 * nb * nb, st, false))) return rc;
+        CK(cudaMemcpyAsync(d_modes, et.modes.data(), et.modes.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_ts, et.tstart.data(), et.tstart.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_ti, et.tridx.data(), et.tridx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_tc, et.tcoef.data(), et.tcoef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(edge_solve(nnn, nnn_r, nb, L, et.nu, d_modes, d_ts, d_ti, d_tc, zhat, ds->err, st));
+        rc = project(cfg, zhat, nullptr, zeta, st);   // synchronises: the host tables outlive the copies
+        for (void *q : {(void *)d_modes, (void *)d_ts, (void *)d_ti, (void *)d_tc, (void *)zhat}) cudaFreeAsync(q, st);
+        if (rc) return rc;
+    } else if ((rc = project(cfg, nnn, rrr, zeta, st))) {
+        return rc;
+    }
+    if (xi) CK(xi_from_sums(rr_mode, wsums, mono, pairs_r, s0, S, n_ell, 2, nb, rr, xi, st));
+    if (pair_counts) CK(i64_from_u64(pairs, pair_counts, nb, st));
+    if (triplet_counts) CK(i64_from_u64(T, triplet_counts, nb * nb, st));
+    free_grid_dev(gf, st);
+    free_grid_dev(gr, st);
+    for (void *q : {(void *)wsums, (void *)alm, (void *)cnt, (void *)diag, (void *)wsp, (void *)pairs, (void *)T,
+                    (void *)wprim, (void *)mono, (void *)cnt_r, (void *)TR, (void *)pairs_r, (void *)alm_r,
+                    (void *)wprim_r, (void *)diag_r, (void *)wsp_r, (void *)S, (void *)s0, (void *)rr})
+        if (q) cudaFreeAsync(q, st);
+    if (nnn_r && nnn_r != rfull_out) cudaFreeAsync(nnn_r, st);
+    if (!nnn_out) cudaFreeAsync(nnn, st);
+    if (!rrr_out) cudaFreeAsync(rrr, st);
+    CK(cudaGetLastError());
     return TPCF_OK;
 }
 
@@ -799,121 +1005,17 @@ int tpcf_estimate_3pcf_xi(const tpcf_config *cfg, const uint32_t *d_xyz, const f
                           double *rrr_out, int64_t *pair_counts, int64_t *triplet_counts, double *xi,
                           void *stream)
 {
-    int rc = check_config(cfg);
-    if (rc) return rc;
-    if (!zeta) return fail(TPCF_ERR_ARG, "zeta is required");
-    if (nd < 1 || !d_xyz) return fail(TPCF_ERR_ARG, "need at least one data point");
-    if (nr < 0 || (nr > 0 && !r_xyz)) return fail(TPCF_ERR_ARG, "bad randoms");
-    const bool analytic = (nr == 0);
-    if (analytic && !cfg->periodic) return fail(TPCF_ERR_ARG, "analytic randoms need a periodic box");
-    if (nd + nr >= kMaxPoints) return fail(TPCF_ERR_ARG, "catalogue too large (nd + nr < 2^28)");
-    cudaStream_t st = (cudaStream_t)stream;
-    DevState *ds;
-    if ((rc = dev_state(&ds))) return rc;
-    const int nb = cfg->n_bins, L = cfg->l_max;
-    const int nlm = (L + 1) * (L + 1), ndiag = (L + 1) * (L + 2) / 2;
-    const int L1 = L + 1;
-    const int n_ell = L / 2 + 1;   // even multipoles 0, 2, ..., l_max
-    // weighted randoms: RRR_00^0 and the pair normaliser come from the l = 0 harmonic
-    // sums of the randoms; unit randoms (r_w NULL or all ones): from integer counts
-    bool weighted_r = false;
-    if (!analytic && r_w) {
-        int *d_n = nullptr, h_n = 0;
-        if ((rc = dalloc(&d_n, 1, st, true))) return rc;
-        CK(count_not_one(r_w, nr, d_n, st));
-        CK(cudaMemcpyAsync(&h_n, d_n, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        cudaFreeAsync(d_n, st);
-        weighted_r = h_n != 0;
-    }
+    return estimate_impl(cfg, d_xyz, d_w, nd, r_xyz, r_w, nr, zeta, nnn_out, rrr_out, pair_counts, triplet_counts,
+                         xi, false, nullptr, (cudaStream_t)stream);
+}
 
-    double *wsums = nullptr, *diag = nullptr, *wsp = nullptr, *nnn = nnn_out, *rrr = rrr_out, *mono = nullptr;
-    double *S = nullptr, *s0 = nullptr, *rr = nullptr;
-    float *alm = nullptr;
-    int32_t *cnt = nullptr, *cnt_r = nullptr;
-    unsigned long long *pairs = nullptr, *T = nullptr, *TR = nullptr, *pairs_r = nullptr;
-    float *alm_r = nullptr, *wprim_r = nullptr;
-    double *diag_r = nullptr, *wsp_r = nullptr, *nnn_r = nullptr;
-    GridDev gf, gr;
-    if ((rc = dalloc(&wsums, 2, st, true))) return rc;
-    CK(weight_sums(d_w, nd, r_w, nr, wsums, st));
-    const int64_t K = nd + nr;
-    // neighbour field grid: D, or D - (W_D/W_R) R
-    CK(build_grid_dev(d_xyz, d_w, nd, r_xyz, r_w, nr, analytic ? nullptr : wsums, choose_nc(cfg, K), gf, ds->err, st));
-    if ((rc = dalloc(&alm, (size_t)K * nb * nlm, st, false))) return rc;
-    if ((rc = dalloc(&cnt, (size_t)K * nb, st, false))) return rc;
-    if ((rc = dalloc(&diag, (size_t)ndiag * nb, st, true))) return rc;
-    if ((rc = dalloc(&wsp, (size_t)L1 * nb, st, true))) return rc;
-    if ((rc = dalloc(&pairs, (size_t)nb, st, true))) return rc;
-    if ((rc = dalloc(&T, (size_t)nb * nb, st, true))) return rc;
-    if (!nnn && (rc = dalloc(&nnn, (size_t)L1 * L1 * L1 * nb * nb, st, false))) return rc;
-    if (!rrr && (rc = dalloc(&rrr, (size_t)nb * nb, st, false))) return rc;
-    rc = run_pairs(cfg, gf, gf.rec, K, false, 0.0, analytic ? wsums : nullptr, analytic, alm, cnt, diag, wsp, pairs,
-                   st);
-    if (rc) return rc;
-    // primary weights in grid order are the records' w fields: pass them through a strided copy
-    float *wprim = nullptr;
-    if ((rc = dalloc(&wprim, (size_t)K, st, false))) return rc;
-    CK(cudaMemcpy2DAsync(wprim, 4, (const char *)gf.rec + 12, 16, 4, K, cudaMemcpyDeviceToDevice, st));
-    if ((rc = couple(cfg, alm, wprim, cnt, K, diag, wsp, nnn, T, st))) return rc;
-    if (xi) {
-        if ((rc = dalloc(&S, (size_t)n_ell * nb, st, true))) return rc;
-        if ((rc = dalloc(&rr, (size_t)nb, st, false))) return rc;
-        CK(m0_sums(alm, wprim, K, nb, L, n_ell, 2, S, st));
-    }
-    int rr_mode = 0;
-    if (analytic) {
-        if ((rc = mono_coef_dev(cfg, &mono, st))) return rc;
-        CK(rrr_analytic(wsums, mono, nb, rrr, st));
-    } else if (!weighted_r) {
-        CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
-        if ((rc = dalloc(&cnt_r, (size_t)nr * nb, st, false))) return rc;
-        if ((rc = dalloc(&TR, (size_t)nb * nb, st, true))) return rc;
-        if (xi && (rc = dalloc(&pairs_r, (size_t)nb, st, true))) return rc;
-        rc = run_pairs(cfg, gr, gr.rec, nr, true, 0.0, nullptr, false, nullptr, cnt_r, nullptr, nullptr, pairs_r,
-                       st);
-        if (rc) return rc;
-        CK(tpcf::triplet_counts(cnt_r, nr, nb, TR, st));
-        CK(rrr_from_counts(TR, wsums, nb, rrr, st));
-        rr_mode = 1;
-    } else {
-        // the l = 0 pass over the randoms with their own weights, then its coupling
-        tpcf_config c0 = *cfg;
-        c0.l_max = 0;
-        c0.n_L = 1;
-        c0.L[0] = 0;
-        CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
-        if ((rc = dalloc(&alm_r, (size_t)nr * nb, st, false))) return rc;
-        if ((rc = dalloc(&cnt_r, (size_t)nr * nb, st, false))) return rc;
-        if ((rc = dalloc(&diag_r, (size_t)nb, st, true))) return rc;
-        if ((rc = dalloc(&wsp_r, (size_t)nb, st, true))) return rc;
-        if ((rc = dalloc(&nnn_r, (size_t)nb * nb, st, false))) return rc;
-        if ((rc = dalloc(&wprim_r, (size_t)nr, st, false))) return rc;
-        rc = run_pairs(&c0, gr, gr.rec, nr, false, 0.0, nullptr, false, alm_r, cnt_r, diag_r, wsp_r, nullptr, st);
-        if (rc) return rc;
-        CK(cudaMemcpy2DAsync(wprim_r, 4, (const char *)gr.rec + 12, 16, 4, nr, cudaMemcpyDeviceToDevice, st));
-        if ((rc = couple(&c0, alm_r, wprim_r, nullptr, nr, diag_r, wsp_r, nnn_r, nullptr, st))) return rc;
-        CK(rrr_weighted(nnn_r, wsums, nb, rrr, st));
-        if (xi) {
-            if ((rc = dalloc(&s0, (size_t)nb, st, true))) return rc;
-            CK(m0_sums(alm_r, wprim_r, nr, nb, 0, 1, 2, s0, st));
-        }
-        rr_mode = 2;
-    }
-    if ((rc = project(cfg, nnn, rrr, zeta, st))) return rc;
-    if (xi) CK(xi_from_sums(rr_mode, wsums, mono, pairs_r, s0, S, n_ell, 2, nb, rr, xi, st));
-    if (pair_counts) CK(i64_from_u64(pairs, pair_counts, nb, st));
-    if (triplet_counts) CK(i64_from_u64(T, triplet_counts, nb * nb, st));
-    free_grid_dev(gf, st);
-    free_grid_dev(gr, st);
-    for (void *q : {(void *)wsums, (void *)alm, (void *)cnt, (void *)diag, (void *)wsp, (void *)pairs, (void *)T,
-                    (void *)wprim, (void *)mono, (void *)cnt_r, (void *)TR, (void *)pairs_r, (void *)alm_r,
-                    (void *)wprim_r, (void *)diag_r, (void *)wsp_r, (void *)nnn_r, (void *)S, (void *)s0, (void *)rr})
-        if (q) cudaFreeAsync(q, st);
-    if (!nnn_out) cudaFreeAsync(nnn, st);
-    if (!rrr_out) cudaFreeAsync(rrr, st);
-    CK(cudaGetLastError());
-    return TPCF_OK;
+int tpcf_estimate_3pcf_full_edge(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                                 const uint32_t *r_xyz, const float *r_w, int64_t nr, double *zeta, double *nnn,
+                                 double *rrr_multipoles, double *xi, void *stream)
+{
+    if (nr < 1 || !r_xyz) return fail(TPCF_ERR_ARG, "the full edge correction needs explicit randoms");
+    return estimate_impl(cfg, d_xyz, d_w, nd, r_xyz, r_w, nr, zeta, nnn, nullptr, nullptr, nullptr, xi, true,
+                         rrr_multipoles, (cudaStream_t)stream);
 }
 
 int tpcf_estimate_3pcf_host(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,

@@ -26,7 +26,7 @@ CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
 EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
            "tpcf_bin_edges", "tpcf_build_grid", "tpcf_grid_destroy", "tpcf_grid_info", "tpcf_grid_points",
            "tpcf_accumulate_alm", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
-           "tpcf_estimate_3pcf_xi",
+           "tpcf_estimate_3pcf_xi", "tpcf_estimate_3pcf_full_edge",
            "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
            "tpcf_estimate_3pcf_batched", "tpcf_autotune",
@@ -105,6 +105,7 @@ def lib():
             "tpcf_project": ([CFG, P, P, P, P], ctypes.c_int),
             "tpcf_estimate_3pcf": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_estimate_3pcf_xi": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P, P], ctypes.c_int),
+            "tpcf_estimate_3pcf_full_edge": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P], ctypes.c_int),
             "tpcf_estimate_3pcf_host": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_stream_status": ([P], ctypes.c_int),
             "tpcf_couple_multipoles_static": ([P, P, P, I64, CFG, P, P, P, P, P], ctypes.c_int),
@@ -275,6 +276,27 @@ def estimate_3pcf(cfg: Config, d_xyz, d_w=None, r_xyz=None, r_w=None, stream=Non
     _check(lib().tpcf_estimate_3pcf(ctypes.byref(c), _ptr(dx), _ptr(dw), nd, _ptr(rx), _ptr(rw), nr,
                                     _ptr(z), _ptr(nnn), _ptr(rrr), _ptr(pc), _ptr(tc), _stream(stream)))
     return Result(z, mults, nnn, rrr, pc, tc)
+
+
+def estimate_3pcf_full_edge(cfg: Config, d_xyz, d_w, r_xyz, r_w=None, stream=None, device="cuda",
+                            want_xi=False) -> Result:
+    """tpcf_estimate_3pcf_full_edge on device tensors: zeta with the full anisotropic
+    edge correction; Result.rrr holds RRR^m_{l1 l2} [L1, L1, L1, nb, nb]."""
+    dx = _as_dev_xyz(d_xyz, device)
+    dw = _as_dev_w(d_w, device)
+    rx = _as_dev_xyz(r_xyz, device)
+    rw = _as_dev_w(r_w, device)
+    mults = multipole_index(cfg)
+    nb, L1 = cfg.n_bins, cfg.l_max + 1
+    z = torch.empty((len(mults), nb, nb), dtype=torch.float64, device=device)
+    nnn = torch.empty((L1, L1, L1, nb, nb), dtype=torch.float64, device=device)
+    rrr = torch.empty((L1, L1, L1, nb, nb), dtype=torch.float64, device=device)
+    xi = torch.empty((cfg.l_max // 2 + 1, nb), dtype=torch.float64, device=device) if want_xi else None
+    c = cfg.c()
+    _check(lib().tpcf_estimate_3pcf_full_edge(ctypes.byref(c), _ptr(dx), _ptr(dw), dx.shape[0], _ptr(rx), _ptr(rw),
+                                              rx.shape[0], _ptr(z), _ptr(nnn), _ptr(rrr), _ptr(xi),
+                                              _stream(stream)))
+    return Result(z, mults, nnn, rrr, xi=xi)
 
 
 def estimate_3pcf_host(cfg: Config, d_xyz, d_w=None, r_xyz=None, r_w=None, stream=None):

@@ -300,3 +300,60 @@ def test_tensor_core_tile_plans_match_fp32_gram(gpu, prec, nb, lmax):
                     worst = max(worst, np.abs(got[m, l1, l2] - ref[m, l1, l2]).max() / den)
     assert worst <= 1e-4, worst
     grid.close()
+
+
+# ------------------------------------------------------- full edge correction
+def compare_full_edge(gpu, gcfg, ocfg, ora, d, dw, r, rw, tol=TOL_FP32):
+    """zeta, RRR^m_{l1 l2}, NNN and xi of the full anisotropic edge correction
+    against the oracle.  RRR is held to tol of its largest (l = 0) block."""
+    res = tpcf.estimate_3pcf_full_edge(gcfg, d, dw, r, rw, want_xi=True)
+    tpcf.stream_status()
+    est = ora.estimate(ocfg, d, dw, r, rw, want_xi=True, edge="full")
+    L = gcfg.l_max
+    err = per_mult_err(res.zeta.cpu().numpy(), est.zeta)
+    assert err.max() <= tol, dict(zip(map(str, est.mults), err))
+    rg, ro = res.rrr.cpu().numpy(), est.extra["rrr_full"]
+    scale = np.abs(ro[L, 0, 0].real).max()
+    for (l1, l2, m) in ora.edge_modes(L):
+        assert np.abs(rg[m, l1, l2] - ro[m + L, l1, l2].real).max() <= tol * scale, (l1, l2, m)
+    assert nnn_err(res.nnn.cpu().numpy(), est.nnn, L) <= tol
+    xg, xo = res.xi.cpu().numpy(), est.extra["xi"]
+    for e in range(xo.shape[0]):
+        assert np.abs(xg[e] - xo[e]).max() <= tol * np.abs(xo[e]).max(), e
+    return res, est
+
+
+def test_full_edge_open_volume(gpu, ora):
+    g, o = cfg_pair(ora, r_min=10.0, r_max=100.0, n_bins=9, l_max=4, Ls=(0, 2, 4), box=600.0, periodic=False)
+    d, dw = synth.lognormal(8000, 600.0, 3, mesh=64)
+    r, rw = synth.randoms(24000, 4)
+    compare_full_edge(gpu, g, o, ora, d, dw, r, rw)
+
+
+def test_full_edge_weighted_randoms(gpu, ora):
+    g, o = cfg_pair(ora, r_min=10.0, r_max=80.0, n_bins=7, l_max=2, Ls=(0, 2), box=500.0, periodic=False)
+    d, _ = synth.lognormal(6000, 500.0, 31, mesh=64)
+    r, _ = synth.randoms(18000, 32)
+    rng = np.random.default_rng(33)
+    dw = rng.uniform(0.5, 1.5, d.shape[0]).astype(np.float32)
+    rw = rng.uniform(0.2, 1.8, r.shape[0]).astype(np.float32)
+    compare_full_edge(gpu, g, o, ora, d, dw, r, rw)
+
+
+def test_full_edge_thin_slab(gpu, ora):
+    """Data and randoms confined to a slab a third of the box thick in z: RRR is
+    strongly anisotropic, and the full correction moves the multipoles well
+    away from the bin-wise division (which it must, to undo the window)."""
+    g, o = cfg_pair(ora, r_min=10.0, r_max=70.0, n_bins=6, l_max=4, Ls=(0, 2), box=500.0, periodic=False)
+    d, dw = synth.lognormal(20000, 500.0, 41, mesh=64)
+    r, rw = synth.randoms(40000, 42)
+    cut = 2 ** 32 // 3
+    d, dw = d[d[:, 2] < cut], dw[d[:, 2] < cut]
+    r, rw = r[r[:, 2] < cut], rw[r[:, 2] < cut]
+    res, est = compare_full_edge(gpu, g, o, ora, d, dw, r, rw)
+    rf = est.extra["rrr_full"]
+    L = 4
+    assert np.abs(rf[L, 2, 0].real).max() > 0.05 * np.abs(rf[L, 0, 0].real).max()
+    binwise = ora.project(o, est.nnn, est.rrr, est.mults)[0]
+    k = est.mults.index((0, 0, 0))
+    assert np.abs(binwise[k] - est.zeta[k]).max() > 0.01 * np.abs(est.zeta[k]).max()
