@@ -330,6 +330,8 @@ def batch_mocks(args, dev, stream, tpcf, flush, rank=0):
         out[prec] = {"mocks_per_hour": n_mocks * args.batch_steps / (ms / 1000.0) * 3600.0,
                      "s_per_batch": ms / 1000.0 / args.batch_steps, "groups": groups, "cells_per_axis": nc}
         zs[prec] = z.cpu().numpy()
+        if prec == "fp32":
+            out["covariance"] = covariance_report(cfg, z, stream, tpcf, dev)
         b.close()
         del z
     # mixed against plain: worst over mocks and multipoles of max|diff| / max|plain|
@@ -356,6 +358,37 @@ def batch_mocks(args, dev, stream, tpcf, flush, rank=0):
     pts = int(off[ns] - off[0])
     out["sequential_fp32"] = {"mocks_per_hour": pts / t / (off[-1] / n_mocks) * 3600.0, "sample_mocks": ns,
                               "note": "per-mock calls on the first mocks, scaled by the batch's mean mock size"}
+    return out
+
+
+def covariance_report(cfg, z, stream, tpcf, dev, reps=3):
+    """Eq. covariance over the batch's mocks, on its zeta array in place: the
+    paper's six multipoles with eta = 3, and every entry of every multipole.
+    FLOP: 2 per multiply-add over the computed upper-triangle tiles."""
+    import torch
+    sel = [(0, 0, 0), (1, 1, 0), (2, 2, 0), (2, 0, 2), (1, 1, 2), (3, 1, 2)]
+    cases = {"six_multipoles_eta3": tpcf.data_vector_index(cfg, sel, 3), "all_entries": None}
+    out = {"mocks": int(z.shape[0])}
+    for name, idx in cases.items():
+        di = None if idx is None else torch.as_tensor(idx).to(dev)
+        nd = z[0].numel() if idx is None else int(idx.size)
+        tpcf.covariance(z, idx=di, n_dv=nd, stream=stream)
+        torch.cuda.synchronize(dev)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(reps):
+            tpcf.covariance(z, idx=di, n_dv=nd, stream=stream)
+        e.record(stream)
+        torch.cuda.synchronize(dev)
+        tpcf.stream_status(stream)
+        t = s.elapsed_time(e) / 1000.0 / reps
+        nt = (nd + 63) // 64
+        flop = 2.0 * (nt * (nt + 1) // 2) * 64 * 64 * int(z.shape[0])
+        r = {"n_dv": nd, "ms": t * 1000.0, "fp64_gflops": flop / t / 1e9}
+        if int(z.shape[0]) > nd + 4:
+            h, m1 = tpcf.covariance_factors(int(z.shape[0]), nd, 7)
+            r.update({"hartlap": h, "percival_m1_7_params": m1})
+        out[name] = r
     return out
 
 
