@@ -33,6 +33,10 @@ Readings of the paper recorded here (the same list is in the design doc):
     L-even multipoles use), dropping the imaginary and odd-parity parts of
     RRR, which vanish for a random catalogue symmetric under the reflections
     z -> -z and y -> -y and are shot noise otherwise;
+  * ``los="observer"`` replaces the fixed z line of sight (Sec. 4.1) by the
+    direction from an observer to each primary: every separation is turned
+    by R_y(-theta_i) R_z(-phi_i), which takes that direction to z, before
+    its harmonics are taken (the coupling and projection are unchanged);
   * ``convention="PAPER_EQ"`` is Eq. slep2sugy as printed with orthonormal
     Y; ``"S_COEFF"`` (default) multiplies it by sqrt((2 l1 + 1)(2 l2 + 1)), the
     coefficient of the Schmidt-normalised basis function S_{l1 l2 L} of
@@ -69,7 +73,8 @@ class _Cfg(ctypes.Structure):
     _fields_ = [("r_min", ctypes.c_double), ("r_max", ctypes.c_double),
                 ("n_bins", ctypes.c_int32), ("l_max", ctypes.c_int32),
                 ("periodic", ctypes.c_int32), ("remove_self", ctypes.c_int32),
-                ("box", ctypes.c_double), ("offset_weight", ctypes.c_double)]
+                ("box", ctypes.c_double), ("offset_weight", ctypes.c_double),
+                ("los_mode", ctypes.c_int32), ("observer", ctypes.c_double * 3)]
 
 
 def lib():
@@ -107,6 +112,8 @@ class Config:
     box: float = 500.0
     remove_self: bool = True
     convention: str = "S_COEFF"
+    los: str = "z"               # "z": fixed line of sight; "observer": from observer to primary
+    observer: tuple = (0.0, 0.0, 0.0)   # observer position (length units, box coordinates)
 
 
 def edges(cfg: Config):
@@ -164,8 +171,11 @@ def run(cfg: Config, xyz, w, offset_weight=-1.0, prim=None, want_alm=False, nthr
     w = np.ascontiguousarray(w, dtype=np.float64)
     n = xyz.shape[0]
     nb = cfg.n_bins
+    if cfg.los not in ("z", "observer"):
+        raise ValueError(cfg.los)
+    obs = (ctypes.c_double * 3)(*[float(v) / cfg.box * 4294967296.0 for v in cfg.observer])
     c = _Cfg(cfg.r_min, cfg.r_max, nb, L, int(cfg.periodic), int(cfg.remove_self), cfg.box,
-             float(offset_weight))
+             float(offset_weight), 1 if cfg.los == "observer" else 0, obs)
     nm = 2 * L + 1
     re = np.zeros((nm, L + 1, L + 1, nb, nb))
     im = np.zeros_like(re)

@@ -11,7 +11,9 @@
  *   - for every primary x_i and every secondary j in radial bin b
  *     (step function phi of Eq. alm):
  *         a_l^m[b](x_i) = sum_j w_j Y_l^m(r_hat_ij),   Y orthonormal (Eq. alm),
- *     for all l <= l_max and m = -l..l, with the line of sight fixed along z;
+ *     for all l <= l_max and m = -l..l, with the line of sight fixed along z
+ *     (Sec. 4.1), or, with los_mode 1, along the direction from an observer to
+ *     the primary (a varying line of sight, the survey generalisation);
  *   - the local product of Eq. measured_mult, kept for m = m' (common LOS),
  *     with the second coefficient conjugated, summed over primaries with the
  *     primary weight (average over x, Sec. 4.2):
@@ -156,6 +158,8 @@ typedef struct {
     int32_t remove_self;
     double box;
     double offset_weight;   /* periodic analytic randoms: W of the catalogue; < 0: no offset */
+    int32_t los_mode;       /* 0: line of sight z for every primary; 1: from the observer */
+    double observer[3];     /* observer position in fixed-point units (los_mode 1) */
 } ora_cfg;
 
 static int cell_of(uint32_t u, int nc) { return (int)(((uint64_t)u * (uint64_t)nc) >> 32); }
@@ -249,6 +253,17 @@ int ora_run(const ora_cfg *c, const uint32_t *xyz, const double *w, int64_t n,
             memset(cnt, 0, (size_t)nb * sizeof(int64_t));
             const uint32_t ux = xyz[3 * i], uy = xyz[3 * i + 1], uz = xyz[3 * i + 2];
             const int cx = cell_of(ux, nc), cy = cell_of(uy, nc), cz = cell_of(uz, nc);
+            /* varying line of sight: n_i = (x_i - observer) / |x_i - observer| at polar
+             * angle th and azimuth ph; separations are turned by R_y(-th) R_z(-ph),
+             * which takes n_i to z, before their harmonics are taken */
+            double cth = 1.0, sth = 0.0, cph = 1.0, sph = 0.0;
+            if (c->los_mode == 1) {
+                const double nx = (double)ux - c->observer[0], ny = (double)uy - c->observer[1],
+                             nz = (double)uz - c->observer[2];
+                const double nr = sqrt(nx * nx + ny * ny + nz * nz);
+                const double th = acos(nz / nr), ph = atan2(ny, nx);
+                cth = cos(th); sth = sin(th); cph = cos(ph); sph = sin(ph);
+            }
             for (int oz = 0; oz < noff; ++oz)
             for (int oy = 0; oy < noff; ++oy)
             for (int ox = 0; ox < noff; ++ox) {
@@ -279,7 +294,14 @@ int ora_run(const ora_cfg *c, const uint32_t *xyz, const double *w, int64_t n,
                     int b = 0;
                     while (b + 1 < nb && r2 >= E[b + 1]) ++b;
                     double r = sqrt((double)dx * dx + (double)dy * dy + (double)dz * dz);
-                    ora_ylm((double)dx / r, (double)dy / r, (double)dz / r, L, Y);
+                    double vx = (double)dx / r, vy = (double)dy / r, vz = (double)dz / r;
+                    if (c->los_mode == 1) {
+                        const double x1 = cph * vx + sph * vy, y1 = -sph * vx + cph * vy;
+                        vx = cth * x1 - sth * vz;
+                        vz = sth * x1 + cth * vz;
+                        vy = y1;
+                    }
+                    ora_ylm(vx, vy, vz, L, Y);
                     const double wj = w[j];
                     cplx *ab = a + (size_t)b * nlm;
                     for (int k = 0; k < nlm; ++k) ab[k] += wj * Y[k];

@@ -67,10 +67,11 @@ def dirs(d):
     return v, theta, phi
 
 
-def triplets(xyz, w, periodic, E, n_bins, lmax, prim=None):
+def triplets(xyz, w, periodic, E, n_bins, lmax, prim=None, frame=None):
     """Brute-force NNN^m_{l1 l2}[b1][b2] = sum_i w_i sum_{j != k} w_j w_k Y Y*,
     the addition-theorem sums A_l = sum_i w_i sum_{j != k} w_j w_k P_l(r_j . r_k),
-    and the integer triplet counts."""
+    and the integer triplet counts.  frame(i), if given, is a 3 x 3 matrix that
+    turns primary i's separations into the frame their harmonics are taken in."""
     w = np.asarray(w, dtype=np.float64)
     nb = n_bins
     L = lmax
@@ -83,6 +84,8 @@ def triplets(xyz, w, periodic, E, n_bins, lmax, prim=None):
         ok, bins, d = nbl[i]
         if ok.size == 0:
             continue
+        if frame is not None:
+            d = d @ np.asarray(frame(i)).T
         v, th, ph = dirs(d)
         wj = w[ok]
         B = np.zeros((ok.size, nb))

@@ -350,3 +350,56 @@ def test_xi_normaliser_is_the_random_pair_sum(ora):
     for i, (js, bins, _) in enumerate(bf.neighbours(r, False, bf.exact_edges(5.0, 40.0, 5, box))):
         np.add.at(ref, bins, alpha2 ** 2 * rw2[i] * rw2[js])
     np.testing.assert_allclose(est2.extra["rr"], ref, rtol=1e-12)
+
+
+# ------------------------------------------------------ varying line of sight
+def test_varying_los_vs_brute_force_with_scipy_frames(ora):
+    """NNN^m with the line of sight from an observer to each primary equals the
+    brute-force triplet sum in frames from scipy's Rotation.align_vectors (a
+    different azimuth about the line of sight, to which NNN^m is blind)."""
+    from scipy.spatial.transform import Rotation
+    box = 150.0
+    xyz, w = _dense_tiny(21, n=150)
+    w = w.astype(np.float64)
+    w[::4] = -0.5
+    obs = (-0.7 * box, 0.3 * box, 1.6 * box)
+    cfg = ora.Config(10.0, 45.0, 4, 3, (0, 2), False, box, los="observer", observer=obs)
+    E, _ = ora.edges(cfg)
+    o = ora.run(cfg, xyz, w, nthreads=2)
+    ou = np.array(obs) / box * 2.0 ** 32
+
+    def frame(i):
+        n = xyz[i].astype(np.float64) - ou
+        return Rotation.align_vectors([[0.0, 0.0, 1.0]], [n / np.linalg.norm(n)])[0].as_matrix()
+
+    nnn, _, _ = bf.triplets(xyz, w, False, E, cfg.n_bins, cfg.l_max, frame=frame)
+    assert np.abs(o.nnn - nnn).max() <= 1e-11 * np.abs(nnn).max()
+    fixed = ora.run(ora.Config(10.0, 45.0, 4, 3, (0, 2), False, box), xyz, w, nthreads=2)
+    assert np.abs(o.nnn - fixed.nnn).max() > 1e-3 * np.abs(nnn).max()   # the frames matter
+
+
+def test_distant_observer_on_the_z_axis_is_the_fixed_los(ora):
+    box = 150.0
+    xyz, w = _dense_tiny(22, n=150)
+    base = dict(r_min=10.0, r_max=45.0, n_bins=4, l_max=3, Ls=(0, 2), periodic=False, box=box)
+    far = ora.run(ora.Config(**base, los="observer", observer=(0.5 * box, 0.5 * box, -1e7 * box)), xyz, w)
+    fixed = ora.run(ora.Config(**base), xyz, w)
+    assert np.abs(far.nnn - fixed.nnn).max() <= 1e-6 * np.abs(fixed.nnn).max()
+
+
+def test_varying_los_is_rotation_invariant(ora):
+    """Cycling the axes of the catalogue and of the observer (exact in fixed point)
+    leaves the varying-LOS multipoles unchanged; the fixed-z ones change."""
+    box = 150.0
+    d, _ = synth.lognormal(1200, box, 23, mesh=32)
+    w = np.ones(d.shape[0])
+    obs = (0.2 * box, -1.1 * box, 0.4 * box)
+    cyc = np.ascontiguousarray(d[:, [2, 0, 1]])        # (x, y, z) -> (z, x, y)
+    obs_c = (obs[2], obs[0], obs[1])
+    base = dict(r_min=10.0, r_max=40.0, n_bins=3, l_max=2, Ls=(0, 2), periodic=False, box=box)
+    a = ora.run(ora.Config(**base, los="observer", observer=obs), d, w, nthreads=4).nnn
+    b = ora.run(ora.Config(**base, los="observer", observer=obs_c), cyc, w, nthreads=4).nnn
+    assert np.abs(a - b).max() <= 1e-10 * np.abs(a).max()
+    fa = ora.run(ora.Config(**base), d, w, nthreads=4).nnn
+    fb = ora.run(ora.Config(**base), cyc, w, nthreads=4).nnn
+    assert np.abs(fa - fb).max() > 1e-3 * np.abs(fa).max()
