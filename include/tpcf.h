@@ -87,6 +87,12 @@ typedef struct {
                                tile_primaries * n_bins <= 128); 0 = automatic */
     int32_t chunk;          /* staged pairs per CTA (multiple of 256, 512..12288, above 32 per bin);
                                0 = automatic (6144 up to l_max 4, else 12288) */
+    int32_t los;            /* line of sight: 0 = z for every primary (Sec. 4.1, default);
+                               1 = from `observer` to each primary (survey geometry): every
+                               separation's harmonics are taken in a frame whose polar axis is
+                               the primary's line of sight */
+    double observer[3];     /* observer position for los = 1 (box coordinates, same length unit;
+                               it may lie outside the box; |x| <= 1e6 box) */
 } tpcf_config;
 
 typedef struct tpcf_grid_s *tpcf_grid;   /* library-owned cell list (opaque) */

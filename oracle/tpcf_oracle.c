@@ -261,8 +261,10 @@ int ora_run(const ora_cfg *c, const uint32_t *xyz, const double *w, int64_t n,
                 const double nx = (double)ux - c->observer[0], ny = (double)uy - c->observer[1],
                              nz = (double)uz - c->observer[2];
                 const double nr = sqrt(nx * nx + ny * ny + nz * nz);
-                const double th = acos(nz / nr), ph = atan2(ny, nx);
-                cth = cos(th); sth = sin(th); cph = cos(ph); sph = sin(ph);
+                if (nr > 0.0) {   /* a primary at the observer keeps z */
+                    const double th = acos(nz / nr), ph = atan2(ny, nx);
+                    cth = cos(th); sth = sin(th); cph = cos(ph); sph = sin(ph);
+                }
             }
             for (int oz = 0; oz < noff; ++oz)
             for (int oy = 0; oy < noff; ++oy)

@@ -52,6 +52,8 @@ struct PairParams {
     double mono_w;            // W used when mono_w_dev is null
     const double *mono_w_dev; // device W (overrides mono_w)
     int use_mono;
+    int vlos;                 // 1: line of sight from obs to each primary (else z)
+    double obs[3];            // observer in fixed-point units (may lie outside the box)
     int remove_self;
     float *alm;
     int32_t *counts;

@@ -417,7 +417,10 @@ __host__ __device__ inline QMap make_qmap(int P, int nb, int s, int chunk, int b
     return m;
 }
 
-template <int LMAX>
+// static shared memory of the varying-line-of-sight variant (the frames of a tile)
+constexpr int kVlosStaticSmem = 3 * TPCF_MAX_TILE * 16;
+
+template <int LMAX, bool VLOS = false>
 __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const PairParams p, const HarmTables H)
 {
     constexpr int NLM = Layout<LMAX>::NLM;
@@ -461,6 +464,8 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
     volatile int &s_flag = misc[2];   // a queue is full
     int &s_nr = misc[3];              // non-empty candidate ranges of the tile
     int *wdone = misc + 16;           // [W] warp has no more ranges and nothing pending
+    // VLOS: rows e1, e2, e3 of each slot's rotation (e3 = line of sight), as float4
+    __shared__ float4 sRot[VLOS ? 3 * TPCF_MAX_TILE : 1];   // kVlosStaticSmem bytes
 
     for (int i = tid; i <= nb; i += T) {
         sE[i] = p.E[i];
@@ -540,6 +545,36 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                                  (int)(((unsigned long long)uz * nc) >> 32), 0);
             const float wq = __int_as_float(q.w);
             if (!(wq == wq) || isinf(wq)) latch_error(p.err, DEV_ERR_DATA);
+            if constexpr (VLOS) {
+                // line of sight n = (x_i - obs) / |x_i - obs| and an orthonormal frame
+                // (e1, e2, n); the harmonics of the m = m' coupling do not depend on
+                // the azimuth of e1 about n
+                double n0 = (double)ux - p.obs[0], n1 = (double)uy - p.obs[1], n2 = (double)uz - p.obs[2];
+                const double nr = sqrt(n0 * n0 + n1 * n1 + n2 * n2);
+                if (nr > 0.0) {
+                    n0 /= nr;
+                    n1 /= nr;
+                    n2 /= nr;
+                } else {   // a primary at the observer keeps z
+                    n0 = 0.0;
+                    n1 = 0.0;
+                    n2 = 1.0;
+                }
+                // e1 = normalise(a x n) with a the coordinate axis least aligned with n
+                double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+                if (fabs(n0) <= fabs(n1) && fabs(n0) <= fabs(n2)) a0 = 1.0;
+                else if (fabs(n1) <= fabs(n2)) a1 = 1.0;
+                else a2 = 1.0;
+                double e0 = a1 * n2 - a2 * n1, e1 = a2 * n0 - a0 * n2, e2 = a0 * n1 - a1 * n0;
+                const double er = sqrt(e0 * e0 + e1 * e1 + e2 * e2);
+                e0 /= er;
+                e1 /= er;
+                e2 /= er;
+                const double f0 = n1 * e2 - n2 * e1, f1 = n2 * e0 - n0 * e2, f2 = n0 * e1 - n1 * e0;
+                sRot[3 * tid + 0] = make_float4((float)e0, (float)e1, (float)e2, 0.f);
+                sRot[3 * tid + 1] = make_float4((float)f0, (float)f1, (float)f2, 0.f);
+                sRot[3 * tid + 2] = make_float4((float)n0, (float)n1, (float)n2, 0.f);
+            }
         }
         // tile plan (warp 0): queue capacities and lane groups in proportion to the
         // expected share e_b / np of every key; at least 32 entries and one lane each
@@ -601,7 +636,18 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                 const int n = min(live[myk], mycap);
                 const float4 *qq = queue + myq;
                 for (int e = myr; e < n; e += myg) {
-                    const float4 v = qq[e];
+                    float4 v = qq[e];
+                    if constexpr (VLOS) {
+                        // the separation in the primary's frame (e1, e2, line of sight)
+                        const float4 *R = sRot + 3 * (myk / nb);
+                        const float4 r0 = R[0], r1 = R[1], r2 = R[2];
+                        const float x = fmaf(r0.x, v.x, fmaf(r0.y, v.y, r0.z * v.z));
+                        const float y = fmaf(r1.x, v.x, fmaf(r1.y, v.y, r1.z * v.z));
+                        const float z = fmaf(r2.x, v.x, fmaf(r2.y, v.y, r2.z * v.z));
+                        v.x = x;
+                        v.y = y;
+                        v.z = z;
+                    }
                     const float r2f = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
                     // correctly rounded 1/sqrt: |n|^2 = 1 up to unbiased rounding,
                     // which the j = k cancellation on diagonal bins needs

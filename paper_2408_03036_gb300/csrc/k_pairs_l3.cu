@@ -4,8 +4,9 @@
 
 namespace tpcf {
 
-// COUNTS: integer pair counts only (k_counts); otherwise the queued harmonic kernel.
-template <int LMAX, bool COUNTS>
+// COUNTS: integer pair counts only (k_counts); otherwise the queued harmonic kernel,
+// with the line of sight along z or (VLOS) from the observer to each primary.
+template <int LMAX, bool COUNTS, bool VLOS = false>
 static cudaError_t launch_one(const PairParams &p, const HarmTables &h, int grid, int block,
                               size_t smem, cudaStream_t st)
 {
@@ -16,12 +17,13 @@ static cudaError_t launch_one(const PairParams &p, const HarmTables &h, int grid
         if constexpr (COUNTS)
             e = cudaFuncSetAttribute(k_counts<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         else
-            e = cudaFuncSetAttribute(k_pairs_q<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+            e = cudaFuncSetAttribute(k_pairs_q<LMAX, VLOS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     227 * 1024 - (VLOS ? kVlosStaticSmem : 0));
         if (e != cudaSuccess) return e;
         attr_done.fetch_or(bit, std::memory_order_acq_rel);
     }
     if constexpr (COUNTS) k_counts<0><<<grid, block, smem, st>>>(p);
-    else k_pairs_q<LMAX><<<grid, block, smem, st>>>(p, h);
+    else k_pairs_q<LMAX, VLOS><<<grid, block, smem, st>>>(p, h);
     note_launch();
     return cudaGetLastError();
 }
@@ -30,6 +32,7 @@ cudaError_t launch_pairs_l3(bool counts_only, const PairParams &p, const HarmTab
                              int block, size_t smem, cudaStream_t st)
 {
     if (counts_only) return cudaErrorInvalidValue;
+    if (p.vlos) return launch_one<3, false, true>(p, h, grid, block, smem, st);
     return launch_one<3, false>(p, h, grid, block, smem, st);
 }
 

@@ -125,6 +125,11 @@ int check_config(const tpcf_config *c)
     if (c->remove_self != 0 && c->remove_self != 1) return fail(TPCF_ERR_ARG, "remove_self must be 0 or 1");
     if (c->cell_div < 0 || c->cell_div > 6) return fail(TPCF_ERR_ARG, "cell_div must be 0..6");
     if (c->tile_primaries < 0 || c->tile_primaries > TPCF_MAX_TILE) return fail(TPCF_ERR_ARG, "tile_primaries must be 0..8");
+    if (c->los != 0 && c->los != 1) return fail(TPCF_ERR_ARG, "los must be 0 (z) or 1 (observer)");
+    if (c->los == 1)
+        for (int k = 0; k < 3; ++k)
+            if (!std::isfinite(c->observer[k]) || std::fabs(c->observer[k]) > 1e6 * c->box)
+                return fail(TPCF_ERR_ARG, "observer coordinates must be finite and within 1e6 box lengths");
     if (c->chunk != 0 && (c->chunk < 512 || (c->chunk % 256) != 0 || c->chunk > 12288))
         return fail(TPCF_ERR_ARG, "chunk must be 0 or a multiple of 256 in 512..12288");
     return TPCF_OK;
@@ -447,6 +452,8 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
         p.mono_coef[b] = vb / (c->box * c->box * c->box) / std::sqrt(4.0 * kPi);
     }
     p.use_mono = use_mono ? 1 : 0;
+    p.vlos = (c->los && !counts_only) ? 1 : 0;
+    for (int k = 0; k < 3; ++k) p.obs[k] = c->observer[k] / c->box * kTwo32;
     p.mono_w = mono_w;
     p.mono_w_dev = mono_w_dev;
     p.remove_self = c->remove_self;
@@ -459,15 +466,17 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
     const HarmTables h = make_tables(counts_only ? 0 : c->l_max);
 
     size_t smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
-    while (smem > 227 * 1024 && pl.chunk > 512) {
+    // the varying-line-of-sight kernel keeps its tile's frames in static shared memory
+    const size_t smem_cap = 227 * 1024 - ((c->los && !counts_only) ? 3 * TPCF_MAX_TILE * 16 : 0);
+    while (smem > smem_cap && pl.chunk > 512) {
         pl.chunk -= 256;
         smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
     }
-    while (smem > 227 * 1024 && pl.P > 1) {
+    while (smem > smem_cap && pl.P > 1) {
         --pl.P;
         smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
     }
-    if (smem > 227 * 1024) return fail(TPCF_ERR_UNSUPPORTED, "pair stage needs %zu bytes of shared memory", smem);
+    if (smem > smem_cap) return fail(TPCF_ERR_UNSUPPORTED, "pair stage needs %zu bytes of shared memory", smem);
     if (!counts_only) {
         // the harmonic kernel gives every key at least 32 queue entries
         while (pl.P > 1 && pl.chunk < 32 * (pl.P * c->n_bins + 1)) --pl.P;

@@ -20,6 +20,7 @@ TPCF_OK = 0
 STATUS = {0: "TPCF_OK", -1: "TPCF_ERR_ARG", -2: "TPCF_ERR_OOM", -3: "TPCF_ERR_CUDA",
           -4: "TPCF_ERR_TIMEOUT", -5: "TPCF_ERR_UNSUPPORTED", -6: "TPCF_ERR_DATA"}
 PREC = {"fp32": 0, "bf16x3": 1, "tf32x3": 2}
+LOS = {"z": 0, "observer": 1}
 CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
 
 # Names of every entry point include/tpcf.h declares (checked by the tests).
@@ -49,7 +50,8 @@ class tpcf_config(ctypes.Structure):
                 ("periodic", ctypes.c_int32), ("box", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("remove_self", ctypes.c_int32),
                 ("convention", ctypes.c_int32), ("cell_div", ctypes.c_int32),
-                ("tile_primaries", ctypes.c_int32), ("chunk", ctypes.c_int32)]
+                ("tile_primaries", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("los", ctypes.c_int32), ("observer", ctypes.c_double * 3)]
 
 
 @dataclass
@@ -68,12 +70,16 @@ class Config:
     cell_div: int = 0
     tile_primaries: int = 0
     chunk: int = 0
+    los: str = "z"                      # "z" (fixed) or "observer" (observer to each primary)
+    observer: tuple = (0.0, 0.0, 0.0)   # observer position (box coordinates) for los="observer"
 
     def c(self) -> tpcf_config:
         arr = (ctypes.c_int32 * 8)(*(list(self.Ls) + [0] * (8 - len(self.Ls))))
+        obs = (ctypes.c_double * 3)(*[float(v) for v in self.observer])
         return tpcf_config(self.r_min, self.r_max, self.n_bins, self.l_max, len(self.Ls), arr,
                            int(self.periodic), self.box, PREC[self.precision], int(self.remove_self),
-                           CONV[self.convention], self.cell_div, self.tile_primaries, self.chunk)
+                           CONV[self.convention], self.cell_div, self.tile_primaries, self.chunk,
+                           LOS[self.los], obs)
 
 
 _lib = None

@@ -33,7 +33,7 @@ def cfg_pair(ora, **kw):
     g = tpcf.Config(**kw)
     o = ora.Config(kw["r_min"], kw["r_max"], kw["n_bins"], kw["l_max"], kw.get("Ls", (0, 2, 4)),
                    kw.get("periodic", True), kw.get("box", 500.0), kw.get("remove_self", True),
-                   kw.get("convention", "S_COEFF"))
+                   kw.get("convention", "S_COEFF"), kw.get("los", "z"), kw.get("observer", (0.0, 0.0, 0.0)))
     return g, o
 
 
@@ -357,3 +357,33 @@ def test_full_edge_thin_slab(gpu, ora):
     binwise = ora.project(o, est.nnn, est.rrr, est.mults)[0]
     k = est.mults.index((0, 0, 0))
     assert np.abs(binwise[k] - est.zeta[k]).max() > 0.01 * np.abs(est.zeta[k]).max()
+
+
+# ------------------------------------------------------ varying line of sight
+def test_varying_los_open_volume(gpu, ora):
+    """Line of sight from an observer outside the cube to each primary (survey
+    geometry): harmonics in each primary's frame; zeta, NNN and xi vs the oracle."""
+    g, o = cfg_pair(ora, r_min=10.0, r_max=100.0, n_bins=9, l_max=4, Ls=(0, 2, 4), box=600.0, periodic=False,
+                    los="observer", observer=(-300.0, -180.0, -480.0))
+    d, dw = synth.lognormal(8000, 600.0, 51, mesh=64)
+    r, rw = synth.randoms(24000, 52)
+    compare(gpu, g, o, ora, d, dw, r, rw, xi=True)
+
+
+@pytest.mark.parametrize("lmax,tile", [(2, 4), (6, 0)])
+def test_varying_los_observer_inside_periodic(gpu, ora, lmax, tile):
+    """Observer at the box centre (lines of sight in every direction), analytic
+    randoms, several primaries per tile (each slot with its own frame)."""
+    g, o = cfg_pair(ora, r_min=10.0, r_max=60.0, n_bins=5, l_max=lmax, Ls=(0, 2), box=250.0,
+                    los="observer", observer=(125.0, 125.0, 125.0), tile_primaries=tile)
+    xyz, w = synth.lognormal(6000, 250.0, 53, mesh=32)
+    tol = TOL_FP32 if lmax <= 4 else TOL_FP32_L6
+    compare(gpu, g, o, ora, xyz, w, xi=True, tol=tol)
+
+
+def test_varying_los_full_edge(gpu, ora):
+    g, o = cfg_pair(ora, r_min=10.0, r_max=80.0, n_bins=6, l_max=2, Ls=(0, 2), box=500.0, periodic=False,
+                    los="observer", observer=(250.0, 250.0, -900.0))
+    d, dw = synth.lognormal(6000, 500.0, 55, mesh=64)
+    r, rw = synth.randoms(18000, 56)
+    compare_full_edge(gpu, g, o, ora, d, dw, r, rw)
