@@ -349,6 +349,15 @@ int tpcf_covariance_factors(int64_t n_mocks, int64_t n_dv, int64_t n_params, dou
 int tpcf_data_vector_index(const tpcf_config *cfg, const int32_t *l1l2L, int32_t n_sel, int32_t eta,
                            int64_t *idx, int64_t cap, int64_t *n_out);
 
+/* Diagnostic (no counterpart in the paper): compares the pair stage's
+ * reciprocal square root (the hardware estimate refined by one Newton-Raphson
+ * step) with CUDA's correctly rounded __frsqrt_rn on n log-uniform inputs in
+ * [1, 2^62) drawn from seed.  Host stats[5]: max |difference| in units in the
+ * last place, mean relative difference, mean of x y^2 - 1 for the pair stage's
+ * y, the same for the correctly rounded y, fraction of inputs that differ.
+ * Synchronises the stream. */
+int tpcf_check_rsqrt(int64_t n, uint64_t seed, double *stats, void *stream);
+
 /* Synchronises the stream and reports any latched device-side error
  * (TPCF_ERR_DATA, TPCF_ERR_TIMEOUT) or CUDA error; clears the latch. */
 int tpcf_stream_status(void *stream);

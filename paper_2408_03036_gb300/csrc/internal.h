@@ -144,6 +144,9 @@ cudaError_t edge_solve(const double *nnn, const double *rfull, int nb, int lmax,
                        const int *tstart, const int *tridx, const double *tcoef, double *zhat, int *err,
                        cudaStream_t st);
 cudaError_t scale_alpha3(double *x, int64_t n, const double *wsums, cudaStream_t st);
+// Self-check of the pair stage's reciprocal square root (see tpcf_check_rsqrt).
+cudaError_t check_rsqrt(int64_t n, unsigned long long seed, double *stats, unsigned long long *maxulp,
+                        cudaStream_t st);
 cudaError_t i64_from_u64(const unsigned long long *src, int64_t *dst, int n, cudaStream_t st);
 
 // Offsets of the per-m Gram blocks in the packed G array: block m is

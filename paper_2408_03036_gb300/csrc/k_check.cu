@@ -1,0 +1,59 @@
+// Self-check of the pair stage's reciprocal square root (rsqrt_newton) against
+// CUDA's correctly rounded __frsqrt_rn on pseudo-random inputs.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "k_pairs.cuh"
+
+namespace tpcf {
+
+namespace {
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    // splitmix64 finaliser (Steele, Lea and Flood, 2014)
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// stats: [0] max |ulp difference| (atomicMax on an integer), [1] sum of relative
+// differences, [2] sum of x y^2 - 1 for rsqrt_newton, [3] the same for __frsqrt_rn,
+// [4] count of differing results.  Inputs are log-uniform on [1, 2^62).
+__global__ void k_check_rsqrt(int64_t n, unsigned long long seed, double *stats, unsigned long long *maxulp)
+{
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0, s4 = 0.0;
+    unsigned long long mu = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long h = mix64(seed ^ mix64((unsigned long long)i));
+        const unsigned e = 127u + (unsigned)(h % 62ull);
+        const unsigned mant = (unsigned)(h >> 40) & 0x7fffffu;
+        const float x = __uint_as_float((e << 23) | mant);
+        const float a = rsqrt_newton(x), b = __frsqrt_rn(x);
+        const long long d = (long long)__float_as_uint(a) - (long long)__float_as_uint(b);
+        const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+        mu = ad > mu ? ad : mu;
+        s1 += ((double)a - (double)b) / (double)b;
+        s2 += (double)x * (double)a * (double)a - 1.0;
+        s3 += (double)x * (double)b * (double)b - 1.0;
+        s4 += d != 0 ? 1.0 : 0.0;
+    }
+    atomicAdd(stats + 1, s1);
+    atomicAdd(stats + 2, s2);
+    atomicAdd(stats + 3, s3);
+    atomicAdd(stats + 4, s4);
+    atomicMax(maxulp, mu);
+}
+
+}  // namespace
+
+cudaError_t check_rsqrt(int64_t n, unsigned long long seed, double *stats, unsigned long long *maxulp,
+                        cudaStream_t st)
+{
+    k_check_rsqrt<<<152 * 4, 256, 0, st>>>(n, seed, stats, maxulp);
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace tpcf

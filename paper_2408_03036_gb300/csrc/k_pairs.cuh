@@ -55,67 +55,120 @@ __device__ __forceinline__ void latch_error(int *err, int code)
     atomicCAS(err, 0, code);
 }
 
-// Accumulates one pair (unit vector x, y, z and weight w) into acc:
-// acc[l^2 + ...] += w V_l^m(z) (x + i y)^m (real / imaginary parts), and the
-// self sums acc[NLM + j] += w^2 f_j(z).
-template <int LMAX>
-__device__ __forceinline__ void accum_pair(float x, float y, float z, float w, float (&acc)[Layout<LMAX>::NACC])
+// 1/sqrt(x) for finite x >= 1: the hardware estimate y0 = rsqrtf(x) refined by
+// one Newton-Raphson step for f(y) = y^-2 - x, y1 = y0 + y0 (1 - x y0^2) / 2.
+// The step leaves a truncation error of -(3/2) e0^2 for a relative estimate
+// error e0 (below 1e-13), so what remains is the rounding of its last
+// operations, with no coherent bias in x y1^2 - 1 over many pairs; the j = k
+// cancellation on diagonal bins needs that (the raw estimate alone is biased).
+// tpcf_check_rsqrt compares it with the correctly rounded __frsqrt_rn.
+__device__ __forceinline__ float rsqrt_newton(float x)
 {
-    constexpr int NLM = Layout<LMAX>::NLM;
+    const float y0 = rsqrtf(x);
+    const float r = fmaf(-x * y0, y0, 1.0f);
+    return fmaf(0.5f * y0, r, y0);
+}
+
+// Packed accumulators of one lane (float2, so that every update is one paired
+// FP32 instruction with the rounding of the two scalar ones):
+//   A[l]          = (sum w V_l^0,  sum w^2 f_l)            l = 0..LMAX
+//   A[q(l, m)]    = (Re, Im of sum w V_l^m (x + i y)^m)    m = 1..LMAX, l = m..LMAX
+// f_0 = 1 and f_l = V_{2l}^0 (the self-sum polynomials).  unpack() maps them to
+// the tile layout: index l^2 (m = 0), l^2 + 2m - 1 / l^2 + 2m (Re / Im), NLM + l.
+template <int LMAX>
+struct Packed {
+    static constexpr int N0 = LMAX + 1;
+    static constexpr int N2 = N0 + LMAX * (LMAX + 1) / 2;
+    static __host__ __device__ constexpr int q(int l, int m)
+    {
+        int o = N0;
+        for (int k = 1; k < m; ++k) o += LMAX - k + 1;
+        return o + (l - m);
+    }
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Accumulates one pair (unit vector x, y, z and weight w) into the packed sums.
+template <int LMAX>
+__device__ __forceinline__ void accum_pair(float x, float y, float z, float w, float2 (&A)[Packed<LMAX>::N2])
+{
     constexpr int LZ = (2 * LMAX > 1) ? 2 * LMAX : 1;
-    float wc[LMAX + 1], ws[LMAX + 1];
-    wc[0] = w;
-    ws[0] = 0.f;
-    if (LMAX >= 1) {
-        wc[1] = w * x;
-        ws[1] = w * y;
-    }
+    // (w Re, w Im) of (x + i y)^m
+    float2 cs[LMAX + 1];
+    cs[0] = f2(w, 0.f);
+    if (LMAX >= 1) cs[1] = __fmul2_rn(f2(w, w), f2(x, y));
+    const float2 myx = f2(-y, x);
 #pragma unroll
-    for (int m = 2; m <= LMAX; ++m) {
-        wc[m] = fmaf(wc[m - 1], x, -ws[m - 1] * y);
-        ws[m] = fmaf(wc[m - 1], y, ws[m - 1] * x);
-    }
-    float zl[LZ + 1];                 // zl[l] = (2l - 1) z
+    for (int m = 2; m <= LMAX; ++m)
+        cs[m] = __ffma2_rn(f2(cs[m - 1].x, cs[m - 1].x), f2(x, y), __fmul2_rn(f2(cs[m - 1].y, cs[m - 1].y), myx));
+    float zl[LZ + 2];                 // zl[l] = (2l - 1) z
     zl[0] = 0.f;
 #pragma unroll
-    for (int l = 1; l <= LZ; ++l) zl[l] = (float)(2 * l - 1) * z;
-    float v0[LZ + 1];                 // V_l^0, kept for the self sums
+    for (int l = 1; l <= LZ; l += 2) {
+        const float2 t = __fmul2_rn(f2((float)(2 * l - 1), (float)(2 * l + 1)), f2(z, z));
+        zl[l] = t.x;
+        zl[l + 1] = t.y;
+    }
+    // V_l^0 for l <= 2 LMAX (the m = 0 chain also feeds the self sums) and V_l^1,
+    // advanced together where both exist
+    float v0[LZ + 1], v1[LMAX + 1];
+    v0[0] = 1.f;
+    if (LZ >= 1) v0[1] = zl[1];
+    if (LMAX >= 1) v1[1] = 1.f;
+    if (LMAX >= 2) v1[2] = zl[2];
 #pragma unroll
-    for (int m = 0; m <= LMAX; ++m) {
+    for (int l = 2; l <= LZ; ++l) {
+        if (LMAX >= 3 && l >= 3 && l <= LMAX) {
+            const float2 c = f2(-(float)((l - 1) * (l - 1)), -(float)(l * (l - 2)));
+            const float2 t = __ffma2_rn(f2(zl[l], zl[l]), f2(v0[l - 1], v1[l - 1]),
+                                        __fmul2_rn(c, f2(v0[l - 2], v1[l - 2])));
+            v0[l] = t.x;
+            v1[l] = t.y;
+        } else {
+            v0[l] = fmaf(zl[l], v0[l - 1], -(float)((l - 1) * (l - 1)) * v0[l - 2]);
+        }
+    }
+    const float w2 = w * w;
+    A[0] = __fadd2_rn(A[0], f2(w, w2));
+#pragma unroll
+    for (int l = 1; l <= LMAX; ++l) A[l] = __ffma2_rn(f2(v0[l], v0[2 * l]), f2(w, w2), A[l]);
+#pragma unroll
+    for (int m = 1; m <= LMAX; ++m) {
         float vm2 = 0.f, vm1 = 0.f;
 #pragma unroll
         for (int l = m; l <= LMAX; ++l) {
             float v;
-            if (l == m) v = 1.f;
+            if (m == 1) v = v1[l];
+            else if (l == m) v = 1.f;
             else if (l == m + 1) v = zl[m + 1];
             else v = fmaf(zl[l], vm1, -(float)((l + m - 1) * (l - m - 1)) * vm2);
             vm2 = vm1;
             vm1 = v;
-            if (m == 0) {
-                v0[l] = v;
-                if (l == 0) acc[0] += w;
-                else acc[l * l] = fmaf(v, wc[0], acc[l * l]);
-            } else {
-                if (l == m) {
-                    acc[l * l + 2 * m - 1] += wc[m];
-                    acc[l * l + 2 * m] += ws[m];
-                } else {
-                    acc[l * l + 2 * m - 1] = fmaf(v, wc[m], acc[l * l + 2 * m - 1]);
-                    acc[l * l + 2 * m] = fmaf(v, ws[m], acc[l * l + 2 * m]);
-                }
-            }
+            const int qi = Packed<LMAX>::q(l, m);
+            if (l == m) A[qi] = __fadd2_rn(A[qi], cs[m]);
+            else A[qi] = __ffma2_rn(f2(v, v), cs[m], A[qi]);
         }
     }
-    // continue V_l^0 up to l = 2 LMAX for the self sums
+}
+
+// Writes the packed sums of one lane to a row of the tile layout.
+template <int LMAX>
+__device__ __forceinline__ void unpack(const float2 (&A)[Packed<LMAX>::N2], float *row)
+{
+    constexpr int NLM = Layout<LMAX>::NLM;
 #pragma unroll
-    for (int l = LMAX + 1; l <= 2 * LMAX; ++l) {
-        if (l == 1) v0[1] = zl[1];
-        else v0[l] = fmaf(zl[l], v0[l - 1], -(float)((l - 1) * (l - 1)) * v0[l - 2]);
+    for (int l = 0; l <= LMAX; ++l) {
+        row[l * l] = A[l].x;
+        row[NLM + l] = A[l].y;
     }
-    const float w2 = w * w;
-    acc[NLM] += w2;
 #pragma unroll
-    for (int j = 1; j <= LMAX; ++j) acc[NLM + j] = fmaf(w2, v0[2 * j], acc[NLM + j]);
+    for (int m = 1; m <= LMAX; ++m)
+#pragma unroll
+        for (int l = m; l <= LMAX; ++l) {
+            row[l * l + 2 * m - 1] = A[Packed<LMAX>::q(l, m)].x;
+            row[l * l + 2 * m] = A[Packed<LMAX>::q(l, m)].y;
+        }
 }
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -619,9 +672,9 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         const int myr = myk >= 0 ? tid - gfirst[myk] : 0;
         const int myq = myk >= 0 ? qinfo[myk].x : 0;
         const int mycap = myk >= 0 ? qinfo[myk].y : 0;
-        float acc[NACC];
+        float2 acc[Packed<LMAX>::N2];
 #pragma unroll
-        for (int j = 0; j < NACC; ++j) acc[j] = 0.f;
+        for (int j = 0; j < Packed<LMAX>::N2; ++j) acc[j] = make_float2(0.f, 0.f);
 
         // drains the queues (all threads); returns whether every warp has finished
         auto drain = [&]() -> bool {
@@ -649,9 +702,8 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                         v.z = z;
                     }
                     const float r2f = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
-                    // correctly rounded 1/sqrt: |n|^2 = 1 up to unbiased rounding,
-                    // which the j = k cancellation on diagonal bins needs
-                    const float inv = __frsqrt_rn(r2f);
+                    // |n|^2 = 1 up to unbiased rounding (see rsqrt_newton)
+                    const float inv = rsqrt_newton(r2f);
                     accum_pair<LMAX>(v.x * inv, v.y * inv, v.z * inv, v.w, acc);
                 }
             }
@@ -739,8 +791,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         // ----- tile sums: every key's lanes added through one transpose
         {
             float *st = stage + (size_t)tid * NACCP;
-#pragma unroll
-            for (int j = 0; j < NACC; ++j) st[j] = acc[j];
+            unpack<LMAX>(acc, st);
         }
         __syncthreads();
         for (int i = tid; i < nk * NACC; i += T) {

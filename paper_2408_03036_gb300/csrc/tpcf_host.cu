@@ -1445,6 +1445,31 @@ int tpcf_data_vector_index(const tpcf_config *cfg, const int32_t *l1l2L, int32_t
     return TPCF_OK;
 }
 
+int tpcf_check_rsqrt(int64_t n, uint64_t seed, double *stats, void *stream)
+{
+    if (n < 1 || !stats) return fail(TPCF_ERR_ARG, "n >= 1 and host stats[5] required");
+    cudaStream_t st = (cudaStream_t)stream;
+    double *d = nullptr;
+    unsigned long long *mu = nullptr;
+    int rc;
+    if ((rc = dalloc(&d, 5, st, true))) return rc;
+    if ((rc = dalloc(&mu, 1, st, true))) return rc;
+    CK(check_rsqrt(n, (unsigned long long)seed, d, mu, st));
+    double h[5];
+    unsigned long long hm = 0;
+    CK(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hm, mu, sizeof(hm), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    cudaFreeAsync(d, st);
+    cudaFreeAsync(mu, st);
+    stats[0] = (double)hm;
+    stats[1] = h[1] / (double)n;
+    stats[2] = h[2] / (double)n;
+    stats[3] = h[3] / (double)n;
+    stats[4] = h[4] / (double)n;
+    return TPCF_OK;
+}
+
 int tpcf_stream_status(void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;

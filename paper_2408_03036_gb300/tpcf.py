@@ -31,7 +31,7 @@ EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_mult
            "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
            "tpcf_estimate_3pcf_batched", "tpcf_autotune",
-           "tpcf_covariance", "tpcf_covariance_factors", "tpcf_data_vector_index",
+           "tpcf_covariance", "tpcf_covariance_factors", "tpcf_data_vector_index", "tpcf_check_rsqrt",
            "tpcf_emu_create", "tpcf_emu_destroy", "tpcf_emu_param_count", "tpcf_emu_set_input_box",
            "tpcf_emu_fit_output_scaling", "tpcf_emu_train_step", "tpcf_emu_gradients", "tpcf_emu_predict",
            "tpcf_emu_get_params", "tpcf_emu_set_params", "tpcf_emu_get_output_scaling"]
@@ -123,6 +123,7 @@ def lib():
             "tpcf_estimate_3pcf_batched": ([CFG, P, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
             "tpcf_autotune": ([CFG, P, P, I64, P, CFG], ctypes.c_int),
             "tpcf_covariance": ([P, I64, I64, P, I64, P, P, P], ctypes.c_int),
+            "tpcf_check_rsqrt": ([I64, ctypes.c_uint64, P, P], ctypes.c_int),
             "tpcf_covariance_factors": ([I64, I64, I64, P, P], ctypes.c_int),
             "tpcf_data_vector_index": ([CFG, P, ctypes.c_int32, ctypes.c_int32, P, I64, P], ctypes.c_int),
             "tpcf_emu_create": ([P, ctypes.c_int32, ctypes.c_uint64, P], ctypes.c_int),
@@ -209,6 +210,14 @@ def covariance(src, idx=None, n_dv=None, stream=None):
     _check(lib().tpcf_covariance(_ptr(src), n_mocks, stride, _ptr(di), n_dv, _ptr(mean), _ptr(cov),
                                  _stream(stream)))
     return mean, cov
+
+
+def check_rsqrt(n: int, seed: int = 1, stream=None) -> dict:
+    """tpcf_check_rsqrt: the pair stage's reciprocal square root against __frsqrt_rn."""
+    st = (ctypes.c_double * 5)()
+    _check(lib().tpcf_check_rsqrt(n, seed, ctypes.addressof(st), _stream(stream)))
+    return {"max_ulp": st[0], "mean_rel_diff": st[1], "mean_norm_err": st[2], "mean_norm_err_rn": st[3],
+            "frac_differ": st[4]}
 
 
 def covariance_factors(n_mocks: int, n_dv: int, n_params: int):

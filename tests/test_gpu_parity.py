@@ -387,3 +387,15 @@ def test_varying_los_full_edge(gpu, ora):
     d, dw = synth.lognormal(6000, 500.0, 55, mesh=64)
     r, rw = synth.randoms(18000, 56)
     compare_full_edge(gpu, g, o, ora, d, dw, r, rw)
+
+
+def test_pair_stage_rsqrt_against_correctly_rounded(gpu):
+    """The pair stage's reciprocal square root (estimate + one Newton step) stays
+    within one unit in the last place of __frsqrt_rn on 2^24 log-uniform inputs,
+    and |n|^2 - 1 carries no bias beyond that of the correctly rounded result
+    (a biased |n|^2 would break the j = k cancellation on diagonal bins)."""
+    s = tpcf.check_rsqrt(1 << 24, seed=7)
+    print(s)
+    assert s["max_ulp"] <= 1
+    assert abs(s["mean_rel_diff"]) < 5e-9
+    assert abs(s["mean_norm_err"] - s["mean_norm_err_rn"]) < 5e-9
