@@ -39,9 +39,9 @@ WORKLOAD = ("clustered lognormal halos N_D=400000 (512^3 mesh, P~k^-1.5 exp(-(k/
 FLOP_PER_PAIR = 4 * 25 + 15   # algorithmic FP32 work per accepted pair at l_max = 4
 # DRAM bytes (read + write) per primary of the harmonic pair kernel, from one ncu
 # capture of the current kernel at this workload's density (400,000 primaries in
-# a 630 Mpc/h cube: 16.5 MB read + 776.9 MB written, the a_lm output); the
+# a 630 Mpc/h cube: 18.8 MB read + 777.9 MB written, the a_lm output); the
 # traffic grows with the primaries, so a launch moves this times its primaries
-PAIR_DRAM_BYTES_PER_PRIMARY = 1983.0
+PAIR_DRAM_BYTES_PER_PRIMARY = 1992.0
 # covariance batch: lognormal mocks (same field recipe, 256^3 mesh) in a periodic
 # cube of side 1000 Mpc/h, sizes uniform in [100k, 400k], analytic randoms
 N_MOCKS, MOCK_LO, MOCK_HI, MOCK_MESH, SEED_MOCKS = 256, 100_000, 400_000, 256, 77
@@ -254,6 +254,10 @@ def run_ours(args):
     # dominant kernel: the pair stage on the D-R field, timed alone with events
     roof = roofline(cfg, d, dw, r, rw, dev, stream, tpcf)
 
+    # the other estimator forms on the same workload (one call each per step)
+    variants = None if args.no_variants else variants_report(cfg, dx, dwt, rx, rwt, dev, stream, tpcf, flush,
+                                                             ms_max / args.steps)
+
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = end_to_end(cfg, d, dw, r, rw, args, stream, tpcf)
 
@@ -270,6 +274,8 @@ def run_ours(args):
                        "primaries_per_step": prim_per_step, "pairs_per_step": pairs_per_step,
                        "l2": "flushed between timed steps (256 MB write, outside the events)"},
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof, "e2e": e2e}
+    if variants is not None:
+        line["variants"] = variants
     if mocks is not None:
         line["mocks_per_hour"] = mocks
     if not args.no_precision:
@@ -282,6 +288,41 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def variants_report(cfg, dx, dwt, rx, rwt, dev, stream, tpcf, flush, plain_ms, reps=2):
+    """Primaries per second of the estimator's other forms on the headline
+    workload: with the even 2PCF multipoles, with the full anisotropic edge
+    correction (every RRR^m_{l1 l2} and the per-bin-pair solve), and with a
+    varying line of sight from an observer outside the cube."""
+    import dataclasses
+    import torch
+    n = dx.shape[0] + rx.shape[0]
+    vlos = dataclasses.replace(cfg, los="observer", observer=(-0.5 * BOX, -0.5 * BOX, -0.5 * BOX))
+    calls = {
+        "with_2pcf": lambda: tpcf.estimate_3pcf(cfg, dx, dwt, rx, rwt, stream=stream, device=dev, want_xi=True),
+        "full_edge_correction": lambda: tpcf.estimate_3pcf_full_edge(cfg, dx, dwt, rx, rwt, stream=stream,
+                                                                     device=dev),
+        "varying_los": lambda: tpcf.estimate_3pcf(vlos, dx, dwt, rx, rwt, stream=stream, device=dev),
+    }
+    out = {"plain_ms": plain_ms}
+    for name, call in calls.items():
+        call()
+        torch.cuda.synchronize(dev)
+        tpcf.stream_status(stream)
+        ms = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            call()
+            e.record(stream)
+            torch.cuda.synchronize(dev)
+            ms += s.elapsed_time(e)
+        tpcf.stream_status(stream)
+        ms /= reps
+        out[name] = {"ms_per_step": ms, "primaries_per_s": n / (ms / 1000.0), "over_plain": ms / plain_ms}
+    return out
 
 
 def batch_mocks(args, dev, stream, tpcf, flush, rank=0):
@@ -610,6 +651,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mocks", type=int, default=N_MOCKS, help="mocks in the covariance batch (0: skip)")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-multipole precision report")
+    ap.add_argument("--no-variants", action="store_true", help="skip the 2PCF / full-edge / varying-LOS timings")
     ap.add_argument("--no-emulator", action="store_true", help="skip the emulator throughput report")
     ap.add_argument("--batch-steps", type=int, default=1, help="timed graph launches of the batch")
     args = ap.parse_args()
