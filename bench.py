@@ -251,6 +251,31 @@ def run_ours(args):
     prim_per_step = ND + NR
     value = ws * prim_per_step * args.steps / (ms_max / 1000.0)
 
+    # the plain FP32 form of the same step (FP32 Gram coupling), timed the same way
+    plain = None
+    if args.precision != "fp32":
+        pcfg = config("fp32")
+        for _ in range(max(1, args.warmup // 2)):
+            pres = tpcf.estimate_3pcf(pcfg, dx, dwt, rx, rwt, stream=stream, device=dev)
+        torch.cuda.synchronize(dev)
+        # the mixed step's multipoles against the plain step's, per multipole
+        zm, zp = res.zeta.cpu().numpy(), pres.zeta.cpu().numpy()
+        den = np.abs(zp).max(axis=(1, 2))
+        mixed_err = float((np.abs(zm - zp).max(axis=(1, 2)) / np.where(den > 0, den, 1.0)).max())
+        pms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            tpcf.estimate_3pcf(pcfg, dx, dwt, rx, rwt, stream=stream, device=dev)
+            e0.record(stream)
+            torch.cuda.synchronize(dev)
+            pms += s0.elapsed_time(e0)
+        tpcf.stream_status(stream)
+        pvalue = ws * prim_per_step * args.steps / (pms / 1000.0)
+        plain = {"value": pvalue, "unit": UNIT, "ms_per_step": pms / args.steps, "mixed_over_plain": value / pvalue,
+                 "mixed_vs_plain_max_rel_err": mixed_err}
+
     # dominant kernel: the pair stage on the D-R field, timed alone with events
     roof = roofline(cfg, d, dw, r, rw, dev, stream, tpcf)
 
@@ -269,11 +294,14 @@ def run_ours(args):
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f32/" + args.precision, "data": "synthetic",
             "config": {"workload": WORKLOAD, "precision": args.precision, "parallelism": "replicas",
                        "primaries_per_step": prim_per_step, "pairs_per_step": pairs_per_step,
                        "l2": "flushed between timed steps (256 MB write, outside the events)"},
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof, "e2e": e2e}
+    if plain is not None:
+        line["plain_fp32"] = plain
     if variants is not None:
         line["variants"] = variants
     if mocks is not None:
@@ -647,7 +675,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp32", "bf16x3", "tf32x3"], default="fp32")
+    ap.add_argument("--precision", choices=["fp32", "bf16x3", "tf32x3"], default="bf16x3",
+                    help="coupling arithmetic of the headline step (the plain FP32 step is timed beside it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mocks", type=int, default=N_MOCKS, help="mocks in the covariance batch (0: skip)")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-multipole precision report")

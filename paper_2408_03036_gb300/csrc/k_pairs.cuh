@@ -280,9 +280,13 @@ __device__ __forceinline__ int cand_bin(const PairParams &p, const unsigned long
 
 // ---------------------------------------------------------------------------
 // Integer pair counts only (the random-only RRR pass): the same tiles, ranges
-// and exact binning, with one shared atomic per pair on the (slot, bin) counts.
+// and exact binning.  With one primary per tile every thread counts into its own
+// column of a [bin][thread] array (no atomics, no bank conflicts), added up per
+// tile; with several, one shared atomic per pair on the (slot, bin) counts.
+constexpr int kCountThreads = 256;
+
 struct CMap {
-    int off_E, off_prim, off_pf, off_pc, off_rstart, off_rlen, off_rslot, off_cnt, off_pairs, off_misc;
+    int off_E, off_prim, off_pf, off_pc, off_rstart, off_rlen, off_rslot, off_cnt, off_red, off_pairs, off_misc;
     int total;
 };
 
@@ -298,7 +302,8 @@ __host__ __device__ inline CMap make_cmap(int P, int nb, int s)
     m.off_rstart = o; o = align_up(o + 4 * maxr, 16);
     m.off_rlen = o;   o = align_up(o + 4 * maxr, 16);
     m.off_rslot = o;  o = align_up(o + 4 * maxr, 16);
-    m.off_cnt = o;    o = align_up(o + 4 * P * nb, 16);
+    m.off_cnt = o;    o = align_up(o + 4 * (P == 1 ? nb * kCountThreads : P * nb), 16);
+    m.off_red = o;    o = align_up(o + 4 * TPCF_MAX_BINS, 16);
     m.off_pairs = o;  o = align_up(o + 8 * nb, 16);
     m.off_misc = o;   o = align_up(o + 16, 16);
     m.total = o;
@@ -321,8 +326,10 @@ __global__ void __launch_bounds__(256, 2) k_counts(const PairParams p)
     int *rlen = reinterpret_cast<int *>(smem + M.off_rlen);
     int *rslot = reinterpret_cast<int *>(smem + M.off_rslot);
     int *cnt = reinterpret_cast<int *>(smem + M.off_cnt);
+    int *red = reinterpret_cast<int *>(smem + M.off_red);
     unsigned long long *spairs = reinterpret_cast<unsigned long long *>(smem + M.off_pairs);
     int *misc = reinterpret_cast<int *>(smem + M.off_misc);
+    const bool own = P == 1;   // per-thread counters [bin][thread]
     int &s_tile = misc[0];
     int &s_next = misc[1];
     int &s_nr = misc[2];
@@ -362,7 +369,7 @@ __global__ void __launch_bounds__(256, 2) k_counts(const PairParams p)
             sPc[tid] = make_int4((int)(((unsigned long long)ux * nc) >> 32), (int)(((unsigned long long)uy * nc) >> 32),
                                  (int)(((unsigned long long)uz * nc) >> 32), 0);
         }
-        for (int i = tid; i < np * nb; i += blockDim.x) cnt[i] = 0;
+        for (int i = tid; i < (own ? nb * kCountThreads : np * nb); i += blockDim.x) cnt[i] = 0;
         __syncthreads();
         tile_ranges(p, np, (long long)mock * p.ncell_mock, sPc, sPf, rstart, rlen, rslot, &s_nr);
         __syncthreads();
@@ -386,16 +393,34 @@ __global__ void __launch_bounds__(256, 2) k_counts(const PairParams p)
                 const int dz0 = (int)((uint32_t)q0.z - (uint32_t)pr.z), dz1 = (int)((uint32_t)q1.z - (uint32_t)pr.z);
                 const int b0 = cand_bin(p, sE, nb, i0 < len, dx0, dy0, dz0, (float)dx0, (float)dy0, (float)dz0);
                 const int b1 = cand_bin(p, sE, nb, i1 < len, dx1, dy1, dz1, (float)dx1, (float)dy1, (float)dz1);
-                if (b0 >= 0) atomicAdd(&cnt[sl * nb + b0], 1);
-                if (b1 >= 0) atomicAdd(&cnt[sl * nb + b1], 1);
+                if (own) {
+                    if (b0 >= 0) cnt[b0 * kCountThreads + tid] += 1;
+                    if (b1 >= 0) cnt[b1 * kCountThreads + tid] += 1;
+                } else {
+                    if (b0 >= 0) atomicAdd(&cnt[sl * nb + b0], 1);
+                    if (b1 >= 0) atomicAdd(&cnt[sl * nb + b1], 1);
+                }
             }
         }
         __syncthreads();
+        const int *tc = cnt;   // the tile's (slot, bin) counts
+        if (own) {
+            // one warp per bin adds the threads' columns
+            const int warp = tid >> 5, nw = blockDim.x >> 5;
+            for (int b = warp; b < nb; b += nw) {
+                int v = 0;
+                for (int t = lane; t < kCountThreads; t += 32) v += cnt[b * kCountThreads + t];
+                v = __reduce_add_sync(FULL, v);
+                if (lane == 0) red[b] = v;
+            }
+            __syncthreads();
+            tc = red;
+        }
         if (p.counts)
-            for (int i = tid; i < np * nb; i += blockDim.x) p.counts[t0 * nb + i] = cnt[i];
+            for (int i = tid; i < np * nb; i += blockDim.x) p.counts[t0 * nb + i] = tc[i];
         for (int b = tid; b < nb; b += blockDim.x) {
             unsigned long long t = 0;
-            for (int q = 0; q < np; ++q) t += (unsigned long long)cnt[q * nb + b];
+            for (int q = 0; q < np; ++q) t += (unsigned long long)tc[q * nb + b];
             spairs[b] += t;
         }
         __syncthreads();
