@@ -278,6 +278,50 @@ __device__ __forceinline__ int cand_bin(const PairParams &p, const unsigned long
     return ok ? b : -1;
 }
 
+// cand_bin for a lane's two candidates at once: the float steps as paired FP32
+// instructions (the scalar steps' roundings, so the same bins) and one warp vote
+// for the exact fallback.
+__device__ __forceinline__ int2 cand_bin2(const PairParams &p, const unsigned long long *sE, int nb, bool valid0,
+                                          bool valid1, int dx0, int dy0, int dz0, int dx1, int dy1, int dz1,
+                                          float fx0, float fy0, float fz0, float fx1, float fy1, float fz1)
+{
+    const float2 r2 = __ffma2_rn(make_float2(fx0, fx1), make_float2(fx0, fx1),
+                                 __ffma2_rn(make_float2(fy0, fy1), make_float2(fy0, fy1),
+                                            __fmul2_rn(make_float2(fz0, fz1), make_float2(fz0, fz1))));
+    const float rg0 = fmaxf(r2.x, 1.f), rg1 = fmaxf(r2.y, 1.f);
+    const float2 r = __fmul2_rn(make_float2(rg0, rg1), make_float2(rsqrtf(rg0), rsqrtf(rg1)));
+    const float2 t = __ffma2_rn(r, make_float2(p.inv_dr_u, p.inv_dr_u), make_float2(p.t_off, p.t_off));
+    const float tf0 = floorf(t.x), tf1 = floorf(t.y);
+    const float2 fr = __fadd2_rn(t, make_float2(-tf0, -tf1));
+    int b0 = (int)tf0, b1 = (int)tf1;
+    const bool sure0 = fr.x > p.tdelta && fr.x < 1.f - p.tdelta, sure1 = fr.y > p.tdelta && fr.y < 1.f - p.tdelta;
+    bool ok0 = valid0 && sure0 && b0 >= 0 && b0 < nb;
+    bool ok1 = valid1 && sure1 && b1 >= 0 && b1 < nb;
+    const bool unsure0 = valid0 && !sure0 && t.x > -1.f && t.x < (float)(nb + 1);
+    const bool unsure1 = valid1 && !sure1 && t.y > -1.f && t.y < (float)(nb + 1);
+    if (__any_sync(0xffffffffu, unsure0 || unsure1)) {
+        if (unsure0) {
+            const long long lx = dx0, ly = dy0, lz = dz0;
+            const unsigned long long q = (unsigned long long)(lx * lx) + (unsigned long long)(ly * ly)
+                                       + (unsigned long long)(lz * lz);
+            ok0 = q >= sE[0] && q < sE[nb];
+            b0 = min(max(b0, 0), nb - 1);
+            while (b0 > 0 && q < sE[b0]) --b0;
+            while (b0 < nb - 1 && q >= sE[b0 + 1]) ++b0;
+        }
+        if (unsure1) {
+            const long long lx = dx1, ly = dy1, lz = dz1;
+            const unsigned long long q = (unsigned long long)(lx * lx) + (unsigned long long)(ly * ly)
+                                       + (unsigned long long)(lz * lz);
+            ok1 = q >= sE[0] && q < sE[nb];
+            b1 = min(max(b1, 0), nb - 1);
+            while (b1 > 0 && q < sE[b1]) --b1;
+            while (b1 < nb - 1 && q >= sE[b1 + 1]) ++b1;
+        }
+    }
+    return make_int2(ok0 ? b0 : -1, ok1 ? b1 : -1);
+}
+
 // ---------------------------------------------------------------------------
 // Integer pair counts only (the random-only RRR pass): the same tiles, ranges
 // and exact binning.  With one primary per tile every thread counts into its own
@@ -391,8 +435,9 @@ __global__ void __launch_bounds__(256, 2) k_counts(const PairParams p)
                 const int dx0 = (int)((uint32_t)q0.x - (uint32_t)pr.x), dx1 = (int)((uint32_t)q1.x - (uint32_t)pr.x);
                 const int dy0 = (int)((uint32_t)q0.y - (uint32_t)pr.y), dy1 = (int)((uint32_t)q1.y - (uint32_t)pr.y);
                 const int dz0 = (int)((uint32_t)q0.z - (uint32_t)pr.z), dz1 = (int)((uint32_t)q1.z - (uint32_t)pr.z);
-                const int b0 = cand_bin(p, sE, nb, i0 < len, dx0, dy0, dz0, (float)dx0, (float)dy0, (float)dz0);
-                const int b1 = cand_bin(p, sE, nb, i1 < len, dx1, dy1, dz1, (float)dx1, (float)dy1, (float)dz1);
+                const int2 bb = cand_bin2(p, sE, nb, i0 < len, i1 < len, dx0, dy0, dz0, dx1, dy1, dz1, (float)dx0,
+                                          (float)dy0, (float)dz0, (float)dx1, (float)dy1, (float)dz1);
+                const int b0 = bb.x, b1 = bb.y;
                 if (own) {
                     if (b0 >= 0) cnt[b0 * kCountThreads + tid] += 1;
                     if (b1 >= 0) cnt[b1 * kCountThreads + tid] += 1;
@@ -800,8 +845,9 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                 const int dz0 = (int)((uint32_t)q0.z - pz), dz1 = (int)((uint32_t)q1.z - pz);
                 const float fx0 = (float)dx0, fy0 = (float)dy0, fz0 = (float)dz0;
                 const float fx1 = (float)dx1, fy1 = (float)dy1, fz1 = (float)dz1;
-                const int b0 = cand_bin(p, sE, nb, v0, dx0, dy0, dz0, fx0, fy0, fz0);
-                const int b1 = cand_bin(p, sE, nb, v1, dx1, dy1, dz1, fx1, fy1, fz1);
+                const int2 bb = cand_bin2(p, sE, nb, v0, v1, dx0, dy0, dz0, dx1, dy1, dz1, fx0, fy0, fz0, fx1, fy1,
+                                          fz1);
+                const int b0 = bb.x, b1 = bb.y;
                 have0 = b0 >= 0;
                 have1 = b1 >= 0;
                 ent0 = make_float4(fx0, fy0, fz0, __int_as_float(q0.w));
