@@ -14,6 +14,8 @@
 
 namespace tpcf {
 
+struct HarmTables;   // harmonic normalisation and self-sum tables (k_pairs.cuh)
+
 // Device-side error latch values (first error wins).
 enum : int { DEV_OK = 0, DEV_ERR_DATA = 1, DEV_ERR_TIMEOUT = 2, DEV_ERR_CAPACITY = 3, DEV_ERR_INDEX = 4 };
 
@@ -52,6 +54,7 @@ struct PairParams {
     double mono_w;            // W used when mono_w_dev is null
     const double *mono_w_dev; // device W (overrides mono_w)
     int use_mono;
+    const HarmTables *harm;   // device copy of the harmonic tables
     int vlos;                 // 1: line of sight from obs to each primary (else z)
     double obs[3];            // observer in fixed-point units (may lie outside the box)
     int remove_self;

@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                     int l = 1;
                     while ((l + 1) * (l + 1) <= k) ++l;
                     const int m = (k - l * l + 1) >> 1;
-                    v = (float)((double)raw * H.K[l][m]);
+                    v = (float)((double)raw * __ldg(&p.harm->K[l][m]));
                 }
                 p.alm[(g0 + slot) * nb * NLM + rem] = v;
             }
@@ -906,14 +906,15 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
             while ((l + 1) * (l + 2) / 2 <= jd) ++l;
             const int m = jd - l * (l + 1) / 2;
             float acc2 = 0.f;
-            const float k2 = (float)(H.K[l][m] * H.K[l][m]);
+            const double kd = __ldg(&p.harm->K[l][m]);
+            const float k2 = (float)(kd * kd);
             for (int sl = 0; sl < np; ++sl) {
                 const float *a = sacc + (sl * nb + b) * NACCP;
                 float self = 0.f;
                 if (p.remove_self)
                     for (int j = 0; j <= LMAX; ++j) {
-                        self = fmaf(H.gd_hi[jd][j], a[NLM + j], self);
-                        self = fmaf(H.gd_lo[jd][j], a[NLM + j], self);
+                        self = fmaf(__ldg(&p.harm->gd_hi[jd][j]), a[NLM + j], self);
+                        self = fmaf(__ldg(&p.harm->gd_lo[jd][j]), a[NLM + j], self);
                     }
                 float d;
                 if (l == 0) {

@@ -306,6 +306,9 @@ void multipole_list(const tpcf_config *c, std::vector<int> &out)
 struct DevState {
     int *err = nullptr;
     int sms = 0;
+    // device copies of the harmonic tables, one per l_max (read by the pair
+    // stage's tile epilogue with lane-dependent indices)
+    HarmTables *harm[TPCF_MAX_LMAX + 1] = {};
 };
 std::mutex g_mu;
 DevState g_dev[64];
@@ -464,6 +467,16 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
     p.pair_counts = pair_counts;
     p.err = ds->err;
     const HarmTables h = make_tables(counts_only ? 0 : c->l_max);
+    {
+        const int hl = counts_only ? 0 : c->l_max;
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!ds->harm[hl]) {
+            // once per device and l_max, before any capture: a synchronous upload
+            CK(cudaMalloc((void **)&ds->harm[hl], sizeof(HarmTables)));
+            CK(cudaMemcpy(ds->harm[hl], &h, sizeof(HarmTables), cudaMemcpyHostToDevice));
+        }
+        p.harm = ds->harm[hl];
+    }
 
     size_t smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
     // the varying-line-of-sight kernel keeps its tile's frames in static shared memory
