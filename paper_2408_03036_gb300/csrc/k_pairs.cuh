@@ -1,7 +1,8 @@
 // Pair stage of the anisotropic 3PCF estimator (Eq. alm of arXiv:2408.03036,
 // Sec. 4.2): for every primary, neighbour search to r_max over a cell list,
 // exact integer radial binning, and per-bin sums of w_j Y_l^m(r_hat_ij) with
-// the line of sight along z.  Also the per-bin sums of w_j^2 f_j(mu) that give
+// the line of sight along z (or, in the VLOS variant, from an observer to the
+// primary).  Also the per-bin sums of w_j^2 f_j(mu) that give
 // the degenerate j = k triangle term, and integer pair counts.
 //
 // Both kernels are persistent: a CTA takes tiles of P primaries from an atomic
@@ -9,8 +10,8 @@
 // contiguous record ranges (cells are stored x-fastest, so a run of cells along
 // x is one range), trimmed to the sphere of radius r_max; warps take ranges in
 // a strided order (which mixes radii) and sweep them 32 candidates per step,
-// binning each candidate exactly (cand_bin).  k_counts adds integer counts;
-// k_pairs_q (below) accumulates the harmonic sums.
+// binning each candidate exactly (cand_bin2, two per lane).  k_counts adds
+// integer counts; k_pairs_q (below) accumulates the harmonic sums.
 #pragma once
 
 #include <cstdint>
@@ -20,7 +21,9 @@
 
 namespace tpcf {
 
-// Constant tables passed by value (kernel parameter space is a constant bank).
+// Constant tables, passed by value (kernel parameter space is a constant bank,
+// fine for warp-uniform reads) and as a device copy (PairParams::harm) for the
+// tile epilogue, whose lanes read different entries.
 //
 // Harmonics are accumulated unnormalised: for a unit vector (x, y, z),
 //     Y_l^m = K_lm V_l^m(z) (x + i y)^m,
