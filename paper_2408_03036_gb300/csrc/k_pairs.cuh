@@ -795,6 +795,9 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         bool done = false, have0 = false, have1 = false;
         float4 ent0 = make_float4(0.f, 0.f, 0.f, 0.f), ent1 = ent0;
         int ek0 = 0, ek1 = 0;
+        // the next step's records of the current range, loaded one step ahead
+        int4 nx0 = make_int4(0, 0, 0, 0), nx1 = nx0;
+        bool have_next = false;
         // appends a pending entry (one shared atomic); an entry that finds its queue
         // full stays pending and raises the flag.  (Aggregating equal keys across the
         // warp with a match instruction measured slower.)
@@ -837,12 +840,24 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                     pz = (uint32_t)pr.z;
                     kb = sl * nb;
                     my_pos = 0;
+                    have_next = false;
                 }
                 const int i0 = my_pos + lane, i1 = i0 + 32;
-                my_pos += 64;
                 const bool v0 = i0 < my_len, v1 = i1 < my_len;
-                const int4 q0 = p.rec[my_start + min(i0, my_len - 1)];
-                const int4 q1 = p.rec[my_start + min(i1, my_len - 1)];
+                int4 q0, q1;
+                if (have_next) {
+                    q0 = nx0;
+                    q1 = nx1;
+                } else {
+                    q0 = p.rec[my_start + min(i0, my_len - 1)];
+                    q1 = p.rec[my_start + min(i1, my_len - 1)];
+                }
+                my_pos += 64;
+                have_next = my_pos < my_len;   // warp-uniform
+                if (have_next) {
+                    nx0 = p.rec[my_start + min(my_pos + lane, my_len - 1)];
+                    nx1 = p.rec[my_start + min(my_pos + lane + 32, my_len - 1)];
+                }
                 const int dx0 = (int)((uint32_t)q0.x - px), dx1 = (int)((uint32_t)q1.x - px);
                 const int dy0 = (int)((uint32_t)q0.y - py), dy1 = (int)((uint32_t)q1.y - py);
                 const int dz0 = (int)((uint32_t)q0.z - pz), dz1 = (int)((uint32_t)q1.z - pz);
