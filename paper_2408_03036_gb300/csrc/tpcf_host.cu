@@ -400,6 +400,45 @@ cudaError_t pair_launch(int lmax, bool counts, const PairParams &p, const HarmTa
 }
 
 // Runs the pair stage over `n_prim` primary records against grid g.
+template <class T>
+int dalloc(T **p, size_t n, cudaStream_t st, bool zero)
+{
+    CK(cudaMallocAsync((void **)p, (n ? n : 1) * sizeof(T), st));
+    if (zero) CK(cudaMemsetAsync(*p, 0, (n ? n : 1) * sizeof(T), st));
+    return TPCF_OK;
+}
+
+// Device buffers and grids a host function allocates for itself, released in
+// stream order on every return path (success or error).
+class Scratch {
+public:
+    explicit Scratch(cudaStream_t st) : st_(st) {}
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+    ~Scratch()
+    {
+        for (void *q : ptrs_) cudaFreeAsync(q, st_);
+        for (GridDev *g : grids_) free_grid_dev(*g, st_);
+    }
+    template <class T>
+    int alloc(T **p, size_t n, bool zero)
+    {
+        const int rc = dalloc(p, n, st_, zero);
+        keep(*p);
+        return rc;
+    }
+    void keep(void *q)
+    {
+        if (q) ptrs_.push_back(q);
+    }
+    void own(GridDev &g) { grids_.push_back(&g); }
+
+private:
+    cudaStream_t st_;
+    std::vector<void *> ptrs_;
+    std::vector<GridDev *> grids_;
+};
+
 struct BatchInfo {
     const int *prim_mock;       // mock of every primary
     int64_t ncell_mock;         // cells per mock
@@ -506,9 +545,9 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
     }
     p.P = pl.P;
     p.chunk = pl.chunk;
+    Scratch sc(st);
     int *work = nullptr;
-    CK(cudaMallocAsync((void **)&work, sizeof(int), st));
-    CK(cudaMemsetAsync(work, 0, sizeof(int), st));
+    if ((rc = sc.alloc(&work, 1, true))) return rc;
     p.work = work;
     // the count kernel is small (about 50 registers, a few KB of shared memory): four CTAs per SM
     const int per_sm = counts_only ? 4 : (smem <= 110 * 1024 ? 2 : 1);
@@ -516,7 +555,6 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
     const int64_t tiles = (n_prim + pl.P - 1) / pl.P;
     if (grid > tiles) grid = (int)tiles;
     cudaError_t e = pair_launch(c->l_max, counts_only, p, h, grid, smem, st);
-    cudaFreeAsync(work, st);
     if (e != cudaSuccess) return cuda_fail(e, "pair stage launch");
     return TPCF_OK;
 }
@@ -529,9 +567,9 @@ int couple(const tpcf_config *c, const float *alm, const float *w, const int32_t
     int rc0 = dev_state(&ds);
     if (rc0) return rc0;
     int64_t gsz = gram_offset(nb, L, L + 1);
+    Scratch sc(st);
     double *G = nullptr, *gaunt = nullptr;
-    CK(cudaMallocAsync((void **)&G, gsz * sizeof(double), st));
-    CK(cudaMemsetAsync(G, 0, gsz * sizeof(double), st));
+    if ((rc0 = sc.alloc(&G, (size_t)gsz, true))) return rc0;
     const int L1 = L + 1;
     std::vector<double> hg((size_t)L1 * L1 * L1 * L1, 0.0);
     for (int m = 0; m <= L; ++m)
@@ -542,7 +580,7 @@ int couple(const tpcf_config *c, const float *alm, const float *w, const int32_t
                 const double kk = k_scale(l1, m) * k_scale(l2, m);
                 for (int j = 0; j <= L; ++j) hg[(((size_t)m * L1 + l1) * L1 + l2) * L1 + j] = kk * g[j];
             }
-    CK(cudaMallocAsync((void **)&gaunt, hg.size() * sizeof(double), st));
+    if ((rc0 = sc.alloc(&gaunt, hg.size(), false))) return rc0;
     CK(cudaMemcpyAsync(gaunt, hg.data(), hg.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     if (c->precision == TPCF_PREC_FP32) {
         CK(couple_gram_simt(alm, w, K, nb, L, G, ds->sms, st));
@@ -556,8 +594,6 @@ int couple(const tpcf_config *c, const float *alm, const float *w, const int32_t
     if (counts && trip_u64) CK(tpcf::triplet_counts(counts, K, nb, trip_u64, st));
     // the host vector must outlive the asynchronous copy
     CK(cudaStreamSynchronize(st));
-    cudaFreeAsync(G, st);
-    cudaFreeAsync(gaunt, st);
     return TPCF_OK;
 }
 
@@ -648,16 +684,16 @@ int project(const tpcf_config *c, const double *nnn, const double *rrr, double *
             coef[(size_t)k * L1 + m] = conv * (2.0 * L + 1.0) * H * (m == 0 ? t : 2.0 * t);
         }
     }
+    Scratch sc(st);
     double *dcoef = nullptr;
     int *dml = nullptr;
-    CK(cudaMallocAsync((void **)&dcoef, coef.size() * sizeof(double) + 8, st));
-    CK(cudaMallocAsync((void **)&dml, ml.size() * sizeof(int) + 4, st));
+    int rc = sc.alloc(&dcoef, coef.size() + 1, false);
+    if (!rc) rc = sc.alloc(&dml, ml.size() + 1, false);
+    if (rc) return rc;
     CK(cudaMemcpyAsync(dcoef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(dml, ml.data(), ml.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(project_zeta(nnn, rrr, c->n_bins, c->l_max, nm, dcoef, dml, zeta, st));
     CK(cudaStreamSynchronize(st));
-    cudaFreeAsync(dcoef, st);
-    cudaFreeAsync(dml, st);
     return TPCF_OK;
 }
 
@@ -682,13 +718,6 @@ int mono_coef_dev(const tpcf_config *c, double **out, cudaStream_t st)
     return TPCF_OK;
 }
 
-template <class T>
-int dalloc(T **p, size_t n, cudaStream_t st, bool zero)
-{
-    CK(cudaMallocAsync((void **)p, (n ? n : 1) * sizeof(T), st));
-    if (zero) CK(cudaMemsetAsync(*p, 0, (n ? n : 1) * sizeof(T), st));
-    return TPCF_OK;
-}
 
 int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,
                   const uint32_t *r_xyz, const float *r_w, int64_t nr, double *zeta, double *nnn_out,
@@ -705,6 +734,10 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
     if (nd + nr >= kMaxPoints) return fail(TPCF_ERR_ARG, "catalogue too large (nd + nr < 2^28)");
     DevState *ds;
     if ((rc = dev_state(&ds))) return rc;
+    GridDev gf, gr;   // declared before the guard that releases them
+    Scratch sc(st);
+    sc.own(gf);
+    sc.own(gr);
     const int nb = cfg->n_bins, L = cfg->l_max;
     const int nlm = (L + 1) * (L + 1), ndiag = (L + 1) * (L + 2) / 2;
     const int L1 = L + 1;
@@ -714,11 +747,10 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
     bool weighted_r = false;
     if (!analytic && r_w) {
         int *d_n = nullptr, h_n = 0;
-        if ((rc = dalloc(&d_n, 1, st, true))) return rc;
+        if ((rc = sc.alloc(&d_n, 1, true))) return rc;
         CK(count_not_one(r_w, nr, d_n, st));
         CK(cudaMemcpyAsync(&h_n, d_n, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        cudaFreeAsync(d_n, st);
         weighted_r = h_n != 0;
     }
 
@@ -729,42 +761,43 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
     unsigned long long *pairs = nullptr, *T = nullptr, *TR = nullptr, *pairs_r = nullptr;
     float *alm_r = nullptr, *wprim_r = nullptr;
     double *diag_r = nullptr, *wsp_r = nullptr, *nnn_r = nullptr;
-    GridDev gf, gr;
-    if ((rc = dalloc(&wsums, 2, st, true))) return rc;
+    if ((rc = sc.alloc(&wsums, 2, true))) return rc;
     CK(weight_sums(d_w, nd, r_w, nr, wsums, st));
     const int64_t K = nd + nr;
     // neighbour field grid: D, or D - (W_D/W_R) R
     CK(build_grid_dev(d_xyz, d_w, nd, r_xyz, r_w, nr, analytic ? nullptr : wsums, choose_nc(cfg, K), gf, ds->err, st));
-    if ((rc = dalloc(&alm, (size_t)K * nb * nlm, st, false))) return rc;
-    if ((rc = dalloc(&cnt, (size_t)K * nb, st, false))) return rc;
-    if ((rc = dalloc(&diag, (size_t)ndiag * nb, st, true))) return rc;
-    if ((rc = dalloc(&wsp, (size_t)L1 * nb, st, true))) return rc;
-    if ((rc = dalloc(&pairs, (size_t)nb, st, true))) return rc;
-    if ((rc = dalloc(&T, (size_t)nb * nb, st, true))) return rc;
-    if (!nnn && (rc = dalloc(&nnn, (size_t)L1 * L1 * L1 * nb * nb, st, false))) return rc;
-    if (!rrr && (rc = dalloc(&rrr, (size_t)nb * nb, st, false))) return rc;
+    if ((rc = sc.alloc(&alm, (size_t)K * nb * nlm, false))) return rc;
+    if ((rc = sc.alloc(&cnt, (size_t)K * nb, false))) return rc;
+    if ((rc = sc.alloc(&diag, (size_t)ndiag * nb, true))) return rc;
+    if ((rc = sc.alloc(&wsp, (size_t)L1 * nb, true))) return rc;
+    if ((rc = sc.alloc(&pairs, (size_t)nb, true))) return rc;
+    if ((rc = sc.alloc(&T, (size_t)nb * nb, true))) return rc;
+    if (!nnn && (rc = sc.alloc(&nnn, (size_t)L1 * L1 * L1 * nb * nb, false))) return rc;
+    if (!rrr && (rc = sc.alloc(&rrr, (size_t)nb * nb, false))) return rc;
     rc = run_pairs(cfg, gf, gf.rec, K, false, 0.0, analytic ? wsums : nullptr, analytic, alm, cnt, diag, wsp, pairs,
                    st);
     if (rc) return rc;
     // primary weights in grid order are the records' w fields: pass them through a strided copy
     float *wprim = nullptr;
-    if ((rc = dalloc(&wprim, (size_t)K, st, false))) return rc;
+    if ((rc = sc.alloc(&wprim, (size_t)K, false))) return rc;
     CK(cudaMemcpy2DAsync(wprim, 4, (const char *)gf.rec + 12, 16, 4, K, cudaMemcpyDeviceToDevice, st));
     if ((rc = couple(cfg, alm, wprim, cnt, K, diag, wsp, nnn, T, st))) return rc;
     if (xi) {
-        if ((rc = dalloc(&S, (size_t)n_ell * nb, st, true))) return rc;
-        if ((rc = dalloc(&rr, (size_t)nb, st, false))) return rc;
+        if ((rc = sc.alloc(&S, (size_t)n_ell * nb, true))) return rc;
+        if ((rc = sc.alloc(&rr, (size_t)nb, false))) return rc;
         CK(m0_sums(alm, wprim, K, nb, L, n_ell, 2, S, st));
     }
     int rr_mode = 0;
     if (analytic) {
-        if ((rc = mono_coef_dev(cfg, &mono, st))) return rc;
+        rc = mono_coef_dev(cfg, &mono, st);
+        sc.keep(mono);
+        if (rc) return rc;
         CK(rrr_analytic(wsums, mono, nb, rrr, st));
     } else if (!weighted_r && !edge_full) {
         CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
-        if ((rc = dalloc(&cnt_r, (size_t)nr * nb, st, false))) return rc;
-        if ((rc = dalloc(&TR, (size_t)nb * nb, st, true))) return rc;
-        if (xi && (rc = dalloc(&pairs_r, (size_t)nb, st, true))) return rc;
+        if ((rc = sc.alloc(&cnt_r, (size_t)nr * nb, false))) return rc;
+        if ((rc = sc.alloc(&TR, (size_t)nb * nb, true))) return rc;
+        if (xi && (rc = sc.alloc(&pairs_r, (size_t)nb, true))) return rc;
         rc = run_pairs(cfg, gr, gr.rec, nr, true, 0.0, nullptr, false, nullptr, cnt_r, nullptr, nullptr, pairs_r,
                        st);
         if (rc) return rc;
@@ -783,13 +816,13 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
         const int Lr = cr.l_max, L1r = Lr + 1;
         const size_t nfull = (size_t)L1r * L1r * L1r * nb * nb;
         CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
-        if ((rc = dalloc(&alm_r, (size_t)nr * nb * L1r * L1r, st, false))) return rc;
-        if ((rc = dalloc(&cnt_r, (size_t)nr * nb, st, false))) return rc;
-        if ((rc = dalloc(&diag_r, (size_t)nb * L1r * (Lr + 2) / 2, st, true))) return rc;
-        if ((rc = dalloc(&wsp_r, (size_t)nb * L1r, st, true))) return rc;
+        if ((rc = sc.alloc(&alm_r, (size_t)nr * nb * L1r * L1r, false))) return rc;
+        if ((rc = sc.alloc(&cnt_r, (size_t)nr * nb, false))) return rc;
+        if ((rc = sc.alloc(&diag_r, (size_t)nb * L1r * (Lr + 2) / 2, true))) return rc;
+        if ((rc = sc.alloc(&wsp_r, (size_t)nb * L1r, true))) return rc;
         if (rfull_out) nnn_r = rfull_out;
-        else if ((rc = dalloc(&nnn_r, nfull, st, false))) return rc;
-        if ((rc = dalloc(&wprim_r, (size_t)nr, st, false))) return rc;
+        else if ((rc = sc.alloc(&nnn_r, nfull, false))) return rc;
+        if ((rc = sc.alloc(&wprim_r, (size_t)nr, false))) return rc;
         rc = run_pairs(&cr, gr, gr.rec, nr, false, 0.0, nullptr, false, alm_r, cnt_r, diag_r, wsp_r, nullptr, st);
         if (rc) return rc;
         CK(cudaMemcpy2DAsync(wprim_r, 4, (const char *)gr.rec + 12, 16, 4, nr, cudaMemcpyDeviceToDevice, st));
@@ -798,7 +831,7 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
         CK(scale_alpha3(nnn_r, (int64_t)nfull, wsums, st));
         CK(cudaMemcpyAsync(rrr, nnn_r, (size_t)nb * nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
         if (xi) {
-            if ((rc = dalloc(&s0, (size_t)nb, st, true))) return rc;
+            if ((rc = sc.alloc(&s0, (size_t)nb, true))) return rc;
             CK(m0_sums(alm_r, wprim_r, nr, nb, Lr, 1, 2, s0, st));
         }
         rr_mode = 2;
@@ -808,34 +841,23 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
         edge_corr_tables(L, et);
         int *d_modes = nullptr, *d_ts = nullptr, *d_ti = nullptr;
         double *d_tc = nullptr, *zhat = nullptr;
-        if ((rc = dalloc(&d_modes, et.modes.size(), st, false))) return rc;
-        if ((rc = dalloc(&d_ts, et.tstart.size(), st, false))) return rc;
-        if ((rc = dalloc(&d_ti, et.tridx.size() + 1, st, false))) return rc;
-        if ((rc = dalloc(&d_tc, et.tcoef.size() + 1, st, false))) return rc;
-        if ((rc = dalloc(&zhat, (size_t)L1 * L1 * L1 * nb * nb, st, false))) return rc;
+        if ((rc = sc.alloc(&d_modes, et.modes.size(), false))) return rc;
+        if ((rc = sc.alloc(&d_ts, et.tstart.size(), false))) return rc;
+        if ((rc = sc.alloc(&d_ti, et.tridx.size() + 1, false))) return rc;
+        if ((rc = sc.alloc(&d_tc, et.tcoef.size() + 1, false))) return rc;
+        if ((rc = sc.alloc(&zhat, (size_t)L1 * L1 * L1 * nb * nb, false))) return rc;
         CK(cudaMemcpyAsync(d_modes, et.modes.data(), et.modes.size() * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(d_ts, et.tstart.data(), et.tstart.size() * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(d_ti, et.tridx.data(), et.tridx.size() * sizeof(int), cudaMemcpyHostToDevice, st));
         CK(cudaMemcpyAsync(d_tc, et.tcoef.data(), et.tcoef.size() * sizeof(double), cudaMemcpyHostToDevice, st));
         CK(edge_solve(nnn, nnn_r, nb, L, et.nu, d_modes, d_ts, d_ti, d_tc, zhat, ds->err, st));
-        rc = project(cfg, zhat, nullptr, zeta, st);   // synchronises: the host tables outlive the copies
-        for (void *q : {(void *)d_modes, (void *)d_ts, (void *)d_ti, (void *)d_tc, (void *)zhat}) cudaFreeAsync(q, st);
-        if (rc) return rc;
+        if ((rc = project(cfg, zhat, nullptr, zeta, st))) return rc;   // synchronises: the host tables outlive the copies
     } else if ((rc = project(cfg, nnn, rrr, zeta, st))) {
         return rc;
     }
     if (xi) CK(xi_from_sums(rr_mode, wsums, mono, pairs_r, s0, S, n_ell, 2, nb, rr, xi, st));
     if (pair_counts) CK(i64_from_u64(pairs, pair_counts, nb, st));
     if (triplet_counts) CK(i64_from_u64(T, triplet_counts, nb * nb, st));
-    free_grid_dev(gf, st);
-    free_grid_dev(gr, st);
-    for (void *q : {(void *)wsums, (void *)alm, (void *)cnt, (void *)diag, (void *)wsp, (void *)pairs, (void *)T,
-                    (void *)wprim, (void *)mono, (void *)cnt_r, (void *)TR, (void *)pairs_r, (void *)alm_r,
-                    (void *)wprim_r, (void *)diag_r, (void *)wsp_r, (void *)S, (void *)s0, (void *)rr})
-        if (q) cudaFreeAsync(q, st);
-    if (nnn_r && nnn_r != rfull_out) cudaFreeAsync(nnn_r, st);
-    if (!nnn_out) cudaFreeAsync(nnn, st);
-    if (!rrr_out) cudaFreeAsync(rrr, st);
     CK(cudaGetLastError());
     return TPCF_OK;
 }
@@ -969,9 +991,10 @@ int tpcf_accumulate_alm(tpcf_grid grid, const uint32_t *prim_xyz, const float *p
     DevState *ds;
     if ((rc = dev_state(&ds))) return rc;
     const int4 *prim = grid->g.rec;
+    Scratch sc(st);
     int4 *packed = nullptr;
     if (prim_xyz) {
-        if ((rc = dalloc(&packed, (size_t)n_prim, st, false))) return rc;
+        if ((rc = sc.alloc(&packed, (size_t)n_prim, false))) return rc;
         CK(pack_records(prim_xyz, prim_w, n_prim, packed, ds->err, st));
         prim = packed;
     } else if (n_prim != grid->g.n) {
@@ -979,7 +1002,6 @@ int tpcf_accumulate_alm(tpcf_grid grid, const uint32_t *prim_xyz, const float *p
     }
     rc = run_pairs(cfg, grid->g, prim, n_prim, false, monopole_weight, nullptr, monopole_weight >= 0.0, alm, counts,
                    diag, wsp, (unsigned long long *)pair_counts, st);
-    if (packed) cudaFreeAsync(packed, st);
     return rc;
 }
 
@@ -993,16 +1015,16 @@ int tpcf_couple_multipoles(const float *alm, const float *prim_w, const int32_t 
     if (n_prim < 0) return fail(TPCF_ERR_ARG, "n_prim < 0");
     cudaStream_t st = (cudaStream_t)stream;
     const int nb = cfg->n_bins;
+    Scratch sc(st);
     unsigned long long *T = nullptr;
     if (triplet_counts && counts) {
-        if ((rc = dalloc(&T, (size_t)nb * nb, st, true))) return rc;
+        if ((rc = sc.alloc(&T, (size_t)nb * nb, true))) return rc;
     }
     rc = couple(cfg, alm, prim_w, counts, n_prim, diag, wsp, nnn, T, st);
     if (!rc && T) {
         cudaError_t e = i64_from_u64(T, triplet_counts, nb * nb, st);
         if (e != cudaSuccess) rc = cuda_fail(e, "triplet counts");
     }
-    if (T) cudaFreeAsync(T, st);
     return rc;
 }
 
@@ -1049,6 +1071,7 @@ int tpcf_estimate_3pcf_host(const tpcf_config *cfg, const uint32_t *d_xyz, const
     if (!zeta || !d_xyz || nd < 1) return fail(TPCF_ERR_ARG, "zeta and data are required");
     if (nr < 0 || (nr > 0 && !r_xyz)) return fail(TPCF_ERR_ARG, "bad randoms");
     cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
     int32_t nm = 0;
     tpcf_multipole_count(cfg, &nm);
     const int nb = cfg->n_bins, L1 = cfg->l_max + 1;
@@ -1056,25 +1079,25 @@ int tpcf_estimate_3pcf_host(const tpcf_config *cfg, const uint32_t *d_xyz, const
     float *dw = nullptr, *rw = nullptr;
     double *z = nullptr, *n3 = nullptr, *r3 = nullptr;
     int64_t *pc = nullptr, *tc = nullptr;
-    if ((rc = dalloc(&dx, (size_t)nd * 3, st, false))) return rc;
+    if ((rc = sc.alloc(&dx, (size_t)nd * 3, false))) return rc;
     CK(cudaMemcpyAsync(dx, d_xyz, (size_t)nd * 12, cudaMemcpyHostToDevice, st));
     if (d_w) {
-        if ((rc = dalloc(&dw, (size_t)nd, st, false))) return rc;
+        if ((rc = sc.alloc(&dw, (size_t)nd, false))) return rc;
         CK(cudaMemcpyAsync(dw, d_w, (size_t)nd * 4, cudaMemcpyHostToDevice, st));
     }
     if (nr > 0) {
-        if ((rc = dalloc(&rx, (size_t)nr * 3, st, false))) return rc;
+        if ((rc = sc.alloc(&rx, (size_t)nr * 3, false))) return rc;
         CK(cudaMemcpyAsync(rx, r_xyz, (size_t)nr * 12, cudaMemcpyHostToDevice, st));
         if (r_w) {
-            if ((rc = dalloc(&rw, (size_t)nr, st, false))) return rc;
+            if ((rc = sc.alloc(&rw, (size_t)nr, false))) return rc;
             CK(cudaMemcpyAsync(rw, r_w, (size_t)nr * 4, cudaMemcpyHostToDevice, st));
         }
     }
-    if ((rc = dalloc(&z, (size_t)nm * nb * nb, st, false))) return rc;
-    if (nnn && (rc = dalloc(&n3, (size_t)L1 * L1 * L1 * nb * nb, st, false))) return rc;
-    if (rrr && (rc = dalloc(&r3, (size_t)nb * nb, st, false))) return rc;
-    if (pair_counts && (rc = dalloc(&pc, (size_t)nb, st, false))) return rc;
-    if (triplet_counts && (rc = dalloc(&tc, (size_t)nb * nb, st, false))) return rc;
+    if ((rc = sc.alloc(&z, (size_t)nm * nb * nb, false))) return rc;
+    if (nnn && (rc = sc.alloc(&n3, (size_t)L1 * L1 * L1 * nb * nb, false))) return rc;
+    if (rrr && (rc = sc.alloc(&r3, (size_t)nb * nb, false))) return rc;
+    if (pair_counts && (rc = sc.alloc(&pc, (size_t)nb, false))) return rc;
+    if (triplet_counts && (rc = sc.alloc(&tc, (size_t)nb * nb, false))) return rc;
     rc = tpcf_estimate_3pcf(cfg, dx, dw, nd, rx, rw, nr, z, n3, r3, pc, tc, stream);
     if (rc) return rc;
     CK(cudaMemcpyAsync(zeta, z, (size_t)nm * nb * nb * 8, cudaMemcpyDeviceToHost, st));
@@ -1082,9 +1105,6 @@ int tpcf_estimate_3pcf_host(const tpcf_config *cfg, const uint32_t *d_xyz, const
     if (rrr) CK(cudaMemcpyAsync(rrr, r3, (size_t)nb * nb * 8, cudaMemcpyDeviceToHost, st));
     if (pair_counts) CK(cudaMemcpyAsync(pair_counts, pc, (size_t)nb * 8, cudaMemcpyDeviceToHost, st));
     if (triplet_counts) CK(cudaMemcpyAsync(triplet_counts, tc, (size_t)nb * nb * 8, cudaMemcpyDeviceToHost, st));
-    for (void *p : {(void *)dx, (void *)rx, (void *)dw, (void *)rw, (void *)z, (void *)n3, (void *)r3, (void *)pc,
-                    (void *)tc})
-        if (p) cudaFreeAsync(p, st);
     CK(cudaStreamSynchronize(st));
     return tpcf_stream_status(stream);
 }
@@ -1334,20 +1354,28 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
     const int nb = cfg->n_bins, L1 = cfg->l_max + 1;
     const int64_t ns = std::min<int64_t>(n, 6144);       // sampled primaries per trial
     const int64_t stride = std::max<int64_t>(1, n / ns);
+    Scratch sc(st);
     float *alm = nullptr;
     int32_t *cnt = nullptr;
     double *diag = nullptr, *wsp = nullptr;
     unsigned long long *pc = nullptr;
     int4 *prim = nullptr;
-    CK(cudaMalloc((void **)&alm, (size_t)ns * nb * L1 * L1 * sizeof(float)));
-    CK(cudaMalloc((void **)&cnt, (size_t)ns * nb * sizeof(int32_t)));
-    CK(cudaMalloc((void **)&diag, (size_t)L1 * (L1 + 1) / 2 * nb * sizeof(double)));
-    CK(cudaMalloc((void **)&wsp, (size_t)L1 * nb * sizeof(double)));
-    CK(cudaMalloc((void **)&pc, nb * sizeof(unsigned long long)));
-    CK(cudaMalloc((void **)&prim, ns * sizeof(int4)));
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
+    if ((rc = sc.alloc(&alm, (size_t)ns * nb * L1 * L1, false)) || (rc = sc.alloc(&cnt, (size_t)ns * nb, false)) ||
+        (rc = sc.alloc(&diag, (size_t)L1 * (L1 + 1) / 2 * nb, false)) || (rc = sc.alloc(&wsp, (size_t)L1 * nb, false)) ||
+        (rc = sc.alloc(&pc, (size_t)nb, false)) || (rc = sc.alloc(&prim, (size_t)ns, false)))
+        return rc;
+    // timing events, destroyed on every return path
+    struct Events {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events()
+        {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    CK(cudaEventCreate(&ev.a));
+    CK(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     float best = 1e30f;
     const int divs[] = {2, 3, 4, 5, 6};
     const int tiles_all[] = {1, 2, 4};
@@ -1360,6 +1388,8 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
         const Plan pl = make_plan(&t, n, n);
         if (pl.s != dv) continue;   // the box cannot hold this many cells per r_max
         GridDev g;
+        Scratch gs(st);   // releases this cell size's grid on every path
+        gs.own(g);
         CK(build_grid_dev(xyz, w, n, nullptr, nullptr, 0, nullptr, pl.nc, g, ds->err, st));
         CK(cudaMemcpy2DAsync(prim, 16, g.rec, 16 * stride, 16, ns, cudaMemcpyDeviceToDevice, st));
         for (int ti = 0; ti < (fixed_tile ? 1 : 3); ++ti) {
@@ -1389,13 +1419,9 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
             }
             if (rc) break;
         }
-        free_grid_dev(g, st);
         if (rc) break;
     }
     cudaStreamSynchronize(st);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    for (void *ptr : {(void *)alm, (void *)cnt, (void *)diag, (void *)wsp, (void *)pc, (void *)prim}) cudaFree(ptr);
     return rc;
 }
 
@@ -1462,19 +1488,18 @@ int tpcf_check_rsqrt(int64_t n, uint64_t seed, double *stats, void *stream)
 {
     if (n < 1 || !stats) return fail(TPCF_ERR_ARG, "n >= 1 and host stats[5] required");
     cudaStream_t st = (cudaStream_t)stream;
+    Scratch sc(st);
     double *d = nullptr;
     unsigned long long *mu = nullptr;
     int rc;
-    if ((rc = dalloc(&d, 5, st, true))) return rc;
-    if ((rc = dalloc(&mu, 1, st, true))) return rc;
+    if ((rc = sc.alloc(&d, 5, true))) return rc;
+    if ((rc = sc.alloc(&mu, 1, true))) return rc;
     CK(check_rsqrt(n, (unsigned long long)seed, d, mu, st));
     double h[5];
     unsigned long long hm = 0;
     CK(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(&hm, mu, sizeof(hm), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    cudaFreeAsync(d, st);
-    cudaFreeAsync(mu, st);
     stats[0] = (double)hm;
     stats[1] = h[1] / (double)n;
     stats[2] = h[2] / (double)n;
