@@ -252,6 +252,31 @@ int grid_blocks(int64_t n, int block)
 
 }  // namespace
 
+namespace {
+
+// Temporaries of a grid build, released in stream order on every return path.
+struct Temps {
+    cudaStream_t st;
+    void *p[8] = {};
+    int n = 0;
+    explicit Temps(cudaStream_t s) : st(s) {}
+    Temps(const Temps &) = delete;
+    Temps &operator=(const Temps &) = delete;
+    template <class T>
+    cudaError_t alloc(T **q, size_t bytes)
+    {
+        const cudaError_t e = cudaMallocAsync((void **)q, bytes, st);
+        if (e == cudaSuccess) p[n++] = *q;
+        return e;
+    }
+    ~Temps()
+    {
+        for (int i = 0; i < n; ++i) cudaFreeAsync(p[i], st);
+    }
+};
+
+}  // namespace
+
 cudaError_t build_grid_dev(const uint32_t *xyz, const float *w, int64_t n,
                            const uint32_t *xyz2, const float *w2, int64_t n2, const double *wsums,
                            int nc, GridDev &g, int *err, cudaStream_t st)
@@ -262,6 +287,7 @@ cudaError_t build_grid_dev(const uint32_t *xyz, const float *w, int64_t n,
     g.nc = nc;
     g.ncell = ncell;
     cudaError_t e;
+    Temps tmps(st);
     int32_t *cid = nullptr, *hist = nullptr, *cursor = nullptr;
     int4 *tmp = nullptr;
     int64_t *scratch = nullptr;
@@ -269,11 +295,11 @@ cudaError_t build_grid_dev(const uint32_t *xyz, const float *w, int64_t n,
     if ((e = cudaMallocAsync((void **)&g.rec, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&g.order, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&g.cell_start, (ncell + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&cid, alloc_n * sizeof(int32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&tmp, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&scratch, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&hist, ncell * sizeof(int32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&cursor, ncell * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&cid, alloc_n * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&tmp, alloc_n * sizeof(int4))) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&scratch, alloc_n * sizeof(int64_t))) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&hist, ncell * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&cursor, ncell * sizeof(int32_t))) != cudaSuccess) return e;
     cudaMemsetAsync(hist, 0, ncell * sizeof(int32_t), st);
     const int B = 256;
     if (tot > 0) {
@@ -288,11 +314,6 @@ cudaError_t build_grid_dev(const uint32_t *xyz, const float *w, int64_t n,
         note_launch(2);
     }
     e = cudaGetLastError();
-    cudaFreeAsync(cid, st);
-    cudaFreeAsync(tmp, st);
-    cudaFreeAsync(scratch, st);
-    cudaFreeAsync(hist, st);
-    cudaFreeAsync(cursor, st);
     return e;
 }
 
@@ -305,6 +326,7 @@ cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t 
     g.nc = nc;
     g.ncell = ncell;
     cudaError_t e;
+    Temps tmps(st);
     int32_t *cid = nullptr, *hist = nullptr, *cursor = nullptr, *mock_of = nullptr;
     int4 *tmp = nullptr;
     int64_t *scratch = nullptr;
@@ -312,12 +334,12 @@ cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t 
     if ((e = cudaMallocAsync((void **)&g.rec, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&g.order, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync((void **)&g.cell_start, (ncell + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&cid, alloc_n * sizeof(int32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&mock_of, alloc_n * sizeof(int32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&tmp, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&scratch, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&hist, ncell * sizeof(int32_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&cursor, ncell * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&cid, alloc_n * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&mock_of, alloc_n * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&tmp, alloc_n * sizeof(int4))) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&scratch, alloc_n * sizeof(int64_t))) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&hist, ncell * sizeof(int32_t))) != cudaSuccess) return e;
+    if ((e = tmps.alloc(&cursor, ncell * sizeof(int32_t))) != cudaSuccess) return e;
     cudaMemsetAsync(hist, 0, ncell * sizeof(int32_t), st);
     const int B = 256;
     if (n > 0) {
@@ -334,12 +356,6 @@ cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t 
         note_launch(3);
     }
     e = cudaGetLastError();
-    cudaFreeAsync(cid, st);
-    cudaFreeAsync(mock_of, st);
-    cudaFreeAsync(tmp, st);
-    cudaFreeAsync(scratch, st);
-    cudaFreeAsync(hist, st);
-    cudaFreeAsync(cursor, st);
     return e;
 }
 
