@@ -107,3 +107,33 @@ def test_covariance_factors_match_oracle(lib, nm, nd, npar):
     assert abs(m1 - CV.percival_m1(nm, nd, npar)) < 1e-14
     with pytest.raises(tpcf.TpcfError):
         tpcf.covariance_factors(nd + 4, nd, npar)
+
+
+def test_entry_points_reject_bad_arguments_before_device_work(lib):
+    """Argument errors are reported by the host checks, with a message, before
+    any CUDA call (so they run here without a GPU)."""
+    cfg = tpcf.Config(10.0, 60.0, 5, 2, (0, 2), box=250.0)
+    c = cfg.c()
+    z = ctypes.c_void_p(1)   # never dereferenced: the checks fail first
+    # no data points
+    rc = lib.tpcf_estimate_3pcf_xi(ctypes.byref(c), None, None, 0, None, None, 0, z, None, None, None, None, None,
+                                   None)
+    assert rc == -1 and b"data point" in lib.tpcf_last_error()
+    # analytic randoms in an open volume
+    oc = tpcf.Config(10.0, 60.0, 5, 2, (0, 2), periodic=False, box=250.0).c()
+    rc = lib.tpcf_estimate_3pcf(ctypes.byref(oc), z, None, 10, None, None, 0, z, None, None, None, None, None)
+    assert rc == -1 and b"periodic" in lib.tpcf_last_error()
+    # the full edge correction needs explicit randoms
+    rc = lib.tpcf_estimate_3pcf_full_edge(ctypes.byref(c), z, None, 10, None, None, 0, z, None, None, None, None)
+    assert rc == -1 and b"randoms" in lib.tpcf_last_error()
+    # a covariance needs two mocks and a consistent selection
+    rc = lib.tpcf_covariance(z, 1, 10, None, 5, z, z, None)
+    assert rc == -1 and b"two mocks" in lib.tpcf_last_error()
+    rc = lib.tpcf_covariance(z, 5, 10, None, 11, z, z, None)
+    assert rc == -1 and b"stride" in lib.tpcf_last_error()
+    # the rsqrt check needs inputs and an output
+    assert lib.tpcf_check_rsqrt(0, 1, None, None) == -1
+    # a varying line of sight needs a finite observer
+    vc = tpcf.Config(10.0, 60.0, 5, 2, (0, 2), box=250.0, los="observer", observer=(float("nan"), 0.0, 0.0))
+    with pytest.raises(tpcf.TpcfError):
+        tpcf.multipole_index(vc)
