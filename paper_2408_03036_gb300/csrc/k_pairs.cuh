@@ -44,13 +44,35 @@ struct HarmTables {
     float gd_lo[(TPCF_MAX_LMAX + 1) * (TPCF_MAX_LMAX + 2) / 2][TPCF_MAX_LMAX + 1];
 };
 
+// Direct j = k sums for l_max >= 5: sum_j w_j^2 |V_l^m(z_j) (x_j + i y_j)^m|^2 per
+// (l, m >= 0), accumulated from the same rounded values as the harmonic sums.
+// The polynomial identity behind the shared self sums (below) assumes |n| = 1;
+// FP32 unit vectors miss it by about an ulp, and for m >= 1 the miss
+// (|x + iy|^2 versus 1 - z^2) is amplified near the poles, which at l = 5, 6
+// leaves about 1e-6 of |Y|^2 per pair in |a|^2 - self.  Bins with one or two
+// pairs per primary, where |a|^2 - self is almost all j = k term, then carry
+// that into the diagonal.  Pairs of consecutive l at one m share a float2.
+template <int LMAX>
+struct Direct {
+    static constexpr bool ON = LMAX >= 5;
+    static constexpr int np(int m) { return (LMAX - m + 2) / 2; }
+    static constexpr int off(int m)
+    {
+        int o = 0;
+        for (int k = 0; k < m; ++k) o += np(k);
+        return o;
+    }
+    static constexpr int N2 = ON ? off(LMAX + 1) : 1;
+};
+
 template <int LMAX>
 struct Layout {
     static constexpr int NLM = (LMAX + 1) * (LMAX + 1);
     static constexpr int NSP = LMAX + 1;
-    static constexpr int NACC = NLM + NSP;
-    static constexpr int NACCP = NACC | 1;  // odd row stride: distinct banks for distinct keys
     static constexpr int NDIAG = (LMAX + 1) * (LMAX + 2) / 2;
+    static constexpr int NDS = Direct<LMAX>::ON ? NDIAG : 0;   // direct j = k sums, index l(l+1)/2 + m
+    static constexpr int NACC = NLM + NSP + NDS;
+    static constexpr int NACCP = NACC | 1;  // odd row stride: distinct banks for distinct keys
 };
 
 __device__ __forceinline__ void latch_error(int *err, int code)
@@ -94,7 +116,8 @@ __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b
 
 // Accumulates one pair (unit vector x, y, z and weight w) into the packed sums.
 template <int LMAX>
-__device__ __forceinline__ void accum_pair(float x, float y, float z, float w, float2 (&A)[Packed<LMAX>::N2])
+__device__ __forceinline__ void accum_pair(float x, float y, float z, float w, float2 (&A)[Packed<LMAX>::N2],
+                                           float2 (&S)[Direct<LMAX>::N2])
 {
     constexpr int LZ = (2 * LMAX > 1) ? 2 * LMAX : 1;
     // (w Re, w Im) of (x + i y)^m
@@ -136,9 +159,19 @@ __device__ __forceinline__ void accum_pair(float x, float y, float z, float w, f
     A[0] = __fadd2_rn(A[0], f2(w, w2));
 #pragma unroll
     for (int l = 1; l <= LMAX; ++l) A[l] = __ffma2_rn(f2(v0[l], v0[2 * l]), f2(w, w2), A[l]);
+    if constexpr (Direct<LMAX>::ON) {
+        // m = 0: w^2 V_l^0^2, two l per paired instruction
+#pragma unroll
+        for (int p = 0; p < Direct<LMAX>::np(0); ++p) {
+            const int l = 2 * p;
+            const float va = v0[l], vb = (l + 1 <= LMAX) ? v0[l + 1] : 0.f;
+            S[p] = __ffma2_rn(__fmul2_rn(f2(va, vb), f2(va, vb)), f2(w2, w2), S[p]);
+        }
+    }
 #pragma unroll
     for (int m = 1; m <= LMAX; ++m) {
         float vm2 = 0.f, vm1 = 0.f;
+        float vv[LMAX + 1];
 #pragma unroll
         for (int l = m; l <= LMAX; ++l) {
             float v;
@@ -148,18 +181,32 @@ __device__ __forceinline__ void accum_pair(float x, float y, float z, float w, f
             else v = fmaf(zl[l], vm1, -(float)((l + m - 1) * (l - m - 1)) * vm2);
             vm2 = vm1;
             vm1 = v;
+            vv[l] = v;
             const int qi = Packed<LMAX>::q(l, m);
             if (l == m) A[qi] = __fadd2_rn(A[qi], cs[m]);
             else A[qi] = __ffma2_rn(f2(v, v), cs[m], A[qi]);
+        }
+        if constexpr (Direct<LMAX>::ON) {
+            // |w (x + i y)^m|^2 V_l^m^2, two l per paired instruction
+            const float qm = fmaf(cs[m].x, cs[m].x, cs[m].y * cs[m].y);
+#pragma unroll
+            for (int p = 0; p < Direct<LMAX>::np(m); ++p) {
+                const int l = m + 2 * p;
+                const float va = vv[l], vb = (l + 1 <= LMAX) ? vv[l + 1] : 0.f;
+                const int si = Direct<LMAX>::off(m) + p;
+                S[si] = __ffma2_rn(__fmul2_rn(f2(va, vb), f2(va, vb)), f2(qm, qm), S[si]);
+            }
         }
     }
 }
 
 // Writes the packed sums of one lane to a row of the tile layout.
 template <int LMAX>
-__device__ __forceinline__ void unpack(const float2 (&A)[Packed<LMAX>::N2], float *row)
+__device__ __forceinline__ void unpack(const float2 (&A)[Packed<LMAX>::N2], const float2 (&S)[Direct<LMAX>::N2],
+                                       float *row)
 {
     constexpr int NLM = Layout<LMAX>::NLM;
+    constexpr int NSP = Layout<LMAX>::NSP;
 #pragma unroll
     for (int l = 0; l <= LMAX; ++l) {
         row[l * l] = A[l].x;
@@ -172,6 +219,40 @@ __device__ __forceinline__ void unpack(const float2 (&A)[Packed<LMAX>::N2], floa
             row[l * l + 2 * m - 1] = A[Packed<LMAX>::q(l, m)].x;
             row[l * l + 2 * m] = A[Packed<LMAX>::q(l, m)].y;
         }
+    if constexpr (Direct<LMAX>::ON) {
+#pragma unroll
+        for (int m = 0; m <= LMAX; ++m)
+#pragma unroll
+            for (int p = 0; p < Direct<LMAX>::np(m); ++p) {
+                const int l = m + 2 * p;
+                const float2 v = S[Direct<LMAX>::off(m) + p];
+                row[NLM + NSP + l * (l + 1) / 2 + m] = v.x;
+                if (l + 1 <= LMAX) row[NLM + NSP + (l + 1) * (l + 2) / 2 + m] = v.y;
+            }
+    }
+}
+
+// Compensated evaluation of a^2 + b^2 - c: the squares are split exactly
+// (TwoProduct with an FMA) and the sums carried as unevaluated pairs (Knuth's
+// TwoSum), so the one rounding is of the result, however much a^2 + b^2 and c
+// cancel.  The round-to-nearest intrinsics keep the compiler from fusing the
+// steps.
+__device__ __forceinline__ float two_sum(float a, float b, float &e)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fadd_rn(s, -a);
+    e = __fadd_rn(__fadd_rn(a, -__fadd_rn(s, -bb)), __fadd_rn(b, -bb));
+    return s;
+}
+
+__device__ __forceinline__ float sq2_minus(float a, float b, float ch, float cl)
+{
+    const float p = __fmul_rn(a, a), ep = fmaf(a, a, -p);
+    const float q = __fmul_rn(b, b), eq = fmaf(b, b, -q);
+    float e1, e2;
+    const float s = two_sum(p, q, e1);
+    const float t = two_sum(s, -ch, e2);
+    return __fadd_rn(t, __fadd_rn(__fadd_rn(ep, eq), __fadd_rn(__fadd_rn(e1, e2), -cl)));
 }
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -500,7 +581,7 @@ struct QMap {
     int off_rstart, off_rlen, off_rslot;
     int off_qinfo, off_qcnt, off_cnt, off_gfirst, off_gsize, off_lanekey, off_hist;
     int off_sacc, off_queue;
-    int off_d32, off_w32, off_d64, off_w64, off_pairs, off_misc;
+    int off_d64, off_w64, off_pairs, off_misc;
     int total;
     int maxr;
 };
@@ -533,8 +614,6 @@ __host__ __device__ inline QMap make_qmap(int P, int nb, int s, int chunk, int b
     // the queues; reused as the [block][NACCP] transpose area at the end of a tile
     const int qbytes = 16 * chunk, stage = 4 * block * naccp;
     m.off_queue = o;   o = align_up(o + (qbytes > stage ? qbytes : stage), 16);
-    m.off_d32 = o;     o = align_up(o + 4 * nb * Layout<LMAX>::NDIAG, 16);
-    m.off_w32 = o;     o = align_up(o + 4 * nb * Layout<LMAX>::NSP, 16);
     m.off_d64 = o;     o = align_up(o + 8 * nb * Layout<LMAX>::NDIAG, 16);
     m.off_w64 = o;     o = align_up(o + 8 * nb * Layout<LMAX>::NSP, 16);
     m.off_pairs = o;   o = align_up(o + 8 * nb, 16);
@@ -579,8 +658,6 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
     float *sacc = reinterpret_cast<float *>(smem + M.off_sacc);  // [nk][NACCP] tile sums
     float4 *queue = reinterpret_cast<float4 *>(smem + M.off_queue);
     float *stage = reinterpret_cast<float *>(smem + M.off_queue);
-    float *d32 = reinterpret_cast<float *>(smem + M.off_d32);
-    float *w32 = reinterpret_cast<float *>(smem + M.off_w32);
     double *d64 = reinterpret_cast<double *>(smem + M.off_d64);
     double *w64 = reinterpret_cast<double *>(smem + M.off_w64);
     unsigned long long *spairs = reinterpret_cast<unsigned long long *>(smem + M.off_pairs);
@@ -596,8 +673,8 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
     for (int i = tid; i <= nb; i += T) {
         sE[i] = p.E[i];
     }
-    for (int i = tid; i < nb * NDIAG; i += T) { d32[i] = 0.f; d64[i] = 0.0; }
-    for (int i = tid; i < nb * NSP; i += T) { w32[i] = 0.f; w64[i] = 0.0; }
+    for (int i = tid; i < nb * NDIAG; i += T) d64[i] = 0.0;
+    for (int i = tid; i < nb * NSP; i += T) w64[i] = 0.0;
     for (int i = tid; i < nb; i += T) spairs[i] = 0ull;
     for (int i = tid; i < 2 * nkmax; i += T) qcnt[i] = 0;
     if (tid < nb) {
@@ -607,7 +684,6 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
     }
     if (tid == 0) s_flag = 0;
     double mono_w = p.use_mono ? (p.mono_w_dev ? *p.mono_w_dev : p.mono_w) : 0.0;
-    int tiles_since_flush = 0;
     int cta_mock = -1;
     int par = 0;                      // live half of the double-buffered queue counters
     __syncthreads();
@@ -621,24 +697,21 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
     auto flush_cta = [&](int mk) {
         __syncthreads();
         for (int i = tid; i < nb * NDIAG; i += T) {
-            const double v = d64[i] + (double)d32[i];
+            const double v = d64[i];
             const int b = i / NDIAG, jd = i % NDIAG;
             if (p.diag && v != 0.0) atomicAdd(p.diag + ((size_t)mk * NDIAG + jd) * nb + b, v);
             d64[i] = 0.0;
-            d32[i] = 0.f;
         }
         for (int i = tid; i < nb * NSP; i += T) {
-            const double v = w64[i] + (double)w32[i];
+            const double v = w64[i];
             const int b = i / NSP, j = i % NSP;
             if (p.wsp && v != 0.0) atomicAdd(p.wsp + ((size_t)mk * NSP + j) * nb + b, v);
             w64[i] = 0.0;
-            w32[i] = 0.f;
         }
         for (int b = tid; b < nb; b += T) {
             if (p.pair_counts && spairs[b]) atomicAdd(p.pair_counts + (size_t)mk * nb + b, spairs[b]);
             spairs[b] = 0ull;
         }
-        tiles_since_flush = 0;
         __syncthreads();
     };
 
@@ -746,8 +819,11 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         const int myq = myk >= 0 ? qinfo[myk].x : 0;
         const int mycap = myk >= 0 ? qinfo[myk].y : 0;
         float2 acc[Packed<LMAX>::N2];
+        float2 dacc[Direct<LMAX>::N2];
 #pragma unroll
         for (int j = 0; j < Packed<LMAX>::N2; ++j) acc[j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < Direct<LMAX>::N2; ++j) dacc[j] = make_float2(0.f, 0.f);
 
         // drains the queues (all threads); returns whether every warp has finished
         auto drain = [&]() -> bool {
@@ -777,7 +853,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                     const float r2f = fmaf(v.x, v.x, fmaf(v.y, v.y, v.z * v.z));
                     // |n|^2 = 1 up to unbiased rounding (see rsqrt_newton)
                     const float inv = rsqrt_newton(r2f);
-                    accum_pair<LMAX>(v.x * inv, v.y * inv, v.z * inv, v.w, acc);
+                    accum_pair<LMAX>(v.x * inv, v.y * inv, v.z * inv, v.w, acc, dacc);
                 }
             }
             __syncthreads();                                   // (B) queues consumed
@@ -880,7 +956,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         // ----- tile sums: every key's lanes added through one transpose
         {
             float *st = stage + (size_t)tid * NACCP;
-            unpack<LMAX>(acc, st);
+            unpack<LMAX>(acc, dacc, st);
         }
         __syncthreads();
         for (int i = tid; i < nk * NACC; i += T) {
@@ -918,46 +994,70 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
             for (int sl = 0; sl < np; ++sl) t += (unsigned long long)cnt[sl * nb + b];
             spairs[b] += t;
         }
+        // diagonal residuals w_i (|a_l^m[b]|^2 - s_ll^m[b]), the j = k term s removed: for
+        // l >= 1 compensated (sq2_minus) on the unnormalised sums, then scaled by K_lm^2;
+        // for l = 0 (where the periodic offset enters) in FP64; exactly zero for keys
+        // with at most one pair (no j != k term) unless the offset makes a_0^0 differ
+        // from the single pair's own term.  Summed into FP64 every tile.
         for (int i = tid; i < nb * NDIAG; i += T) {
             const int b = i / NDIAG, jd = i % NDIAG;
             int l = 0;
             while ((l + 1) * (l + 2) / 2 <= jd) ++l;
             const int m = jd - l * (l + 1) / 2;
-            float acc2 = 0.f;
             const double kd = __ldg(&p.harm->K[l][m]);
             const float k2 = (float)(kd * kd);
+            double acc2 = 0.0;
             for (int sl = 0; sl < np; ++sl) {
                 const float *a = sacc + (sl * nb + b) * NACCP;
-                float self = 0.f;
-                if (p.remove_self)
-                    for (int j = 0; j <= LMAX; ++j) {
-                        self = fmaf(__ldg(&p.harm->gd_hi[jd][j]), a[NLM + j], self);
-                        self = fmaf(__ldg(&p.harm->gd_lo[jd][j]), a[NLM + j], self);
-                    }
-                float d;
+                const bool single = cnt[sl * nb + b] <= 1;
+                double d;
                 if (l == 0) {
-                    const float re = a00(a[0], b);
-                    d = fmaf(re, re, -k2 * self);
+                    const double raw = (double)a[0];
+                    double dd = raw * raw - (p.remove_self ? (double)a[NLM] : 0.0);
+                    if (p.remove_self && single) dd = 0.0;   // raw^2 = w^2 up to the rounding of the self sum
+                    d = kd * kd * dd;
+                    if (p.use_mono) {
+                        const double c = (mono_w - 1.0) * p.mono_coef[b];
+                        d += c * (c - 2.0 * kd * raw);
+                    }
                 } else {
                     const float re = a[l * l + (m ? 2 * m - 1 : 0)];
                     const float im = m ? a[l * l + 2 * m] : 0.f;
-                    d = k2 * (fmaf(re, re, im * im) - self);
+                    if (!p.remove_self) {
+                        d = (double)k2 * (double)fmaf(re, re, im * im);
+                    } else if (single) {
+                        d = 0.0;
+                    } else {
+                        float ch = 0.f, cl = 0.f;
+                        if constexpr (Direct<LMAX>::ON) {
+                            ch = a[NLM + NSP + jd];
+                        } else {
+                            // s = sum_j (gd_hi + gd_lo)[j] acc_j as an unevaluated pair
+#pragma unroll
+                            for (int j = 0; j <= LMAX; ++j) {
+                                const float h = __ldg(&p.harm->gd_hi[jd][j]), lo = __ldg(&p.harm->gd_lo[jd][j]);
+                                const float x = a[NLM + j];
+                                const float ph = __fmul_rn(h, x);
+                                float pe = fmaf(h, x, -ph);
+                                pe = fmaf(lo, x, pe);
+                                float e;
+                                ch = two_sum(ch, ph, e);
+                                cl = __fadd_rn(cl, __fadd_rn(e, pe));
+                            }
+                        }
+                        d = (double)k2 * (double)sq2_minus(re, im, ch, cl);
+                    }
                 }
-                acc2 += __int_as_float(sPrim[sl].w) * d;
+                acc2 = fma((double)__int_as_float(sPrim[sl].w), d, acc2);
             }
-            d32[i] += acc2;
+            d64[i] += acc2;
         }
         for (int i = tid; i < nb * NSP; i += T) {
             const int b = i / NSP, j = i % NSP;
-            float acc2 = 0.f;
+            double acc2 = 0.0;
             for (int sl = 0; sl < np; ++sl)
-                acc2 += __int_as_float(sPrim[sl].w) * sacc[(sl * nb + b) * NACCP + NLM + j];
-            w32[i] += acc2;
-        }
-        if (++tiles_since_flush >= 16) {
-            tiles_since_flush = 0;
-            for (int i = tid; i < nb * NDIAG; i += T) { d64[i] += (double)d32[i]; d32[i] = 0.f; }
-            for (int i = tid; i < nb * NSP; i += T) { w64[i] += (double)w32[i]; w32[i] = 0.f; }
+                acc2 = fma((double)__int_as_float(sPrim[sl].w), (double)sacc[(sl * nb + b) * NACCP + NLM + j], acc2);
+            w64[i] += acc2;
         }
         // the bin shares for the next tile: half the old estimate, half this tile's counts
         if (warp == 0) {
