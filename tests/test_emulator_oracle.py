@@ -193,3 +193,173 @@ def test_bf16_rounding_ties_to_even():
     assert got[2] == 1.015625      # 1 + 3 * 2^-8 ties to 1 + 2^-6 (even)
     assert got[3] == 1.0
     assert got[4] == -3.5 and got[5] == 65536.0
+
+
+# ------------------------------------------------------------------------------
+# Pins of the perturbation-theory kernels, the P(k) normalisation and the real-
+# space 3PCF against results published independently of the model's own
+# formulas (Bernardeau et al. 2002 for F2 / G2; Kaiser 1987 for Z1; the
+# configuration-space tree-level 3PCF built from 1D Hankel transforms).
+
+def _kernels(ka, kb, cab, ma, mb, mab, kab, b1, b2, f):
+    """Z1(k_a) Z1(k_b) Z2(k_a, k_b) from the model's monomial split."""
+    parts = T._kernel_parts(ka, kb, cab, ma, mb, mab, kab)
+    return sum(c * p for c, p in zip(T.monomial_coeffs(b1, b2, f), parts))
+
+
+def _f2_g2(ka, kb, c):
+    """F2 and G2 isolated from the monomial parts: the b1^3 coefficient is
+    Z1 Z1 (b1 part) x F2 = F2; with both LOS cosines 0 and a unit LOS cosine of
+    k_a + k_b the b1^2 f coefficient is G2 alone."""
+    z = np.zeros_like(np.asarray(c, dtype=float))
+    kab = np.sqrt(ka ** 2 + kb ** 2 + 2 * ka * kb * c)
+    parts = T._kernel_parts(ka, kb, c, z, z, z + 1.0, kab)
+    return parts[T.MONOMIALS.index((3, 0, 0))], parts[T.MONOMIALS.index((2, 0, 1))]
+
+
+def test_f2_g2_special_values():
+    """F2(k, -k) = G2(k, -k) = 0 (momentum conservation) and F2 = G2 = 2 for two
+    equal parallel wavevectors."""
+    for k in (0.01, 0.1, 0.37):
+        F, G = _f2_g2(np.array([k, k]), np.array([k, k]), np.array([-1.0, 1.0]))
+        assert abs(F[0]) < 1e-14 and abs(G[0]) < 1e-14
+        assert abs(F[1] - 2.0) < 1e-14 and abs(G[1] - 2.0) < 1e-14
+
+
+def test_f2_g2_legendre_multipoles():
+    """In the cosine mu of the angle between k1 and k2:
+    F2 = 17/21 + (k1/k2 + k2/k1)/2 P1(mu) + 4/21 P2(mu),
+    G2 = 13/21 + (k1/k2 + k2/k1)/2 P1(mu) + 8/21 P2(mu)."""
+    from scipy.special import eval_legendre, roots_legendre
+    x, wx = roots_legendre(16)
+    for ka, kb in [(0.05, 0.05), (0.02, 0.11), (0.3, 0.07)]:
+        F, G = _f2_g2(np.full(16, ka), np.full(16, kb), x)
+        r = 0.5 * (ka / kb + kb / ka)
+        for l, (cf, cg) in enumerate([(17 / 21, 13 / 21), (r, r), (4 / 21, 8 / 21)]):
+            pf = (2 * l + 1) / 2 * np.sum(wx * F * eval_legendre(l, x))
+            pg = (2 * l + 1) / 2 * np.sum(wx * G * eval_legendre(l, x))
+            assert abs(pf - cf) < 1e-13 and abs(pg - cg) < 1e-13, (l, pf, pg)
+        for l in range(3, 8):
+            assert abs(np.sum(wx * F * eval_legendre(l, x))) < 1e-13
+
+
+def test_kaiser_factor_of_z1():
+    """Z1 = b1 + f mu^2: averaged over the LOS angle, Z1(mu)^2 gives the Kaiser
+    factor b1^2 + 2 b1 f / 3 + f^2 / 5.  Z1(k_a) Z1(k_b) is twice the b2
+    derivative of Z1 Z1 Z2 (Z2 carries b2 / 2)."""
+    from scipy.special import roots_legendre
+    x, wx = roots_legendre(12)
+    k = np.full(12, 0.1)
+    b1, f = 1.6, 0.7
+    z1z1 = 2.0 * (_kernels(k, k, np.ones(12), x, x, x, 2 * k, b1, 1.0, f)
+                  - _kernels(k, k, np.ones(12), x, x, x, 2 * k, b1, 0.0, f))
+    assert abs(0.5 * np.sum(wx * z1z1) - (b1 ** 2 + 2 * b1 * f / 3 + f ** 2 / 5)) < 1e-13
+
+
+def test_z2_squeezed_limit_is_the_redshift_space_shift():
+    """As k2 -> 0 the long mode only displaces the short one; in redshift space
+    the displacement has the extra f (Psi . n) n part, so
+    Z2(k1, k2) -> (k1 / 2 k2) (k1_hat . k2_hat + f mu1 mu2) Z1(k1)
+    (leading order in k2 / k1)."""
+    rng = np.random.default_rng(11)
+    b1, f = 1.9, 0.8
+    for _ in range(10):
+        v1, v2, n = rng.normal(size=(3, 3))
+        n /= np.linalg.norm(n)
+        k1 = 0.2 * v1 / np.linalg.norm(v1)
+        k2 = 0.2e-6 * v2 / np.linalg.norm(v2)
+        ka, kb = np.linalg.norm(k1), np.linalg.norm(k2)
+        kab = np.linalg.norm(k1 + k2)
+        c = k1 @ k2 / (ka * kb)
+        m1, m2, m12 = k1 @ n / ka, k2 @ n / kb, (k1 + k2) @ n / kab
+        a = [np.array([v]) for v in (ka, kb, c, m1, m2, m12, kab)]
+        tot0 = _kernels(*a, b1, 0.0, f)[0]
+        z1z1 = 2.0 * (_kernels(*a, b1, 1.0, f)[0] - tot0)
+        z2 = tot0 / z1z1
+        z1 = b1 + f * m1 ** 2
+        lim = ka / (2 * kb) * (c + f * m1 * m2) * z1
+        assert abs(z2 - lim) <= 1e-5 * abs(ka / (2 * kb) * z1), (z2, lim)
+
+
+def test_power_spectrum_sigma8_is_one():
+    """PowerNW is normalised to sigma(R = 8 Mpc/h) = 1 with the top-hat window:
+    adaptive quadrature in linear k (the model itself uses a trapezoid in ln k)."""
+    pk = T.PowerNW()
+    R = 8.0
+
+    def integrand(k):
+        x = k * R
+        wth = 3.0 * (math.sin(x) - x * math.cos(x)) / x ** 3
+        return k * k * float(pk(k)) * wth * wth / (2.0 * math.pi ** 2)
+
+    edges = [1e-6, 1e-3, 0.01, 0.1, 0.5, 1.0, 2.0, 5.0, 20.0, 100.0, 1000.0]
+    s2 = sum(quad(integrand, a, b, limit=500, epsrel=1e-11)[0] for a, b in zip(edges[:-1], edges[1:]))
+    assert abs(math.sqrt(s2) - 1.0) < 1e-4
+
+
+def _xi_tables(pk, r, k_hi=1.6, nk=16001):
+    """xi_l^[n](r) = int dk k^(2+n) P(k) j_l(k r) / (2 pi^2) for (l, n) = (0, 0),
+    (1, 1), (1, -1), (2, 0), on a fine k grid (P is Gaussian-damped)."""
+    k = np.linspace(1e-6, k_hi, nk)
+    P = pk(k)
+    out = {}
+    for (l, n) in ((0, 0), (1, 1), (1, -1), (2, 0)):
+        f = (k ** (2 + n) * P)[None, :] * spherical_jn(l, np.outer(r, k)) / (2 * math.pi ** 2)
+        out[(l, n)] = np.trapezoid(f, k, axis=1)
+    return out
+
+
+def test_real_space_isotropic_multipoles_against_configuration_space():
+    """f = 0, alpha = 1, eps = 0: the model's zeta_{l l 0} (l = 0, 1, 2) against the
+    tree-level 3PCF computed in configuration space.  Each vertex with legs a, b
+    and opening cosine g contributes
+        2 b1^3 [17/21 xi0(a) xi0(b) - 1/2 (xi1+(a) xi1-(b) + xi1-(a) xi1+(b)) g
+                + 4/21 xi2(a) xi2(b) P2(g)] + b1^2 b2 xi0(a) xi0(b)
+    (the Legendre form of F2 transformed leg by leg), summed over the three
+    vertices of the triangle (r1, r2, r3 = |r2 - r1|), projected on P_l(mu) and
+    bin-averaged with r^2 weights.  The model instead integrates the bispectrum
+    multipoles of Eq. bisp with the 2D transform of Eq. TriRelBtoZ.  P is damped
+    by exp(-(k / 0.25)^2) on both sides so that the model's k cut does not enter."""
+    from scipy.interpolate import CubicSpline
+    from scipy.special import eval_legendre, roots_legendre
+    base = T.PowerNW()
+
+    def pk(k):
+        k = np.asarray(k, dtype=np.float64)
+        return base(k) * np.exp(-(k / 0.25) ** 2)
+
+    setup = T.ModelSetup(n_bins=6, r_min=20.0, r_max=110.0, k_max=0.6, n_log=40, dk=0.0125,
+                         grid=T.AngularGrid(48, 4, 4))
+    setup.pk = pk
+    b1, b2 = 1.7, 0.6
+    z = T.model_direct(setup, (0.0, b1, b2, 1.0, 1.0, 0.0))
+    rg = np.linspace(0.0, 240.0, 961)
+    X = {key: CubicSpline(rg, v) for key, v in _xi_tables(pk, rg).items()}
+
+    def vertex(a, b, g):
+        t = 2 * b1 ** 3 * (17 / 21 * X[0, 0](a) * X[0, 0](b)
+                           - 0.5 * (X[1, 1](a) * X[1, -1](b) + X[1, -1](a) * X[1, 1](b)) * g
+                           + 4 / 21 * X[2, 0](a) * X[2, 0](b) * eval_legendre(2, g))
+        return t + b1 ** 2 * b2 * X[0, 0](a) * X[0, 0](b)
+
+    xr, wr = roots_legendre(16)
+    xm, wm = roots_legendre(64)
+    e = setup.edges
+    nb = len(e) - 1
+    ref = np.zeros((3, nb, nb))
+    for i in range(nb):
+        r1 = 0.5 * (e[i + 1] - e[i]) * xr + 0.5 * (e[i + 1] + e[i])
+        w1 = wr * r1 ** 2
+        for j in range(nb):
+            r2 = 0.5 * (e[j + 1] - e[j]) * xr + 0.5 * (e[j + 1] + e[j])
+            w2 = wr * r2 ** 2
+            R1, R2, MU = np.meshgrid(r1, r2, xm, indexing="ij")
+            R3 = np.sqrt(np.maximum(R1 ** 2 + R2 ** 2 - 2 * R1 * R2 * MU, 1e-12))
+            zz = vertex(R1, R2, MU) + vertex(R1, R3, (R1 - R2 * MU) / R3) + vertex(R2, R3, (R2 - R1 * MU) / R3)
+            for l in range(3):
+                c = (2 * l + 1) / 2 * np.einsum("abm,m->ab", zz, wm * eval_legendre(l, xm))
+                ref[l, i, j] = np.einsum("ab,a,b->", c, w1, w2) / (w1.sum() * w2.sum())
+    for l, tol in ((0, 2e-3), (1, 6e-3), (2, 2e-3)):
+        q = T.MULTIPOLES.index((l, l, 0))
+        err = np.abs(z[q] - ref[l]).max() / np.abs(ref[l]).max()
+        assert err < tol, (l, err)
