@@ -187,7 +187,8 @@ int tpcf_couple_multipoles(const float *alm, const float *prim_w, const int32_t 
  * fit in 65,536 doubles (l_max <= 4 with up to 32 bins; l_max = 6 with up to 21
  * bins); larger requests return TPCF_ERR_ARG.  The first call on each device
  * sets the block up with a synchronous copy, so make it before any stream
- * capture.  All calls on a device share the block (the parts that must start
+ * capture; the set-up belongs to the device's CUDA context, and the first call
+ * after a cudaDeviceReset repeats it.  All calls on a device share the block (the parts that must start
  * at zero are cleared by each call): calls whose work overlaps on the GPU race
  * and must be serialised by the caller. */
 int tpcf_couple_multipoles_static(const float *alm, const float *prim_w, const int32_t *counts, int64_t n_prim,

@@ -16,7 +16,7 @@ with H_{l1 l2 L} = (l1 l2 L; 0 0 0) (Sec. 2.2, TripoSH basis) and
 zeta^m = NNN^m / RRR_{00}^0 (Eq. ssest: (D-R)^3 / R^3, bin-wise by the l = 0
 random triplet count).
 
-Readings of the paper recorded here (the same list is in the design doc):
+Readings of the paper recorded here:
   * the second a_l^m of Eq. measured_mult is conjugated (Eq. zeta_meas puts
     Y* on r_hat_2);
   * degenerate j = k triangles are removed (remove_self = 1);

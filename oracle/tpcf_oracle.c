@@ -245,7 +245,7 @@ int ora_run(const ora_cfg *c, const uint32_t *xyz, const double *w, int64_t n,
         int64_t *cnt = (int64_t *)malloc((size_t)nb * sizeof(int64_t));
         cplx Y[169];
 
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(static)
         for (int64_t ip = 0; ip < np; ++ip) {
             const int64_t i = prim ? prim[ip] : ip;
             memset(a, 0, (size_t)nb * nlm * sizeof(cplx));
@@ -353,7 +353,9 @@ int ora_run(const ora_cfg *c, const uint32_t *xyz, const double *w, int64_t n,
         free(self);
         free(cnt);
     }
-    /* fixed-order reduction over threads */
+    /* fixed-order reduction over threads; with the static schedule every thread
+     * sums a fixed contiguous block of primaries in order, so for a given thread
+     * count the FP64 result is the same from run to run */
     for (int t = 0; t < nthr; ++t) {
         const cplx *p = part + (size_t)t * nnn_sz;
         for (size_t k = 0; k < nnn_sz; ++k) {

@@ -82,6 +82,22 @@ inline unsigned long long device_bit()
     return 1ull << (d & 63);
 }
 
+// Streaming multiprocessors of the current device (queried once per device and
+// cached), for grid sizing in multiples of the SM count.
+inline int sm_count()
+{
+    static int cache[64] = {0};
+    int d = 0;
+    cudaGetDevice(&d);
+    int &c = cache[d & 63];
+    if (c <= 0) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0) v = 1;
+        c = v;
+    }
+    return c;
+}
+
 // Counts kernel launches made by the library (reported by tpcf_kernel_launches).
 void note_launch(int n = 1);
 

@@ -51,7 +51,7 @@ __global__ void k_check_rsqrt(int64_t n, unsigned long long seed, double *stats,
 cudaError_t check_rsqrt(int64_t n, unsigned long long seed, double *stats, unsigned long long *maxulp,
                         cudaStream_t st)
 {
-    k_check_rsqrt<<<152 * 4, 256, 0, st>>>(n, seed, stats, maxulp);
+    k_check_rsqrt<<<sm_count() * 4, 256, 0, st>>>(n, seed, stats, maxulp);
     note_launch();
     return cudaGetLastError();
 }

@@ -304,7 +304,7 @@ cudaError_t couple_gram_fp32_tiles(const float *alm, const float *w, int64_t K, 
     const int nt = gram_tile_count(nb, lmax);
     k_gram_tiles<<<(nt + 127) / 128, 128, 0, st>>>(nb, lmax, d_tiles, nt);
     note_launch();
-    int64_t ks = (152 * 8 + nt - 1) / nt;
+    int64_t ks = (sm_count() * 8 + nt - 1) / nt;
     const int64_t maxks = (K + 1023) / 1024;
     if (ks > maxks) ks = maxks;
     if (ks < 1) ks = 1;
@@ -319,7 +319,7 @@ cudaError_t triplet_counts(const int32_t *counts, int64_t K, int nb, unsigned lo
 {
     int64_t g = (K + 4095) / 4096;
     if (g < 1) g = 1;
-    if (g > 152 * 4) g = 152 * 4;
+    if (g > sm_count() * 4) g = sm_count() * 4;
     if (K > 0) {
         k_triplets<<<(unsigned)g, ((nb * nb + 31) / 32) * 32, 0, st>>>(counts, K, nb, T);
         note_launch();
@@ -371,7 +371,7 @@ cudaError_t m0_sums(const float *alm, const float *w, int64_t K, int nb, int lma
     if (n_ell * nb > 128 || lstep * (n_ell - 1) > lmax) return cudaErrorInvalidValue;
     if (K <= 0) return cudaSuccess;
     int64_t g = (K + 7) / 8;
-    if (g > 152 * 4) g = 152 * 4;
+    if (g > sm_count() * 4) g = sm_count() * 4;
     k_m0_sums<<<(unsigned)g, 256, 0, st>>>(alm, w, K, nb, lmax, n_ell, lstep, out);
     note_launch();
     return cudaGetLastError();

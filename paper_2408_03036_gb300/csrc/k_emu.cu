@@ -218,7 +218,7 @@ __global__ void k_init(float *__restrict__ p, int64_t w_off, int64_t w_count, fl
     }
 }
 
-int grid1(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), 152 * 8); }
+int grid1(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>((n + 255) / 256, 1), (int64_t)tpcf::sm_count() * 8); }
 
 }  // namespace
 

@@ -246,7 +246,7 @@ int grid_blocks(int64_t n, int block)
 {
     int64_t b = (n + block - 1) / block;
     if (b < 1) b = 1;
-    if (b > 152 * 16) b = 152 * 16;
+    if (b > sm_count() * 16) b = sm_count() * 16;
     return (int)b;
 }
 

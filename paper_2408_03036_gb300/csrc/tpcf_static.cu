@@ -18,7 +18,9 @@
 // Set-up: the first call on each device (with that device current) looks up
 // the block's device address with cudaGetSymbolAddress and copies the j = k
 // coefficient tables into it with a synchronous cudaMemcpy.  Make that first
-// call before any stream capture.
+// call before any stream capture.  The set-up is tied to the device's current
+// CUDA context (its unique context id): after cudaDeviceReset the module is
+// loaded again with a zeroed block, and the next call repeats the set-up.
 //
 // Sharing: every call on a device uses the same block.  The Gram area and the
 // triplet-count accumulator are cleared at the start of each call (they must
@@ -38,7 +40,15 @@ namespace {
 constexpr int64_t kGramMax = 65536;                 // doubles of packed Gram blocks
 constexpr int kTilesMax = 512;                      // (m, tr, tc) tiles
 constexpr int kSelfLmax = TPCF_MAX_LMAX;
-constexpr int64_t kSelfDoubles = 1 + 16 + 81 + 256 + 625 + 1296 + 2401;   // sum of (L+1)^4, L = 0..6
+
+constexpr int64_t self_doubles(int lmax)   // sum of (L+1)^4, L = 0..lmax
+{
+    int64_t s = 0;
+    for (int L = 0; L <= lmax; ++L) s += (int64_t)(L + 1) * (L + 1) * (L + 1) * (L + 1);
+    return s;
+}
+constexpr int64_t kSelfDoubles = self_doubles(kSelfLmax);
+static_assert(kSelfDoubles == 1 + 16 + 81 + 256 + 625 + 1296 + 2401 || kSelfLmax != 6, "table size");
 
 constexpr size_t kOffGram = 0;
 constexpr size_t kOffSelf = kOffGram + kGramMax * sizeof(double);
@@ -59,25 +69,58 @@ int64_t self_offset(int lmax)
 
 std::mutex g_mu;
 unsigned char *g_ptr[64] = {nullptr};
+unsigned long long g_ctx[64] = {0};   // id of the context the block was set up in
 
-// Device address of the scratch block on the current device, set up on first use.
+// Unique id of the current CUDA context (the driver's cuCtxGetId, reached through
+// the runtime's entry-point query so the library does not link libcuda); 0 if
+// unavailable.  cudaDeviceReset replaces the primary context, and its id.
+unsigned long long context_id()
+{
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
+
+// Device address of the scratch block on the current device, set up on first use
+// in the current context.
 int scratch_on(unsigned char **out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return tpcf::set_error(TPCF_ERR_CUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= 64) return tpcf::set_error(TPCF_ERR_CUDA, "device index out of range");
+    // every call: the block's address (this also brings up the device's context)
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_couple_scratch);
+    if (e != cudaSuccess || !p) return tpcf::set_error(TPCF_ERR_CUDA, "cudaGetSymbolAddress failed for the static scratch");
+    const unsigned long long ctx = context_id();
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_couple_scratch);
-        if (e != cudaSuccess || !p) return tpcf::set_error(TPCF_ERR_CUDA, "cudaGetSymbolAddress failed for the static scratch");
+    if (g_ptr[dev] != (unsigned char *)p || g_ctx[dev] != ctx) {
         static double tables[kSelfDoubles];
         for (int L = 0; L <= kSelfLmax; ++L) tpcf::self_term_table(L, tables + self_offset(L));
         e = cudaMemcpy((unsigned char *)p + kOffSelf, tables, kSelfDoubles * sizeof(double),
                        cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return tpcf::set_error(TPCF_ERR_CUDA, cudaGetErrorString(e));
         g_ptr[dev] = (unsigned char *)p;
+        g_ctx[dev] = ctx;
     }
     *out = g_ptr[dev];
     return TPCF_OK;
