@@ -161,6 +161,17 @@ int tpcf_accumulate_alm(tpcf_grid grid, const uint32_t *prim_xyz, const float *p
                         float *alm, int32_t *counts, double *diag, double *wsp, int64_t *pair_counts,
                         void *stream);
 
+/* Integer pair counts only (the random-only pass behind RRR_00^0, the R^3 term
+ * of Eq. ssest, with unit random weights): the same neighbour search and exact
+ * binning as tpcf_accumulate_alm, without harmonics.
+ *   prim_xyz: dev primaries [n_prim][3] (NULL: the grid's own points in grid
+ *     order, n_prim equal to the grid's point count);
+ *   counts: dev int32 [n_prim][n_bins] pair counts per primary (or NULL);
+ *   pair_counts: dev int64 [n_bins], += total pairs per bin (or NULL).
+ * Errors: TPCF_ERR_ARG for a NULL grid, n_prim < 0 or a mismatched n_prim. */
+int tpcf_pair_counts(tpcf_grid grid, const uint32_t *prim_xyz, int64_t n_prim, const tpcf_config *cfg,
+                     int32_t *counts, int64_t *pair_counts, void *stream);
+
 /* Coupling over primaries (Eq. measured_mult summed over x): with the outputs of
  * tpcf_accumulate_alm for the same primaries (dev alm, dev prim_w or NULL for
  * unit weights, dev counts or NULL, dev diag, dev wsp), writes

@@ -1005,6 +1005,30 @@ int tpcf_accumulate_alm(tpcf_grid grid, const uint32_t *prim_xyz, const float *p
     return rc;
 }
 
+int tpcf_pair_counts(tpcf_grid grid, const uint32_t *prim_xyz, int64_t n_prim, const tpcf_config *cfg,
+                     int32_t *counts, int64_t *pair_counts, void *stream)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!grid) return fail(TPCF_ERR_ARG, "grid is NULL");
+    if (n_prim < 0) return fail(TPCF_ERR_ARG, "n_prim < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevState *ds;
+    if ((rc = dev_state(&ds))) return rc;
+    const int4 *prim = grid->g.rec;
+    Scratch sc(st);
+    int4 *packed = nullptr;
+    if (prim_xyz) {
+        if ((rc = sc.alloc(&packed, (size_t)n_prim, false))) return rc;
+        CK(pack_records(prim_xyz, nullptr, n_prim, packed, ds->err, st));
+        prim = packed;
+    } else if (n_prim != grid->g.n) {
+        return fail(TPCF_ERR_ARG, "n_prim must equal the grid size when prim_xyz is NULL");
+    }
+    return run_pairs(cfg, grid->g, prim, n_prim, true, -1.0, nullptr, false, nullptr, counts, nullptr, nullptr,
+                     (unsigned long long *)pair_counts, st);
+}
+
 int tpcf_couple_multipoles(const float *alm, const float *prim_w, const int32_t *counts, int64_t n_prim,
                            const tpcf_config *cfg, const double *diag, const double *wsp, double *nnn,
                            int64_t *triplet_counts, void *stream)

@@ -26,7 +26,7 @@ CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
 # Names of every entry point include/tpcf.h declares (checked by the tests).
 EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
            "tpcf_bin_edges", "tpcf_build_grid", "tpcf_grid_destroy", "tpcf_grid_info", "tpcf_grid_points",
-           "tpcf_accumulate_alm", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
+           "tpcf_accumulate_alm", "tpcf_pair_counts", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
            "tpcf_estimate_3pcf_xi", "tpcf_estimate_3pcf_full_edge",
            "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
@@ -107,6 +107,7 @@ def lib():
             "tpcf_grid_info": ([P, P, P], ctypes.c_int),
             "tpcf_grid_points": ([P, P, P, P, P], ctypes.c_int),
             "tpcf_accumulate_alm": ([P, P, P, I64, CFG, ctypes.c_double, P, P, P, P, P, P], ctypes.c_int),
+            "tpcf_pair_counts": ([P, P, I64, CFG, P, P, P], ctypes.c_int),
             "tpcf_couple_multipoles": ([P, P, P, I64, CFG, P, P, P, P, P], ctypes.c_int),
             "tpcf_project": ([CFG, P, P, P, P], ctypes.c_int),
             "tpcf_estimate_3pcf": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
@@ -394,6 +395,22 @@ def accumulate_alm(grid: Grid, cfg: Config, prim_xyz=None, prim_w=None, monopole
     _check(lib().tpcf_accumulate_alm(grid.handle, _ptr(px), _ptr(pw), n, ctypes.byref(c), float(monopole_weight),
                                      _ptr(alm), _ptr(counts), _ptr(diag), _ptr(wsp), _ptr(pc), _stream(stream)))
     return alm, counts, diag, wsp, pc
+
+
+def pair_counts(grid: Grid, cfg: Config, prim_xyz=None, stream=None):
+    """tpcf_pair_counts; returns (counts [n_prim][n_bins] int32, pair_counts [n_bins] int64)."""
+    dev = grid.xyz.device
+    if prim_xyz is None:
+        n = grid.info()[0]
+        px = None
+    else:
+        px = _as_dev_xyz(prim_xyz, dev)
+        n = px.shape[0]
+    counts = torch.empty((n, cfg.n_bins), dtype=torch.int32, device=dev)
+    pc = torch.zeros(cfg.n_bins, dtype=torch.int64, device=dev)
+    c = cfg.c()
+    _check(lib().tpcf_pair_counts(grid.handle, _ptr(px), n, ctypes.byref(c), _ptr(counts), _ptr(pc), _stream(stream)))
+    return counts, pc
 
 
 def couple_multipoles(cfg: Config, alm, prim_w, counts, diag, wsp, stream=None):

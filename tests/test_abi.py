@@ -133,6 +133,9 @@ def test_entry_points_reject_bad_arguments_before_device_work(lib):
     assert rc == -1 and b"stride" in lib.tpcf_last_error()
     # the rsqrt check needs inputs and an output
     assert lib.tpcf_check_rsqrt(0, 1, None, None) == -1
+    # the count pass needs a grid
+    rc = lib.tpcf_pair_counts(None, None, 10, ctypes.byref(c), None, None, None)
+    assert rc == -1 and b"grid" in lib.tpcf_last_error()
     # a varying line of sight needs a finite observer
     vc = tpcf.Config(10.0, 60.0, 5, 2, (0, 2), box=250.0, los="observer", observer=(float("nan"), 0.0, 0.0))
     with pytest.raises(tpcf.TpcfError):
