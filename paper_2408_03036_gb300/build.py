@@ -20,8 +20,26 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxe
          "-Xptxas", "-v", "-I", os.path.join(HERE, "..", "include")]
 
 
+# compiled once per l_max with -DTPCF_LMAX=n (the pair-stage kernels)
+PER_LMAX = "k_pairs_inst.cu"
+MAX_LMAX = 6
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+
+
+def _units():
+    """(source, object, extra flags) for every translation unit."""
+    out = []
+    for src in _sources():
+        base = os.path.basename(src)
+        if base == PER_LMAX:
+            for l in range(MAX_LMAX + 1):
+                out.append((src, os.path.join(OBJ, "%s.l%d.o" % (base, l)), ["-DTPCF_LMAX=%d" % l]))
+        else:
+            out.append((src, os.path.join(OBJ, base + ".o"), []))
+    return out
 
 
 def _deps():
@@ -36,9 +54,9 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def _compile(src: str) -> tuple[str, str]:
-    obj = os.path.join(OBJ, os.path.basename(src) + ".o")
-    cmd = [NVCC] + ARCH + FLAGS + ["-c", src, "-o", obj]
+def _compile(unit) -> tuple[str, str]:
+    src, obj, extra = unit
+    cmd = [NVCC] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
@@ -51,10 +69,10 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
         return LIB
     os.makedirs(OBJ, exist_ok=True)
     t0 = time.time()
-    srcs = _sources()
-    jobs = jobs or min(len(srcs), max(2, os.cpu_count() or 2))
+    units = _units()
+    jobs = jobs or min(len(units), max(2, os.cpu_count() or 2))
     with ThreadPoolExecutor(max_workers=jobs) as ex:
-        results = list(ex.map(_compile, srcs))
+        results = list(ex.map(_compile, units))
     with open(os.path.join(OBJ, "ptxas.log"), "w") as f:
         for obj, log in results:
             f.write("== %s\n%s\n" % (obj, log))

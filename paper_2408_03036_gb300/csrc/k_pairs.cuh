@@ -115,86 +115,63 @@ struct Packed {
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
 // Accumulates one pair (unit vector x, y, z and weight w) into the packed sums.
+// Every chain is streamed (each value used as soon as it is formed, two values
+// of a recurrence kept), which keeps the live registers to the accumulators and
+// a handful of temporaries.
 template <int LMAX>
 __device__ __forceinline__ void accum_pair(float x, float y, float z, float w, float2 (&A)[Packed<LMAX>::N2],
                                            float2 (&S)[Direct<LMAX>::N2])
 {
     constexpr int LZ = (2 * LMAX > 1) ? 2 * LMAX : 1;
-    // (w Re, w Im) of (x + i y)^m
-    float2 cs[LMAX + 1];
-    cs[0] = f2(w, 0.f);
-    if (LMAX >= 1) cs[1] = __fmul2_rn(f2(w, w), f2(x, y));
-    const float2 myx = f2(-y, x);
-#pragma unroll
-    for (int m = 2; m <= LMAX; ++m)
-        cs[m] = __ffma2_rn(f2(cs[m - 1].x, cs[m - 1].x), f2(x, y), __fmul2_rn(f2(cs[m - 1].y, cs[m - 1].y), myx));
-    float zl[LZ + 2];                 // zl[l] = (2l - 1) z
-    zl[0] = 0.f;
-#pragma unroll
-    for (int l = 1; l <= LZ; l += 2) {
-        const float2 t = __fmul2_rn(f2((float)(2 * l - 1), (float)(2 * l + 1)), f2(z, z));
-        zl[l] = t.x;
-        zl[l + 1] = t.y;
-    }
-    // V_l^0 for l <= 2 LMAX (the m = 0 chain also feeds the self sums) and V_l^1,
-    // advanced together where both exist
-    float v0[LZ + 1], v1[LMAX + 1];
-    v0[0] = 1.f;
-    if (LZ >= 1) v0[1] = zl[1];
-    if (LMAX >= 1) v1[1] = 1.f;
-    if (LMAX >= 2) v1[2] = zl[2];
-#pragma unroll
-    for (int l = 2; l <= LZ; ++l) {
-        if (LMAX >= 3 && l >= 3 && l <= LMAX) {
-            const float2 c = f2(-(float)((l - 1) * (l - 1)), -(float)(l * (l - 2)));
-            const float2 t = __ffma2_rn(f2(zl[l], zl[l]), f2(v0[l - 1], v1[l - 1]),
-                                        __fmul2_rn(c, f2(v0[l - 2], v1[l - 2])));
-            v0[l] = t.x;
-            v1[l] = t.y;
-        } else {
-            v0[l] = fmaf(zl[l], v0[l - 1], -(float)((l - 1) * (l - 1)) * v0[l - 2]);
-        }
-    }
     const float w2 = w * w;
+    // m = 0: V_l^0 for l <= 2 LMAX; a_l^0 (l <= LMAX) and the self sums w^2 f_j, f_j = V_2j^0
     A[0] = __fadd2_rn(A[0], f2(w, w2));
+    {
+        float vm2 = 1.f, vm1 = z;   // V_0^0, V_1^0
+        if (LMAX >= 1) A[1].x = fmaf(vm1, w, A[1].x);
+        if constexpr (Direct<LMAX>::ON) S[0] = __fadd2_rn(S[0], f2(w2, w2 * z * z));
 #pragma unroll
-    for (int l = 1; l <= LMAX; ++l) A[l] = __ffma2_rn(f2(v0[l], v0[2 * l]), f2(w, w2), A[l]);
-    if constexpr (Direct<LMAX>::ON) {
-        // m = 0: w^2 V_l^0^2, two l per paired instruction
-#pragma unroll
-        for (int p = 0; p < Direct<LMAX>::np(0); ++p) {
-            const int l = 2 * p;
-            const float va = v0[l], vb = (l + 1 <= LMAX) ? v0[l + 1] : 0.f;
-            S[p] = __ffma2_rn(__fmul2_rn(f2(va, vb), f2(va, vb)), f2(w2, w2), S[p]);
+        for (int l = 2; l <= LZ; ++l) {
+            const float v = fmaf((float)(2 * l - 1) * z, vm1, -(float)((l - 1) * (l - 1)) * vm2);
+            if (l <= LMAX) A[l].x = fmaf(v, w, A[l].x);
+            if ((l & 1) == 0) A[l / 2].y = fmaf(v, w2, A[l / 2].y);
+            if constexpr (Direct<LMAX>::ON) {
+                if (l <= LMAX) {   // w^2 V_l^0^2 into slot (l, 0)
+                    const float t = v * v * w2;
+                    if (l & 1) S[l / 2].y += t;
+                    else S[l / 2].x += t;
+                }
+            }
+            vm2 = vm1;
+            vm1 = v;
         }
     }
+    // m >= 1: cs = w (x + i y)^m advanced by one complex product per m
+    float cr = w, ci = 0.f;
 #pragma unroll
     for (int m = 1; m <= LMAX; ++m) {
+        const float nr = fmaf(cr, x, -ci * y), ni = fmaf(cr, y, ci * x);
+        cr = nr;
+        ci = ni;
+        float qm = 0.f;
+        if constexpr (Direct<LMAX>::ON) qm = fmaf(cr, cr, ci * ci);
         float vm2 = 0.f, vm1 = 0.f;
-        float vv[LMAX + 1];
 #pragma unroll
         for (int l = m; l <= LMAX; ++l) {
             float v;
-            if (m == 1) v = v1[l];
-            else if (l == m) v = 1.f;
-            else if (l == m + 1) v = zl[m + 1];
-            else v = fmaf(zl[l], vm1, -(float)((l + m - 1) * (l - m - 1)) * vm2);
+            if (l == m) v = 1.f;
+            else if (l == m + 1) v = (float)(2 * m + 1) * z;
+            else v = fmaf((float)(2 * l - 1) * z, vm1, -(float)((l + m - 1) * (l - m - 1)) * vm2);
             vm2 = vm1;
             vm1 = v;
-            vv[l] = v;
             const int qi = Packed<LMAX>::q(l, m);
-            if (l == m) A[qi] = __fadd2_rn(A[qi], cs[m]);
-            else A[qi] = __ffma2_rn(f2(v, v), cs[m], A[qi]);
-        }
-        if constexpr (Direct<LMAX>::ON) {
-            // |w (x + i y)^m|^2 V_l^m^2, two l per paired instruction
-            const float qm = fmaf(cs[m].x, cs[m].x, cs[m].y * cs[m].y);
-#pragma unroll
-            for (int p = 0; p < Direct<LMAX>::np(m); ++p) {
-                const int l = m + 2 * p;
-                const float va = vv[l], vb = (l + 1 <= LMAX) ? vv[l + 1] : 0.f;
-                const int si = Direct<LMAX>::off(m) + p;
-                S[si] = __ffma2_rn(__fmul2_rn(f2(va, vb), f2(va, vb)), f2(qm, qm), S[si]);
+            if (l == m) A[qi] = __fadd2_rn(A[qi], f2(cr, ci));
+            else A[qi] = __ffma2_rn(f2(v, v), f2(cr, ci), A[qi]);
+            if constexpr (Direct<LMAX>::ON) {
+                const int si = Direct<LMAX>::off(m) + (l - m) / 2;
+                const float t = v * v * qm;
+                if ((l - m) & 1) S[si].y += t;
+                else S[si].x += t;
             }
         }
     }
@@ -622,11 +599,13 @@ __host__ __device__ inline QMap make_qmap(int P, int nb, int s, int chunk, int b
     return m;
 }
 
-// static shared memory of the varying-line-of-sight variant (the frames of a tile)
+// static shared memory of the harmonic kernel (one double), and the extra of the
+// varying-line-of-sight variant (the frames of a tile)
+constexpr int kPairsStaticSmem = 16;
 constexpr int kVlosStaticSmem = 3 * TPCF_MAX_TILE * 16;
 
 template <int LMAX, bool VLOS = false>
-__global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const PairParams p, const HarmTables H)
+__global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const PairParams p, const HarmTables H)
 {
     constexpr int NLM = Layout<LMAX>::NLM;
     constexpr int NACC = Layout<LMAX>::NACC;
@@ -683,14 +662,16 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         hist[tid] = b * b * b - a * a * a;
     }
     if (tid == 0) s_flag = 0;
-    double mono_w = p.use_mono ? (p.mono_w_dev ? *p.mono_w_dev : p.mono_w) : 0.0;
+    // the periodic offset's total weight, in shared memory (read only at the tile ends)
+    __shared__ double s_mono_w;
+    if (tid == 0) s_mono_w = p.use_mono ? (p.mono_w_dev ? *p.mono_w_dev : p.mono_w) : 0.0;
     int cta_mock = -1;
     int par = 0;                      // live half of the double-buffered queue counters
     __syncthreads();
 
     auto a00 = [&](float wsum, int b) -> float {
         double v = (double)wsum * H.K[0][0];
-        if (p.use_mono) v -= (mono_w - 1.0) * p.mono_coef[b];
+        if (p.use_mono) v -= (s_mono_w - 1.0) * p.mono_coef[b];
         return (float)v;
     };
 
@@ -730,7 +711,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         if (mock != cta_mock) {
             if (cta_mock >= 0) flush_cta(cta_mock);
             cta_mock = mock;
-            if (p.prim_mock && p.use_mono) mono_w = p.mono_w_mock[mock];
+            if (p.prim_mock && p.use_mono && tid == 0) s_mono_w = p.mono_w_mock[mock];
         }
         const long long mock_cells = (long long)mock * p.ncell_mock;
 
@@ -865,15 +846,11 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         // queues fill evenly) and sweep them 32 candidates per step
         int stride = (nr * 5) / 8 + 1;
         while (nr > 1 && gcd_int(stride, nr) != 1) ++stride;
-        int my_start = 0, my_len = 0, my_pos = 0, kb = 0;
-        uint32_t px = 0, py = 0, pz = 0;
+        int my_start = 0, my_len = 0, my_pos = 0, my_sl = 0;
         // two candidates per lane and step (i and i + 32): independent loads and bins
         bool done = false, have0 = false, have1 = false;
         float4 ent0 = make_float4(0.f, 0.f, 0.f, 0.f), ent1 = ent0;
         int ek0 = 0, ek1 = 0;
-        // the next step's records of the current range, loaded one step ahead
-        int4 nx0 = make_int4(0, 0, 0, 0), nx1 = nx0;
-        bool have_next = false;
         // appends a pending entry (one shared atomic); an entry that finds its queue
         // full stays pending and raises the flag.  (Aggregating equal keys across the
         // warp with a match instruction measured slower.)
@@ -909,31 +886,20 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                     const int rr = (int)(((unsigned)r * (unsigned)stride) % (unsigned)nr);
                     my_start = rstart[rr];
                     my_len = rlen[rr];
-                    const int sl = rslot[rr];
-                    const int4 pr = sPrim[sl];
-                    px = (uint32_t)pr.x;
-                    py = (uint32_t)pr.y;
-                    pz = (uint32_t)pr.z;
-                    kb = sl * nb;
+                    my_sl = rslot[rr];
                     my_pos = 0;
-                    have_next = false;
                 }
                 const int i0 = my_pos + lane, i1 = i0 + 32;
                 const bool v0 = i0 < my_len, v1 = i1 < my_len;
-                int4 q0, q1;
-                if (have_next) {
-                    q0 = nx0;
-                    q1 = nx1;
-                } else {
-                    q0 = p.rec[my_start + min(i0, my_len - 1)];
-                    q1 = p.rec[my_start + min(i1, my_len - 1)];
-                }
+                const int4 q0 = p.rec[my_start + min(i0, my_len - 1)];
+                const int4 q1 = p.rec[my_start + min(i1, my_len - 1)];
                 my_pos += 64;
-                have_next = my_pos < my_len;   // warp-uniform
-                if (have_next) {
-                    nx0 = p.rec[my_start + min(my_pos + lane, my_len - 1)];
-                    nx1 = p.rec[my_start + min(my_pos + lane + 32, my_len - 1)];
-                }
+                // the range's primary, re-read every step (fewer registers live across the
+                // drains; a register prefetch of the next step measured 2 % at two CTAs per
+                // SM but costs the third)
+                const int4 pr = sPrim[my_sl];
+                const uint32_t px = (uint32_t)pr.x, py = (uint32_t)pr.y, pz = (uint32_t)pr.z;
+                const int kb = my_sl * nb;
                 const int dx0 = (int)((uint32_t)q0.x - px), dx1 = (int)((uint32_t)q1.x - px);
                 const int dy0 = (int)((uint32_t)q0.y - py), dy1 = (int)((uint32_t)q1.y - py);
                 const int dz0 = (int)((uint32_t)q0.z - pz), dz1 = (int)((uint32_t)q1.z - pz);
@@ -969,7 +935,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
         __syncthreads();
 
         // ----- tile outputs (as in k_pairs)
-        const long long g0 = t0;
+        const long long g0 = (long long)s_tile * P;   // the tile's first primary (re-read: t0 is not kept)
         if (p.alm) {
             for (int i = tid; i < np * nb * NLM; i += T) {
                 const int slot = i / (nb * NLM), rem = i % (nb * NLM);
@@ -1017,7 +983,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 2 : 1)) k_pairs_q(const Pair
                     if (p.remove_self && single) dd = 0.0;   // raw^2 = w^2 up to the rounding of the self sum
                     d = kd * kd * dd;
                     if (p.use_mono) {
-                        const double c = (mono_w - 1.0) * p.mono_coef[b];
+                        const double c = (s_mono_w - 1.0) * p.mono_coef[b];
                         d += c * (c - 2.0 * kd * raw);
                     }
                 } else {

@@ -30,6 +30,13 @@ size_t pairs_smem_l3(bool, int, int, int, int, int);
 size_t pairs_smem_l4(bool, int, int, int, int, int);
 size_t pairs_smem_l5(bool, int, int, int, int, int);
 size_t pairs_smem_l6(bool, int, int, int, int, int);
+int pairs_per_sm_l0(bool, bool, int, size_t);
+int pairs_per_sm_l1(bool, bool, int, size_t);
+int pairs_per_sm_l2(bool, bool, int, size_t);
+int pairs_per_sm_l3(bool, bool, int, size_t);
+int pairs_per_sm_l4(bool, bool, int, size_t);
+int pairs_per_sm_l5(bool, bool, int, size_t);
+int pairs_per_sm_l6(bool, bool, int, size_t);
 }  // namespace tpcf
 
 using namespace tpcf;
@@ -366,8 +373,8 @@ Plan make_plan(const tpcf_config *c, int64_t n_sec, int64_t n_prim_hint)
     // the chunk's lane groups need P * n_bins <= 128 keys (half the CTA's lanes)
     P = std::min(P, std::max(1, 128 / c->n_bins));
     p.P = P;
-    // queue entries per CTA: two CTAs per SM up to l_max 4, one above
-    p.chunk = c->chunk ? c->chunk : (c->l_max <= 4 ? 6144 : 12288);
+    // queue entries per CTA: three CTAs per SM up to l_max 4, one above
+    p.chunk = c->chunk ? c->chunk : (c->l_max <= 4 ? 3840 : 12288);
     (void)n_prim_hint;
     return p;
 }
@@ -382,6 +389,19 @@ size_t pair_smem(int lmax, bool counts, const Plan &pl, int nb)
     case 4: return pairs_smem_l4(counts, pl.P, nb, pl.s, pl.chunk, 256);
     case 5: return pairs_smem_l5(counts, pl.P, nb, pl.s, pl.chunk, 256);
     default: return pairs_smem_l6(counts, pl.P, nb, pl.s, pl.chunk, 256);
+    }
+}
+
+int pair_per_sm(int lmax, bool counts, bool vlos, size_t smem)
+{
+    switch (counts ? 0 : lmax) {
+    case 0: return pairs_per_sm_l0(counts, vlos, 256, smem);
+    case 1: return pairs_per_sm_l1(counts, vlos, 256, smem);
+    case 2: return pairs_per_sm_l2(counts, vlos, 256, smem);
+    case 3: return pairs_per_sm_l3(counts, vlos, 256, smem);
+    case 4: return pairs_per_sm_l4(counts, vlos, 256, smem);
+    case 5: return pairs_per_sm_l5(counts, vlos, 256, smem);
+    default: return pairs_per_sm_l6(counts, vlos, 256, smem);
     }
 }
 
@@ -519,7 +539,8 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
 
     size_t smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
     // the varying-line-of-sight kernel keeps its tile's frames in static shared memory
-    const size_t smem_cap = 227 * 1024 - ((c->los && !counts_only) ? 3 * TPCF_MAX_TILE * 16 : 0);
+    const size_t smem_cap = 227 * 1024 - (counts_only ? 0 : kPairsStaticSmem)
+                          - ((c->los && !counts_only) ? kVlosStaticSmem : 0);
     while (smem > smem_cap && pl.chunk > 512) {
         pl.chunk -= 256;
         smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
@@ -549,8 +570,8 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
     int *work = nullptr;
     if ((rc = sc.alloc(&work, 1, true))) return rc;
     p.work = work;
-    // the count kernel is small (about 50 registers, a few KB of shared memory): four CTAs per SM
-    const int per_sm = counts_only ? 4 : (smem <= 110 * 1024 ? 2 : 1);
+    // resident CTAs per SM from the occupancy calculator (registers and shared memory)
+    const int per_sm = pair_per_sm(c->l_max, counts_only, p.vlos != 0, smem);
     int grid = ds->sms * per_sm;
     const int64_t tiles = (n_prim + pl.P - 1) / pl.P;
     if (grid > tiles) grid = (int)tiles;
