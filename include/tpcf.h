@@ -137,6 +137,19 @@ int tpcf_grid_info(tpcf_grid grid, int64_t *n_points, int32_t *cells_per_axis);
  * dev order[n] = input index of each point.  Any output may be NULL. */
 int tpcf_grid_points(tpcf_grid grid, uint32_t *xyz, float *w, int64_t *order, void *stream);
 
+/* Testing aid for the device-side failure path (the paper has no counterpart).
+ *   polls: how many non-blocking polls a tensor-core kernel (the split-precision
+ *     coupling, the emulator's products) spends in each mbarrier wait before it
+ *     gives up; 0 restores the default (2^26 polls, far longer than any stage).
+ *   unmet_wait: nonzero makes every such kernel, once its own tensor-core work
+ *     has completed, wait once more on an mbarrier phase that nothing completes
+ *     (a flag that nothing sets), with that limit.
+ * A wait that gives up sets the device error latch (TPCF_ERR_TIMEOUT at the next
+ * tpcf_stream_status), waits on the long bound for the kernel's own tensor-core
+ * work in flight, releases its tensor memory and returns: no fault, and the
+ * context stays usable.  Process-wide; TPCF_ERR_ARG for a negative count. */
+int tpcf_set_wait_limit(int64_t polls, int32_t unmet_wait);
+
 /* Pair stage (Eq. alm): for every primary, the neighbour search to r_max over
  * the secondaries in `grid`, exact radial binning and the FP32 harmonic sums.
  *   prim_xyz/prim_w: dev primaries [n_prim][3] / [n_prim] (NULL: unit weights).

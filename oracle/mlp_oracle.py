@@ -2,14 +2,20 @@
 
 TEST INFRASTRUCTURE ONLY (the tests are the only callers).
 
-The network: inputs scaled to [-1, 1] by a box, linear layers z = a W + b with
-the weights rounded to bfloat16 (round to nearest even of the FP32 value, as
-the device stores them), SiLU a = z / (1 + exp(-z)) on hidden layers, a linear
-output layer, and the loss L = mean over rows and outputs of
+The network: inputs scaled to [-1, 1] by a box (in FP32, as the device scales
+them), linear layers z = a W + b, SiLU a = z / (1 + exp(-z)) on hidden layers,
+a linear output layer, and the loss L = mean over rows and outputs of
 (y_hat - (y - mu) / sd)^2.  Backpropagation by the chain rule: dL/dy_hat =
 2 (y_hat - y_s) / (rows * outputs), dz = da * SiLU'(z), dW = a_prev^T dz,
 db = sum over rows of dz, da_prev = dz W^T.  The gradient with respect to the
 FP32 master weight is the one with respect to the rounded weight.
+
+Rounding (rounding=True): every operand of the three products is rounded to
+bfloat16 (round to nearest even of its FP32 value) as the device's tensor
+cores take them: the weights as stored, and the activations a, the output
+gradient dz and the inputs of each product as they are staged; the products
+and sums are then exact here (FP64), where the device accumulates in FP32.
+The bias gradient is the plain FP32-valued sum of dz.
 """
 from __future__ import annotations
 
@@ -36,16 +42,25 @@ def unpack(params, widths):
     return out
 
 
+def scale_inputs(x, lo, hi):
+    """2 (x - lo) / (hi - lo) - 1 in FP32 operations, as the device scales them."""
+    x, lo, hi = (np.asarray(v, dtype=np.float32) for v in (x, lo, hi))
+    return (np.float32(2.0) * (x - lo) / (hi - lo) - np.float32(1.0)).astype(np.float32)
+
+
 def loss_and_grad(params, widths, x, y, lo, hi, mu, sd, rounding=True):
-    """FP64 loss and gradient (same layout as params); rounding=False keeps the
-    weights exact (for finite-difference checks of the backpropagation)."""
+    """FP64 loss and gradient (same layout as params); rounding=False keeps every
+    operand exact (for finite-difference checks of the backpropagation)."""
     rnd = bf16_round if rounding else (lambda w: np.asarray(w, dtype=np.float64))
     params = np.asarray(params, dtype=np.float32 if rounding else np.float64)
     layers = unpack(params, widths)
-    a = 2.0 * (np.asarray(x, np.float64) - lo) / (np.asarray(hi, np.float64) - lo) - 1.0
+    if rounding:
+        a = scale_inputs(x, lo, hi).astype(np.float64)
+    else:
+        a = 2.0 * (np.asarray(x, np.float64) - lo) / (np.asarray(hi, np.float64) - lo) - 1.0
     acts, zs = [a], []
     for l, (W, b) in enumerate(layers):
-        z = acts[-1] @ rnd(W) + b.astype(np.float64)
+        z = rnd(acts[-1]) @ rnd(W) + b.astype(np.float64)
         zs.append(z)
         if l + 1 < len(layers):
             acts.append(z / (1.0 + np.exp(-z)))
@@ -61,17 +76,18 @@ def loss_and_grad(params, widths, x, y, lo, hi, mu, sd, rounding=True):
             z = zs[l]
             s = 1.0 / (1.0 + np.exp(-z))
             d = d * s * (1.0 + z * (1.0 - s))
-        grads.append((acts[l].T @ d, d.sum(0)))
-        d = d @ rnd(W).T
+        dr = rnd(d)
+        grads.append((rnd(acts[l]).T @ dr, d.sum(0)))
+        d = dr @ rnd(W).T
     grads.reverse()
     return loss, np.concatenate([np.concatenate([gW.ravel(), gb]) for gW, gb in grads])
 
 
 def predict(params, widths, x, lo, hi, mu, sd):
     params = np.asarray(params, dtype=np.float32)
-    a = 2.0 * (np.asarray(x, np.float64) - lo) / (np.asarray(hi, np.float64) - lo) - 1.0
+    a = scale_inputs(x, lo, hi).astype(np.float64)
     layers = unpack(params, widths)
     for l, (W, b) in enumerate(layers):
-        z = a @ bf16_round(W) + b.astype(np.float64)
+        z = bf16_round(a) @ bf16_round(W) + b.astype(np.float64)
         a = z / (1.0 + np.exp(-z)) if l + 1 < len(layers) else z
     return a * sd + mu

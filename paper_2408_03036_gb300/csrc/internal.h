@@ -98,6 +98,13 @@ inline int sm_count()
     return c;
 }
 
+// Polls of a per-stage mbarrier wait in the tensor-core kernels before they give
+// up and latch DEV_ERR_TIMEOUT (tpcf_set_wait_limit; default 2^26), and the
+// current device's error latch (read and cleared by tpcf_stream_status).
+long long device_wait_limit();
+int device_wait_unmet();   // test mode: one extra wait on an mbarrier phase that nothing completes
+int *device_error_flag();
+
 // Counts kernel launches made by the library (reported by tpcf_kernel_launches).
 void note_launch(int n = 1);
 

@@ -1,11 +1,13 @@
 // MLP emulator of the tree-level 3PCF multipoles: forward, backward and Adam
 // kernels behind the tpcf_emu_* C ABI (include/tpcf_emu.h).
 //
-// Every product of the network is one tiled GEMM kernel (64 x 64 output tiles,
-// 16-deep K slices in shared memory, 4 x 4 outputs per thread, FP32
-// accumulation) with BF16 weights read through the same tile loader; the
-// epilogue adds the bias and applies SiLU in the forward pass.  Backward:
-// dZ = dA * SiLU'(Z), dW = A_prev^T dZ, db = column sums of dZ, dA_prev = dZ W^T.
+// Every product of the network runs on the 5th-generation tensor cores: one GEMM
+// kernel (k_gemm_tc) computes a 128-row x NT-column tile of C = A B with bf16
+// operands (FP32 activations and gradients rounded to bf16 as they are staged,
+// bf16 weights as stored) and FP32 accumulation in tensor memory; the epilogue
+// reads the tile back from tensor memory and adds the bias and applies SiLU in
+// the forward pass.  Backward: dZ = dA * SiLU'(Z), dW = A_prev^T dZ, db = column
+// sums of dZ, dA_prev = dZ W^T, all three products on the same kernel.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -16,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "tc_common.cuh"
 #include "../../include/tpcf_emu.h"
 
 namespace {
@@ -26,11 +29,11 @@ constexpr int kChunk = 4096;          // rows per internal pass (scratch capacit
 
 struct Layer {
     int in, out;
+    int ldi, ldo;                     // in and out rounded up to 8 (16-byte bf16 rows)
     int64_t w_off, b_off;             // offsets in the parameter vector
 };
 
-__device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
-__device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+inline int round8(int n) { return (n + 7) / 8 * 8; }
 
 __device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z)
@@ -41,70 +44,246 @@ __device__ __forceinline__ float silu_grad(float z)
 
 enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_SILU = 2 };
 
-// C[m][n] = sum_k A(m, k) B(k, n) with A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn].
-template <class TA, class TB, int EPI>
-__global__ void __launch_bounds__(256) k_gemm(const TA *__restrict__ A, int64_t sam, int64_t sak,
-                                              const TB *__restrict__ B, int64_t sbk, int64_t sbn, int M, int N,
-                                              int K, float *__restrict__ C, int64_t ldc,
-                                              const float *__restrict__ bias, float *__restrict__ act)
+// C[m][n] = sum_k A(m, k) B(k, n) with A(m, k) = A[m sam + k sak] and
+// B(k, n) = B[k sbk + n sbn], both bf16.
+struct GemmArgs {
+    const __nv_bfloat16 *A;
+    int64_t sam, sak;
+    const __nv_bfloat16 *B;
+    int64_t sbk, sbn;
+    int M, N, K;
+    float *C;               // FP32 output, row stride ldc
+    int64_t ldc;
+    const float *bias;
+    __nv_bfloat16 *act;     // bf16 SiLU(C), row stride ld_act (EPI_BIAS_SILU)
+    int64_t ld_act;
+    int a_vec, b_vec;       // operand contiguous in K with 16-byte aligned rows: 16-byte staging
+    int NT;                 // tile columns: a power of two from 16 to 256
+    int k_per;              // K values per split (a multiple of kKS); blockIdx.z takes split z
+    int split;              // more than one split: the tiles are added into C (zeroed first)
+    int tmem_cols;          // tensor-memory columns allocated: a power of two >= max(32, NT)
+    int *err;
+    long long wait_limit;   // polls of a per-stage mbarrier wait
+    int wait_unmet;         // test mode: one more wait on a phase that nothing completes
+};
+
+constexpr int kGemmThreads = 256;
+constexpr int kTM = 128;                 // tile rows (tensor-memory lanes, the MMA's M)
+constexpr int kKS = 32;                  // K per stage: two MMAs of K = 16
+constexpr uint32_t kRowBytes = kKS * 2;  // bytes of one operand row in a stage (bf16)
+constexpr uint32_t kSBO = 4 * 128;       // bytes between 8-row core-matrix groups
+
+// One CTA per (NT-column, 128-row) tile of C.  A stage holds the tile's 128 A rows
+// and NT B columns for kKS values of K as bf16 in the canonical no-swizzle
+// K-major layout (16-byte core-matrix rows, core matrices 128 bytes apart along K
+// and kSBO apart across 8-row groups); stages are double-buffered (the next one
+// is loaded into registers while the tensor cores read the current one), one
+// thread issues the MMAs and commits them to the stage's mbarrier, and every
+// wait is bounded: a timeout latches DEV_ERR_TIMEOUT, waits for the MMAs in
+// flight, releases the tensor memory and returns.
+template <int EPI>
+__global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_tc(const GemmArgs g)
 {
-    __shared__ __align__(16) float As[16][68];   // [k][m]
-    __shared__ __align__(16) float Bs[16][68];   // [k][n]
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = tid + 256 * q;
-            int mm, kk;
-            if (sak == 1) { kk = e & 15; mm = e >> 4; } else { mm = e & 63; kk = e >> 6; }
-            const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? ld(A + m * sam + k * sak) : 0.f;
-            int nn;
-            if (sbn == 1) { nn = e & 63; kk = e >> 6; } else { kk = e & 15; nn = e >> 4; }
-            const int n = n0 + nn, k2 = k0 + kk;
-            Bs[kk][nn] = (n < N && k2 < K) ? ld(B + k2 * sbk + n * sbn) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            const float4 a = *reinterpret_cast<const float4 *>(&As[kk][ty * 4]);
-            const float4 b = *reinterpret_cast<const float4 *>(&Bs[kk][tx * 4]);
-            const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-        }
-        __syncthreads();
+    using namespace tpcf::tc;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * g.NT;
+    const int NT = g.NT;
+    const uint32_t a_bytes = kTM * kRowBytes, stage_bytes = a_bytes + (uint32_t)NT * kRowBytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * stage_bytes + 16);
+    volatile int *s_abort = reinterpret_cast<int *>(smem + 2 * stage_bytes + 20);
+
+    if (tid == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = m0 + ty * 4 + i;
-        if (m >= M) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = n0 + tx * 4 + j;
-            if (n >= N) continue;
-            float z = acc[i][j];
-            if (EPI != EPI_STORE) z += bias[n];
-            C[m * ldc + n] = z;
-            if (EPI == EPI_BIAS_SILU) act[m * ldc + n] = silu(z);
-        }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(g.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // staging, per operand: 16-byte loads of 8 consecutive K values straight into a
+    // core-matrix row when the operand is contiguous in K with aligned rows
+    // (consecutive threads take consecutive octets of a row), otherwise one bf16
+    // at a time with the lanes along whichever index is contiguous in memory
+    // (every warp load one coalesced run)
+    const bool a_kc = g.sak == 1, b_kc = g.sbk == 1;
+    const int k_beg = blockIdx.z * g.k_per, k_end = min(g.K, k_beg + g.k_per);
+    const int nbe = NT / 8;                      // scalar B elements per thread (NT x kKS / 256)
+    const int nbu = NT * 4;                      // 16-byte B units (NT rows x 4 octets)
+    uint4 va[2], vb[4];
+    __nv_bfloat16 sa[16], sb[32];
+    auto cm_off = [](int r, int k) -> uint32_t {   // byte offset of element (r, k) in an operand tile
+        return (uint32_t)(((r >> 3) * 4 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
+    };
+    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+    auto load = [&](int st) {
+        const int k0 = k_beg + st * kKS;
+        if (g.a_vec) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int u = tid + kGemmThreads * q, r = u >> 2, k = k0 + 8 * (u & 3), m = m0 + r;
+                va[q] = (m < g.M && k < k_end) ? __ldg(reinterpret_cast<const uint4 *>(g.A + m * g.sam + k))
+                                                : make_uint4(0u, 0u, 0u, 0u);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                int r, k;
+                if (a_kc) { r = (tid >> 5) + 8 * e; k = lane; }
+                else { r = tid & (kTM - 1); k = (tid >> 7) + 2 * e; }
+                const int m = m0 + r;
+                k += k0;
+                sa[e] = (m < g.M && k < k_end) ? g.A[m * g.sam + k * g.sak] : zero;
+            }
+        }
+        if (g.b_vec) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int u = tid + kGemmThreads * q, nn = u >> 2, k = k0 + 8 * (u & 3), n = n0 + nn;
+                vb[q] = (u < nbu && n < g.N && k < k_end)
+                            ? __ldg(reinterpret_cast<const uint4 *>(g.B + n * g.sbn + k))
+                            : make_uint4(0u, 0u, 0u, 0u);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                if (e >= nbe) break;
+                int nn, k;
+                if (b_kc) { nn = (tid >> 5) + 8 * e; k = lane; }
+                else { nn = tid % NT; k = tid / NT + (kGemmThreads / NT) * e; }
+                const int n = n0 + nn;
+                k += k0;
+                sb[e] = (n < g.N && k < k_end) ? g.B[k * g.sbk + n * g.sbn] : zero;
+            }
+        }
+    };
+    auto store = [&](int buf) {
+        unsigned char *stg = smem + buf * stage_bytes;
+        if (g.a_vec) {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int u = tid + kGemmThreads * q;
+                *reinterpret_cast<uint4 *>(stg + cm_off(u >> 2, 8 * (u & 3))) = va[q];
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                int r, k;
+                if (a_kc) { r = (tid >> 5) + 8 * e; k = lane; }
+                else { r = tid & (kTM - 1); k = (tid >> 7) + 2 * e; }
+                *reinterpret_cast<__nv_bfloat16 *>(stg + cm_off(r, k)) = sa[e];
+            }
+        }
+        if (g.b_vec) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int u = tid + kGemmThreads * q;
+                if (u < nbu) *reinterpret_cast<uint4 *>(stg + a_bytes + cm_off(u >> 2, 8 * (u & 3))) = vb[q];
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                if (e >= nbe) break;
+                int nn, k;
+                if (b_kc) { nn = (tid >> 5) + 8 * e; k = lane; }
+                else { nn = tid % NT; k = tid / NT + (kGemmThreads / NT) * e; }
+                *reinterpret_cast<__nv_bfloat16 *>(stg + a_bytes + cm_off(nn, k)) = sb[e];
+            }
+        }
+    };
+
+    const int nst = k_end > k_beg ? (k_end - k_beg + kKS - 1) / kKS : 0;
+    uint32_t phase[2] = {0u, 0u};
+    bool used[2] = {false, false};
+    bool ok = true;
+    const uint32_t idesc = make_idesc(1u, kTM, NT);
+    if (nst > 0) load(0);
+    for (int st = 0; st < nst; ++st) {
+        const int b = st & 1;
+        // the MMAs that last read this buffer must have completed
+        if (tid == 0 && used[b] && !mbar_wait(&bars[b], phase[b] ^ 1u, g.wait_limit)) *s_abort = 1;
+        __syncthreads();
+        if (*s_abort) { ok = false; break; }
+        store(b);
+        if (st + 1 < nst) load(st + 1);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t base = smem_u32(smem + b * stage_bytes);
+#pragma unroll
+            for (int ks = 0; ks < kKS / 16; ++ks) {
+                const uint64_t da = make_desc(base + 256u * ks, 128, kSBO);
+                const uint64_t db = make_desc(base + a_bytes + 256u * ks, 128, kSBO);
+                mma_issue<false>(tmem, da, db, idesc, (st > 0 || ks > 0) ? 1u : 0u);
+            }
+            mma_commit(&bars[b]);
+        }
+        used[b] = true;
+        phase[b] ^= 1u;
+    }
+    // the last MMAs: every buffer's latest commit
+    if (ok && tid == 0) {
+        for (int b = 0; b < 2; ++b)
+            if (used[b] && !mbar_wait(&bars[b], phase[b] ^ 1u, g.wait_limit)) *s_abort = 1;
+        // test mode: buffer 0's next phase, which no commit completes
+        if (g.wait_unmet && !*s_abort && !mbar_wait(&bars[0], phase[0], g.wait_limit)) *s_abort = 1;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (*s_abort) ok = false;
+    if (ok && nst > 0) {
+        // warp w reads tensor-memory lanes 32 (w % 4) ..; the two warps of a lane
+        // quarter take alternate 16-column chunks
+        const int quarter = warp & 3, set = warp >> 2;
+        const int row = m0 + 32 * quarter + lane;
+        for (int c0 = 16 * set; c0 < NT; c0 += 32) {
+            float v[16];
+            tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
+            if (row < g.M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n >= g.N) break;
+                    float z = v[j];
+                    if (EPI != EPI_STORE) z += __ldg(g.bias + n);
+                    if (EPI == EPI_STORE && g.split) atomicAdd(g.C + row * g.ldc + n, z);
+                    else g.C[row * g.ldc + n] = z;
+                    if (EPI == EPI_BIAS_SILU) g.act[row * g.ld_act + n] = __float2bfloat16_rn(silu(z));
+                }
+            }
+        }
+    } else if (!ok && tid == 0) {
+        if (g.err) atomicCAS(g.err, 0, tpcf::DEV_ERR_TIMEOUT);
+        // wait (on the long bound) for anything still in flight before releasing TMEM
+        for (int b = 0; b < 2; ++b)
+            if (used[b]) mbar_wait(&bars[b], phase[b] ^ 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols));
 }
 
+// scaled inputs 2 (x - lo) / (hi - lo) - 1 as bf16 rows of stride ld (padding stays zero)
 __global__ void k_scale_in(const float *__restrict__ x, int64_t n, int w, const float *__restrict__ lo,
-                           const float *__restrict__ hi, float *__restrict__ xs)
+                           const float *__restrict__ hi, __nv_bfloat16 *__restrict__ xs, int ld)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * w; i += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(i % w);
-        xs[i] = 2.f * (x[i] - lo[c]) / (hi[c] - lo[c]) - 1.f;
+        const int64_t r = i / w;
+        xs[r * ld + c] = __float2bfloat16_rn(2.f * (x[i] - lo[c]) / (hi[c] - lo[c]) - 1.f);
     }
 }
 
@@ -126,10 +305,11 @@ __global__ void k_col_stats(const float *__restrict__ y, int64_t n, int w, float
     sd[c] = (float)(var > 0.0 ? sqrt(var) : 1.0);
 }
 
-// dY = 2 (yhat - (y - mean) / sd) / (rows * w); loss += mean squared error
+// dY = 2 (yhat - (y - mean) / sd) / (rows * w); loss += mean squared error; dY also
+// as bf16 rows of stride ld (the products' operand)
 __global__ void k_loss_grad(const float *__restrict__ yhat, const float *__restrict__ y, int64_t rows, int w,
                             const float *__restrict__ mean, const float *__restrict__ sd, double inv_count,
-                            float *__restrict__ dy, double *__restrict__ loss)
+                            float *__restrict__ dy, __nv_bfloat16 *__restrict__ dyb, int ld, double *__restrict__ loss)
 {
     __shared__ double red[8];
     double s = 0.0;
@@ -137,7 +317,9 @@ __global__ void k_loss_grad(const float *__restrict__ yhat, const float *__restr
          i += (int64_t)gridDim.x * blockDim.x) {
         const int c = (int)(i % w);
         const float d = yhat[i] - (y[i] - mean[c]) / sd[c];
-        dy[i] = (float)(2.0 * inv_count) * d;
+        const float g = (float)(2.0 * inv_count) * d;
+        dy[i] = g;
+        dyb[(i / w) * ld + c] = __float2bfloat16_rn(g);
         s += (double)d * d;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -150,10 +332,16 @@ __global__ void k_loss_grad(const float *__restrict__ yhat, const float *__restr
     }
 }
 
-__global__ void k_silu_back(const float *__restrict__ z, float *__restrict__ d, int64_t n)
+// d *= SiLU'(z) over rows x w, and the result as bf16 rows of stride ld
+__global__ void k_silu_back(const float *__restrict__ z, float *__restrict__ d, int64_t rows, int w,
+                            __nv_bfloat16 *__restrict__ db, int ld)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        d[i] *= silu_grad(z[i]);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * w;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = d[i] * silu_grad(z[i]);
+        d[i] = v;
+        db[(i / w) * ld + (int)(i % w)] = __float2bfloat16_rn(v);
+    }
 }
 
 // db[c] (+)= sum over rows of d[r][c]; one thread per column
@@ -183,8 +371,7 @@ __global__ void k_unscale_out(const float *__restrict__ yhat, int64_t rows, int 
 }
 
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
-                       float *__restrict__ v, __nv_bfloat16 *__restrict__ pb, int64_t n, float lr_t, float b1,
-                       float b2, float eps_t)
+                       float *__restrict__ v, int64_t n, float lr_t, float b1, float b2, float eps_t)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float gi = g[i];
@@ -192,16 +379,23 @@ __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float
         const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
         m[i] = mi;
         v[i] = vi;
-        const float pi = p[i] - lr_t * mi / (sqrtf(vi) + eps_t);
-        p[i] = pi;
-        pb[i] = __float2bfloat16_rn(pi);
+        p[i] = p[i] - lr_t * mi / (sqrtf(vi) + eps_t);
     }
 }
 
-__global__ void k_to_bf16(const float *__restrict__ p, __nv_bfloat16 *__restrict__ pb, int64_t n)
+// bf16 copies of one layer's weights W[in][out] (FP32 master): wT[o][ldi] = W[i][o]
+// (the forward product's operand, contiguous in i) and wP[i][ldo] = W[i][o] (the
+// backward product's, contiguous in o); the padding columns stay zero
+__global__ void k_wcopy(const float *__restrict__ W, int in, int out, __nv_bfloat16 *__restrict__ wT, int ldi,
+                        __nv_bfloat16 *__restrict__ wP, int ldo)
 {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        pb[i] = __float2bfloat16_rn(p[i]);
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)in * out;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / out), o = (int)(idx % out);
+        const __nv_bfloat16 b = __float2bfloat16_rn(W[idx]);
+        wT[(int64_t)o * ldi + i] = b;
+        wP[(int64_t)i * ldo + o] = b;
+    }
 }
 
 // Glorot-uniform weights from splitmix64(seed ^ index) (a counter-based hash), zero biases
@@ -227,14 +421,18 @@ struct tpcf_emu_s {
     int widths[kMaxLayers + 1] = {0};
     Layer layers[kMaxLayers];
     int64_t n_params = 0;
-    int maxw = 0;
+    int maxw = 0, maxw8 = 0;
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
-    __nv_bfloat16 *pbf = nullptr;
     float *in_lo = nullptr, *in_hi = nullptr, *out_mean = nullptr, *out_sd = nullptr;
-    float *xs = nullptr;                      // scaled inputs [kChunk][in]
-    float *Z[kMaxLayers] = {nullptr}, *A[kMaxLayers] = {nullptr};   // [kChunk][out_l]
-    float *d0 = nullptr, *d1 = nullptr;       // gradient ping-pong [kChunk][maxw]
-    float *gtmp = nullptr;                    // per-chunk gradient [n_params]
+    // bf16 operands of the products, rows padded to multiples of 8 (padding zero)
+    __nv_bfloat16 *wT[kMaxLayers] = {nullptr};   // [out][ldi] transposed weights
+    __nv_bfloat16 *wP[kMaxLayers] = {nullptr};   // [in][ldo] weights
+    __nv_bfloat16 *xs = nullptr;                 // scaled inputs [kChunk][ldi of layer 0]
+    __nv_bfloat16 *act[kMaxLayers] = {nullptr};  // hidden activations [kChunk][ldo]
+    __nv_bfloat16 *db = nullptr;                 // output gradient of the current layer [kChunk][maxw8]
+    float *Z[kMaxLayers] = {nullptr};            // pre-activations [kChunk][out] (FP32)
+    float *d0 = nullptr, *d1 = nullptr;          // gradient ping-pong [kChunk][maxw] (FP32)
+    float *gtmp = nullptr;                       // per-chunk gradient [n_params]
     int64_t step = 0;
 };
 
@@ -251,33 +449,109 @@ int emu_cuda(cudaError_t e)
         if (e_ != cudaSuccess) return emu_cuda(e_);      \
     } while (0)
 
-template <class TA, class TB, int EPI>
-cudaError_t gemm(const TA *A, int64_t sam, int64_t sak, const TB *B, int64_t sbk, int64_t sbn, int M, int N, int K,
-                 float *C, int64_t ldc, const float *bias, float *act, cudaStream_t st)
+template <int EPI>
+cudaError_t gemm(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B, int64_t sbk, int64_t sbn,
+                 int M, int N, int K, float *C, int64_t ldc, const float *bias, __nv_bfloat16 *act, int64_t ld_act,
+                 cudaStream_t st)
 {
-    const dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<TA, TB, EPI><<<grid, 256, 0, st>>>(A, sam, sak, B, sbk, sbn, M, N, K, C, ldc, bias, act);
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    GemmArgs g;
+    g.A = A;
+    g.sam = sam;
+    g.sak = sak;
+    g.B = B;
+    g.sbk = sbk;
+    g.sbn = sbn;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.C = C;
+    g.ldc = ldc;
+    g.bias = bias;
+    g.act = act;
+    g.ld_act = ld_act;
+    auto aligned16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
+    g.a_vec = sak == 1 && sam % 8 == 0 && aligned16(A);
+    g.b_vec = sbk == 1 && sbn % 8 == 0 && aligned16(B);
+    // tile width: 256 columns for wide outputs; narrow ones (hidden layers) in tiles
+    // of at most 64 so that their few row tiles still spread over the SMs (a power
+    // of two from 16 to 256: the staging map needs NT to divide 256)
+    g.NT = 256;
+    if (N <= 256) {
+        g.NT = 16;
+        while (g.NT < 64 && g.NT < N) g.NT <<= 1;
+    }
+    g.tmem_cols = 32;
+    while (g.tmem_cols < g.NT) g.tmem_cols <<= 1;
+    g.err = tpcf::device_error_flag();
+    g.wait_limit = tpcf::device_wait_limit();
+    g.wait_unmet = tpcf::device_wait_unmet();
+    // split K when the output has too few tiles to fill the SMs (the weight
+    // gradients: 256 x 256 outputs over thousands of rows); the splits' tiles
+    // are added into the zeroed output with FP32 atomics
+    const int tiles = ((N + g.NT - 1) / g.NT) * ((M + kTM - 1) / kTM);
+    const int nst = (K + kKS - 1) / kKS;
+    int splits = 1;
+    if (EPI == EPI_STORE && tiles < 2 * tpcf::sm_count()) {
+        splits = (2 * tpcf::sm_count() + tiles - 1) / tiles;
+        splits = std::max(1, std::min(splits, nst / 4));
+    }
+    g.k_per = ((nst + splits - 1) / splits) * kKS;
+    splits = (K + g.k_per - 1) / g.k_per;
+    g.split = splits > 1 ? 1 : 0;
+    if (g.split) {
+        cudaError_t e = cudaMemsetAsync(C, 0, (size_t)M * ldc * sizeof(float), st);
+        if (e != cudaSuccess) return e;
+    }
+    // two stages and the barriers; enough that the CTAs sharing an SM never ask for
+    // more than its 512 tensor-memory columns (allocations never wait)
+    size_t smem = 2 * ((size_t)kTM + g.NT) * kRowBytes + 64;
+    const size_t floor_bytes = (size_t)(228 * 1024) / (512 / g.tmem_cols + 1) + 1024;
+    if (smem < floor_bytes) smem = floor_bytes;
+    static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
+    const unsigned long long bit = tpcf::device_bit();
+    if (!(attr_done.load(std::memory_order_acquire) & bit)) {
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done.fetch_or(bit, std::memory_order_acq_rel);
+    }
+    const dim3 grid((N + g.NT - 1) / g.NT, (M + kTM - 1) / kTM, splits);
+    k_gemm_tc<EPI><<<grid, kGemmThreads, smem, st>>>(g);
     tpcf::note_launch();
+    return cudaGetLastError();
+}
+
+// bf16 weight copies of every layer from the FP32 master parameters
+cudaError_t weight_copies(tpcf_emu e, cudaStream_t st)
+{
+    for (int l = 0; l < e->nl; ++l) {
+        const Layer &L = e->layers[l];
+        k_wcopy<<<grid1((int64_t)L.in * L.out), 256, 0, st>>>(e->params + L.w_off, L.in, L.out, e->wT[l], L.ldi,
+                                                               e->wP[l], L.ldo);
+        tpcf::note_launch();
+    }
     return cudaGetLastError();
 }
 
 // forward pass of rows [0, rows) of the scaled inputs already in e->xs
 cudaError_t forward(tpcf_emu e, int64_t rows, cudaStream_t st)
 {
-    const float *in = e->xs;
+    const __nv_bfloat16 *in = e->xs;
+    int ld_in = e->layers[0].ldi;
     for (int l = 0; l < e->nl; ++l) {
         const Layer &L = e->layers[l];
-        const __nv_bfloat16 *W = e->pbf + L.w_off;
         const float *b = e->params + L.b_off;
+        // Z[r][o] = sum_i in[r][i] W[i][o] + b[o]: A = in (contiguous in i), B(i, o) = wT[o][i]
         cudaError_t err;
         if (l + 1 < e->nl)
-            err = gemm<float, __nv_bfloat16, EPI_BIAS_SILU>(in, L.in, 1, W, L.out, 1, (int)rows, L.out, L.in, e->Z[l],
-                                                            L.out, b, e->A[l], st);
+            err = gemm<EPI_BIAS_SILU>(in, ld_in, 1, e->wT[l], 1, L.ldi, (int)rows, L.out, L.in, e->Z[l], L.out, b,
+                                      e->act[l], L.ldo, st);
         else
-            err = gemm<float, __nv_bfloat16, EPI_BIAS>(in, L.in, 1, W, L.out, 1, (int)rows, L.out, L.in, e->Z[l], L.out,
-                                                       b, nullptr, st);
+            err = gemm<EPI_BIAS>(in, ld_in, 1, e->wT[l], 1, L.ldi, (int)rows, L.out, L.in, e->Z[l], L.out, b,
+                                 nullptr, 0, st);
         if (err != cudaSuccess) return err;
-        in = e->A[l];
+        in = e->act[l];
+        ld_in = L.ldo;
     }
     return cudaSuccess;
 }
@@ -288,26 +562,27 @@ cudaError_t backward_chunk(tpcf_emu e, const float *y, int64_t rows, double inv_
 {
     const int nl = e->nl, w_out = e->widths[nl];
     k_loss_grad<<<grid1(rows * w_out), 256, 0, st>>>(e->Z[nl - 1], y, rows, w_out, e->out_mean, e->out_sd,
-                                                      inv_count, e->d0, loss);
+                                                      inv_count, e->d0, e->db, e->layers[nl - 1].ldo, loss);
     tpcf::note_launch();
     float *dcur = e->d0, *dnext = e->d1;
     for (int l = nl - 1; l >= 0; --l) {
         const Layer &L = e->layers[l];
         if (l + 1 < nl) {
-            k_silu_back<<<grid1(rows * L.out), 256, 0, st>>>(e->Z[l], dcur, rows * L.out);
+            k_silu_back<<<grid1(rows * L.out), 256, 0, st>>>(e->Z[l], dcur, rows, L.out, e->db, L.ldo);
             tpcf::note_launch();
         }
-        const float *aprev = l > 0 ? e->A[l - 1] : e->xs;
-        // dW[i][o] = sum_r aprev[r][i] dZ[r][o]
-        cudaError_t err = gemm<float, float, EPI_STORE>(aprev, 1, L.in, dcur, L.out, 1, L.in, L.out, (int)rows,
-                                                        g + L.w_off, L.out, nullptr, nullptr, st);
+        const __nv_bfloat16 *aprev = l > 0 ? e->act[l - 1] : e->xs;
+        const int ld_prev = L.ldi;
+        // dW[i][o] = sum_r aprev[r][i] dZ[r][o]: A(i, r) = aprev[r][i], B(r, o) = db[r][o]
+        cudaError_t err = gemm<EPI_STORE>(aprev, 1, ld_prev, e->db, L.ldo, 1, L.in, L.out, (int)rows,
+                                          g + L.w_off, L.out, nullptr, nullptr, 0, st);
         if (err != cudaSuccess) return err;
         k_col_sum<<<(L.out + 127) / 128, 128, 0, st>>>(dcur, rows, L.out, g + L.b_off, 0);
         tpcf::note_launch();
         if (l > 0) {
-            // dA_prev[r][i] = sum_o dZ[r][o] W[i][o]
-            err = gemm<float, __nv_bfloat16, EPI_STORE>(dcur, L.out, 1, e->pbf + L.w_off, 1, L.out, (int)rows, L.in,
-                                                        L.out, dnext, L.in, nullptr, nullptr, st);
+            // dA_prev[r][i] = sum_o dZ[r][o] W[i][o]: A = db (contiguous in o), B(o, i) = wP[i][o]
+            err = gemm<EPI_STORE>(e->db, L.ldo, 1, e->wP[l], 1, L.ldo, (int)rows, L.in, L.out, dnext, L.in, nullptr,
+                                  nullptr, 0, st);
             if (err != cudaSuccess) return err;
             std::swap(dcur, dnext);
         }
@@ -323,7 +598,8 @@ int batch_gradient(tpcf_emu e, const float *x, const float *y, int64_t batch, do
     if (loss) ECK(cudaMemsetAsync(loss, 0, sizeof(double), st));
     for (int64_t r0 = 0; r0 < batch; r0 += kChunk) {
         const int64_t rows = std::min<int64_t>(kChunk, batch - r0);
-        k_scale_in<<<grid1(rows * w_in), 256, 0, st>>>(x + r0 * w_in, rows, w_in, e->in_lo, e->in_hi, e->xs);
+        k_scale_in<<<grid1(rows * w_in), 256, 0, st>>>(x + r0 * w_in, rows, w_in, e->in_lo, e->in_hi, e->xs,
+                                                        e->layers[0].ldi);
         tpcf::note_launch();
         ECK(forward(e, rows, st));
         float *g = r0 == 0 ? e->grads : e->gtmp;
@@ -357,6 +633,9 @@ int tpcf_emu_create(const int32_t *widths, int32_t n_layers, uint64_t seed, tpcf
         Layer &L = e->layers[l];
         L.in = widths[l];
         L.out = widths[l + 1];
+        L.ldi = round8(L.in);
+        L.ldo = round8(L.out);
+        e->maxw8 = std::max(e->maxw8, L.ldo);
         L.w_off = off;
         off += (int64_t)L.in * L.out;
         L.b_off = off;
@@ -372,18 +651,31 @@ int tpcf_emu_create(const int32_t *widths, int32_t n_layers, uint64_t seed, tpcf
     A((void **)&e->gtmp, off * sizeof(float));
     A((void **)&e->m, off * sizeof(float));
     A((void **)&e->v, off * sizeof(float));
-    A((void **)&e->pbf, off * sizeof(__nv_bfloat16));
     A((void **)&e->in_lo, widths[0] * sizeof(float));
     A((void **)&e->in_hi, widths[0] * sizeof(float));
     A((void **)&e->out_mean, widths[n_layers] * sizeof(float));
     A((void **)&e->out_sd, widths[n_layers] * sizeof(float));
-    A((void **)&e->xs, (size_t)kChunk * widths[0] * sizeof(float));
+    const size_t bf = sizeof(__nv_bfloat16);
+    A((void **)&e->xs, (size_t)kChunk * e->layers[0].ldi * bf);
     for (int l = 0; l < n_layers; ++l) {
-        A((void **)&e->Z[l], (size_t)kChunk * widths[l + 1] * sizeof(float));
-        A((void **)&e->A[l], (size_t)kChunk * widths[l + 1] * sizeof(float));
+        const Layer &L = e->layers[l];
+        A((void **)&e->wT[l], (size_t)L.out * L.ldi * bf);
+        A((void **)&e->wP[l], (size_t)L.in * L.ldo * bf);
+        A((void **)&e->Z[l], (size_t)kChunk * L.out * sizeof(float));
+        if (l + 1 < n_layers) A((void **)&e->act[l], (size_t)kChunk * L.ldo * bf);
     }
+    A((void **)&e->db, (size_t)kChunk * e->maxw8 * bf);
     A((void **)&e->d0, (size_t)kChunk * e->maxw * sizeof(float));
     A((void **)&e->d1, (size_t)kChunk * e->maxw * sizeof(float));
+    // zero the padded bf16 buffers once: their padding is never written
+    if (err == cudaSuccess) err = cudaMemset(e->xs, 0, (size_t)kChunk * e->layers[0].ldi * bf);
+    for (int l = 0; l < n_layers && err == cudaSuccess; ++l) {
+        const Layer &L = e->layers[l];
+        err = cudaMemset(e->wT[l], 0, (size_t)L.out * L.ldi * bf);
+        if (err == cudaSuccess) err = cudaMemset(e->wP[l], 0, (size_t)L.in * L.ldo * bf);
+        if (err == cudaSuccess && e->act[l]) err = cudaMemset(e->act[l], 0, (size_t)kChunk * L.ldo * bf);
+    }
+    if (err == cudaSuccess) err = cudaMemset(e->db, 0, (size_t)kChunk * e->maxw8 * bf);
     if (err == cudaSuccess) err = cudaMemset(e->params, 0, off * sizeof(float));
     if (err == cudaSuccess) err = cudaMemset(e->m, 0, off * sizeof(float));
     if (err == cudaSuccess) err = cudaMemset(e->v, 0, off * sizeof(float));
@@ -397,10 +689,9 @@ int tpcf_emu_create(const int32_t *widths, int32_t n_layers, uint64_t seed, tpcf
         k_init<<<grid1((int64_t)L.in * L.out), 256>>>(e->params, L.w_off, (int64_t)L.in * L.out, a, seed);
         tpcf::note_launch();
     }
-    k_to_bf16<<<grid1(off), 256>>>(e->params, e->pbf, off);
-    tpcf::note_launch();
+    if (err == cudaSuccess) err = weight_copies(e, 0);
     std::vector<float> lo(widths[0], -1.f), hi(widths[0], 1.f), mu(widths[n_layers], 0.f), sd(widths[n_layers], 1.f);
-    err = cudaMemcpy(e->in_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess) err = cudaMemcpy(e->in_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(e->in_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(e->out_mean, mu.data(), mu.size() * 4, cudaMemcpyHostToDevice);
     if (err == cudaSuccess) err = cudaMemcpy(e->out_sd, sd.data(), sd.size() * 4, cudaMemcpyHostToDevice);
@@ -417,14 +708,13 @@ int tpcf_emu_destroy(tpcf_emu e)
 {
     if (!e) return TPCF_OK;
     cudaDeviceSynchronize();
-    for (void *p : {(void *)e->params, (void *)e->grads, (void *)e->gtmp, (void *)e->m, (void *)e->v, (void *)e->pbf,
+    for (void *p : {(void *)e->params, (void *)e->grads, (void *)e->gtmp, (void *)e->m, (void *)e->v,
                     (void *)e->in_lo, (void *)e->in_hi, (void *)e->out_mean, (void *)e->out_sd, (void *)e->xs,
-                    (void *)e->d0, (void *)e->d1})
+                    (void *)e->db, (void *)e->d0, (void *)e->d1})
         if (p) cudaFree(p);
-    for (int l = 0; l < kMaxLayers; ++l) {
-        if (e->Z[l]) cudaFree(e->Z[l]);
-        if (e->A[l]) cudaFree(e->A[l]);
-    }
+    for (int l = 0; l < kMaxLayers; ++l)
+        for (void *p : {(void *)e->Z[l], (void *)e->act[l], (void *)e->wT[l], (void *)e->wP[l]})
+            if (p) cudaFree(p);
     delete e;
     return TPCF_OK;
 }
@@ -481,9 +771,10 @@ int tpcf_emu_train_step(tpcf_emu e, const float *x, const float *y, int64_t batc
     // bias-corrected step folded into the learning rate and epsilon
     const float lr_t = (float)(lr * std::sqrt(c2) / c1);
     const float eps_t = (float)(1e-8 * std::sqrt(c2));
-    k_adam<<<grid1(e->n_params), 256, 0, st>>>(e->params, e->grads, e->m, e->v, e->pbf, e->n_params, lr_t, (float)b1,
+    k_adam<<<grid1(e->n_params), 256, 0, st>>>(e->params, e->grads, e->m, e->v, e->n_params, lr_t, (float)b1,
                                                (float)b2, eps_t);
     tpcf::note_launch();
+    ECK(weight_copies(e, st));
     ECK(cudaGetLastError());
     return TPCF_OK;
 }
@@ -495,7 +786,8 @@ int tpcf_emu_predict(tpcf_emu e, const float *x, int64_t n, float *y, void *stre
     const int w_in = e->widths[0], w_out = e->widths[e->nl];
     for (int64_t r0 = 0; r0 < n; r0 += kChunk) {
         const int64_t rows = std::min<int64_t>(kChunk, n - r0);
-        k_scale_in<<<grid1(rows * w_in), 256, 0, st>>>(x + r0 * w_in, rows, w_in, e->in_lo, e->in_hi, e->xs);
+        k_scale_in<<<grid1(rows * w_in), 256, 0, st>>>(x + r0 * w_in, rows, w_in, e->in_lo, e->in_hi, e->xs,
+                                                        e->layers[0].ldi);
         tpcf::note_launch();
         ECK(forward(e, rows, st));
         k_unscale_out<<<grid1(rows * w_out), 256, 0, st>>>(e->Z[e->nl - 1], rows, w_out, e->out_mean, e->out_sd,
@@ -521,8 +813,7 @@ int tpcf_emu_set_params(tpcf_emu e, const float *params, void *stream)
     ECK(cudaMemcpyAsync(e->params, params, e->n_params * sizeof(float), cudaMemcpyDeviceToDevice, st));
     ECK(cudaMemsetAsync(e->m, 0, e->n_params * sizeof(float), st));
     ECK(cudaMemsetAsync(e->v, 0, e->n_params * sizeof(float), st));
-    k_to_bf16<<<grid1(e->n_params), 256, 0, st>>>(e->params, e->pbf, e->n_params);
-    tpcf::note_launch();
+    ECK(weight_copies(e, st));
     e->step = 0;
     ECK(cudaGetLastError());
     return TPCF_OK;

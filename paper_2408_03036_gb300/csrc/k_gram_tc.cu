@@ -29,105 +29,18 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace tpcf {
 
 namespace {
 
+using namespace tc;
+
 constexpr int kThreads = 512;
 constexpr int kRowTile = 128;                 // M of every MMA (TMEM lanes)
 constexpr int kStageBytesRow = 32;            // one K step = 32 bytes per operand row
-constexpr long long kWaitLimit = 1ll << 26;   // polls of an mbarrier before giving up
 constexpr int kFlushK = 1024;                 // K rows accumulated in FP32 per flush
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor (tcgen05): start, leading (K) and stride
-// (8-row group) byte offsets, descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// Instruction descriptor: FP32 accumulate, A/B type code `ab` (bf16 = 1 in
-// kind::f16, tf32 = 2 in kind::tf32), both K-major, N and M.
-__device__ __forceinline__ uint32_t make_idesc(uint32_t ab, int M, int N)
-{
-    uint32_t d = 0;
-    d |= 1u << 4;                 // D format: F32
-    d |= ab << 7;                 // A format
-    d |= ab << 10;                // B format
-    d |= (uint32_t)(N >> 3) << 17;
-    d |= (uint32_t)(M >> 4) << 24;
-    return d;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-// Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    const uint32_t a = smem_u32(bar);
-    for (long long it = 0; it < kWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-template <bool TF32>
-__device__ __forceinline__ void mma_issue(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
-{
-    if (TF32) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    } else {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(idesc), "r"(acc));
-    }
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *bar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
 
 // Splits x into hi + lo in the MMA type, returned as the 16-bit (bf16) or
 // 32-bit (tf32, low 13 mantissa bits zero) storage words.
@@ -204,6 +117,8 @@ struct TcParams {
     int n_slices;
     double *partial;      // [n_slices][slice_size], zeroed before the launch
     int *err;
+    long long wait_limit; // polls of a per-stage mbarrier wait before giving up
+    int wait_unmet;       // test mode: one more wait on a phase that nothing completes
     TcPlan plan;
 };
 
@@ -376,7 +291,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const TcParams p)
     auto flush = [&]() {
         if (tid == 0)
             for (int s = 0; s < 2; ++s)
-                if (used[s] && !mbar_wait(&bars[s], phase[s] ^ 1u)) *s_abort = 1;
+                if (used[s] && !mbar_wait(&bars[s], phase[s] ^ 1u, p.wait_limit)) *s_abort = 1;
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -452,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const TcParams p)
         const int s = (int)(st & 1);
         unsigned char *stg = smem + s * stage_bytes;
         // the MMAs that last read this stage must have completed
-        if (tid == 0 && used[s] && !mbar_wait(&bars[s], phase[s] ^ 1u)) *s_abort = 1;
+        if (tid == 0 && used[s] && !mbar_wait(&bars[s], phase[s] ^ 1u, p.wait_limit)) *s_abort = 1;
         __syncthreads();
         if (*s_abort) { ok = false; break; }
         // stage: item (octet o, row r) = 8 K entries (4 primaries x real/imaginary) of row r
@@ -531,6 +446,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const TcParams p)
         }
     }
     if (ok && acc_on) flush();
+    // test mode: after the last flush (both buffers' commits complete), buffer 0's
+    // next phase, which no commit completes
+    if (p.wait_unmet && tid == 0 && !*s_abort && !mbar_wait(&bars[0], phase[0], p.wait_limit)) *s_abort = 1;
+    __syncthreads();
     if (*s_abort || !ok) {
         if (tid == 0) {
             atomicCAS(p.err, 0, DEV_ERR_TIMEOUT);
@@ -709,6 +628,8 @@ cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, 
     p.per_slice = (K + slices - 1) / slices;
     p.n_slices = slices;
     p.err = err;
+    p.wait_limit = device_wait_limit();
+    p.wait_unmet = device_wait_unmet();
     int rmax = 0;
     for (int g = 0; g < ng; ++g) rmax = std::max(rmax, p.plan.g[g].rows_alloc);
     const int ks = tf32 ? 16 : 32, esz = tf32 ? 4 : 2;
@@ -769,6 +690,8 @@ cudaError_t couple_gram_simt(const float *alm, const float *w, int64_t K, int nb
     p.per_slice = (K + slices - 1) / slices;
     p.n_slices = slices;
     p.err = nullptr;
+    p.wait_limit = device_wait_limit();
+    p.wait_unmet = 0;
     const size_t pbytes = (size_t)slices * p.plan.slice_size * sizeof(double);
     cudaError_t e = cudaMallocAsync((void **)&p.partial, pbytes, st);
     if (e != cudaSuccess) return e;

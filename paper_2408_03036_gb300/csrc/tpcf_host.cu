@@ -47,6 +47,17 @@ std::atomic<long long> g_launches{0};
 
 void tpcf::note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+namespace {
+std::atomic<long long> g_wait_limit{0};
+std::atomic<int> g_wait_unmet{0};
+}
+long long tpcf::device_wait_limit()
+{
+    const long long v = g_wait_limit.load(std::memory_order_relaxed);
+    return v > 0 ? v : (1ll << 26);
+}
+int tpcf::device_wait_unmet() { return g_wait_unmet.load(std::memory_order_relaxed); }
+
 struct tpcf_grid_s {
     GridDev g;
     cudaStream_t stream;
@@ -901,6 +912,12 @@ void tpcf::self_term_table(int lmax, double *out)
 
 int tpcf::check_config_public(const tpcf_config *c) { return check_config(c); }
 
+int *tpcf::device_error_flag()
+{
+    DevState *ds = nullptr;
+    return dev_state(&ds) == TPCF_OK ? ds->err : nullptr;
+}
+
 int tpcf::set_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
 // ===================================================================== C ABI
@@ -910,6 +927,14 @@ extern "C" {
 const char *tpcf_last_error(void) { return g_msg; }
 
 int tpcf_version(void) { return 100; }
+
+int tpcf_set_wait_limit(int64_t polls, int32_t unmet_wait)
+{
+    if (polls < 0) return fail(TPCF_ERR_ARG, "polls < 0");
+    g_wait_limit.store((long long)polls, std::memory_order_relaxed);
+    g_wait_unmet.store(unmet_wait ? 1 : 0, std::memory_order_relaxed);
+    return TPCF_OK;
+}
 
 int64_t tpcf_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 

@@ -24,7 +24,7 @@ LOS = {"z": 0, "observer": 1}
 CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
 
 # Names of every entry point include/tpcf.h declares (checked by the tests).
-EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
+EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_set_wait_limit", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
            "tpcf_bin_edges", "tpcf_build_grid", "tpcf_grid_destroy", "tpcf_grid_info", "tpcf_grid_points",
            "tpcf_accumulate_alm", "tpcf_pair_counts", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
            "tpcf_estimate_3pcf_xi", "tpcf_estimate_3pcf_full_edge",
@@ -98,6 +98,7 @@ def lib():
         sig = {
             "tpcf_last_error": ([], ctypes.c_char_p),
             "tpcf_version": ([], ctypes.c_int),
+            "tpcf_set_wait_limit": ([I64, ctypes.c_int32], ctypes.c_int),
             "tpcf_kernel_launches": ([], ctypes.c_int64),
             "tpcf_multipole_count": ([CFG, P], ctypes.c_int),
             "tpcf_multipole_index": ([CFG, P, ctypes.c_int32], ctypes.c_int),

@@ -26,6 +26,18 @@ def gpu():
     return torch
 
 
+_MODEL = None
+
+
+def _set_model(m):
+    global _MODEL
+    _MODEL = m
+
+
+def _evaluate(th):
+    return _MODEL(th)
+
+
 @pytest.fixture(scope="module")
 def plain_model():
     """The plain model's templates on the (alpha, eps) grid, built in a process
@@ -36,6 +48,14 @@ def plain_model():
     ep = np.linspace(-0.065, 0.065, 7)
     with mp.get_context("spawn").Pool(min(16, mp.cpu_count())) as pool:
         return T.TemplateModel.build(setup, al, ep, pool=pool)
+
+
+def evaluate_parallel(model, th):
+    """The plain model at every row of th, in a spawn process pool (host cores)."""
+    n = min(16, mp.cpu_count())
+    chunks = np.array_split(th, n)
+    with mp.get_context("spawn").Pool(n, initializer=_set_model, initargs=(model,)) as pool:
+        return np.concatenate(pool.map(_evaluate, chunks))
 
 
 def rand_net(torch, widths, seed):
@@ -89,7 +109,11 @@ def test_predictions_match_fp64_reference(gpu):
     ref = MO.predict(p, widths, x, BOX_LO.astype(np.float64), BOX_HI.astype(np.float64), mu.astype(np.float64),
                      sd.astype(np.float64))
     tpcf.stream_status()
-    assert np.abs(out - ref).max() <= 1e-4 * np.abs(ref).max()
+    # the products take bf16 operands on both sides; an FP32 activation within an
+    # ulp of a bf16 rounding boundary can round the other way on the device (its
+    # SiLU is FP32) than in the FP64 reference: one bf16 ulp (2^-8) on that
+    # element, which moves the outputs by a few 1e-4 of their largest value
+    assert np.abs(out - ref).max() <= 5e-4 * np.abs(ref).max()
     emu.close()
 
 
@@ -102,20 +126,22 @@ def per_multipole_error(pred, ref, n_mult):
 
 def test_trained_emulator_reproduces_the_plain_model(gpu, plain_model):
     """Trained on Latin-hypercube samples of the plain model with the project's
-    own kernels; on held-out parameters its multipoles stay within 1 % of the
-    plain model's, and it evaluates far faster than the plain model."""
+    own tensor-core kernels; on held-out parameters the per-sample, per-multipole
+    error max|zeta_emu - zeta_model| / max|zeta_model| has its median and its
+    95th percentile within 1 %, and the network evaluates far faster than the
+    plain model."""
     from oracle import treelevel as T
     torch = gpu
-    n_train, n_test = 40000, 1000
+    n_train, n_test = 200000, 2000    # the emulator configuration's 200k Latin-hypercube samples
     th = T.latin_hypercube(n_train + n_test, 7).astype(np.float32)
-    z = plain_model(th).astype(np.float32)
+    z = evaluate_parallel(plain_model, th).astype(np.float32)
     xtr, ytr = torch.from_numpy(th[:n_train]).cuda(), torch.from_numpy(z[:n_train]).cuda()
     widths = [6, 256, 256, 256, 256, z.shape[1]]
     emu = tpcf.Emulator(widths, seed=11)
     emu.set_input_box(BOX_LO, BOX_HI)
     emu.fit_output_scaling(ytr)
     g = torch.Generator(device="cuda").manual_seed(5)
-    steps, bs = 6000, 512
+    steps, bs = 20000, 512
     for s in range(steps):
         idx = torch.randint(0, n_train, (bs,), device="cuda", generator=g)
         lr = 2e-3 * 0.5 * (1 + np.cos(np.pi * s / steps)) + 1e-5
@@ -123,7 +149,10 @@ def test_trained_emulator_reproduces_the_plain_model(gpu, plain_model):
     pred = emu.predict(torch.from_numpy(th[n_train:]).cuda()).cpu().numpy()
     tpcf.stream_status()
     err = per_multipole_error(pred, z[n_train:], len(T.MULTIPOLES))
+    print("emulator error: median %.3g %%, 95th percentile %.3g %%, max %.3g %%"
+          % (100 * np.median(err), 100 * np.percentile(err, 95), 100 * err.max()))
     assert np.median(err) <= 0.01, np.median(err)
+    assert np.percentile(err, 95) <= 0.01, np.percentile(err, 95)
     # what the network gains: evaluations per second against the plain model
     setup = plain_model.setup
     t0 = time.perf_counter()
