@@ -207,17 +207,23 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
+    from paper_2408_03036_gb300 import shard
     dev = torch.device("cuda", local)
     cfg = config(args.precision)
-    d, dw, r, rw = make_inputs(rank)
+    # one catalogue; with several ranks each takes the primaries of its z slab
+    # (secondaries within r_max of it) and the partials are summed over the group
+    d, dw, r, rw = make_inputs()
     dx = torch.from_numpy(d.view(np.int32)).to(dev)
     dwt = torch.from_numpy(dw).to(dev)
     rx = torch.from_numpy(r.view(np.int32)).to(dev)
     rwt = torch.from_numpy(rw).to(dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    share = shard.ShardInputs(cfg, d, dw, r, rw, rank, ws, dev) if ws > 1 else None
 
     def step():
+        if share is not None:
+            return shard.estimate_prepared(cfg, share, stream=stream)
         return tpcf.estimate_3pcf(cfg, dx, dwt, rx, rwt, stream=stream, device=dev)
 
     for _ in range(args.warmup):
@@ -248,15 +254,20 @@ def run_ours(args):
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    prim_per_step = ND + NR
-    value = ws * prim_per_step * args.steps / (ms_max / 1000.0)
+    prim_per_step = ND + NR   # the whole catalogue, shared out over the ranks
+    value = prim_per_step * args.steps / (ms_max / 1000.0)
 
     # the plain FP32 form of the same step (FP32 Gram coupling), timed the same way
     plain = None
     if args.precision != "fp32":
         pcfg = config("fp32")
+        def pstep():
+            if share is not None:
+                return shard.estimate_prepared(pcfg, share, stream=stream)
+            return tpcf.estimate_3pcf(pcfg, dx, dwt, rx, rwt, stream=stream, device=dev)
+
         for _ in range(max(1, args.warmup // 2)):
-            pres = tpcf.estimate_3pcf(pcfg, dx, dwt, rx, rwt, stream=stream, device=dev)
+            pres = pstep()
         torch.cuda.synchronize(dev)
         # the mixed step's multipoles against the plain step's, per multipole
         zm, zp = res.zeta.cpu().numpy(), pres.zeta.cpu().numpy()
@@ -267,12 +278,16 @@ def run_ours(args):
             flush.zero_()
             s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s0.record(stream)
-            tpcf.estimate_3pcf(pcfg, dx, dwt, rx, rwt, stream=stream, device=dev)
+            pstep()
             e0.record(stream)
             torch.cuda.synchronize(dev)
             pms += s0.elapsed_time(e0)
         tpcf.stream_status(stream)
-        pvalue = ws * prim_per_step * args.steps / (pms / 1000.0)
+        if dist:
+            tp = torch.tensor([pms], dtype=torch.float64, device=dev)
+            dist.all_reduce(tp, op=dist.ReduceOp.MAX)
+            pms = float(tp.item())
+        pvalue = prim_per_step * args.steps / (pms / 1000.0)
         plain = {"value": pvalue, "unit": UNIT, "ms_per_step": pms / args.steps, "mixed_over_plain": value / pvalue,
                  "mixed_vs_plain_max_rel_err": mixed_err}
 
@@ -284,7 +299,7 @@ def run_ours(args):
                                                              ms_max / args.steps)
 
     # end to end through the host-buffer entry point (copies inside the timed region)
-    e2e = end_to_end(cfg, d, dw, r, rw, args, stream, tpcf)
+    e2e = end_to_end(cfg, d, dw, r, rw, args, stream, tpcf, ws, rank)
 
     del dx, dwt, rx, rwt
     torch.cuda.empty_cache()   # the batch sizes its groups from the free device memory
@@ -294,9 +309,10 @@ def run_ours(args):
         return 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else "f32/" + args.precision, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": args.precision, "parallelism": "replicas",
+            "config": {"workload": WORKLOAD, "precision": args.precision,
+                       "parallelism": "z-slab shards, FP64 partials summed (NCCL)" if ws > 1 else "one GPU",
                        "primaries_per_step": prim_per_step, "pairs_per_step": pairs_per_step,
                        "l2": "flushed between timed steps (256 MB write, outside the events)"},
             "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof, "e2e": e2e}
@@ -647,24 +663,44 @@ def roofline(cfg, d, dw, r, rw, dev, stream, tpcf, reps=3):
             "coupling": coupling}
 
 
-def end_to_end(cfg, d, dw, r, rw, args, stream, tpcf):
+def end_to_end(cfg, d, dw, r, rw, args, stream, tpcf, ws=1, rank=0):
+    """The same metric through the public entry point from host buffers: the
+    host-buffer estimate on one GPU; with several ranks the sharded estimate
+    (partition, copies of the rank's share, partials, the sum over the group and
+    the finished multipoles back on the host), timed as the slowest rank."""
     import numpy as np
     import torch
+    from paper_2408_03036_gb300 import shard
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
     hd, hdw, hr, hrw = pin(d), pin(dw), pin(r), pin(rw)
     steps = max(1, min(args.steps, 3))
-    tpcf.estimate_3pcf_host(cfg, hd, hdw, hr, hrw, stream=stream)   # warm
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def call():
+        if ws > 1:
+            res = shard.estimate_3pcf_sharded(cfg, hd, hdw, hr, hrw, rank, ws, device=dev, stream=stream)
+            out = [res.zeta.cpu(), res.nnn.cpu(), res.rrr.cpu(), res.pair_counts.cpu(), res.triplet_counts.cpu()]
+            return out, sum(t.numel() * t.element_size() for t in out)
+        res = tpcf.estimate_3pcf_host(cfg, hd, hdw, hr, hrw, stream=stream)
+        return res, res.zeta.nbytes + res.nnn.nbytes + res.rrr.nbytes + res.pair_counts.nbytes + \
+            res.triplet_counts.nbytes
+
+    call()   # warm
     s = torch.cuda.Event(enable_timing=True)
     e = torch.cuda.Event(enable_timing=True)
     tot = 0.0
     for _ in range(steps):
         s.record(stream)
-        res = tpcf.estimate_3pcf_host(cfg, hd, hdw, hr, hrw, stream=stream)
+        _, bo = call()
         e.record(stream)
         torch.cuda.synchronize()
         tot += s.elapsed_time(e)
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([tot], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot = float(t.item())
     bi = hd.nbytes + hdw.nbytes + hr.nbytes + hrw.nbytes
-    bo = res.zeta.nbytes + res.nnn.nbytes + res.rrr.nbytes + res.pair_counts.nbytes + res.triplet_counts.nbytes
     return {"value": (ND + NR) * steps / (tot / 1000.0), "unit": UNIT, "h2d_bytes_per_step": int(bi),
             "d2h_bytes_per_step": int(bo), "steps": steps}
 

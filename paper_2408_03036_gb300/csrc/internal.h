@@ -121,8 +121,9 @@ cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t 
 cudaError_t count_not_one(const float *w, int64_t n, int *out, cudaStream_t st);
 cudaError_t weight_sums_mocks(const float *w, const int64_t *d_offsets, int n_mocks, double *out, cudaStream_t st);
 
+// records of n points; wsums = {W_D, W_R} (device) turns the weights into -(W_D / W_R) w
 cudaError_t pack_records(const uint32_t *xyz, const float *w, int64_t n, int4 *out, int *err,
-                         cudaStream_t st);
+                         cudaStream_t st, const double *wsums = nullptr);
 cudaError_t weight_sums(const float *w1, int64_t n1, const float *w2, int64_t n2, double *out2,
                         cudaStream_t st);
 

@@ -135,12 +135,15 @@ __global__ void k_sort_cells(const int32_t *__restrict__ start, int64_t ncell, i
     }
 }
 
+// records (x, y, z, w) of n points; with wsums = {W_D, W_R} the weights become
+// -(W_D / W_R) w, the random part of the data-minus-random field (as in the grid)
 __global__ void k_pack(const uint32_t *__restrict__ xyz, const float *__restrict__ w, int64_t n,
-                       int4 *__restrict__ out, int *err)
+                       const double *__restrict__ wsums, int4 *__restrict__ out, int *err)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        const float wt = w ? w[i] : 1.0f;
+        float wt = w ? w[i] : 1.0f;
+        if (wsums) wt = (float)(-(wsums[0] / wsums[1]) * (double)wt);
         if (!(wt == wt) || isinf(wt)) atomicCAS(err, 0, DEV_ERR_DATA);
         out[i] = make_int4((int)xyz[3 * i], (int)xyz[3 * i + 1], (int)xyz[3 * i + 2], __float_as_int(wt));
     }
@@ -387,10 +390,11 @@ void free_grid_dev(GridDev &g, cudaStream_t st)
     g.cell_start = nullptr;
 }
 
-cudaError_t pack_records(const uint32_t *xyz, const float *w, int64_t n, int4 *out, int *err, cudaStream_t st)
+cudaError_t pack_records(const uint32_t *xyz, const float *w, int64_t n, int4 *out, int *err, cudaStream_t st,
+                         const double *wsums)
 {
     if (n > 0) {
-        k_pack<<<grid_blocks(n, 256), 256, 0, st>>>(xyz, w, n, out, err);
+        k_pack<<<grid_blocks(n, 256), 256, 0, st>>>(xyz, w, n, wsums, out, err);
         note_launch();
     }
     return cudaGetLastError();

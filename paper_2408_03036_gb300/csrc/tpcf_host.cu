@@ -894,6 +894,206 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
     return TPCF_OK;
 }
 
+// ----------------------------------------------------------- sharded form
+// Sizes of the additive partial results of one shard (doubles, int64 counts).
+// doubles: nnn [L1^3 nb^2], S [n_ell nb] (2PCF sums), R00 [nb^2] and s0 [nb] (the
+// randoms' l = 0 coupling and 2PCF sums, weighted randoms);
+// int64: pair counts [nb], triplet counts [nb^2], random triplet counts [nb^2],
+// random pair counts [nb].
+struct PartLayout {
+    int64_t nnn, S, R00, s0, nf;
+    int64_t pairs, T, TR, pairs_r, ni;
+};
+
+PartLayout part_layout(const tpcf_config *c)
+{
+    PartLayout P;
+    const int64_t nb = c->n_bins, L1 = c->l_max + 1, n_ell = c->l_max / 2 + 1;
+    P.nnn = 0;
+    P.S = P.nnn + L1 * L1 * L1 * nb * nb;
+    P.R00 = P.S + n_ell * nb;
+    P.s0 = P.R00 + nb * nb;
+    P.nf = P.s0 + nb;
+    P.pairs = 0;
+    P.T = P.pairs + nb;
+    P.TR = P.T + nb * nb;
+    P.pairs_r = P.TR + nb * nb;
+    P.ni = P.pairs_r + nb;
+    return P;
+}
+
+// One shard's additive partials: primaries dp (data, weights as given) and rp
+// (randoms, weights -(W_D / W_R) w in the D - R field) against the secondaries
+// d, r given (every point within r_max of a primary), with the weight totals of
+// the whole catalogue.  Periodic analytic randoms when nr = nrp = 0.
+int partial_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd, const uint32_t *r_xyz,
+                 const float *r_w, int64_t nr, const uint32_t *dp_xyz, const float *dp_w, int64_t ndp,
+                 const uint32_t *rp_xyz, const float *rp_w, int64_t nrp, double w_d, double w_r, int weighted_r,
+                 double *part_f, int64_t *part_i, cudaStream_t st)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!part_f || !part_i) return fail(TPCF_ERR_ARG, "the partial outputs are required");
+    const bool analytic = (nr == 0 && nrp == 0);
+    if (analytic && !cfg->periodic) return fail(TPCF_ERR_ARG, "analytic randoms need a periodic box");
+    if (nd < 0 || nr < 0 || ndp < 0 || nrp < 0) return fail(TPCF_ERR_ARG, "negative point count");
+    if ((nd > 0 && !d_xyz) || (nr > 0 && !r_xyz) || (ndp > 0 && !dp_xyz) || (nrp > 0 && !rp_xyz))
+        return fail(TPCF_ERR_ARG, "coordinates are required for every non-empty set");
+    if (!(w_d > 0.0) || (!analytic && !(w_r != 0.0)))
+        return fail(TPCF_ERR_ARG, "the catalogue's weight totals are required");
+    if (nd + nr >= kMaxPoints) return fail(TPCF_ERR_ARG, "catalogue too large (nd + nr < 2^28)");
+    DevState *ds;
+    if ((rc = dev_state(&ds))) return rc;
+    const PartLayout PL = part_layout(cfg);
+    CK(cudaMemsetAsync(part_f, 0, PL.nf * sizeof(double), st));
+    CK(cudaMemsetAsync(part_i, 0, PL.ni * sizeof(int64_t), st));
+    const int nb = cfg->n_bins, L = cfg->l_max;
+    const int nlm = (L + 1) * (L + 1), ndiag = (L + 1) * (L + 2) / 2, L1 = L + 1, n_ell = L / 2 + 1;
+    GridDev gf, gr;
+    Scratch sc(st);
+    sc.own(gf);
+    sc.own(gr);
+    double *wsums = nullptr;
+    if ((rc = sc.alloc(&wsums, 2, false))) return rc;
+    const double hw[2] = {w_d, w_r};
+    CK(cudaMemcpyAsync(wsums, hw, sizeof(hw), cudaMemcpyHostToDevice, st));
+    const int64_t K = ndp + nrp;
+    if (nd + nr > 0 && K > 0) {
+        CK(build_grid_dev(d_xyz, d_w, nd, r_xyz, r_w, nr, analytic ? nullptr : wsums, choose_nc(cfg, nd + nr), gf,
+                          ds->err, st));
+        int4 *prim = nullptr;
+        float *alm = nullptr, *wprim = nullptr;
+        int32_t *cnt = nullptr;
+        double *diag = nullptr, *wsp = nullptr;
+        unsigned long long *pairs = nullptr, *T = nullptr;
+        if ((rc = sc.alloc(&prim, (size_t)K, false))) return rc;
+        CK(pack_records(dp_xyz, dp_w, ndp, prim, ds->err, st));
+        CK(pack_records(rp_xyz, rp_w, nrp, prim + ndp, ds->err, st, wsums));
+        if ((rc = sc.alloc(&alm, (size_t)K * nb * nlm, false))) return rc;
+        if ((rc = sc.alloc(&cnt, (size_t)K * nb, false))) return rc;
+        if ((rc = sc.alloc(&diag, (size_t)ndiag * nb, true))) return rc;
+        if ((rc = sc.alloc(&wsp, (size_t)L1 * nb, true))) return rc;
+        if ((rc = sc.alloc(&pairs, (size_t)nb, true))) return rc;
+        if ((rc = sc.alloc(&T, (size_t)nb * nb, true))) return rc;
+        if ((rc = sc.alloc(&wprim, (size_t)K, false))) return rc;
+        rc = run_pairs(cfg, gf, prim, K, false, 0.0, analytic ? wsums : nullptr, analytic, alm, cnt, diag, wsp,
+                       pairs, st);
+        if (rc) return rc;
+        CK(cudaMemcpy2DAsync(wprim, 4, (const char *)prim + 12, 16, 4, K, cudaMemcpyDeviceToDevice, st));
+        if ((rc = couple(cfg, alm, wprim, cnt, K, diag, wsp, part_f + PL.nnn, T, st))) return rc;
+        CK(m0_sums(alm, wprim, K, nb, L, n_ell, 2, part_f + PL.S, st));
+        CK(i64_from_u64(pairs, part_i + PL.pairs, nb, st));
+        CK(i64_from_u64(T, part_i + PL.T, nb * nb, st));
+    }
+    if (!analytic && nr > 0 && nrp > 0) {
+        if (!weighted_r) {
+            // integer random triplet counts of the shard's random primaries
+            int4 *rprim = nullptr;
+            int32_t *cnt_r = nullptr;
+            unsigned long long *TR = nullptr, *pairs_r = nullptr;
+            CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
+            if ((rc = sc.alloc(&rprim, (size_t)nrp, false))) return rc;
+            CK(pack_records(rp_xyz, rp_w, nrp, rprim, ds->err, st));
+            if ((rc = sc.alloc(&cnt_r, (size_t)nrp * nb, false))) return rc;
+            if ((rc = sc.alloc(&TR, (size_t)nb * nb, true))) return rc;
+            if ((rc = sc.alloc(&pairs_r, (size_t)nb, true))) return rc;
+            rc = run_pairs(cfg, gr, rprim, nrp, true, 0.0, nullptr, false, nullptr, cnt_r, nullptr, nullptr, pairs_r,
+                           st);
+            if (rc) return rc;
+            CK(tpcf::triplet_counts(cnt_r, nrp, nb, TR, st));
+            CK(i64_from_u64(TR, part_i + PL.TR, nb * nb, st));
+            CK(i64_from_u64(pairs_r, part_i + PL.pairs_r, nb, st));
+        } else {
+            // the randoms' own l = 0 coupling with their weights (alpha^3 applied at the end)
+            tpcf_config cr = *cfg;
+            cr.l_max = 0;
+            cr.n_L = 1;
+            cr.L[0] = 0;
+            int4 *rprim = nullptr;
+            float *alm_r = nullptr, *wprim_r = nullptr;
+            int32_t *cnt_r = nullptr;
+            double *diag_r = nullptr, *wsp_r = nullptr, *nnn_r = nullptr;
+            CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
+            if ((rc = sc.alloc(&rprim, (size_t)nrp, false))) return rc;
+            CK(pack_records(rp_xyz, rp_w, nrp, rprim, ds->err, st));
+            if ((rc = sc.alloc(&alm_r, (size_t)nrp * nb, false))) return rc;
+            if ((rc = sc.alloc(&cnt_r, (size_t)nrp * nb, false))) return rc;
+            if ((rc = sc.alloc(&diag_r, (size_t)nb, true))) return rc;
+            if ((rc = sc.alloc(&wsp_r, (size_t)nb, true))) return rc;
+            if ((rc = sc.alloc(&nnn_r, (size_t)nb * nb, false))) return rc;
+            if ((rc = sc.alloc(&wprim_r, (size_t)nrp, false))) return rc;
+            rc = run_pairs(&cr, gr, rprim, nrp, false, 0.0, nullptr, false, alm_r, cnt_r, diag_r, wsp_r, nullptr, st);
+            if (rc) return rc;
+            CK(cudaMemcpy2DAsync(wprim_r, 4, (const char *)rprim + 12, 16, 4, nrp, cudaMemcpyDeviceToDevice, st));
+            if ((rc = couple(&cr, alm_r, wprim_r, nullptr, nrp, diag_r, wsp_r, nnn_r, nullptr, st))) return rc;
+            CK(cudaMemcpyAsync(part_f + PL.R00, nnn_r, (size_t)nb * nb * sizeof(double), cudaMemcpyDeviceToDevice,
+                               st));
+            CK(m0_sums(alm_r, wprim_r, nrp, nb, 0, 1, 2, part_f + PL.s0, st));
+        }
+    }
+    CK(cudaStreamSynchronize(st));   // the host copy of the totals outlives the upload
+    CK(cudaGetLastError());
+    return TPCF_OK;
+}
+
+// zeta (and NNN, RRR, counts, xi) from the summed partials of every shard.
+int finish_impl(const tpcf_config *cfg, double w_d, double w_r, int explicit_randoms, int weighted_r,
+                const double *part_f, const int64_t *part_i, double *zeta, double *nnn_out, double *rrr_out,
+                int64_t *pair_counts, int64_t *triplet_counts, double *xi, cudaStream_t st)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!part_f || !part_i || !zeta) return fail(TPCF_ERR_ARG, "partials and zeta are required");
+    const bool analytic = !explicit_randoms;
+    if (analytic && !cfg->periodic) return fail(TPCF_ERR_ARG, "analytic randoms need a periodic box");
+    if (!(w_d > 0.0) || (!analytic && !(w_r != 0.0)))
+        return fail(TPCF_ERR_ARG, "the catalogue's weight totals are required");
+    const PartLayout PL = part_layout(cfg);
+    const int nb = cfg->n_bins, L = cfg->l_max, L1 = L + 1, n_ell = L / 2 + 1;
+    Scratch sc(st);
+    double *wsums = nullptr, *rrr = rrr_out, *mono = nullptr, *r00 = nullptr, *rr = nullptr;
+    unsigned long long *TRu = nullptr, *pr = nullptr;
+    if ((rc = sc.alloc(&wsums, 2, false))) return rc;
+    const double hw[2] = {w_d, w_r};
+    CK(cudaMemcpyAsync(wsums, hw, sizeof(hw), cudaMemcpyHostToDevice, st));
+    if (!rrr && (rc = sc.alloc(&rrr, (size_t)nb * nb, false))) return rc;
+    int rr_mode = 0;
+    if (analytic) {
+        rc = mono_coef_dev(cfg, &mono, st);
+        sc.keep(mono);
+        if (rc) return rc;
+        CK(rrr_analytic(wsums, mono, nb, rrr, st));
+    } else if (!weighted_r) {
+        if ((rc = sc.alloc(&TRu, (size_t)nb * nb, false))) return rc;
+        if ((rc = sc.alloc(&pr, (size_t)nb, false))) return rc;
+        CK(cudaMemcpyAsync(TRu, part_i + PL.TR, (size_t)nb * nb * 8, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(pr, part_i + PL.pairs_r, (size_t)nb * 8, cudaMemcpyDeviceToDevice, st));
+        CK(rrr_from_counts(TRu, wsums, nb, rrr, st));
+        rr_mode = 1;
+    } else {
+        if ((rc = sc.alloc(&r00, (size_t)nb * nb, false))) return rc;
+        CK(cudaMemcpyAsync(r00, part_f + PL.R00, (size_t)nb * nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        CK(scale_alpha3(r00, (int64_t)nb * nb, wsums, st));
+        CK(cudaMemcpyAsync(rrr, r00, (size_t)nb * nb * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        rr_mode = 2;
+    }
+    if (nnn_out)
+        CK(cudaMemcpyAsync(nnn_out, part_f + PL.nnn, (size_t)L1 * L1 * L1 * nb * nb * sizeof(double),
+                           cudaMemcpyDeviceToDevice, st));
+    if ((rc = project(cfg, part_f + PL.nnn, rrr, zeta, st))) return rc;
+    if (xi) {
+        if ((rc = sc.alloc(&rr, (size_t)nb, false))) return rc;
+        CK(xi_from_sums(rr_mode, wsums, mono, pr, part_f + PL.s0, part_f + PL.S, n_ell, 2, nb, rr, xi, st));
+    }
+    if (pair_counts)
+        CK(cudaMemcpyAsync(pair_counts, part_i + PL.pairs, (size_t)nb * 8, cudaMemcpyDeviceToDevice, st));
+    if (triplet_counts)
+        CK(cudaMemcpyAsync(triplet_counts, part_i + PL.T, (size_t)nb * nb * 8, cudaMemcpyDeviceToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    return TPCF_OK;
+}
+
 }  // namespace
 
 void tpcf::self_term_table(int lmax, double *out)
@@ -1130,6 +1330,36 @@ int tpcf_estimate_3pcf_full_edge(const tpcf_config *cfg, const uint32_t *d_xyz, 
     if (nr < 1 || !r_xyz) return fail(TPCF_ERR_ARG, "the full edge correction needs explicit randoms");
     return estimate_impl(cfg, d_xyz, d_w, nd, r_xyz, r_w, nr, zeta, nnn, nullptr, nullptr, nullptr, xi, true,
                          rrr_multipoles, (cudaStream_t)stream);
+}
+
+int tpcf_partial_sizes(const tpcf_config *cfg, int64_t *n_double, int64_t *n_int64)
+{
+    int rc = check_config(cfg);
+    if (rc) return rc;
+    if (!n_double || !n_int64) return fail(TPCF_ERR_ARG, "outputs are required");
+    const PartLayout PL = part_layout(cfg);
+    *n_double = PL.nf;
+    *n_int64 = PL.ni;
+    return TPCF_OK;
+}
+
+int tpcf_estimate_3pcf_partial(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                               const uint32_t *r_xyz, const float *r_w, int64_t nr, const uint32_t *dp_xyz,
+                               const float *dp_w, int64_t ndp, const uint32_t *rp_xyz, const float *rp_w, int64_t nrp,
+                               double w_d_total, double w_r_total, int32_t weighted_randoms, double *part_f,
+                               int64_t *part_i, void *stream)
+{
+    return partial_impl(cfg, d_xyz, d_w, nd, r_xyz, r_w, nr, dp_xyz, dp_w, ndp, rp_xyz, rp_w, nrp, w_d_total,
+                        w_r_total, weighted_randoms, part_f, part_i, (cudaStream_t)stream);
+}
+
+int tpcf_estimate_3pcf_finish(const tpcf_config *cfg, double w_d_total, double w_r_total, int32_t explicit_randoms,
+                              int32_t weighted_randoms, const double *part_f, const int64_t *part_i, double *zeta,
+                              double *nnn, double *rrr, int64_t *pair_counts, int64_t *triplet_counts, double *xi,
+                              void *stream)
+{
+    return finish_impl(cfg, w_d_total, w_r_total, explicit_randoms, weighted_randoms, part_f, part_i, zeta, nnn, rrr,
+                       pair_counts, triplet_counts, xi, (cudaStream_t)stream);
 }
 
 int tpcf_estimate_3pcf_host(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,

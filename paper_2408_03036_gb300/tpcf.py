@@ -26,7 +26,8 @@ CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
 # Names of every entry point include/tpcf.h declares (checked by the tests).
 EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_set_wait_limit", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
            "tpcf_bin_edges", "tpcf_build_grid", "tpcf_grid_destroy", "tpcf_grid_info", "tpcf_grid_points",
-           "tpcf_accumulate_alm", "tpcf_pair_counts", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
+           "tpcf_accumulate_alm", "tpcf_pair_counts", "tpcf_partial_sizes", "tpcf_estimate_3pcf_partial",
+           "tpcf_estimate_3pcf_finish", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
            "tpcf_estimate_3pcf_xi", "tpcf_estimate_3pcf_full_edge",
            "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
@@ -109,6 +110,11 @@ def lib():
             "tpcf_grid_points": ([P, P, P, P, P], ctypes.c_int),
             "tpcf_accumulate_alm": ([P, P, P, I64, CFG, ctypes.c_double, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_pair_counts": ([P, P, I64, CFG, P, P, P], ctypes.c_int),
+            "tpcf_partial_sizes": ([CFG, P, P], ctypes.c_int),
+            "tpcf_estimate_3pcf_partial": ([CFG, P, P, I64, P, P, I64, P, P, I64, P, P, I64, ctypes.c_double,
+                                            ctypes.c_double, ctypes.c_int32, P, P, P], ctypes.c_int),
+            "tpcf_estimate_3pcf_finish": ([CFG, ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                           P, P, P, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_couple_multipoles": ([P, P, P, I64, CFG, P, P, P, P, P], ctypes.c_int),
             "tpcf_project": ([CFG, P, P, P, P], ctypes.c_int),
             "tpcf_estimate_3pcf": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
@@ -412,6 +418,57 @@ def pair_counts(grid: Grid, cfg: Config, prim_xyz=None, stream=None):
     c = cfg.c()
     _check(lib().tpcf_pair_counts(grid.handle, _ptr(px), n, ctypes.byref(c), _ptr(counts), _ptr(pc), _stream(stream)))
     return counts, pc
+
+
+def partial_sizes(cfg: Config):
+    """tpcf_partial_sizes: (doubles, int64 counts) of one shard's partial results."""
+    nf, ni = ctypes.c_int64(), ctypes.c_int64()
+    c = cfg.c()
+    _check(lib().tpcf_partial_sizes(ctypes.byref(c), ctypes.byref(nf), ctypes.byref(ni)))
+    return nf.value, ni.value
+
+
+def estimate_3pcf_partial(cfg: Config, d_xyz, d_w, r_xyz, r_w, dp_xyz, dp_w, rp_xyz, rp_w, w_d_total: float,
+                          w_r_total: float, weighted_randoms: bool, stream=None, device="cuda"):
+    """tpcf_estimate_3pcf_partial: one shard's additive partials (part_f FP64, part_i int64)
+    as device tensors.  r_xyz / rp_xyz None: periodic analytic randoms."""
+    def dx(a):
+        return None if a is None else _as_dev_xyz(a, device)
+
+    def dw(a):
+        return None if a is None else _as_dev_w(a, device)
+    d, dwt, r, rwt = dx(d_xyz), dw(d_w), dx(r_xyz), dw(r_w)
+    dp, dpw, rp, rpw = dx(dp_xyz), dw(dp_w), dx(rp_xyz), dw(rp_w)
+    nf, ni = partial_sizes(cfg)
+    pf = torch.empty(nf, dtype=torch.float64, device=device)
+    pi = torch.empty(ni, dtype=torch.int64, device=device)
+    n = lambda a: 0 if a is None else a.shape[0]
+    c = cfg.c()
+    _check(lib().tpcf_estimate_3pcf_partial(ctypes.byref(c), _ptr(d), _ptr(dwt), n(d), _ptr(r), _ptr(rwt), n(r),
+                                            _ptr(dp), _ptr(dpw), n(dp), _ptr(rp), _ptr(rpw), n(rp),
+                                            float(w_d_total), float(w_r_total), int(bool(weighted_randoms)),
+                                            _ptr(pf), _ptr(pi), _stream(stream)))
+    return pf, pi
+
+
+def estimate_3pcf_finish(cfg: Config, part_f, part_i, w_d_total: float, w_r_total: float, explicit_randoms: bool,
+                         weighted_randoms: bool, want_xi=False, stream=None):
+    """tpcf_estimate_3pcf_finish: the estimate (a Result) from the summed partials."""
+    dev = part_f.device
+    nb, L1 = cfg.n_bins, cfg.l_max + 1
+    mults = multipole_index(cfg)
+    zeta = torch.empty((len(mults), nb, nb), dtype=torch.float64, device=dev)
+    nnn = torch.empty((L1, L1, L1, nb, nb), dtype=torch.float64, device=dev)
+    rrr = torch.empty((nb, nb), dtype=torch.float64, device=dev)
+    pc = torch.empty(nb, dtype=torch.int64, device=dev)
+    tc = torch.empty((nb, nb), dtype=torch.int64, device=dev)
+    xi = torch.empty((cfg.l_max // 2 + 1, nb), dtype=torch.float64, device=dev) if want_xi else None
+    c = cfg.c()
+    _check(lib().tpcf_estimate_3pcf_finish(ctypes.byref(c), float(w_d_total), float(w_r_total),
+                                           int(bool(explicit_randoms)), int(bool(weighted_randoms)), _ptr(part_f),
+                                           _ptr(part_i), _ptr(zeta), _ptr(nnn), _ptr(rrr), _ptr(pc), _ptr(tc),
+                                           _ptr(xi), _stream(stream)))
+    return Result(zeta, mults, nnn, rrr, pc, tc, xi)
 
 
 def couple_multipoles(cfg: Config, alm, prim_w, counts, diag, wsp, stream=None):
