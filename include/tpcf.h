@@ -219,6 +219,50 @@ int tpcf_couple_multipoles_static(const float *alm, const float *prim_w, const i
                                   const tpcf_config *cfg, const double *diag, const double *wsp,
                                   double *nnn, int64_t *triplet_counts, void *stream);
 
+/* Sharded form, for several ranks (one GPU each) sharing one catalogue.  The
+ * estimator is a sum over primaries (Sec. 4.2: the average over positions x of
+ * the local products of Eq. measured_mult), so a rank can compute the part of
+ * every sum that its primaries contribute; the parts are added over the ranks
+ * (one sum reduction, e.g. an NCCL all-reduce) and then finished.
+ *
+ * tpcf_partial_sizes: the lengths of one rank's partial results: n_double
+ * doubles (NNN^m [m][l1][l2][b1][b2], the 2PCF sums, the randoms' l = 0
+ * coupling and 2PCF sums) and n_int64 counts (pair counts, triplet counts, the
+ * randoms' triplet and pair counts).
+ *
+ * tpcf_estimate_3pcf_partial: one rank's partials (dev part_f[n_double],
+ * dev part_i[n_int64], overwritten).
+ *   d_xyz/d_w (nd), r_xyz/r_w (nr): the data and random points within r_max of
+ *     any of this rank's primaries (its secondaries, primaries included);
+ *     nr = nrp = 0: periodic analytic randoms;
+ *   dp_xyz/dp_w (ndp), rp_xyz/rp_w (nrp): this rank's primaries; every primary of
+ *     the catalogue belongs to exactly one rank;
+ *   w_d_total, w_r_total: the weight totals of the whole catalogue (they set the
+ *     periodic offset and the D - R weights -(W_D / W_R) w of the randoms);
+ *   weighted_randoms: nonzero if any random weight of the catalogue is not 1
+ *     (RRR_00^0 then comes from the randoms' l = 0 coupling, else from integer
+ *     random triplet counts); the same on every rank.
+ *   Weights NULL: unit weights.  Arrays are device arrays, layout as in
+ *   tpcf_estimate_3pcf.  Synchronises the stream before returning.
+ *
+ * tpcf_estimate_3pcf_finish: from the partials summed over every rank, the
+ * estimate: dev zeta[n_mult][n_bins][n_bins] (required), and, if not NULL, dev
+ * nnn, rrr, pair_counts, triplet_counts and xi as tpcf_estimate_3pcf_xi gives
+ * them.  explicit_randoms: 0 for periodic analytic randoms.  Synchronises the
+ * stream before returning.
+ * Errors: TPCF_ERR_ARG for missing buffers or totals, analytic randoms in an open
+ * volume, or a bad configuration. */
+int tpcf_partial_sizes(const tpcf_config *cfg, int64_t *n_double, int64_t *n_int64);
+int tpcf_estimate_3pcf_partial(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,
+                               const uint32_t *r_xyz, const float *r_w, int64_t nr, const uint32_t *dp_xyz,
+                               const float *dp_w, int64_t ndp, const uint32_t *rp_xyz, const float *rp_w, int64_t nrp,
+                               double w_d_total, double w_r_total, int32_t weighted_randoms, double *part_f,
+                               int64_t *part_i, void *stream);
+int tpcf_estimate_3pcf_finish(const tpcf_config *cfg, double w_d_total, double w_r_total, int32_t explicit_randoms,
+                              int32_t weighted_randoms, const double *part_f, const int64_t *part_i, double *zeta,
+                              double *nnn, double *rrr, int64_t *pair_counts, int64_t *triplet_counts, double *xi,
+                              void *stream);
+
 /* TripoSH projection (Eq. slep2sugy) of dev nnn (layout as above) divided bin
  * by bin by dev rrr[n_bins][n_bins]; writes dev zeta[n_mult][n_bins][n_bins]. */
 int tpcf_project(const tpcf_config *cfg, const double *nnn, const double *rrr, double *zeta, void *stream);
