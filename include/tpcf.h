@@ -375,9 +375,18 @@ int tpcf_batch_run_graph(tpcf_batch batch, const uint32_t *xyz, const float *w, 
 /* Releases a batch (synchronises the device first). NULL is accepted. */
 int tpcf_batch_destroy(tpcf_batch batch);
 
-/* create + run + tpcf_stream_status + destroy. */
+/* Status of every mock in the batch's last run (host status[n_mocks]; synchronises
+ * the stream): TPCF_OK, TPCF_ERR_DATA (a non-finite weight in that mock: its own
+ * multipoles are not finite, the other mocks are unaffected) or TPCF_ERR_ARG
+ * (fewer than two points: no pair to estimate from). */
+int tpcf_batch_status(tpcf_batch batch, int32_t *status, void *stream);
+
+/* create + run + tpcf_stream_status + destroy; status_per_mock (host
+ * [n_mocks], or NULL) as tpcf_batch_status gives it.  A bad mock does not fail
+ * the call: only whole-batch failures are returned. */
 int tpcf_estimate_3pcf_batched(const tpcf_config *cfg, const uint32_t *xyz, const float *w, const int64_t *offsets,
-                               int32_t n_mocks, double *zeta, int64_t *triplet_counts, void *stream);
+                               int32_t n_mocks, double *zeta, int64_t *triplet_counts, int32_t *status_per_mock,
+                               void *stream);
 
 /* Chooses cell_div (2..6), tile_primaries (1, 2, 4) and chunk (3072, 4096,
  * 6144) for a catalogue like this one by timing the pair stage on a strided

@@ -72,6 +72,8 @@ struct PairParams {
     const int *prim_mock;
     int64_t ncell_mock;
     const double *mono_w_mock;
+    // batches: bad input latches the mock's own status (DEV_ERR_*) instead of err
+    int *mock_status;
 };
 
 // Bit of the current device in a per-device "done" mask (one-time attribute set-up).
@@ -116,7 +118,8 @@ void free_grid_dev(GridDev &g, cudaStream_t st);
 // One grid over many catalogues: points [offsets[k], offsets[k+1]) form mock k,
 // whose cells are k * nc^3 ... (k+1) * nc^3 - 1; rec_mock[i] = mock of record i.
 cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t n, const int64_t *d_offsets,
-                                   int n_mocks, int nc, GridDev &g, int32_t *rec_mock, int *err, cudaStream_t st);
+                                   int n_mocks, int nc, GridDev &g, int32_t *rec_mock, int *err, cudaStream_t st,
+                                   int *mock_status = nullptr);
 // *out (zeroed by the caller) += number of w[i] != 1.
 cudaError_t count_not_one(const float *w, int64_t n, int *out, cudaStream_t st);
 cudaError_t weight_sums_mocks(const float *w, const int64_t *d_offsets, int n_mocks, double *out, cudaStream_t st);

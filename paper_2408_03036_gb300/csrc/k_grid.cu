@@ -188,7 +188,8 @@ __global__ void k_wsum(const float *__restrict__ w1, int64_t n1, const float *__
 __global__ void k_cell_hist_batched(const uint32_t *__restrict__ xyz, const float *__restrict__ w, int64_t n,
                                     const int64_t *__restrict__ offsets, int n_mocks, int nc, int64_t ncell,
                                     int32_t *__restrict__ cid, int32_t *__restrict__ mock_of,
-                                    int32_t *__restrict__ hist, int4 *__restrict__ tmp, int *err)
+                                    int32_t *__restrict__ hist, int4 *__restrict__ tmp, int *err,
+                                    int *__restrict__ mock_status)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int lo = 0, hi = n_mocks - 1;
@@ -198,7 +199,7 @@ __global__ void k_cell_hist_batched(const uint32_t *__restrict__ xyz, const floa
         }
         const uint32_t x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
         const float wt = w ? w[i] : 1.0f;
-        if (!(wt == wt) || isinf(wt)) atomicCAS(err, 0, DEV_ERR_DATA);
+        if (!(wt == wt) || isinf(wt)) atomicCAS(mock_status ? mock_status + lo : err, 0, DEV_ERR_DATA);
         const int64_t c = (int64_t)lo * ncell + (cell1(z, nc) * nc + cell1(y, nc)) * nc + cell1(x, nc);
         cid[i] = (int32_t)c;
         mock_of[i] = lo;
@@ -321,7 +322,8 @@ cudaError_t build_grid_dev(const uint32_t *xyz, const float *w, int64_t n,
 }
 
 cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t n, const int64_t *d_offsets,
-                                   int n_mocks, int nc, GridDev &g, int32_t *rec_mock, int *err, cudaStream_t st)
+                                   int n_mocks, int nc, GridDev &g, int32_t *rec_mock, int *err, cudaStream_t st,
+                                   int *mock_status)
 {
     const int64_t ncell1 = (int64_t)nc * nc * nc;
     const int64_t ncell = ncell1 * n_mocks;
@@ -347,7 +349,7 @@ cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t 
     const int B = 256;
     if (n > 0) {
         k_cell_hist_batched<<<grid_blocks(n, B), B, 0, st>>>(xyz, w, n, d_offsets, n_mocks, nc, ncell1, cid, mock_of,
-                                                            hist, tmp, err);
+                                                            hist, tmp, err, mock_status);
         note_launch();
     }
     k_scan_cells<<<1, 1024, 0, st>>>(hist, ncell, g.cell_start, cursor);

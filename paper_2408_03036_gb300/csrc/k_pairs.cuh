@@ -724,7 +724,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
                                  (int)(((unsigned long long)uy * nc) >> 32),
                                  (int)(((unsigned long long)uz * nc) >> 32), 0);
             const float wq = __int_as_float(q.w);
-            if (!(wq == wq) || isinf(wq)) latch_error(p.err, DEV_ERR_DATA);
+            if (!(wq == wq) || isinf(wq)) latch_error(p.mock_status ? p.mock_status + mock : p.err, DEV_ERR_DATA);
             if constexpr (VLOS) {
                 // line of sight n = (x_i - obs) / |x_i - obs| and an orthonormal frame
                 // (e1, e2, n); the harmonics of the m = m' coupling do not depend on

@@ -86,6 +86,7 @@ struct tpcf_batch_s {
     int32_t *counts = nullptr;
     double *wsum = nullptr, *diag = nullptr, *wsp = nullptr, *G = nullptr, *nnn = nullptr, *rrr = nullptr;
     unsigned long long *pairs = nullptr, *T = nullptr;
+    int *d_status = nullptr;             // [n_mocks] DEV_ERR_* of every mock's last run
     // graph of one run, captured for the buffers in gp
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -474,6 +475,7 @@ struct BatchInfo {
     const int *prim_mock;       // mock of every primary
     int64_t ncell_mock;         // cells per mock
     const double *mono_w_mock;  // W per mock
+    int *mock_status;           // per-mock device status (the group's first mock at index 0)
 };
 
 int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t n_prim, bool counts_only,
@@ -574,6 +576,7 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
         p.prim_mock = bi->prim_mock;
         p.ncell_mock = bi->ncell_mock;
         p.mono_w_mock = bi->mono_w_mock;
+        p.mock_status = bi->mock_status;
     }
     p.P = pl.P;
     p.chunk = pl.chunk;
@@ -1496,6 +1499,8 @@ int tpcf_batch_create(const tpcf_config *cfg, const int64_t *offsets, int32_t n_
     A((void **)&b->rrr, (size_t)nb * nb * sizeof(double));
     A((void **)&b->pairs, (size_t)n_mocks * nb * sizeof(unsigned long long));
     A((void **)&b->T, (size_t)n_mocks * nb * nb * sizeof(unsigned long long));
+    A((void **)&b->d_status, (size_t)n_mocks * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, (size_t)n_mocks * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(b->d_off, offsets, (n_mocks + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_goff, goff.data(), goff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_gaunt, gaunt.data(), gaunt.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -1517,7 +1522,7 @@ int tpcf_batch_destroy(tpcf_batch b)
     for (void *ptr : {(void *)b->d_off, (void *)b->d_goff, (void *)b->d_gaunt, (void *)b->d_coef, (void *)b->d_mults,
                       (void *)b->d_mono, (void *)b->d_tiles, (void *)b->rec_mock, (void *)b->alm, (void *)b->wprim,
                       (void *)b->counts, (void *)b->wsum, (void *)b->diag, (void *)b->wsp, (void *)b->G,
-                      (void *)b->nnn, (void *)b->rrr, (void *)b->pairs, (void *)b->T})
+                      (void *)b->nnn, (void *)b->rrr, (void *)b->pairs, (void *)b->T, (void *)b->d_status})
         if (ptr) cudaFree(ptr);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -1550,6 +1555,7 @@ int tpcf_batch_run(tpcf_batch b, const uint32_t *xyz, const float *w, double *ze
     CK(cudaMemsetAsync(b->wsp, 0, (size_t)b->n_mocks * L1 * nb * sizeof(double), st));
     CK(cudaMemsetAsync(b->pairs, 0, (size_t)b->n_mocks * nb * sizeof(unsigned long long), st));
     CK(cudaMemsetAsync(b->T, 0, (size_t)b->n_mocks * nb * nb * sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(b->d_status, 0, (size_t)b->n_mocks * sizeof(int), st));
     size_t goff_at = 0;
     for (size_t g = 0; g + 1 < b->group.size(); ++g) {
         const int m0 = b->group[g], m1 = b->group[g + 1], nm = m1 - m0;
@@ -1559,8 +1565,9 @@ int tpcf_batch_run(tpcf_batch b, const uint32_t *xyz, const float *w, double *ze
         const float *wg = w ? w + p0 : nullptr;
         CK(weight_sums_mocks(wg, d_goff, nm, b->wsum + m0, st));
         GridDev grid;
-        CK(build_grid_batched_dev(xyz + 3 * p0, wg, np, d_goff, nm, b->nc, grid, b->rec_mock, ds->err, st));
-        BatchInfo bi{b->rec_mock, ncell1, b->wsum + m0};
+        CK(build_grid_batched_dev(xyz + 3 * p0, wg, np, d_goff, nm, b->nc, grid, b->rec_mock, ds->err, st,
+                                  b->d_status + m0));
+        BatchInfo bi{b->rec_mock, ncell1, b->wsum + m0, b->d_status + m0};
         rc = run_pairs(c, grid, grid.rec, np, false, 0.0, nullptr, true, b->alm, b->counts,
                        b->diag + (size_t)m0 * ndiag * nb, b->wsp + (size_t)m0 * L1 * nb, b->pairs + (size_t)m0 * nb,
                        st, &bi);
@@ -1629,14 +1636,32 @@ int tpcf_batch_run_graph(tpcf_batch b, const uint32_t *xyz, const float *w, doub
     return TPCF_OK;
 }
 
+int tpcf_batch_status(tpcf_batch b, int32_t *status, void *stream)
+{
+    if (!b || !status) return fail(TPCF_ERR_ARG, "batch and status are required");
+    std::vector<int> h(b->n_mocks, 0);
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    CK(cudaMemcpy(h.data(), b->d_status, (size_t)b->n_mocks * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < b->n_mocks; ++k) {
+        int v = TPCF_OK;
+        if (b->off[k + 1] - b->off[k] < 2) v = TPCF_ERR_ARG;   // no pair: the estimate is 0 / 0
+        else if (h[k] == DEV_ERR_DATA) v = TPCF_ERR_DATA;
+        else if (h[k]) v = TPCF_ERR_CUDA;
+        status[k] = v;
+    }
+    return TPCF_OK;
+}
+
 int tpcf_estimate_3pcf_batched(const tpcf_config *cfg, const uint32_t *xyz, const float *w, const int64_t *offsets,
-                               int32_t n_mocks, double *zeta, int64_t *triplet_counts, void *stream)
+                               int32_t n_mocks, double *zeta, int64_t *triplet_counts, int32_t *status_per_mock,
+                               void *stream)
 {
     tpcf_batch b = nullptr;
     int rc = tpcf_batch_create(cfg, offsets, n_mocks, 0, &b);
     if (rc) return rc;
     rc = tpcf_batch_run(b, xyz, w, zeta, triplet_counts, stream);
     if (!rc) rc = tpcf_stream_status(stream);
+    if (!rc && status_per_mock) rc = tpcf_batch_status(b, status_per_mock, stream);
     tpcf_batch_destroy(b);
     return rc;
 }

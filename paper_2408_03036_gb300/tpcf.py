@@ -31,6 +31,7 @@ EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_set_wait_limit", "tpcf_kerne
            "tpcf_estimate_3pcf_xi", "tpcf_estimate_3pcf_full_edge",
            "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
+           "tpcf_batch_status",
            "tpcf_estimate_3pcf_batched", "tpcf_autotune",
            "tpcf_covariance", "tpcf_covariance_factors", "tpcf_data_vector_index", "tpcf_check_rsqrt",
            "tpcf_emu_create", "tpcf_emu_destroy", "tpcf_emu_param_count", "tpcf_emu_set_input_box",
@@ -128,7 +129,8 @@ def lib():
             "tpcf_batch_run": ([P, P, P, P, P, P], ctypes.c_int),
             "tpcf_batch_run_graph": ([P, P, P, P, P, P], ctypes.c_int),
             "tpcf_batch_destroy": ([P], ctypes.c_int),
-            "tpcf_estimate_3pcf_batched": ([CFG, P, P, P, ctypes.c_int32, P, P, P], ctypes.c_int),
+            "tpcf_estimate_3pcf_batched": ([CFG, P, P, P, ctypes.c_int32, P, P, P, P], ctypes.c_int),
+            "tpcf_batch_status": ([P, P, P], ctypes.c_int),
             "tpcf_autotune": ([CFG, P, P, I64, P, CFG], ctypes.c_int),
             "tpcf_covariance": ([P, I64, I64, P, I64, P, P, P], ctypes.c_int),
             "tpcf_check_rsqrt": ([I64, ctypes.c_uint64, P, P], ctypes.c_int),
@@ -541,6 +543,13 @@ class Batch:
         _check(lib().tpcf_batch_run_graph(self.handle, _ptr(xyz), _ptr(w), _ptr(zeta), _ptr(triplet_counts),
                                           _stream(stream)))
 
+    def status(self, stream=None):
+        """tpcf_batch_status: per-mock status codes of the last run (int32 numpy array)."""
+        import numpy as np
+        st = np.zeros(self.n_mocks, dtype=np.int32)
+        _check(lib().tpcf_batch_status(self.handle, _ptr(st), _stream(stream)))
+        return st
+
     def close(self):
         if self.handle:
             _check(lib().tpcf_batch_destroy(self.handle))
@@ -553,8 +562,10 @@ class Batch:
             pass
 
 
-def estimate_3pcf_batched(cfg: Config, xyz, w, offsets, stream=None, device="cuda", want_counts=True):
-    """tpcf_estimate_3pcf_batched; returns (zeta [n_mocks, n_mult, nb, nb], triplet counts or None)."""
+def estimate_3pcf_batched(cfg: Config, xyz, w, offsets, stream=None, device="cuda", want_counts=True,
+                          want_status=False):
+    """tpcf_estimate_3pcf_batched; returns (zeta [n_mocks, n_mult, nb, nb], triplet counts or None),
+    and with want_status also the per-mock status codes (int32 numpy array)."""
     import numpy as np
     off = np.ascontiguousarray(offsets, dtype=np.int64)
     dx = _as_dev_xyz(xyz, device)
@@ -563,10 +574,11 @@ def estimate_3pcf_batched(cfg: Config, xyz, w, offsets, stream=None, device="cud
     nb = cfg.n_bins
     z = torch.empty((nm, len(multipole_index(cfg)), nb, nb), dtype=torch.float64, device=device)
     tc = torch.empty((nm, nb, nb), dtype=torch.int64, device=device) if want_counts else None
+    st = np.zeros(nm, dtype=np.int32)
     c = cfg.c()
     _check(lib().tpcf_estimate_3pcf_batched(ctypes.byref(c), _ptr(dx), _ptr(dw), _ptr(off), nm, _ptr(z),
-                                            _ptr(tc), _stream(stream)))
-    return z, tc
+                                            _ptr(tc), _ptr(st), _stream(stream)))
+    return (z, tc, st) if want_status else (z, tc)
 
 
 def autotune(cfg: Config, xyz, w=None, stream=None, device="cuda") -> Config:

@@ -189,3 +189,37 @@ def test_autotune_returns_a_valid_faster_choice(gpu, ora):
     est = ora.estimate(ocfg, xyz[:4000], w[:4000])
     assert np.array_equal(res.triplet_counts.cpu().numpy(), est.trip_counts)
     assert per_mult_err(res.zeta.cpu().numpy(), est.zeta).max() <= TOL_FP32
+
+
+def test_per_mock_status_isolates_a_bad_mock(gpu):
+    """A non-finite weight in one mock and a one-point mock: the call succeeds, the
+    per-mock status names exactly those two mocks (TPCF_ERR_DATA, TPCF_ERR_ARG),
+    and every other mock's multipoles equal their one-catalogue estimates."""
+    cfg = tpcf.Config(**base_cfg())
+    sizes = [2000, 1500, 1, 2500, 1800]
+    xyz, w, off = make_mocks(sizes, seed=300)
+    w = w.copy()
+    w[off[3] + 17] = np.nan
+    zb, tb, st = tpcf.estimate_3pcf_batched(cfg, xyz, w, off, want_status=True)
+    tpcf.stream_status()   # no device-wide error was latched
+    assert list(st) == [0, 0, -1, -6, 0], st
+    zb, tb = zb.cpu().numpy(), tb.cpu().numpy()
+    assert not np.isfinite(zb[3]).all()
+    good = [0, 1, 4]
+    for k in good:
+        a, b = off[k], off[k + 1]
+        res = tpcf.estimate_3pcf(cfg, xyz[a:b], w[a:b])
+        tpcf.stream_status()
+        assert np.array_equal(tb[k], res.triplet_counts.cpu().numpy()), k
+        assert per_mult_err(zb[k], res.zeta.cpu().numpy()).max() <= TOL_FP32, k
+    # the batch object reports the same after a graph run
+    import torch
+    bt = tpcf.Batch(cfg, off)
+    dx = torch.from_numpy(synth.as_int32_bits(xyz)).cuda()
+    dw = torch.from_numpy(w).cuda()
+    z = bt.zeta_buffer()
+    bt.run_graph(dx, dw, z)
+    bt.run_graph(dx, dw, z)
+    assert list(bt.status()) == [0, 0, -1, -6, 0]
+    tpcf.stream_status()
+    bt.close()
