@@ -63,6 +63,12 @@ struct PairParams {
     double *diag;
     double *wsp;
     unsigned long long *pair_counts;
+    // D - R fields whose randoms are the only records of negative weight (sign bit
+    // set): per primary and bin, the count of such secondaries for primaries of
+    // negative weight (zero rows for the others), and its sum over those primaries
+    // per bin; null when not wanted.  Harmonic kernel only.
+    int32_t *counts_r;
+    unsigned long long *pair_counts_r;
     int *work;                // tile counter (zeroed before launch)
     int *err;                 // device error latch
     // Batches of catalogues (null prim_mock: one catalogue).  Primary i belongs to
@@ -122,6 +128,8 @@ cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t 
                                    int *mock_status = nullptr);
 // *out (zeroed by the caller) += number of w[i] != 1.
 cudaError_t count_not_one(const float *w, int64_t n, int *out, cudaStream_t st);
+// out[0] += weights whose sign bit is set, out[1] += weights > 0 (out zeroed by the caller)
+cudaError_t weight_signs(const float *w, int64_t n, int *out, cudaStream_t st);
 cudaError_t weight_sums_mocks(const float *w, const int64_t *d_offsets, int n_mocks, double *out, cudaStream_t st);
 
 // records of n points; wsums = {W_D, W_R} (device) turns the weights into -(W_D / W_R) w

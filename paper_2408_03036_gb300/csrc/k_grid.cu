@@ -227,6 +227,23 @@ __global__ void k_count_not_one(const float *__restrict__ w, int64_t n, int *out
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// out[0] += weights with the sign bit set (negative, -0, negative NaN), out[1] += weights > 0
+__global__ void k_weight_signs(const float *__restrict__ w, int64_t n, int *out)
+{
+    int neg = 0, pos = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = w[i];
+        neg += (int)(__float_as_uint(v) >> 31);
+        pos += v > 0.0f;
+    }
+    neg = __reduce_add_sync(0xffffffffu, neg);
+    pos = __reduce_add_sync(0xffffffffu, pos);
+    if ((threadIdx.x & 31) == 0) {
+        if (neg) atomicAdd(out, neg);
+        if (pos) atomicAdd(out + 1, pos);
+    }
+}
+
 __global__ void k_wsum_mocks(const float *__restrict__ w, const int64_t *__restrict__ offsets, double *out)
 {
     __shared__ double red[32];
@@ -368,6 +385,15 @@ cudaError_t count_not_one(const float *w, int64_t n, int *out, cudaStream_t st)
 {
     if (n > 0) {
         k_count_not_one<<<grid_blocks(n, 256), 256, 0, st>>>(w, n, out);
+        note_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t weight_signs(const float *w, int64_t n, int *out, cudaStream_t st)
+{
+    if (n > 0) {
+        k_weight_signs<<<grid_blocks(n, 256), 256, 0, st>>>(w, n, out);
         note_launch();
     }
     return cudaGetLastError();

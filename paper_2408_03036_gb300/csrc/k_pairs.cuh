@@ -72,7 +72,9 @@ struct Layout {
     static constexpr int NDIAG = (LMAX + 1) * (LMAX + 2) / 2;
     static constexpr int NDS = Direct<LMAX>::ON ? NDIAG : 0;   // direct j = k sums, index l(l+1)/2 + m
     static constexpr int NACC = NLM + NSP + NDS;
-    static constexpr int NACCP = NACC | 1;  // odd row stride: distinct banks for distinct keys
+    // odd row stride (distinct banks for distinct keys) with one spare column: the
+    // key's count of secondaries of negative weight, as an integer
+    static constexpr int NACCP = (NACC + 1) | 1;
 };
 
 __device__ __forceinline__ void latch_error(int *err, int code)
@@ -593,7 +595,7 @@ __host__ __device__ inline QMap make_qmap(int P, int nb, int s, int chunk, int b
     m.off_queue = o;   o = align_up(o + (qbytes > stage ? qbytes : stage), 16);
     m.off_d64 = o;     o = align_up(o + 8 * nb * Layout<LMAX>::NDIAG, 16);
     m.off_w64 = o;     o = align_up(o + 8 * nb * Layout<LMAX>::NSP, 16);
-    m.off_pairs = o;   o = align_up(o + 8 * nb, 16);
+    m.off_pairs = o;   o = align_up(o + 2 * 8 * nb, 16);   // all pairs, then random-random pairs
     m.off_misc = o;    o = align_up(o + 4 * (16 + W), 16);
     m.total = o;
     return m;
@@ -640,6 +642,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
     double *d64 = reinterpret_cast<double *>(smem + M.off_d64);
     double *w64 = reinterpret_cast<double *>(smem + M.off_w64);
     unsigned long long *spairs = reinterpret_cast<unsigned long long *>(smem + M.off_pairs);
+    unsigned long long *spairs_r = spairs + nb;
     int *misc = reinterpret_cast<int *>(smem + M.off_misc);
     int &s_tile = misc[0];
     int &s_next = misc[1];
@@ -654,7 +657,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
     }
     for (int i = tid; i < nb * NDIAG; i += T) d64[i] = 0.0;
     for (int i = tid; i < nb * NSP; i += T) w64[i] = 0.0;
-    for (int i = tid; i < nb; i += T) spairs[i] = 0ull;
+    for (int i = tid; i < 2 * nb; i += T) spairs[i] = 0ull;
     for (int i = tid; i < 2 * nkmax; i += T) qcnt[i] = 0;
     if (tid < nb) {
         // seed: the shell volumes, r^3 in units of the bin edges' squares
@@ -691,7 +694,9 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
         }
         for (int b = tid; b < nb; b += T) {
             if (p.pair_counts && spairs[b]) atomicAdd(p.pair_counts + (size_t)mk * nb + b, spairs[b]);
+            if (p.pair_counts_r && spairs_r[b]) atomicAdd(p.pair_counts_r + (size_t)mk * nb + b, spairs_r[b]);
             spairs[b] = 0ull;
+            spairs_r[b] = 0ull;
         }
         __syncthreads();
     };
@@ -801,6 +806,8 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
         const int mycap = myk >= 0 ? qinfo[myk].y : 0;
         float2 acc[Packed<LMAX>::N2];
         float2 dacc[Direct<LMAX>::N2];
+        // secondaries of negative weight (the randoms of a D - R field) in this lane's share
+        int rcnt = 0;
 #pragma unroll
         for (int j = 0; j < Packed<LMAX>::N2; ++j) acc[j] = make_float2(0.f, 0.f);
 #pragma unroll
@@ -820,6 +827,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
                 const float4 *qq = queue + myq;
                 for (int e = myr; e < n; e += myg) {
                     float4 v = qq[e];
+                    rcnt += (int)(__float_as_uint(v.w) >> 31);
                     if constexpr (VLOS) {
                         // the separation in the primary's frame (e1, e2, line of sight)
                         const float4 *R = sRot + 3 * (myk / nb);
@@ -923,14 +931,21 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
         {
             float *st = stage + (size_t)tid * NACCP;
             unpack<LMAX>(acc, dacc, st);
+            st[NACC] = __int_as_float(rcnt);
         }
         __syncthreads();
-        for (int i = tid; i < nk * NACC; i += T) {
-            const int k = i / NACC, j = i % NACC;
+        for (int i = tid; i < nk * (NACC + 1); i += T) {
+            const int k = i / (NACC + 1), j = i % (NACC + 1);
             const int g0 = gfirst[k], g = gsize[k];
-            float t = 0.f;
-            for (int q = 0; q < g; ++q) t += stage[(g0 + q) * NACCP + j];
-            sacc[k * NACCP + j] = t;
+            if (j < NACC) {
+                float t = 0.f;
+                for (int q = 0; q < g; ++q) t += stage[(g0 + q) * NACCP + j];
+                sacc[k * NACCP + j] = t;
+            } else {
+                int t = 0;
+                for (int q = 0; q < g; ++q) t += __float_as_int(stage[(g0 + q) * NACCP + j]);
+                sacc[k * NACCP + j] = __int_as_float(t);
+            }
         }
         __syncthreads();
 
@@ -955,10 +970,20 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
         }
         if (p.counts)
             for (int i = tid; i < np * nb; i += T) p.counts[g0 * nb + i] = cnt[i];
+        // random-random counts: a primary of negative weight with its secondaries of
+        // negative weight (zero rows for the other primaries)
+        if (p.counts_r)
+            for (int i = tid; i < np * nb; i += T)
+                p.counts_r[g0 * nb + i] =
+                    (sPrim[i / nb].w < 0) ? __float_as_int(sacc[i * NACCP + NACC]) : 0;
         for (int b = tid; b < nb; b += T) {
-            unsigned long long t = 0;
-            for (int sl = 0; sl < np; ++sl) t += (unsigned long long)cnt[sl * nb + b];
+            unsigned long long t = 0, tr = 0;
+            for (int sl = 0; sl < np; ++sl) {
+                t += (unsigned long long)cnt[sl * nb + b];
+                if (sPrim[sl].w < 0) tr += (unsigned long long)__float_as_int(sacc[(sl * nb + b) * NACCP + NACC]);
+            }
             spairs[b] += t;
+            spairs_r[b] += tr;
         }
         // diagonal residuals w_i (|a_l^m[b]|^2 - s_ll^m[b]), the j = k term s removed: for
         // l >= 1 compensated (sq2_minus) on the unnormalised sums, then scaled by K_lm^2;

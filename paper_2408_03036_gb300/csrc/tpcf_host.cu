@@ -478,9 +478,17 @@ struct BatchInfo {
     int *mock_status;           // per-mock device status (the group's first mock at index 0)
 };
 
+// Random-random pair counts taken during a D - R pass (PairParams::counts_r):
+// per primary and bin, and their sum per bin (either may be null).
+struct RRCounts {
+    int32_t *counts;
+    unsigned long long *pairs;
+};
+
 int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t n_prim, bool counts_only,
               double mono_w, const double *mono_w_dev, bool use_mono, float *alm, int32_t *counts, double *diag,
-              double *wsp, unsigned long long *pair_counts, cudaStream_t st, const BatchInfo *bi = nullptr)
+              double *wsp, unsigned long long *pair_counts, cudaStream_t st, const BatchInfo *bi = nullptr,
+              const RRCounts *rrc = nullptr)
 {
     DevState *ds;
     int rc = dev_state(&ds);
@@ -537,6 +545,10 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
     p.diag = diag;
     p.wsp = wsp;
     p.pair_counts = pair_counts;
+    if (rrc && !counts_only) {
+        p.counts_r = rrc->counts;
+        p.pair_counts_r = rrc->pairs;
+    }
     p.err = ds->err;
     const HarmTables h = make_tables(counts_only ? 0 : c->l_max);
     {
@@ -754,6 +766,33 @@ int mono_coef_dev(const tpcf_config *c, double **out, cudaStream_t st)
 }
 
 
+// Whether the randoms of a D - R field are exactly its records whose weight has the
+// sign bit set, so that the harmonic pass can count random-random pairs: true when
+// no data weight has its sign bit set and one is positive (then W_D > 0 and every
+// random's weight -(W_D / W_R) w is negative for w > 0).  Null weights are ones.
+// Synchronises the stream.
+int randoms_are_negative(const float *w1, int64_t n1, const float *w2, int64_t n2, bool *ok, cudaStream_t st)
+{
+    *ok = false;
+    if (!w1 && !w2) {
+        *ok = (n1 + n2) > 0;
+        return TPCF_OK;
+    }
+    int *d = nullptr;
+    CK(cudaMallocAsync((void **)&d, 2 * sizeof(int), st));
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(int), st);
+    if (e == cudaSuccess && w1) e = weight_signs(w1, n1, d, st);
+    if (e == cudaSuccess && w2) e = weight_signs(w2, n2, d, st);
+    int h[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(d, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    CK(e);
+    const int64_t pos_unit = (w1 ? 0 : n1) + (w2 ? 0 : n2);   // null weights are ones
+    *ok = h[0] == 0 && (h[1] > 0 || pos_unit > 0);
+    return TPCF_OK;
+}
+
 int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w, int64_t nd,
                   const uint32_t *r_xyz, const float *r_w, int64_t nr, double *zeta, double *nnn_out,
                   double *rrr_out, int64_t *pair_counts, int64_t *triplet_counts, double *xi, bool edge_full,
@@ -788,6 +827,11 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
         CK(cudaStreamSynchronize(st));
         weighted_r = h_n != 0;
     }
+    // open volume, unit randoms, the l = 0 normaliser: the random-random counts come
+    // with the D - R pass when the randoms are its only negative weights
+    bool rr_fused = false;
+    if (!analytic && !weighted_r && !edge_full)
+        if ((rc = randoms_are_negative(d_w, nd, nullptr, 0, &rr_fused, st))) return rc;
 
     double *wsums = nullptr, *diag = nullptr, *wsp = nullptr, *nnn = nnn_out, *rrr = rrr_out, *mono = nullptr;
     double *S = nullptr, *s0 = nullptr, *rr = nullptr;
@@ -809,8 +853,16 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
     if ((rc = sc.alloc(&T, (size_t)nb * nb, true))) return rc;
     if (!nnn && (rc = sc.alloc(&nnn, (size_t)L1 * L1 * L1 * nb * nb, false))) return rc;
     if (!rrr && (rc = sc.alloc(&rrr, (size_t)nb * nb, false))) return rc;
+    RRCounts rrc = {nullptr, nullptr};
+    if (rr_fused) {
+        if ((rc = sc.alloc(&cnt_r, (size_t)K * nb, false))) return rc;
+        if ((rc = sc.alloc(&TR, (size_t)nb * nb, true))) return rc;
+        if (xi && (rc = sc.alloc(&pairs_r, (size_t)nb, true))) return rc;
+        rrc.counts = cnt_r;
+        rrc.pairs = pairs_r;
+    }
     rc = run_pairs(cfg, gf, gf.rec, K, false, 0.0, analytic ? wsums : nullptr, analytic, alm, cnt, diag, wsp, pairs,
-                   st);
+                   st, nullptr, rr_fused ? &rrc : nullptr);
     if (rc) return rc;
     // primary weights in grid order are the records' w fields: pass them through a strided copy
     float *wprim = nullptr;
@@ -829,14 +881,19 @@ int estimate_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_
         if (rc) return rc;
         CK(rrr_analytic(wsums, mono, nb, rrr, st));
     } else if (!weighted_r && !edge_full) {
-        CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
-        if ((rc = sc.alloc(&cnt_r, (size_t)nr * nb, false))) return rc;
-        if ((rc = sc.alloc(&TR, (size_t)nb * nb, true))) return rc;
-        if (xi && (rc = sc.alloc(&pairs_r, (size_t)nb, true))) return rc;
-        rc = run_pairs(cfg, gr, gr.rec, nr, true, 0.0, nullptr, false, nullptr, cnt_r, nullptr, nullptr, pairs_r,
-                       st);
-        if (rc) return rc;
-        CK(tpcf::triplet_counts(cnt_r, nr, nb, TR, st));
+        if (rr_fused) {
+            // counted by the D - R pass: rows of data primaries are zero
+            CK(tpcf::triplet_counts(cnt_r, K, nb, TR, st));
+        } else {
+            CK(build_grid_dev(r_xyz, r_w, nr, nullptr, nullptr, 0, nullptr, choose_nc(cfg, nr), gr, ds->err, st));
+            if ((rc = sc.alloc(&cnt_r, (size_t)nr * nb, false))) return rc;
+            if ((rc = sc.alloc(&TR, (size_t)nb * nb, true))) return rc;
+            if (xi && (rc = sc.alloc(&pairs_r, (size_t)nb, true))) return rc;
+            rc = run_pairs(cfg, gr, gr.rec, nr, true, 0.0, nullptr, false, nullptr, cnt_r, nullptr, nullptr,
+                           pairs_r, st);
+            if (rc) return rc;
+            CK(tpcf::triplet_counts(cnt_r, nr, nb, TR, st));
+        }
         CK(rrr_from_counts(TR, wsums, nb, rrr, st));
         rr_mode = 1;
     } else {
@@ -961,6 +1018,12 @@ int partial_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w
     const double hw[2] = {w_d, w_r};
     CK(cudaMemcpyAsync(wsums, hw, sizeof(hw), cudaMemcpyHostToDevice, st));
     const int64_t K = ndp + nrp;
+    // unit randoms: their pair counts come with the D - R pass when they are its only
+    // negative weights (as in the one-catalogue estimate)
+    bool rr_fused = false;
+    const bool rr_counts = !analytic && nr > 0 && nrp > 0 && !weighted_r;
+    if (rr_counts && nd + nr > 0 && K > 0)
+        if ((rc = randoms_are_negative(d_w, nd, dp_w, ndp, &rr_fused, st))) return rc;
     if (nd + nr > 0 && K > 0) {
         CK(build_grid_dev(d_xyz, d_w, nd, r_xyz, r_w, nr, analytic ? nullptr : wsums, choose_nc(cfg, nd + nr), gf,
                           ds->err, st));
@@ -979,16 +1042,29 @@ int partial_impl(const tpcf_config *cfg, const uint32_t *d_xyz, const float *d_w
         if ((rc = sc.alloc(&pairs, (size_t)nb, true))) return rc;
         if ((rc = sc.alloc(&T, (size_t)nb * nb, true))) return rc;
         if ((rc = sc.alloc(&wprim, (size_t)K, false))) return rc;
+        RRCounts rrc = {nullptr, nullptr};
+        unsigned long long *TR = nullptr;
+        if (rr_fused) {
+            if ((rc = sc.alloc(&rrc.counts, (size_t)K * nb, false))) return rc;
+            if ((rc = sc.alloc(&rrc.pairs, (size_t)nb, true))) return rc;
+            if ((rc = sc.alloc(&TR, (size_t)nb * nb, true))) return rc;
+        }
         rc = run_pairs(cfg, gf, prim, K, false, 0.0, analytic ? wsums : nullptr, analytic, alm, cnt, diag, wsp,
-                       pairs, st);
+                       pairs, st, nullptr, rr_fused ? &rrc : nullptr);
         if (rc) return rc;
+        if (rr_fused) {
+            // rows of data primaries are zero
+            CK(tpcf::triplet_counts(rrc.counts, K, nb, TR, st));
+            CK(i64_from_u64(TR, part_i + PL.TR, nb * nb, st));
+            CK(i64_from_u64(rrc.pairs, part_i + PL.pairs_r, nb, st));
+        }
         CK(cudaMemcpy2DAsync(wprim, 4, (const char *)prim + 12, 16, 4, K, cudaMemcpyDeviceToDevice, st));
         if ((rc = couple(cfg, alm, wprim, cnt, K, diag, wsp, part_f + PL.nnn, T, st))) return rc;
         CK(m0_sums(alm, wprim, K, nb, L, n_ell, 2, part_f + PL.S, st));
         CK(i64_from_u64(pairs, part_i + PL.pairs, nb, st));
         CK(i64_from_u64(T, part_i + PL.T, nb * nb, st));
     }
-    if (!analytic && nr > 0 && nrp > 0) {
+    if (!analytic && nr > 0 && nrp > 0 && !rr_fused) {
         if (!weighted_r) {
             // integer random triplet counts of the shard's random primaries
             int4 *rprim = nullptr;

@@ -150,6 +150,32 @@ def test_schedules_agree(gpu, ora, tile, chunk, div):
     compare(gpu, g, o, ora, xyz, w)
 
 
+@pytest.mark.parametrize("tile,chunk,div", [(1, 512, 2), (3, 768, 3), (6, 2048, 4)])
+def test_open_volume_random_counts_with_the_harmonic_pass(gpu, ora, tile, chunk, div):
+    """Unit randoms in an open volume: their pair counts per random primary (for
+    RRR_00^0 and the 2PCF normaliser) are taken by the D - R harmonic pass from the
+    records of negative weight, under every tile / queue / cell schedule; RRR must
+    equal the oracle's integer-triplet value."""
+    g, o = cfg_pair(ora, r_min=12.0, r_max=90.0, n_bins=7, l_max=2, Ls=(0, 2), box=420.0, periodic=False,
+                    tile_primaries=tile, chunk=chunk, cell_div=div)
+    d, dw = synth.lognormal(5001, 420.0, 41, mesh=64)   # ragged sizes
+    r, rw = synth.randoms(12007, 42)
+    dw = np.random.default_rng(43).uniform(0.0, 2.0, d.shape[0]).astype(np.float32)
+    dw[::7] = 0.0                                       # zero weights are data too
+    compare(gpu, g, o, ora, d, dw, r, rw, xi=True)
+
+
+def test_open_volume_signed_data_weights_unit_randoms(gpu, ora):
+    """Data weights of both signs with unit randoms: the randoms are then not the only
+    records of negative weight, and their counts come from the separate count pass."""
+    g, o = cfg_pair(ora, r_min=12.0, r_max=90.0, n_bins=7, l_max=2, Ls=(0, 2), box=500.0, periodic=False)
+    d, _ = synth.lognormal(5000, 500.0, 44, mesh=64)
+    r, rw = synth.randoms(12000, 45)
+    dw = np.random.default_rng(46).uniform(0.5, 2.0, d.shape[0]).astype(np.float32)
+    dw[::5] *= -1
+    compare(gpu, g, o, ora, d, dw, r, rw, xi=True)
+
+
 def test_signed_weights_and_clustering(gpu, ora):
     """Non-unit signed weights and strong clustering (many points per cell)."""
     g, o = cfg_pair(ora, r_min=5.0, r_max=60.0, n_bins=11, l_max=3, Ls=(0, 2), box=300.0)
