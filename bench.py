@@ -581,8 +581,8 @@ def _emu_evaluate(th):
 def emulator_report(dev, stream, tpcf, with_cpu=True, steps=2000):
     """The MLP emulator of the tree-level multipoles (the emulator configuration:
     200k Latin-hypercube samples of the plain model):
-      * throughput of the project's tensor-core kernels, training at batches of 512
-        and 4096 and inference over 200k parameter vectors, against the measured
+      * throughput of the project's tensor-core kernels, training at batches of 512,
+        4096 and 32768 and inference over 200k parameter vectors, against the measured
         bf16 peak (random parameters and targets: timing only);
       * accuracy: trained on the 200k samples of the plain model (evaluated on the
         host cores in a spawn process pool) for 20,000 steps of 512, judged on 2000
@@ -606,13 +606,13 @@ def emulator_report(dev, stream, tpcf, with_cpu=True, steps=2000):
     rep = {"widths": EMU_WIDTHS, "peak_tflops": peaks["bf16_tflops"], "peak_note": which + " bf16 (burst)",
            "note": "bf16 operands, FP32 accumulation in tensor memory (tcgen05 GEMM kernels)"}
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for batch in (512, 4096):
+    for batch in (512, 4096, 32768):
         idx = [torch.randint(0, n, (batch,), device=dev, generator=g) for _ in range(8)]
         xb, yb = [x[i].contiguous() for i in idx], [y[i].contiguous() for i in idx]
         for k in range(10):
             emu.train_step(xb[k % 8], yb[k % 8], 1e-3, stream=stream)
         torch.cuda.synchronize(dev)
-        st = steps if batch == 512 else max(50, steps // 8)
+        st = steps if batch == 512 else max(50, steps * 512 // (8 * batch))
         s.record(stream)
         for k in range(st):
             emu.train_step(xb[k % 8], yb[k % 8], 1e-3, stream=stream)

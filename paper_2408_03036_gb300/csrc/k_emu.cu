@@ -1,19 +1,24 @@
 // MLP emulator of the tree-level 3PCF multipoles: forward, backward and Adam
 // kernels behind the tpcf_emu_* C ABI (include/tpcf_emu.h).
 //
-// Every product of the network runs on the 5th-generation tensor cores: one GEMM
-// kernel (k_gemm_tc) computes a 128-row x NT-column tile of C = A B with bf16
-// operands (FP32 activations and gradients rounded to bf16 as they are staged,
-// bf16 weights as stored) and FP32 accumulation in tensor memory; the epilogue
-// reads the tile back from tensor memory and adds the bias and applies SiLU in
-// the forward pass.  Backward: dZ = dA * SiLU'(Z), dW = A_prev^T dZ, db = column
-// sums of dZ, dA_prev = dZ W^T, all three products on the same kernel.
+// Every product of the network runs on the 5th-generation tensor cores through
+// one persistent, warp-specialised GEMM kernel (k_gemm): bf16 operands brought
+// in by TMA (128-byte swizzle, K-major or MN-major), FP32 accumulation in tensor
+// memory, and an epilogue per use that reads the accumulator back and fuses the
+// elementwise work: bias and SiLU in the forward pass, the output scaling in
+// inference, the loss, its gradient and the output bias gradient in training,
+// SiLU'(z) and the bias gradient of every hidden layer in the backward product
+// dA_prev = dZ W, and split-K partials for the weight gradients dW = A_prev^T dZ.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
+#include <atomic>
+
+#include <cuda.h>   // CUtensorMap and the tensor-map encoder's types (the encoder is resolved at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -25,7 +30,7 @@ namespace {
 
 constexpr int kMaxLayers = 8;
 constexpr int kMaxWidth = 4096;
-constexpr int kChunk = 4096;          // rows per internal pass (scratch capacity)
+constexpr int64_t kMaxChunk = 32768;  // most rows per internal pass (per-chunk buffer capacity)
 
 struct Layer {
     int in, out;
@@ -42,238 +47,400 @@ __device__ __forceinline__ float silu_grad(float z)
     return s * (1.f + z * (1.f - s));
 }
 
-enum { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_SILU = 2 };
+// Epilogues of the GEMM kernel (C = A B^T over one 128 x NT tile, FP32 in tensor memory):
+//   EPI_HID   forward hidden layer: z = c + bias; pre-activation z (FP32, training
+//             only) and the activation SiLU(z) (bf16, the next product's operand)
+//   EPI_PRED  forward output layer, inference: y = (c + bias) sd + mean (FP32)
+//   EPI_LOSS  forward output layer, training: d = c + bias - (y - mean) / sd against
+//             the targets y; the gradient g = gscale d (bf16), its column sums into
+//             the bias gradient, and sum d^2 / count into the loss
+//   EPI_BWD   backward product dA_prev = dZ W: g = c SiLU'(z) with the previous
+//             layer's pre-activation z (bf16), its column sums into that layer's
+//             bias gradient
+//   EPI_PART  weight gradient, split over K: the split's FP32 partial tile
+enum { EPI_HID = 0, EPI_PRED = 1, EPI_LOSS = 2, EPI_BWD = 3, EPI_PART = 4 };
 
-// C[m][n] = sum_k A(m, k) B(k, n) with A(m, k) = A[m sam + k sak] and
-// B(k, n) = B[k sbk + n sbn], both bf16.
 struct GemmArgs {
-    const __nv_bfloat16 *A;
-    int64_t sam, sak;
-    const __nv_bfloat16 *B;
-    int64_t sbk, sbn;
     int M, N, K;
-    float *C;               // FP32 output, row stride ldc
-    int64_t ldc;
-    const float *bias;
-    __nv_bfloat16 *act;     // bf16 SiLU(C), row stride ld_act (EPI_BIAS_SILU)
-    int64_t ld_act;
-    int a_vec, b_vec;       // operand contiguous in K with 16-byte aligned rows: 16-byte staging
-    int NT;                 // tile columns: a power of two from 16 to 256
-    int k_per;              // K values per split (a multiple of kKS); blockIdx.z takes split z
-    int split;              // more than one split: the tiles are added into C (zeroed first)
-    int tmem_cols;          // tensor-memory columns allocated: a power of two >= max(32, NT)
+    int a_mn, b_mn;          // 1: operand stored MN-major (contiguous along M or N)
+    int NT;                  // tile columns: 64, 128 or 256
+    int n_mt, n_nt, nkb;     // tiles along M and N, 64-wide K blocks
+    int kper;                // K blocks per split
+    int units;               // splits x n_mt x n_nt work units
+    const float *bias;       // [N]
+    int vec_bias;            // widest aligned float vector of bias (4, 2 or 1)
+    __nv_bfloat16 *out_b;    // bf16 rows, pitch ld_b (HID activation; LOSS, BWD gradient)
+    int64_t ld_b;
+    float *out_f;            // FP32 rows, pitch ld_f (HID pre-activation or null; PRED y; PART workspace)
+    int64_t ld_f;
+    int vec_f;
+    const float *in_f;       // FP32 rows read by the epilogue, pitch ld_in (LOSS targets; BWD pre-activation)
+    int64_t ld_in;
+    int vec_in;
+    const float *mean, *sd;  // output scaling [N]
+    float gscale;            // LOSS: 2 / (rows x outputs of the whole batch)
+    float inv_count;         // LOSS: 1 / (rows x outputs of the whole batch)
+    double *loss;            // LOSS: += sum d^2 inv_count
+    float *colsum;           // LOSS, BWD: += column sums of the gradient
+    int64_t part_stride;     // PART: floats between the splits' partial outputs
     int *err;
-    long long wait_limit;   // polls of a per-stage mbarrier wait
-    int wait_unmet;         // test mode: one more wait on a phase that nothing completes
+    long long wait_limit;    // polls of a bounded wait
+    int wait_unmet;          // test mode: one more wait on a phase that nothing completes
 };
 
-constexpr int kGemmThreads = 256;
-constexpr int kTM = 128;                 // tile rows (tensor-memory lanes, the MMA's M)
-constexpr int kKS = 32;                  // K per stage: two MMAs of K = 16
-constexpr uint32_t kRowBytes = kKS * 2;  // bytes of one operand row in a stage (bf16)
-constexpr uint32_t kSBO = 4 * 128;       // bytes between 8-row core-matrix groups
+constexpr int kGemmThreads = 192;       // warp 0 loads (TMA), warp 1 issues MMAs, warps 2-5 epilogue
+constexpr int kBM = 128;                // tile rows (tensor-memory lanes, the MMA's M)
+constexpr int kBK = 64;                 // K per stage: one 128-byte swizzle row of bf16
+constexpr int kStages = 4;
+constexpr uint32_t kATile = kBM * kBK * 2;
+constexpr uint32_t kMNBox = 64 * kBK * 2;   // one 64 (MN) x 64 (K) box of an MN-major operand
 
-// One CTA per (NT-column, 128-row) tile of C.  A stage holds the tile's 128 A rows
-// and NT B columns for kKS values of K as bf16 in the canonical no-swizzle
-// K-major layout (16-byte core-matrix rows, core matrices 128 bytes apart along K
-// and kSBO apart across 8-row groups); stages are double-buffered (the next one
-// is loaded into registers while the tensor cores read the current one), one
-// thread issues the MMAs and commits them to the stage's mbarrier, and every
-// wait is bounded: a timeout latches DEV_ERR_TIMEOUT, waits for the MMAs in
-// flight, releases the tensor memory and returns.
+__device__ __forceinline__ void ld16f(const float *p, float (&v)[16], int nval, int vec)
+{
+    if (nval == 16 && vec == 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + q);
+            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+        }
+    } else if (nval == 16 && vec == 2) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float2 t = __ldg(reinterpret_cast<const float2 *>(p) + q);
+            v[2 * q] = t.x; v[2 * q + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = j < nval ? __ldg(p + j) : 0.f;
+    }
+}
+
+__device__ __forceinline__ void st16f(float *p, const float (&v)[16], int nval, int vec)
+{
+    if (nval == 16 && vec == 4) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            reinterpret_cast<float4 *>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if (nval == 16 && vec == 2) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) reinterpret_cast<float2 *>(p)[q] = make_float2(v[2 * q], v[2 * q + 1]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nval) p[j] = v[j];
+    }
+}
+
+// 16 bf16 at a 32-byte-aligned position (rows padded to multiples of 8, tiles of 16 columns)
+__device__ __forceinline__ void st16b(__nv_bfloat16 *p, const float (&v)[16], int nval)
+{
+    if (nval == 16) {
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const __nv_bfloat162 t = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+            w[q] = *reinterpret_cast<const uint32_t *>(&t);
+        }
+        reinterpret_cast<uint4 *>(p)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        reinterpret_cast<uint4 *>(p)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (j < nval) p[j] = __float2bfloat16_rn(v[j]);
+    }
+}
+
+// Column sums of a warp's 32 rows x 16 columns: a halving butterfly leaves the sum of
+// column (lane >> 1) in lanes 2c and 2c + 1 (16 shuffles instead of 80)
+__device__ __forceinline__ float colsum16(const float (&v)[16], int lane)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    float a[8], b[4], c[2], d;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float keep = h4 ? v[j + 8] : v[j], send = h4 ? v[j] : v[j + 8];
+        a[j] = keep + __shfl_xor_sync(FULL, send, 16);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float keep = h3 ? a[j + 4] : a[j], send = h3 ? a[j] : a[j + 4];
+        b[j] = keep + __shfl_xor_sync(FULL, send, 8);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float keep = h2 ? b[j + 2] : b[j], send = h2 ? b[j] : b[j + 2];
+        c[j] = keep + __shfl_xor_sync(FULL, send, 4);
+    }
+    {
+        const float keep = h1 ? c[1] : c[0], send = h1 ? c[0] : c[1];
+        d = keep + __shfl_xor_sync(FULL, send, 2);
+    }
+    return d + __shfl_xor_sync(FULL, d, 1);
+}
+
+// One 16-column chunk of the epilogue for this thread's row.
 template <int EPI>
-__global__ void __launch_bounds__(kGemmThreads, 2) k_gemm_tc(const GemmArgs g)
+__device__ __forceinline__ void epi_chunk(const GemmArgs &g, int row, bool rv, int n0, int split, float (&v)[16],
+                                          float &lsum, int lane)
+{
+    const int nval = min(16, g.N - n0);
+    if (EPI == EPI_PART) {
+        if (rv) st16f(g.out_f + split * g.part_stride + (int64_t)row * g.ld_f + n0, v, nval, g.vec_f);
+        return;
+    }
+    if (EPI == EPI_HID || EPI == EPI_PRED || EPI == EPI_LOSS) {
+        float b[16];
+        ld16f(g.bias + n0, b, nval, g.vec_bias);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] += b[j];
+    }
+    if (EPI == EPI_HID) {
+        if (rv) {
+            if (g.out_f) st16f(g.out_f + (int64_t)row * g.ld_f + n0, v, nval, g.vec_f);
+            float a[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = silu(v[j]);
+            st16b(g.out_b + (int64_t)row * g.ld_b + n0, a, nval);
+        }
+        return;
+    }
+    if (EPI == EPI_PRED) {
+        if (rv) {
+            float mu[16], sd[16];
+            ld16f(g.mean + n0, mu, nval, 4);
+            ld16f(g.sd + n0, sd, nval, 4);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = fmaf(v[j], sd[j], mu[j]);
+            st16f(g.out_f + (int64_t)row * g.ld_f + n0, v, nval, g.vec_f);
+        }
+        return;
+    }
+    // LOSS, BWD: the gradient, zero on rows past M
+    float gr[16];
+    if (EPI == EPI_LOSS) {
+        float t[16], mu[16], sd[16];
+        if (rv) ld16f(g.in_f + (int64_t)row * g.ld_in + n0, t, nval, g.vec_in);
+        ld16f(g.mean + n0, mu, nval, 4);
+        ld16f(g.sd + n0, sd, nval, 4);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const float d = (rv && j < nval) ? v[j] - (t[j] - mu[j]) / sd[j] : 0.f;
+            gr[j] = g.gscale * d;
+            lsum = fmaf(d, d, lsum);
+        }
+    } else {
+        float z[16];
+        if (rv) ld16f(g.in_f + (int64_t)row * g.ld_in + n0, z, nval, g.vec_in);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) gr[j] = (rv && j < nval) ? v[j] * silu_grad(z[j]) : 0.f;
+    }
+    if (rv) st16b(g.out_b + (int64_t)row * g.ld_b + n0, gr, nval);
+    const float cs = colsum16(gr, lane);
+    if (!(lane & 1) && (lane >> 1) < nval) atomicAdd(g.colsum + n0 + (lane >> 1), cs);
+}
+
+// Persistent, warp-specialised tcgen05 GEMM: C[m][n] = sum_k A(m, k) B(n, k) in
+// 128 x NT tiles (work units: K splits x row tiles x column tiles, taken by the
+// CTAs in turn).  Warp 0 (one thread) loads 64-wide K blocks of A and B with TMA
+// into a ring of kStages 128-byte-swizzled stages (K-major operands: one box of
+// 64 K x rows; MN-major operands: boxes of 64 MN x 64 K), completing each
+// stage's `full` barrier; warp 1 (one thread) issues four K = 16 MMAs per stage
+// into one of two tensor-memory accumulators and commits them to the stage's
+// `empty` barrier and, after a unit's last stage, to the accumulator's `tfull`
+// barrier; warps 2-5 read the accumulator (one 32-lane quarter each), run the
+// epilogue and release it through `tempty`, so the epilogue of one unit overlaps
+// the products of the next.  Every wait is bounded: a role that gives up raises
+// the CTA's abort flag, the others stop, the loads and products in flight are
+// waited for (long bound) before the tensor memory is released, and the kernel
+// latches DEV_ERR_TIMEOUT.
+template <int EPI>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_gemm(const __grid_constant__ CUtensorMap tma_a, const __grid_constant__ CUtensorMap tma_b, const GemmArgs g)
 {
     using namespace tpcf::tc;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * g.NT;
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw_s = smem_u32(smem_raw);
+    unsigned char *smem = smem_raw + ((1024u - (raw_s & 1023u)) & 1023u);   // swizzled tiles: 1024-byte aligned
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NT = g.NT;
-    const uint32_t a_bytes = kTM * kRowBytes, stage_bytes = a_bytes + (uint32_t)NT * kRowBytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * stage_bytes);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * stage_bytes + 16);
-    volatile int *s_abort = reinterpret_cast<int *>(smem + 2 * stage_bytes + 20);
+    const uint32_t stage_bytes = kATile + (uint32_t)NT * kBK * 2;
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * stage_bytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *tfull = empty + kStages;
+    uint64_t *tempty = tfull + 2;
+    uint64_t *done = tempty + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *s_abort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    const uint32_t tmem_cols = 2u * (uint32_t)NT;
 
-    if (tid == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], 4);
+        }
+        mbar_init(done, 1);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(g.tmem_cols));
+                     "r"(tmem_cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
+    const int per_split = g.n_mt * g.n_nt;
 
-    // staging, per operand: 16-byte loads of 8 consecutive K values straight into a
-    // core-matrix row when the operand is contiguous in K with aligned rows
-    // (consecutive threads take consecutive octets of a row), otherwise one bf16
-    // at a time with the lanes along whichever index is contiguous in memory
-    // (every warp load one coalesced run)
-    const bool a_kc = g.sak == 1, b_kc = g.sbk == 1;
-    const int k_beg = blockIdx.z * g.k_per, k_end = min(g.K, k_beg + g.k_per);
-    const int nbe = NT / 8;                      // scalar B elements per thread (NT x kKS / 256)
-    const int nbu = NT * 4;                      // 16-byte B units (NT rows x 4 octets)
-    uint4 va[2], vb[4];
-    __nv_bfloat16 sa[16], sb[32];
-    auto cm_off = [](int r, int k) -> uint32_t {   // byte offset of element (r, k) in an operand tile
-        return (uint32_t)(((r >> 3) * 4 + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2);
-    };
-    const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
-    auto load = [&](int st) {
-        const int k0 = k_beg + st * kKS;
-        if (g.a_vec) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int u = tid + kGemmThreads * q, r = u >> 2, k = k0 + 8 * (u & 3), m = m0 + r;
-                va[q] = (m < g.M && k < k_end) ? __ldg(reinterpret_cast<const uint4 *>(g.A + m * g.sam + k))
-                                                : make_uint4(0u, 0u, 0u, 0u);
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                int r, k;
-                if (a_kc) { r = (tid >> 5) + 8 * e; k = lane; }
-                else { r = tid & (kTM - 1); k = (tid >> 7) + 2 * e; }
-                const int m = m0 + r;
-                k += k0;
-                sa[e] = (m < g.M && k < k_end) ? g.A[m * g.sam + k * g.sak] : zero;
-            }
-        }
-        if (g.b_vec) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int u = tid + kGemmThreads * q, nn = u >> 2, k = k0 + 8 * (u & 3), n = n0 + nn;
-                vb[q] = (u < nbu && n < g.N && k < k_end)
-                            ? __ldg(reinterpret_cast<const uint4 *>(g.B + n * g.sbn + k))
-                            : make_uint4(0u, 0u, 0u, 0u);
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                if (e >= nbe) break;
-                int nn, k;
-                if (b_kc) { nn = (tid >> 5) + 8 * e; k = lane; }
-                else { nn = tid % NT; k = tid / NT + (kGemmThreads / NT) * e; }
-                const int n = n0 + nn;
-                k += k0;
-                sb[e] = (n < g.N && k < k_end) ? g.B[k * g.sbk + n * g.sbn] : zero;
-            }
-        }
-    };
-    auto store = [&](int buf) {
-        unsigned char *stg = smem + buf * stage_bytes;
-        if (g.a_vec) {
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const int u = tid + kGemmThreads * q;
-                *reinterpret_cast<uint4 *>(stg + cm_off(u >> 2, 8 * (u & 3))) = va[q];
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) {
-                int r, k;
-                if (a_kc) { r = (tid >> 5) + 8 * e; k = lane; }
-                else { r = tid & (kTM - 1); k = (tid >> 7) + 2 * e; }
-                *reinterpret_cast<__nv_bfloat16 *>(stg + cm_off(r, k)) = sa[e];
-            }
-        }
-        if (g.b_vec) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int u = tid + kGemmThreads * q;
-                if (u < nbu) *reinterpret_cast<uint4 *>(stg + a_bytes + cm_off(u >> 2, 8 * (u & 3))) = vb[q];
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-                if (e >= nbe) break;
-                int nn, k;
-                if (b_kc) { nn = (tid >> 5) + 8 * e; k = lane; }
-                else { nn = tid % NT; k = tid / NT + (kGemmThreads / NT) * e; }
-                *reinterpret_cast<__nv_bfloat16 *>(stg + a_bytes + cm_off(nn, k)) = sb[e];
-            }
-        }
-    };
-
-    const int nst = k_end > k_beg ? (k_end - k_beg + kKS - 1) / kKS : 0;
-    uint32_t phase[2] = {0u, 0u};
-    bool used[2] = {false, false};
-    bool ok = true;
-    const uint32_t idesc = make_idesc(1u, kTM, NT);
-    if (nst > 0) load(0);
-    for (int st = 0; st < nst; ++st) {
-        const int b = st & 1;
-        // the MMAs that last read this buffer must have completed
-        if (tid == 0 && used[b] && !mbar_wait(&bars[b], phase[b] ^ 1u, g.wait_limit)) *s_abort = 1;
-        __syncthreads();
-        if (*s_abort) { ok = false; break; }
-        store(b);
-        if (st + 1 < nst) load(st + 1);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t base = smem_u32(smem + b * stage_bytes);
-#pragma unroll
-            for (int ks = 0; ks < kKS / 16; ++ks) {
-                const uint64_t da = make_desc(base + 256u * ks, 128, kSBO);
-                const uint64_t db = make_desc(base + a_bytes + 256u * ks, 128, kSBO);
-                mma_issue<false>(tmem, da, db, idesc, (st > 0 || ks > 0) ? 1u : 0u);
-            }
-            mma_commit(&bars[b]);
-        }
-        used[b] = true;
-        phase[b] ^= 1u;
-    }
-    // the last MMAs: every buffer's latest commit
-    if (ok && tid == 0) {
-        for (int b = 0; b < 2; ++b)
-            if (used[b] && !mbar_wait(&bars[b], phase[b] ^ 1u, g.wait_limit)) *s_abort = 1;
-        // test mode: buffer 0's next phase, which no commit completes
-        if (g.wait_unmet && !*s_abort && !mbar_wait(&bars[0], phase[0], g.wait_limit)) *s_abort = 1;
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (*s_abort) ok = false;
-    if (ok && nst > 0) {
-        // warp w reads tensor-memory lanes 32 (w % 4) ..; the two warps of a lane
-        // quarter take alternate 16-column chunks
-        const int quarter = warp & 3, set = warp >> 2;
-        const int row = m0 + 32 * quarter + lane;
-        for (int c0 = 16 * set; c0 < NT; c0 += 32) {
-            float v[16];
-            tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c0, v);
-            if (row < g.M) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int n = n0 + c0 + j;
-                    if (n >= g.N) break;
-                    float z = v[j];
-                    if (EPI != EPI_STORE) z += __ldg(g.bias + n);
-                    if (EPI == EPI_STORE && g.split) atomicAdd(g.C + row * g.ldc + n, z);
-                    else g.C[row * g.ldc + n] = z;
-                    if (EPI == EPI_BIAS_SILU) g.act[row * g.ld_act + n] = __float2bfloat16_rn(silu(z));
+    if (warp == 0 && lane == 0) {
+        // ---- loads
+        uint32_t it = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+            const int sp = u / per_split, r = u % per_split, mt = r / g.n_nt, nt = r % g.n_nt;
+            const int kb0 = sp * g.kper, kb1 = min(g.nkb, kb0 + g.kper);
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const int s = (int)(it % kStages);
+                const uint32_t ph = (it / kStages) & 1u;
+                if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, g.wait_limit, s_abort)) {
+                    *s_abort = 1;
+                    ok = false;
+                    break;
+                }
+                unsigned char *sa = smem + s * stage_bytes, *sb = sa + kATile;
+                mbar_expect_tx(&full[s], stage_bytes);
+                const int k0 = kb * kBK;
+                if (!g.a_mn) {
+                    tma_load_2d(sa, &tma_a, k0, mt * kBM, &full[s]);
+                } else {
+                    tma_load_2d(sa, &tma_a, mt * kBM, k0, &full[s]);
+                    tma_load_2d(sa + kMNBox, &tma_a, mt * kBM + 64, k0, &full[s]);
+                }
+                if (!g.b_mn) {
+                    tma_load_2d(sb, &tma_b, k0, nt * NT, &full[s]);
+                } else {
+                    for (int h = 0; h < NT / 64; ++h) tma_load_2d(sb + h * kMNBox, &tma_b, nt * NT + 64 * h, k0, &full[s]);
                 }
             }
         }
-    } else if (!ok && tid == 0) {
-        if (g.err) atomicCAS(g.err, 0, tpcf::DEV_ERR_TIMEOUT);
-        // wait (on the long bound) for anything still in flight before releasing TMEM
-        for (int b = 0; b < 2; ++b)
-            if (used[b]) mbar_wait(&bars[b], phase[b] ^ 1u);
+        if (!ok) {
+            // the loads issued must land before the CTA's shared memory goes away
+            for (int s = 0; s < kStages; ++s)
+                if (it > (uint32_t)s) {
+                    const uint32_t j = ((it - 1u - (uint32_t)s) / kStages) * kStages + (uint32_t)s;
+                    mbar_wait(&full[s], (j / kStages) & 1u);
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---- products
+        uint32_t it = 0, tc = 0;
+        bool ok = true, any = false;
+        const uint32_t idesc = make_idesc_major(1u, kBM, NT, g.a_mn, g.b_mn);
+        for (int u = blockIdx.x; u < g.units && ok; u += gridDim.x) {
+            const int sp = u / per_split;
+            const int kb0 = sp * g.kper, kb1 = min(g.nkb, kb0 + g.kper);
+            const uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
+            if (!mbar_wait_or_abort(&tempty[acc], aph ^ 1u, g.wait_limit, s_abort)) {
+                *s_abort = 1;
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t d_tmem = tmem + acc * (uint32_t)NT;
+            for (int kb = kb0; kb < kb1; ++kb, ++it) {
+                const int s = (int)(it % kStages);
+                const uint32_t ph = (it / kStages) & 1u;
+                if (!mbar_wait_or_abort(&full[s], ph, g.wait_limit, s_abort)) {
+                    *s_abort = 1;
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa = smem_u32(smem + s * stage_bytes), sb = sa + kATile;
+#pragma unroll
+                for (int k = 0; k < kBK / 16; ++k) {
+                    const uint64_t da = g.a_mn ? make_desc_sw128(sa + 2048u * k, kMNBox, 1024)
+                                               : make_desc_sw128(sa + 32u * k, 16, 1024);
+                    const uint64_t db = g.b_mn ? make_desc_sw128(sb + 2048u * k, kMNBox, 1024)
+                                               : make_desc_sw128(sb + 32u * k, 16, 1024);
+                    mma_issue<false>(d_tmem, da, db, idesc, (kb > kb0 || k > 0) ? 1u : 0u);
+                }
+                mma_commit(&empty[s]);
+                any = true;
+            }
+            if (!ok) break;
+            mma_commit(&tfull[acc]);
+            ++tc;
+        }
+        // every product issued completes before the accumulators are released
+        if (any) {
+            mma_commit(done);
+            mbar_wait(done, 0u);
+        }
+        // test mode: a phase of `done` that no commit completes
+        if (g.wait_unmet && ok && !mbar_wait(done, any ? 1u : 0u, g.wait_limit)) *s_abort = 1;
+    } else if (warp >= 2) {
+        // ---- epilogue
+        const int q = warp & 3;   // tensor-memory lane quarter of this warp
+        uint32_t tc = 0;
+        float lsum = 0.f;
+        for (int u = blockIdx.x; u < g.units; u += gridDim.x) {
+            const int sp = u / per_split, r = u % per_split, mt = r / g.n_nt, nt = r % g.n_nt;
+            const uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
+            // one poller per warp: the warp's tensor-memory loads below are collective
+            int okw = 1;
+            if (lane == 0) okw = mbar_wait_or_abort(&tfull[acc], aph, g.wait_limit, s_abort) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) {
+                if (lane == 0) *s_abort = 1;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = mt * kBM + 32 * q + lane;
+            const bool rv = row < g.M;
+            for (int c0 = 0; c0 < NT; c0 += 16) {
+                const int n0 = nt * NT + c0;
+                if (n0 >= g.N) break;
+                float v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + acc * (uint32_t)NT + (uint32_t)c0, v);
+                epi_chunk<EPI>(g, row, rv, n0, sp, v, lsum, lane);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+            ++tc;
+        }
+        if (EPI == EPI_LOSS) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            if (lane == 0 && g.loss && lsum != 0.f) atomicAdd(g.loss, (double)lsum * (double)g.inv_count);
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(g.tmem_cols));
+    if (threadIdx.x == 0 && *s_abort && g.err) atomicCAS(g.err, 0, tpcf::DEV_ERR_TIMEOUT);
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+}
+
+// grads[i][o] += sum over splits of the partial weight gradients ws[split][i][ldw]
+__global__ void k_reduce_parts(const float *__restrict__ ws, int splits, int64_t stride, int in, int out, int ldw,
+                               float *__restrict__ grads)
+{
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)in * out;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / out), o = (int)(idx % out);
+        float s = 0.f;
+        for (int sp = 0; sp < splits; ++sp) s += ws[sp * stride + (int64_t)i * ldw + o];
+        grads[idx] += s;
+    }
 }
 
 // scaled inputs 2 (x - lo) / (hi - lo) - 1 as bf16 rows of stride ld (padding stays zero)
@@ -303,71 +470,6 @@ __global__ void k_col_stats(const float *__restrict__ y, int64_t n, int w, float
     const double var = n > 1 ? fmax(s2 / n - mu * mu, 0.0) : 0.0;
     mean[c] = (float)mu;
     sd[c] = (float)(var > 0.0 ? sqrt(var) : 1.0);
-}
-
-// dY = 2 (yhat - (y - mean) / sd) / (rows * w); loss += mean squared error; dY also
-// as bf16 rows of stride ld (the products' operand)
-__global__ void k_loss_grad(const float *__restrict__ yhat, const float *__restrict__ y, int64_t rows, int w,
-                            const float *__restrict__ mean, const float *__restrict__ sd, double inv_count,
-                            float *__restrict__ dy, __nv_bfloat16 *__restrict__ dyb, int ld, double *__restrict__ loss)
-{
-    __shared__ double red[8];
-    double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * w;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % w);
-        const float d = yhat[i] - (y[i] - mean[c]) / sd[c];
-        const float g = (float)(2.0 * inv_count) * d;
-        dy[i] = g;
-        dyb[(i / w) * ld + c] = __float2bfloat16_rn(g);
-        s += (double)d * d;
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0 && loss) {
-        double t = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) t += red[q];
-        atomicAdd(loss, t * inv_count);
-    }
-}
-
-// d *= SiLU'(z) over rows x w, and the result as bf16 rows of stride ld
-__global__ void k_silu_back(const float *__restrict__ z, float *__restrict__ d, int64_t rows, int w,
-                            __nv_bfloat16 *__restrict__ db, int ld)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * w;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = d[i] * silu_grad(z[i]);
-        d[i] = v;
-        db[(i / w) * ld + (int)(i % w)] = __float2bfloat16_rn(v);
-    }
-}
-
-// db[c] (+)= sum over rows of d[r][c]; one thread per column
-__global__ void k_col_sum(const float *__restrict__ d, int64_t rows, int w, float *__restrict__ db, int accumulate)
-{
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= w) return;
-    float s = 0.f;
-    for (int64_t r = 0; r < rows; ++r) s += d[r * w + c];
-    db[c] = accumulate ? db[c] + s : s;
-}
-
-__global__ void k_add(float *__restrict__ a, const float *__restrict__ b, int64_t n)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        a[i] += b[i];
-}
-
-__global__ void k_unscale_out(const float *__restrict__ yhat, int64_t rows, int w, const float *__restrict__ mean,
-                              const float *__restrict__ sd, float *__restrict__ y)
-{
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows * w;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int c = (int)(i % w);
-        y[i] = yhat[i] * sd[c] + mean[c];
-    }
 }
 
 __global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
@@ -421,18 +523,20 @@ struct tpcf_emu_s {
     int widths[kMaxLayers + 1] = {0};
     Layer layers[kMaxLayers];
     int64_t n_params = 0;
-    int maxw = 0, maxw8 = 0;
+    int maxw8 = 0;
     float *params = nullptr, *grads = nullptr, *m = nullptr, *v = nullptr;
     float *in_lo = nullptr, *in_hi = nullptr, *out_mean = nullptr, *out_sd = nullptr;
-    // bf16 operands of the products, rows padded to multiples of 8 (padding zero)
-    __nv_bfloat16 *wT[kMaxLayers] = {nullptr};   // [out][ldi] transposed weights
-    __nv_bfloat16 *wP[kMaxLayers] = {nullptr};   // [in][ldo] weights
-    __nv_bfloat16 *xs = nullptr;                 // scaled inputs [kChunk][ldi of layer 0]
-    __nv_bfloat16 *act[kMaxLayers] = {nullptr};  // hidden activations [kChunk][ldo]
-    __nv_bfloat16 *db = nullptr;                 // output gradient of the current layer [kChunk][maxw8]
-    float *Z[kMaxLayers] = {nullptr};            // pre-activations [kChunk][out] (FP32)
-    float *d0 = nullptr, *d1 = nullptr;          // gradient ping-pong [kChunk][maxw] (FP32)
-    float *gtmp = nullptr;                       // per-chunk gradient [n_params]
+    // bf16 weight copies (rows padded to multiples of 8): the products' B operands
+    __nv_bfloat16 *wT[kMaxLayers] = {nullptr};   // [out][ldi]: forward, contiguous in the input index
+    __nv_bfloat16 *wP[kMaxLayers] = {nullptr};   // [in][ldo]: backward, contiguous in the output index
+    float *ws = nullptr;                         // split-K partial weight gradients
+    int64_t ws_floats = 0;
+    // per-chunk buffers for `cap` rows (grown on demand up to kMaxChunk)
+    int64_t cap = 0;
+    __nv_bfloat16 *xs = nullptr;                 // scaled inputs [cap][ldi of layer 0]
+    __nv_bfloat16 *act[kMaxLayers] = {nullptr};  // hidden activations [cap][ldo]
+    float *Z[kMaxLayers] = {nullptr};            // hidden pre-activations [cap][ldo] (FP32)
+    __nv_bfloat16 *gA = nullptr, *gB = nullptr;  // output-gradient ping-pong [cap][maxw8]
     int64_t step = 0;
 };
 
@@ -449,74 +553,113 @@ int emu_cuda(cudaError_t e)
         if (e_ != cudaSuccess) return emu_cuda(e_);      \
     } while (0)
 
-template <int EPI>
-cudaError_t gemm(const __nv_bfloat16 *A, int64_t sam, int64_t sak, const __nv_bfloat16 *B, int64_t sbk, int64_t sbn,
-                 int M, int N, int K, float *C, int64_t ldc, const float *bias, __nv_bfloat16 *act, int64_t ld_act,
-                 cudaStream_t st)
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry-point query
+// (the library does not link the driver library itself)
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encoder()
 {
-    if (M <= 0 || N <= 0) return cudaSuccess;
-    GemmArgs g;
-    g.A = A;
-    g.sam = sam;
-    g.sak = sak;
-    g.B = B;
-    g.sbk = sbk;
-    g.sbn = sbn;
-    g.M = M;
-    g.N = N;
-    g.K = K;
-    g.C = C;
-    g.ldc = ldc;
-    g.bias = bias;
-    g.act = act;
-    g.ld_act = ld_act;
-    auto aligned16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-    g.a_vec = sak == 1 && sam % 8 == 0 && aligned16(A);
-    g.b_vec = sbk == 1 && sbn % 8 == 0 && aligned16(B);
-    // tile width: 256 columns for wide outputs; narrow ones (hidden layers) in tiles
-    // of at most 64 so that their few row tiles still spread over the SMs (a power
-    // of two from 16 to 256: the staging map needs NT to divide 256)
-    g.NT = 256;
-    if (N <= 256) {
-        g.NT = 16;
-        while (g.NT < 64 && g.NT < N) g.NT <<= 1;
+    static std::once_flag once;
+    static EncodeTiled f = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            f = reinterpret_cast<EncodeTiled>(p);
+    });
+    return f;
+}
+
+// 2D bf16 tensor map: `inner` contiguous elements, `outer` rows `ld` elements apart
+// (a multiple of 8), boxes of 64 x box_outer with the 128-byte swizzle; reads
+// outside the extents return zeros
+cudaError_t make_tmap(CUtensorMap *m, const void *base, int64_t inner, int64_t outer, int64_t ld, int box_outer)
+{
+    const EncodeTiled f = encoder();
+    if (!f) return cudaErrorNotSupported;
+    if (((uintptr_t)base & 15u) || (ld * 2) % 16 || inner < 1 || outer < 1) return cudaErrorInvalidValue;
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+    const cuuint32_t box[2] = {64u, (cuuint32_t)box_outer};
+    const cuuint32_t es[2] = {1u, 1u};
+    const CUresult r = f(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// widest float vector (4, 2 or 1) for rows starting at p, ld floats apart
+int vec_of(const void *p, int64_t ld)
+{
+    const uintptr_t a = (uintptr_t)p;
+    if (a % 16 == 0 && ld % 4 == 0) return 4;
+    if (a % 8 == 0 && ld % 2 == 0) return 2;
+    return 1;
+}
+
+// A bf16 operand: element (mn, k) at p[mn + k ld] when MN-major, p[k + mn ld] when K-major
+struct Operand {
+    const __nv_bfloat16 *p;
+    int64_t ld;
+    int mn;
+};
+
+// C = A B^T through k_gemm<EPI>; g carries M, N, K and the epilogue's fields.  For
+// EPI_PART the K range is split over up to max_splits partial outputs (g.out_f, rows
+// g.ld_f apart, M rows per split) and the number of splits is returned in *splits.
+template <int EPI>
+cudaError_t gemm(GemmArgs g, Operand A, Operand B, cudaStream_t st, int max_splits = 1, int *splits = nullptr)
+{
+    if (splits) *splits = 0;
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+    const int sms = tpcf::sm_count();
+    auto tiles = [&](int nt) { return ((g.M + kBM - 1) / kBM) * ((g.N + nt - 1) / nt); };
+    // tile width: 256 unless narrower tiles are needed to spread the units over the SMs
+    int NT = 256;
+    while (NT > 64 && (NT / 2 >= g.N || tiles(NT) < 2 * sms)) NT >>= 1;
+    g.NT = NT;
+    g.n_mt = (g.M + kBM - 1) / kBM;
+    g.n_nt = (g.N + NT - 1) / NT;
+    g.nkb = (g.K + kBK - 1) / kBK;
+    int sp = 1;
+    if (EPI == EPI_PART) {
+        const int t = g.n_mt * g.n_nt;
+        sp = std::max(1, std::min({(2 * sms + t - 1) / t, g.nkb / 4, max_splits}));
     }
-    g.tmem_cols = 32;
-    while (g.tmem_cols < g.NT) g.tmem_cols <<= 1;
+    g.kper = (g.nkb + sp - 1) / sp;
+    sp = (g.nkb + g.kper - 1) / g.kper;
+    g.units = sp * g.n_mt * g.n_nt;
+    if (EPI == EPI_PART) g.part_stride = (int64_t)g.M * g.ld_f;
+    if (splits) *splits = sp;
+    g.a_mn = A.mn;
+    g.b_mn = B.mn;
     g.err = tpcf::device_error_flag();
     g.wait_limit = tpcf::device_wait_limit();
     g.wait_unmet = tpcf::device_wait_unmet();
-    // split K when the output has too few tiles to fill the SMs (the weight
-    // gradients: 256 x 256 outputs over thousands of rows); the splits' tiles
-    // are added into the zeroed output with FP32 atomics
-    const int tiles = ((N + g.NT - 1) / g.NT) * ((M + kTM - 1) / kTM);
-    const int nst = (K + kKS - 1) / kKS;
-    int splits = 1;
-    if (EPI == EPI_STORE && tiles < 2 * tpcf::sm_count()) {
-        splits = (2 * tpcf::sm_count() + tiles - 1) / tiles;
-        splits = std::max(1, std::min(splits, nst / 4));
-    }
-    g.k_per = ((nst + splits - 1) / splits) * kKS;
-    splits = (K + g.k_per - 1) / g.k_per;
-    g.split = splits > 1 ? 1 : 0;
-    if (g.split) {
-        cudaError_t e = cudaMemsetAsync(C, 0, (size_t)M * ldc * sizeof(float), st);
-        if (e != cudaSuccess) return e;
-    }
-    // two stages and the barriers; enough that the CTAs sharing an SM never ask for
-    // more than its 512 tensor-memory columns (allocations never wait)
-    size_t smem = 2 * ((size_t)kTM + g.NT) * kRowBytes + 64;
-    const size_t floor_bytes = (size_t)(228 * 1024) / (512 / g.tmem_cols + 1) + 1024;
-    if (smem < floor_bytes) smem = floor_bytes;
+    CUtensorMap ta, tb;
+    cudaError_t e = A.mn ? make_tmap(&ta, A.p, g.M, g.K, A.ld, 64) : make_tmap(&ta, A.p, g.K, g.M, A.ld, kBM);
+    if (e != cudaSuccess) return e;
+    e = B.mn ? make_tmap(&tb, B.p, g.N, g.K, B.ld, 64) : make_tmap(&tb, B.p, g.K, g.N, B.ld, NT);
+    if (e != cudaSuccess) return e;
+    const size_t smem = (size_t)kStages * (kATile + (size_t)NT * kBK * 2) + 256 + 1024;
     static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
     const unsigned long long bit = tpcf::device_bit();
     if (!(attr_done.load(std::memory_order_acquire) & bit)) {
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+        e = cudaFuncSetAttribute(k_gemm<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return e;
         attr_done.fetch_or(bit, std::memory_order_acq_rel);
     }
-    const dim3 grid((N + g.NT - 1) / g.NT, (M + kTM - 1) / kTM, splits);
-    k_gemm_tc<EPI><<<grid, kGemmThreads, smem, st>>>(g);
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gemm<EPI>, kGemmThreads, smem);
+    if (e != cudaSuccess) return e;
+    // co-resident CTAs never ask for more than the SM's 512 tensor-memory columns
+    per_sm = std::max(1, std::min(per_sm, 512 / (2 * NT)));
+    const int grid = std::min(g.units, sms * per_sm);
+    k_gemm<EPI><<<grid, kGemmThreads, smem, st>>>(ta, tb, g);
     tpcf::note_launch();
     return cudaGetLastError();
 }
@@ -533,81 +676,163 @@ cudaError_t weight_copies(tpcf_emu e, cudaStream_t st)
     return cudaGetLastError();
 }
 
-// forward pass of rows [0, rows) of the scaled inputs already in e->xs
-cudaError_t forward(tpcf_emu e, int64_t rows, cudaStream_t st)
+void free_chunk_buffers(tpcf_emu e)
 {
-    const __nv_bfloat16 *in = e->xs;
-    int ld_in = e->layers[0].ldi;
+    for (void *p : {(void *)e->xs, (void *)e->gA, (void *)e->gB})
+        if (p) cudaFree(p);
+    e->xs = nullptr;
+    e->gA = e->gB = nullptr;
+    for (int l = 0; l < kMaxLayers; ++l) {
+        if (e->act[l]) cudaFree(e->act[l]);
+        if (e->Z[l]) cudaFree(e->Z[l]);
+        e->act[l] = nullptr;
+        e->Z[l] = nullptr;
+    }
+    e->cap = 0;
+}
+
+// per-chunk buffers for at least `rows` rows (at most kMaxChunk); synchronises the
+// stream when they grow
+int ensure_cap(tpcf_emu e, int64_t rows, cudaStream_t st)
+{
+    rows = std::min<int64_t>(std::max<int64_t>(rows, 1), kMaxChunk);
+    if (e->cap >= rows) return TPCF_OK;
+    const int64_t cap = std::min<int64_t>(kMaxChunk, std::max<int64_t>((rows + 127) / 128 * 128, 2 * e->cap));
+    ECK(cudaStreamSynchronize(st));
+    free_chunk_buffers(e);
+    const size_t bf = sizeof(__nv_bfloat16);
+    cudaError_t err = cudaMalloc((void **)&e->xs, (size_t)cap * e->layers[0].ldi * bf);
+    for (int l = 0; l + 1 < e->nl && err == cudaSuccess; ++l) {
+        const Layer &L = e->layers[l];
+        err = cudaMalloc((void **)&e->act[l], (size_t)cap * L.ldo * bf);
+        if (err == cudaSuccess) err = cudaMalloc((void **)&e->Z[l], (size_t)cap * L.ldo * sizeof(float));
+    }
+    if (err == cudaSuccess) err = cudaMalloc((void **)&e->gA, (size_t)cap * e->maxw8 * bf);
+    if (err == cudaSuccess) err = cudaMalloc((void **)&e->gB, (size_t)cap * e->maxw8 * bf);
+    if (err != cudaSuccess) {
+        free_chunk_buffers(e);
+        return emu_cuda(err);
+    }
+    e->cap = cap;
+    return TPCF_OK;
+}
+
+// forward pass of `rows` rows of the scaled inputs in e->xs.  Inference writes the
+// unscaled outputs to y_out (rows w_out apart); training keeps the hidden
+// pre-activations and turns the output layer into the loss gradient (e->gA) against
+// the targets yt, adding the output bias gradient and the loss.
+cudaError_t forward(tpcf_emu e, int64_t rows, bool training, const float *yt, float *y_out, double *loss,
+                    double inv_count, cudaStream_t st)
+{
+    Operand in = {e->xs, e->layers[0].ldi, 0};
     for (int l = 0; l < e->nl; ++l) {
         const Layer &L = e->layers[l];
-        const float *b = e->params + L.b_off;
-        // Z[r][o] = sum_i in[r][i] W[i][o] + b[o]: A = in (contiguous in i), B(i, o) = wT[o][i]
+        GemmArgs g;
+        std::memset(&g, 0, sizeof(g));
+        g.M = (int)rows;
+        g.N = L.out;
+        g.K = L.in;
+        g.bias = e->params + L.b_off;
+        g.vec_bias = vec_of(g.bias, 4);
+        const Operand W = {e->wT[l], L.ldi, 0};   // B(o, i) = W[i][o], contiguous in i
         cudaError_t err;
-        if (l + 1 < e->nl)
-            err = gemm<EPI_BIAS_SILU>(in, ld_in, 1, e->wT[l], 1, L.ldi, (int)rows, L.out, L.in, e->Z[l], L.out, b,
-                                      e->act[l], L.ldo, st);
-        else
-            err = gemm<EPI_BIAS>(in, ld_in, 1, e->wT[l], 1, L.ldi, (int)rows, L.out, L.in, e->Z[l], L.out, b,
-                                 nullptr, 0, st);
+        if (l + 1 < e->nl) {
+            g.out_b = e->act[l];
+            g.ld_b = L.ldo;
+            g.out_f = training ? e->Z[l] : nullptr;
+            g.ld_f = L.ldo;
+            g.vec_f = vec_of(e->Z[l], L.ldo);
+            err = gemm<EPI_HID>(g, in, W, st);
+            in = {e->act[l], L.ldo, 0};
+        } else {
+            g.mean = e->out_mean;
+            g.sd = e->out_sd;
+            if (training) {
+                g.in_f = yt;
+                g.ld_in = L.out;
+                g.vec_in = vec_of(yt, L.out);
+                g.gscale = (float)(2.0 * inv_count);
+                g.inv_count = (float)inv_count;
+                g.loss = loss;
+                g.colsum = e->grads + L.b_off;
+                g.out_b = e->gA;
+                g.ld_b = L.ldo;
+                err = gemm<EPI_LOSS>(g, in, W, st);
+            } else {
+                g.out_f = y_out;
+                g.ld_f = L.out;
+                g.vec_f = vec_of(y_out, L.out);
+                err = gemm<EPI_PRED>(g, in, W, st);
+            }
+        }
         if (err != cudaSuccess) return err;
-        in = e->act[l];
-        ld_in = L.ldo;
     }
     return cudaSuccess;
 }
 
-// loss gradient of one chunk into g (overwrites), loss added to *loss
-cudaError_t backward_chunk(tpcf_emu e, const float *y, int64_t rows, double inv_count, float *g, double *loss,
-                           cudaStream_t st)
+// backward pass of one chunk from the output-layer gradient in e->gA: weight
+// gradients (split-K partials reduced into e->grads) and, layer by layer, the
+// gradient of the previous layer's pre-activation with its bias gradient
+cudaError_t backward(tpcf_emu e, int64_t rows, cudaStream_t st)
 {
-    const int nl = e->nl, w_out = e->widths[nl];
-    k_loss_grad<<<grid1(rows * w_out), 256, 0, st>>>(e->Z[nl - 1], y, rows, w_out, e->out_mean, e->out_sd,
-                                                      inv_count, e->d0, e->db, e->layers[nl - 1].ldo, loss);
-    tpcf::note_launch();
-    float *dcur = e->d0, *dnext = e->d1;
-    for (int l = nl - 1; l >= 0; --l) {
+    __nv_bfloat16 *gcur = e->gA, *gnext = e->gB;
+    for (int l = e->nl - 1; l >= 0; --l) {
         const Layer &L = e->layers[l];
-        if (l + 1 < nl) {
-            k_silu_back<<<grid1(rows * L.out), 256, 0, st>>>(e->Z[l], dcur, rows, L.out, e->db, L.ldo);
-            tpcf::note_launch();
-        }
         const __nv_bfloat16 *aprev = l > 0 ? e->act[l - 1] : e->xs;
-        const int ld_prev = L.ldi;
-        // dW[i][o] = sum_r aprev[r][i] dZ[r][o]: A(i, r) = aprev[r][i], B(r, o) = db[r][o]
-        cudaError_t err = gemm<EPI_STORE>(aprev, 1, ld_prev, e->db, L.ldo, 1, L.in, L.out, (int)rows,
-                                          g + L.w_off, L.out, nullptr, nullptr, 0, st);
+        // dW[i][o] = sum_r aprev[r][i] g[r][o]: A(i, r) and B(o, r) both MN-major
+        GemmArgs g;
+        std::memset(&g, 0, sizeof(g));
+        g.M = L.in;
+        g.N = L.out;
+        g.K = (int)rows;
+        g.out_f = e->ws;
+        g.ld_f = L.ldo;
+        g.vec_f = 4;
+        int splits = 0;
+        const int max_splits = (int)std::max<int64_t>(1, e->ws_floats / ((int64_t)L.in * L.ldo));
+        cudaError_t err = gemm<EPI_PART>(g, {aprev, L.ldi, 1}, {gcur, L.ldo, 1}, st, max_splits, &splits);
         if (err != cudaSuccess) return err;
-        k_col_sum<<<(L.out + 127) / 128, 128, 0, st>>>(dcur, rows, L.out, g + L.b_off, 0);
+        k_reduce_parts<<<grid1((int64_t)L.in * L.out), 256, 0, st>>>(e->ws, splits, (int64_t)L.in * L.ldo, L.in,
+                                                                     L.out, L.ldo, e->grads + L.w_off);
         tpcf::note_launch();
         if (l > 0) {
-            // dA_prev[r][i] = sum_o dZ[r][o] W[i][o]: A = db (contiguous in o), B(o, i) = wP[i][o]
-            err = gemm<EPI_STORE>(e->db, L.ldo, 1, e->wP[l], 1, L.ldo, (int)rows, L.in, L.out, dnext, L.in, nullptr,
-                                  nullptr, 0, st);
+            // dA_prev[r][i] = sum_o g[r][o] W[i][o], times SiLU'(z_prev): A = g, B(i, o) = wP[i][o]
+            const Layer &Lp = e->layers[l - 1];
+            GemmArgs h;
+            std::memset(&h, 0, sizeof(h));
+            h.M = (int)rows;
+            h.N = L.in;
+            h.K = L.out;
+            h.in_f = e->Z[l - 1];
+            h.ld_in = Lp.ldo;
+            h.vec_in = vec_of(e->Z[l - 1], Lp.ldo);
+            h.out_b = gnext;
+            h.ld_b = Lp.ldo;
+            h.colsum = e->grads + Lp.b_off;
+            err = gemm<EPI_BWD>(h, {gcur, L.ldo, 0}, {e->wP[l], L.ldo, 0}, st);
             if (err != cudaSuccess) return err;
-            std::swap(dcur, dnext);
+            std::swap(gcur, gnext);
         }
     }
     return cudaGetLastError();
 }
 
-// full-batch gradient (in chunks of kChunk rows) into e->grads
+// full-batch gradient (in chunks of up to kMaxChunk rows) into e->grads
 int batch_gradient(tpcf_emu e, const float *x, const float *y, int64_t batch, double *loss, cudaStream_t st)
 {
     const int w_in = e->widths[0], w_out = e->widths[e->nl];
+    int rc = ensure_cap(e, batch, st);
+    if (rc) return rc;
     const double inv = 1.0 / ((double)batch * w_out);
+    ECK(cudaMemsetAsync(e->grads, 0, e->n_params * sizeof(float), st));
     if (loss) ECK(cudaMemsetAsync(loss, 0, sizeof(double), st));
-    for (int64_t r0 = 0; r0 < batch; r0 += kChunk) {
-        const int64_t rows = std::min<int64_t>(kChunk, batch - r0);
+    for (int64_t r0 = 0; r0 < batch; r0 += e->cap) {
+        const int64_t rows = std::min<int64_t>(e->cap, batch - r0);
         k_scale_in<<<grid1(rows * w_in), 256, 0, st>>>(x + r0 * w_in, rows, w_in, e->in_lo, e->in_hi, e->xs,
                                                         e->layers[0].ldi);
         tpcf::note_launch();
-        ECK(forward(e, rows, st));
-        float *g = r0 == 0 ? e->grads : e->gtmp;
-        ECK(backward_chunk(e, y + r0 * w_out, rows, inv, g, loss, st));
-        if (r0 > 0) {
-            k_add<<<grid1(e->n_params), 256, 0, st>>>(e->grads, e->gtmp, e->n_params);
-            tpcf::note_launch();
-        }
+        ECK(forward(e, rows, true, y + r0 * w_out, nullptr, loss, inv, st));
+        ECK(backward(e, rows, st));
     }
     return TPCF_OK;
 }
@@ -622,60 +847,53 @@ int tpcf_emu_create(const int32_t *widths, int32_t n_layers, uint64_t seed, tpcf
     if (n_layers < 1 || n_layers > kMaxLayers) return emu_fail(TPCF_ERR_ARG, "n_layers must be 1..8");
     for (int l = 0; l <= n_layers; ++l)
         if (widths[l] < 1 || widths[l] > kMaxWidth) return emu_fail(TPCF_ERR_ARG, "widths must be 1..4096");
+    if (!encoder()) return emu_fail(TPCF_ERR_UNSUPPORTED, "the driver has no tensor-map encoder");
     tpcf_emu e = new tpcf_emu_s();
     e->nl = n_layers;
     int64_t off = 0;
-    for (int l = 0; l <= n_layers; ++l) {
-        e->widths[l] = widths[l];
-        e->maxw = std::max(e->maxw, (int)widths[l]);
-    }
+    for (int l = 0; l <= n_layers; ++l) e->widths[l] = widths[l];
+    int64_t ws_need = 0;
     for (int l = 0; l < n_layers; ++l) {
         Layer &L = e->layers[l];
         L.in = widths[l];
         L.out = widths[l + 1];
         L.ldi = round8(L.in);
         L.ldo = round8(L.out);
-        e->maxw8 = std::max(e->maxw8, L.ldo);
+        e->maxw8 = std::max({e->maxw8, L.ldo, L.ldi});
+        ws_need = std::max<int64_t>(ws_need, (int64_t)L.in * L.ldo);
         L.w_off = off;
         off += (int64_t)L.in * L.out;
         L.b_off = off;
         off += L.out;
     }
     e->n_params = off;
+    // room for at least 8 split-K partials of the largest weight gradient, 8 M floats at least
+    e->ws_floats = std::max<int64_t>(8 * ws_need, (int64_t)8 << 20);
     cudaError_t err = cudaSuccess;
     auto A = [&](void **p, size_t bytes) {
         if (err == cudaSuccess) err = cudaMalloc(p, bytes);
     };
     A((void **)&e->params, off * sizeof(float));
     A((void **)&e->grads, off * sizeof(float));
-    A((void **)&e->gtmp, off * sizeof(float));
     A((void **)&e->m, off * sizeof(float));
     A((void **)&e->v, off * sizeof(float));
     A((void **)&e->in_lo, widths[0] * sizeof(float));
     A((void **)&e->in_hi, widths[0] * sizeof(float));
     A((void **)&e->out_mean, widths[n_layers] * sizeof(float));
     A((void **)&e->out_sd, widths[n_layers] * sizeof(float));
+    A((void **)&e->ws, (size_t)e->ws_floats * sizeof(float));
     const size_t bf = sizeof(__nv_bfloat16);
-    A((void **)&e->xs, (size_t)kChunk * e->layers[0].ldi * bf);
     for (int l = 0; l < n_layers; ++l) {
         const Layer &L = e->layers[l];
         A((void **)&e->wT[l], (size_t)L.out * L.ldi * bf);
         A((void **)&e->wP[l], (size_t)L.in * L.ldo * bf);
-        A((void **)&e->Z[l], (size_t)kChunk * L.out * sizeof(float));
-        if (l + 1 < n_layers) A((void **)&e->act[l], (size_t)kChunk * L.ldo * bf);
     }
-    A((void **)&e->db, (size_t)kChunk * e->maxw8 * bf);
-    A((void **)&e->d0, (size_t)kChunk * e->maxw * sizeof(float));
-    A((void **)&e->d1, (size_t)kChunk * e->maxw * sizeof(float));
-    // zero the padded bf16 buffers once: their padding is never written
-    if (err == cudaSuccess) err = cudaMemset(e->xs, 0, (size_t)kChunk * e->layers[0].ldi * bf);
+    // the padding of the weight copies is never written: zero it once
     for (int l = 0; l < n_layers && err == cudaSuccess; ++l) {
         const Layer &L = e->layers[l];
         err = cudaMemset(e->wT[l], 0, (size_t)L.out * L.ldi * bf);
         if (err == cudaSuccess) err = cudaMemset(e->wP[l], 0, (size_t)L.in * L.ldo * bf);
-        if (err == cudaSuccess && e->act[l]) err = cudaMemset(e->act[l], 0, (size_t)kChunk * L.ldo * bf);
     }
-    if (err == cudaSuccess) err = cudaMemset(e->db, 0, (size_t)kChunk * e->maxw8 * bf);
     if (err == cudaSuccess) err = cudaMemset(e->params, 0, off * sizeof(float));
     if (err == cudaSuccess) err = cudaMemset(e->m, 0, off * sizeof(float));
     if (err == cudaSuccess) err = cudaMemset(e->v, 0, off * sizeof(float));
@@ -708,12 +926,12 @@ int tpcf_emu_destroy(tpcf_emu e)
 {
     if (!e) return TPCF_OK;
     cudaDeviceSynchronize();
-    for (void *p : {(void *)e->params, (void *)e->grads, (void *)e->gtmp, (void *)e->m, (void *)e->v,
-                    (void *)e->in_lo, (void *)e->in_hi, (void *)e->out_mean, (void *)e->out_sd, (void *)e->xs,
-                    (void *)e->db, (void *)e->d0, (void *)e->d1})
+    free_chunk_buffers(e);
+    for (void *p : {(void *)e->params, (void *)e->grads, (void *)e->m, (void *)e->v, (void *)e->in_lo,
+                    (void *)e->in_hi, (void *)e->out_mean, (void *)e->out_sd, (void *)e->ws})
         if (p) cudaFree(p);
     for (int l = 0; l < kMaxLayers; ++l)
-        for (void *p : {(void *)e->Z[l], (void *)e->act[l], (void *)e->wT[l], (void *)e->wP[l]})
+        for (void *p : {(void *)e->wT[l], (void *)e->wP[l]})
             if (p) cudaFree(p);
     delete e;
     return TPCF_OK;
@@ -782,17 +1000,17 @@ int tpcf_emu_train_step(tpcf_emu e, const float *x, const float *y, int64_t batc
 int tpcf_emu_predict(tpcf_emu e, const float *x, int64_t n, float *y, void *stream)
 {
     if (!e || n < 0 || (n > 0 && (!x || !y))) return emu_fail(TPCF_ERR_ARG, "handle, x and y are required");
+    if (n == 0) return TPCF_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const int w_in = e->widths[0], w_out = e->widths[e->nl];
-    for (int64_t r0 = 0; r0 < n; r0 += kChunk) {
-        const int64_t rows = std::min<int64_t>(kChunk, n - r0);
+    int rc = ensure_cap(e, n, st);
+    if (rc) return rc;
+    for (int64_t r0 = 0; r0 < n; r0 += e->cap) {
+        const int64_t rows = std::min<int64_t>(e->cap, n - r0);
         k_scale_in<<<grid1(rows * w_in), 256, 0, st>>>(x + r0 * w_in, rows, w_in, e->in_lo, e->in_hi, e->xs,
                                                         e->layers[0].ldi);
         tpcf::note_launch();
-        ECK(forward(e, rows, st));
-        k_unscale_out<<<grid1(rows * w_out), 256, 0, st>>>(e->Z[e->nl - 1], rows, w_out, e->out_mean, e->out_sd,
-                                                           y + r0 * w_out);
-        tpcf::note_launch();
+        ECK(forward(e, rows, false, nullptr, y + r0 * w_out, nullptr, 0.0, st));
     }
     ECK(cudaGetLastError());
     return TPCF_OK;

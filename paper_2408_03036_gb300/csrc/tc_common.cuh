@@ -43,6 +43,23 @@ __device__ __forceinline__ uint32_t make_idesc(uint32_t ab, int M, int N)
     return d;
 }
 
+// Shared-memory descriptor of a 128-byte-swizzled operand tile (layout type 2,
+// version 1; the tile starts on a 1024-byte boundary).  K-major: rows of 64
+// bf16 along K, 8-row groups sbo = 1024 bytes apart (lbo unused); MN-major: 64
+// consecutive MN elements per 128-byte row, rows along K, 8-row groups sbo =
+// 1024 bytes apart and 64-element MN blocks lbo bytes apart.
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    return make_desc(saddr, lbo, sbo) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor with operand majors: a_mn / b_mn = 1 for an MN-major
+// (transposed) A or B.
+__device__ __forceinline__ uint32_t make_idesc_major(uint32_t ab, int M, int N, int a_mn, int b_mn)
+{
+    return make_idesc(ab, M, N) | ((uint32_t)(a_mn & 1) << 15) | ((uint32_t)(b_mn & 1) << 16);
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
@@ -66,6 +83,49 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long l
         if (done) return true;
     }
     return false;
+}
+
+// Bounded wait that also gives up when another role of the CTA has raised *abort.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, long long limit,
+                                                   const volatile int *abort)
+{
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && *abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 2D tiled TMA load of one box (coordinates c0 innermost, c1) into shared memory,
+// completing `bar`'s transaction bytes.  The innermost coordinate times the element
+// size must be a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int c0, int c1, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
 }
 
 template <bool TF32>
