@@ -40,10 +40,13 @@ struct Layer {
 
 inline int round8(int n) { return (n + 7) / 8 * 8; }
 
+// SiLU with an IEEE division (its result is rounded to bf16: a less accurate value
+// flips that rounding more often); its derivative with the fast division (it scales
+// a bf16-rounded gradient); z -> -inf gives 0 for both
 __device__ __forceinline__ float silu(float z) { return z / (1.f + __expf(-z)); }
 __device__ __forceinline__ float silu_grad(float z)
 {
-    const float s = 1.f / (1.f + __expf(-z));
+    const float s = __fdividef(1.f, 1.f + __expf(-z));
     return s * (1.f + z * (1.f - s));
 }
 
@@ -67,16 +70,17 @@ struct GemmArgs {
     int n_mt, n_nt, nkb;     // tiles along M and N, 64-wide K blocks
     int kper;                // K blocks per split
     int units;               // splits x n_mt x n_nt work units
+    int stages;              // stages of the load ring (at most kMaxStages)
+    int ncol;                // floats of each per-column parameter array in shared memory (0: none)
     const float *bias;       // [N]
-    int vec_bias;            // widest aligned float vector of bias (4, 2 or 1)
     __nv_bfloat16 *out_b;    // bf16 rows, pitch ld_b (HID activation; LOSS, BWD gradient)
     int64_t ld_b;
     float *out_f;            // FP32 rows, pitch ld_f (HID pre-activation or null; PRED y; PART workspace)
     int64_t ld_f;
-    int vec_f;
+    int pair_f;              // out_f rows take 8-byte pair stores (even ld_f, 8-byte aligned)
     const float *in_f;       // FP32 rows read by the epilogue, pitch ld_in (LOSS targets; BWD pre-activation)
     int64_t ld_in;
-    int vec_in;
+    int pair_in;             // in_f rows take 8-byte pair loads
     const float *mean, *sd;  // output scaling [N]
     float gscale;            // LOSS: 2 / (rows x outputs of the whole batch)
     float inv_count;         // LOSS: 1 / (rows x outputs of the whole batch)
@@ -84,173 +88,212 @@ struct GemmArgs {
     float *colsum;           // LOSS, BWD: += column sums of the gradient
     int64_t part_stride;     // PART: floats between the splits' partial outputs
     int *err;
-    long long wait_limit;    // polls of a bounded wait
+    long long wait_limit;    // bound of a wait: wait_limit / 16 suspending polls (at least one)
     int wait_unmet;          // test mode: one more wait on a phase that nothing completes
 };
 
-constexpr int kGemmThreads = 192;       // warp 0 loads (TMA), warp 1 issues MMAs, warps 2-5 epilogue
+constexpr int kGemmThreads = 320;       // warp 0 loads (TMA), warp 1 issues MMAs, warps 2-9 epilogue
+constexpr int kEpiWarps = 8;
 constexpr int kBM = 128;                // tile rows (tensor-memory lanes, the MMA's M)
 constexpr int kBK = 64;                 // K per stage: one 128-byte swizzle row of bf16
-constexpr int kStages = 4;
+constexpr int kMaxStages = 4;
 constexpr uint32_t kATile = kBM * kBK * 2;
 constexpr uint32_t kMNBox = 64 * kBK * 2;   // one 64 (MN) x 64 (K) box of an MN-major operand
 
-__device__ __forceinline__ void ld16f(const float *p, float (&v)[16], int nval, int vec)
+// The epilogue works on 16-column chunks of the warp's 32 rows in a column-pair
+// layout: the accumulator (one row per lane, as tensor memory hands it out) goes
+// through a per-warp [32][kStg] staging area in shared memory, after which lane l
+// holds columns 2 (l % 8) and 2 (l % 8) + 1 of rows 4 it + l / 8 (it = 0..7), as
+// t[2 it] and t[2 it + 1].  Per-column values (bias, output scaling) are then two
+// registers per lane, column sums are sums over `it` plus two shuffles, and global
+// loads and stores are pairs running along rows: each instruction covers 16
+// consecutive columns of four rows.
+constexpr int kStg = 20;                                   // row pitch (floats): 16-byte rows
+constexpr uint32_t kStgBytes = kEpiWarps * 32 * kStg * 4;
+
+// the accumulator row r (this lane's, 16 raw 32-bit values) to the pair layout t
+__device__ __forceinline__ void to_pairs(float *stg, const uint32_t (&r)[16], float (&t)[16], int lane)
 {
-    if (nval == 16 && vec == 4) {
+    float4 *row = reinterpret_cast<float4 *>(stg + lane * kStg);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + q);
-            v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
-        }
-    } else if (nval == 16 && vec == 2) {
+    for (int q = 0; q < 4; ++q)
+        row[q] = make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]), __uint_as_float(r[4 * q + 2]),
+                             __uint_as_float(r[4 * q + 3]));
+    __syncwarp();
+    const int p = lane & 7, g4 = lane >> 3;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const float2 t = __ldg(reinterpret_cast<const float2 *>(p) + q);
-            v[2 * q] = t.x; v[2 * q + 1] = t.y;
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = j < nval ? __ldg(p + j) : 0.f;
+    for (int it = 0; it < 8; ++it) {
+        const float2 v = *reinterpret_cast<const float2 *>(stg + (4 * it + g4) * kStg + 2 * p);
+        t[2 * it] = v.x;
+        t[2 * it + 1] = v.y;
     }
+    __syncwarp();
 }
 
-__device__ __forceinline__ void st16f(float *p, const float (&v)[16], int nval, int vec)
-{
-    if (nval == 16 && vec == 4) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            reinterpret_cast<float4 *>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    } else if (nval == 16 && vec == 2) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) reinterpret_cast<float2 *>(p)[q] = make_float2(v[2 * q], v[2 * q + 1]);
-    } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-            if (j < nval) p[j] = v[j];
-    }
-}
-
-// 16 bf16 at a 32-byte-aligned position (rows padded to multiples of 8, tiles of 16 columns)
-__device__ __forceinline__ void st16b(__nv_bfloat16 *p, const float (&v)[16], int nval)
-{
-    if (nval == 16) {
-        uint32_t w[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const __nv_bfloat162 t = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-            w[q] = *reinterpret_cast<const uint32_t *>(&t);
-        }
-        reinterpret_cast<uint4 *>(p)[0] = make_uint4(w[0], w[1], w[2], w[3]);
-        reinterpret_cast<uint4 *>(p)[1] = make_uint4(w[4], w[5], w[6], w[7]);
-    } else {
-#pragma unroll
-        for (int j = 0; j < 16; ++j)
-            if (j < nval) p[j] = __float2bfloat16_rn(v[j]);
-    }
-}
-
-// Column sums of a warp's 32 rows x 16 columns: a halving butterfly leaves the sum of
-// column (lane >> 1) in lanes 2c and 2c + 1 (16 shuffles instead of 80)
-__device__ __forceinline__ float colsum16(const float (&v)[16], int lane)
-{
-    constexpr unsigned FULL = 0xffffffffu;
-    float a[8], b[4], c[2], d;
-    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float keep = h4 ? v[j + 8] : v[j], send = h4 ? v[j] : v[j + 8];
-        a[j] = keep + __shfl_xor_sync(FULL, send, 16);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float keep = h3 ? a[j + 4] : a[j], send = h3 ? a[j] : a[j + 4];
-        b[j] = keep + __shfl_xor_sync(FULL, send, 8);
-    }
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const float keep = h2 ? b[j + 2] : b[j], send = h2 ? b[j] : b[j + 2];
-        c[j] = keep + __shfl_xor_sync(FULL, send, 4);
-    }
-    {
-        const float keep = h1 ? c[1] : c[0], send = h1 ? c[0] : c[1];
-        d = keep + __shfl_xor_sync(FULL, send, 2);
-    }
-    return d + __shfl_xor_sync(FULL, d, 1);
-}
-
-// One 16-column chunk of the epilogue for this thread's row.
+// Per-column parameters, two arrays in shared memory filled once per CTA (colA, colB):
+//   HID   z = c + colB                       (colB = bias)
+//   PRED  y = c colA + colB                  (colA = sd, colB = bias sd + mean)
+//   LOSS  d = c + colB - y colA              (colA = 1 / sd, colB = bias + mean / sd)
 template <int EPI>
-__device__ __forceinline__ void epi_chunk(const GemmArgs &g, int row, bool rv, int n0, int split, float (&v)[16],
+__device__ __forceinline__ void col_params(const GemmArgs &g, int n, float &a, float &b)
+{
+    const float bias = g.bias ? g.bias[n] : 0.f;
+    a = 1.f;
+    b = bias;
+    if (EPI == EPI_PRED) {
+        a = g.sd[n];
+        b = fmaf(bias, a, g.mean[n]);
+    } else if (EPI == EPI_LOSS) {
+        a = 1.f / g.sd[n];
+        b = fmaf(g.mean[n], a, bias);
+    }
+}
+
+// Per-chunk row inputs (LOSS targets, BWD pre-activations) in the pair layout, loaded
+// one chunk ahead.
+struct ChunkIn {
+    float x[16];
+};
+
+template <int EPI>
+__device__ __forceinline__ void chunk_load(const GemmArgs &g, int row_base, int n0, int lane, ChunkIn &in)
+{
+    if (EPI != EPI_LOSS && EPI != EPI_BWD) return;
+    const int nval = min(16, g.N - n0);
+    const int p = lane & 7, g4 = lane >> 3;
+    const int c = 2 * p;
+    const bool c0v = c < nval, c1v = c + 1 < nval;
+    const float *base = g.in_f + (int64_t)(row_base + g4) * g.ld_in + n0 + c;
+    const bool full = nval == 16 && row_base + 32 <= g.M && g.pair_in;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const float *a = base + (int64_t)(4 * it) * g.ld_in;
+        const bool rv = row_base + 4 * it + g4 < g.M;
+        if (full || (rv && c1v && g.pair_in)) {
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(a));
+            in.x[2 * it] = v.x;
+            in.x[2 * it + 1] = v.y;
+        } else {
+            in.x[2 * it] = (rv && c0v) ? __ldg(a) : 0.f;
+            in.x[2 * it + 1] = (rv && c1v) ? __ldg(a + 1) : 0.f;
+        }
+    }
+}
+
+// stores of one row pair (FP32 or bf16), paired when both columns are valid and aligned
+__device__ __forceinline__ void st_pair(float *a, float v0, float v1, bool c0v, bool c1v, bool pair)
+{
+    if (c1v && pair) {
+        *reinterpret_cast<float2 *>(a) = make_float2(v0, v1);
+    } else {
+        if (c0v) a[0] = v0;
+        if (c1v) a[1] = v1;
+    }
+}
+
+__device__ __forceinline__ void st_pair(__nv_bfloat16 *a, float v0, float v1, bool c0v, bool c1v)
+{
+    if (c1v) {
+        *reinterpret_cast<__nv_bfloat162 *>(a) = __floats2bfloat162_rn(v0, v1);
+    } else if (c0v) {
+        a[0] = __float2bfloat16_rn(v0);
+    }
+}
+
+// One 16-column chunk of the epilogue; r holds this lane's accumulator row (row_base + lane).
+// FULL: all 32 rows and 16 columns lie inside the output and FP32 rows take pair
+// stores, so the chunk runs without predicates.
+template <int EPI, bool FULL>
+__device__ __forceinline__ void epi_chunk(const GemmArgs &g, int row_base, int n0, int split, const uint32_t (&r)[16],
+                                          const ChunkIn &in, const float *colA, const float *colB, float *stg,
                                           float &lsum, int lane)
 {
     const int nval = min(16, g.N - n0);
+    const int p = lane & 7, g4 = lane >> 3;
+    const int c = 2 * p;
+    float2 pa = make_float2(1.f, 1.f), pb = make_float2(0.f, 0.f);
+    if (EPI == EPI_HID || EPI == EPI_PRED || EPI == EPI_LOSS) {
+        pa = *reinterpret_cast<const float2 *>(colA + n0 + c);
+        pb = *reinterpret_cast<const float2 *>(colB + n0 + c);
+    }
+    const bool c0v = FULL || c < nval, c1v = FULL || c + 1 < nval;
+    auto rowv = [&](int it) { return FULL || row_base + 4 * it + g4 < g.M; };
+    float t[16];
+    to_pairs(stg, r, t, lane);
     if (EPI == EPI_PART) {
-        if (rv) st16f(g.out_f + split * g.part_stride + (int64_t)row * g.ld_f + n0, v, nval, g.vec_f);
+        float *a = g.out_f + split * g.part_stride + (int64_t)(row_base + g4) * g.ld_f + n0 + c;
+#pragma unroll
+        for (int it = 0; it < 8; ++it)
+            if (rowv(it)) st_pair(a + (int64_t)(4 * it) * g.ld_f, t[2 * it], t[2 * it + 1], c0v, c1v, true);
         return;
     }
-    if (EPI == EPI_HID || EPI == EPI_PRED || EPI == EPI_LOSS) {
-        float b[16];
-        ld16f(g.bias + n0, b, nval, g.vec_bias);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] += b[j];
-    }
     if (EPI == EPI_HID) {
-        if (rv) {
-            if (g.out_f) st16f(g.out_f + (int64_t)row * g.ld_f + n0, v, nval, g.vec_f);
-            float a[16];
+        float *az = g.out_f ? g.out_f + (int64_t)(row_base + g4) * g.ld_f + n0 + c : nullptr;
+        __nv_bfloat16 *aa = g.out_b + (int64_t)(row_base + g4) * g.ld_b + n0 + c;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) a[j] = silu(v[j]);
-            st16b(g.out_b + (int64_t)row * g.ld_b + n0, a, nval);
+        for (int it = 0; it < 8; ++it) {
+            if (rowv(it)) {
+                const float z0 = t[2 * it] + pb.x, z1 = t[2 * it + 1] + pb.y;
+                if (az) st_pair(az + (int64_t)(4 * it) * g.ld_f, z0, z1, c0v, c1v, true);
+                st_pair(aa + (int64_t)(4 * it) * g.ld_b, silu(z0), silu(z1), c0v, c1v);
+            }
         }
         return;
     }
     if (EPI == EPI_PRED) {
-        if (rv) {
-            float mu[16], sd[16];
-            ld16f(g.mean + n0, mu, nval, 4);
-            ld16f(g.sd + n0, sd, nval, 4);
+        float *a = g.out_f + (int64_t)(row_base + g4) * g.ld_f + n0 + c;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] = fmaf(v[j], sd[j], mu[j]);
-            st16f(g.out_f + (int64_t)row * g.ld_f + n0, v, nval, g.vec_f);
-        }
+        for (int it = 0; it < 8; ++it)
+            if (rowv(it))
+                st_pair(a + (int64_t)(4 * it) * g.ld_f, fmaf(t[2 * it], pa.x, pb.x), fmaf(t[2 * it + 1], pa.y, pb.y),
+                        c0v, c1v, FULL || g.pair_f);
         return;
     }
-    // LOSS, BWD: the gradient, zero on rows past M
-    float gr[16];
-    if (EPI == EPI_LOSS) {
-        float t[16], mu[16], sd[16];
-        if (rv) ld16f(g.in_f + (int64_t)row * g.ld_in + n0, t, nval, g.vec_in);
-        ld16f(g.mean + n0, mu, nval, 4);
-        ld16f(g.sd + n0, sd, nval, 4);
+    // LOSS, BWD: the gradient (zero outside the M x N output), stored as bf16, and its
+    // column sums into the bias gradient
+    __nv_bfloat16 *ag = g.out_b + (int64_t)(row_base + g4) * g.ld_b + n0 + c;
+    float cs0 = 0.f, cs1 = 0.f;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const float d = (rv && j < nval) ? v[j] - (t[j] - mu[j]) / sd[j] : 0.f;
-            gr[j] = g.gscale * d;
-            lsum = fmaf(d, d, lsum);
+    for (int it = 0; it < 8; ++it) {
+        const bool rv = rowv(it);
+        float g0, g1;
+        if (EPI == EPI_LOSS) {
+            const float d0 = (rv && c0v) ? fmaf(-in.x[2 * it], pa.x, t[2 * it] + pb.x) : 0.f;
+            const float d1 = (rv && c1v) ? fmaf(-in.x[2 * it + 1], pa.y, t[2 * it + 1] + pb.y) : 0.f;
+            lsum = fmaf(d0, d0, fmaf(d1, d1, lsum));
+            g0 = g.gscale * d0;
+            g1 = g.gscale * d1;
+        } else {
+            g0 = (rv && c0v) ? t[2 * it] * silu_grad(in.x[2 * it]) : 0.f;
+            g1 = (rv && c1v) ? t[2 * it + 1] * silu_grad(in.x[2 * it + 1]) : 0.f;
         }
-    } else {
-        float z[16];
-        if (rv) ld16f(g.in_f + (int64_t)row * g.ld_in + n0, z, nval, g.vec_in);
-#pragma unroll
-        for (int j = 0; j < 16; ++j) gr[j] = (rv && j < nval) ? v[j] * silu_grad(z[j]) : 0.f;
+        if (rv) st_pair(ag + (int64_t)(4 * it) * g.ld_b, g0, g1, c0v, c1v);
+        cs0 += g0;
+        cs1 += g1;
     }
-    if (rv) st16b(g.out_b + (int64_t)row * g.ld_b + n0, gr, nval);
-    const float cs = colsum16(gr, lane);
-    if (!(lane & 1) && (lane >> 1) < nval) atomicAdd(g.colsum + n0 + (lane >> 1), cs);
+    cs0 += __shfl_xor_sync(0xffffffffu, cs0, 8);
+    cs1 += __shfl_xor_sync(0xffffffffu, cs1, 8);
+    cs0 += __shfl_xor_sync(0xffffffffu, cs0, 16);
+    cs1 += __shfl_xor_sync(0xffffffffu, cs1, 16);
+    if (g4 == 0) {
+        if (c0v) atomicAdd(g.colsum + n0 + c, cs0);
+        if (c1v) atomicAdd(g.colsum + n0 + c + 1, cs1);
+    }
 }
 
 // Persistent, warp-specialised tcgen05 GEMM: C[m][n] = sum_k A(m, k) B(n, k) in
 // 128 x NT tiles (work units: K splits x row tiles x column tiles, taken by the
 // CTAs in turn).  Warp 0 (one thread) loads 64-wide K blocks of A and B with TMA
-// into a ring of kStages 128-byte-swizzled stages (K-major operands: one box of
+// into a ring of g.stages 128-byte-swizzled stages (K-major operands: one box of
 // 64 K x rows; MN-major operands: boxes of 64 MN x 64 K), completing each
 // stage's `full` barrier; warp 1 (one thread) issues four K = 16 MMAs per stage
 // into one of two tensor-memory accumulators and commits them to the stage's
 // `empty` barrier and, after a unit's last stage, to the accumulator's `tfull`
 // barrier; warps 2-5 read the accumulator (one 32-lane quarter each), run the
 // epilogue and release it through `tempty`, so the epilogue of one unit overlaps
-// the products of the next.  Every wait is bounded: a role that gives up raises
+// the products of the next.  The waiting threads suspend in mbarrier.try_wait
+// rather than spin, so they take no issue slots from the epilogue warps.  Every
+// wait is bounded (wait_limit / 16 polls of up to a microsecond): a role that gives up raises
 // the CTA's abort flag, the others stop, the loads and products in flight are
 // waited for (long bound) before the tensor memory is released, and the kernel
 // latches DEV_ERR_TIMEOUT.
@@ -265,9 +308,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NT = g.NT;
     const uint32_t stage_bytes = kATile + (uint32_t)NT * kBK * 2;
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * stage_bytes);
-    uint64_t *empty = full + kStages;
-    uint64_t *tfull = empty + kStages;
+    const int S = g.stages;
+    float *colA = reinterpret_cast<float *>(smem + S * stage_bytes + kStgBytes);   // per-column parameters
+    float *colB = colA + g.ncol;
+    uint64_t *full = reinterpret_cast<uint64_t *>(colB + g.ncol);
+    uint64_t *empty = full + kMaxStages;
+    uint64_t *tfull = empty + kMaxStages;
     uint64_t *tempty = tfull + 2;
     uint64_t *done = tempty + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
@@ -275,13 +321,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const uint32_t tmem_cols = 2u * (uint32_t)NT;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < S; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&tfull[a], 1);
-            mbar_init(&tempty[a], 4);
+            mbar_init(&tempty[a], kEpiWarps);
         }
         mbar_init(done, 1);
         *s_abort = 0;
@@ -297,6 +343,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
     const int per_split = g.n_mt * g.n_nt;
+    // polls of a suspending wait (up to a microsecond each)
+    const long long polls = g.wait_limit > 16 ? g.wait_limit >> 4 : 1;
 
     if (warp == 0 && lane == 0) {
         // ---- loads
@@ -306,9 +354,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int sp = u / per_split, r = u % per_split, mt = r / g.n_nt, nt = r % g.n_nt;
             const int kb0 = sp * g.kper, kb1 = min(g.nkb, kb0 + g.kper);
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                const int s = (int)(it % kStages);
-                const uint32_t ph = (it / kStages) & 1u;
-                if (!mbar_wait_or_abort(&empty[s], ph ^ 1u, g.wait_limit, s_abort)) {
+                const int s = (int)(it % (uint32_t)S);
+                const uint32_t ph = (it / (uint32_t)S) & 1u;
+                if (!mbar_sleep_wait_or_abort(&empty[s], ph ^ 1u, polls, s_abort)) {
                     *s_abort = 1;
                     ok = false;
                     break;
@@ -331,10 +379,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         if (!ok) {
             // the loads issued must land before the CTA's shared memory goes away
-            for (int s = 0; s < kStages; ++s)
+            for (int s = 0; s < S; ++s)
                 if (it > (uint32_t)s) {
-                    const uint32_t j = ((it - 1u - (uint32_t)s) / kStages) * kStages + (uint32_t)s;
-                    mbar_wait(&full[s], (j / kStages) & 1u);
+                    const uint32_t j = ((it - 1u - (uint32_t)s) / (uint32_t)S) * (uint32_t)S + (uint32_t)s;
+                    mbar_wait(&full[s], (j / (uint32_t)S) & 1u);
                 }
         }
     } else if (warp == 1 && lane == 0) {
@@ -346,7 +394,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int sp = u / per_split;
             const int kb0 = sp * g.kper, kb1 = min(g.nkb, kb0 + g.kper);
             const uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
-            if (!mbar_wait_or_abort(&tempty[acc], aph ^ 1u, g.wait_limit, s_abort)) {
+            if (!mbar_sleep_wait_or_abort(&tempty[acc], aph ^ 1u, polls, s_abort)) {
                 *s_abort = 1;
                 ok = false;
                 break;
@@ -354,9 +402,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t d_tmem = tmem + acc * (uint32_t)NT;
             for (int kb = kb0; kb < kb1; ++kb, ++it) {
-                const int s = (int)(it % kStages);
-                const uint32_t ph = (it / kStages) & 1u;
-                if (!mbar_wait_or_abort(&full[s], ph, g.wait_limit, s_abort)) {
+                const int s = (int)(it % (uint32_t)S);
+                const uint32_t ph = (it / (uint32_t)S) & 1u;
+                if (!mbar_sleep_wait_or_abort(&full[s], ph, polls, s_abort)) {
                     *s_abort = 1;
                     ok = false;
                     break;
@@ -386,30 +434,73 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         // test mode: a phase of `done` that no commit completes
         if (g.wait_unmet && ok && !mbar_wait(done, any ? 1u : 0u, g.wait_limit)) *s_abort = 1;
     } else if (warp >= 2) {
-        // ---- epilogue
-        const int q = warp & 3;   // tensor-memory lane quarter of this warp
+        // ---- epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31; the two
+        // warps of a lane quarter take alternate 16-column chunks, each loading the
+        // next chunk's inputs before it works on the current one
+        const int q = warp & 3;
+        const int c_first = 16 * ((warp - 2) >> 2);
+        float *stg = reinterpret_cast<float *>(smem + S * stage_bytes) + (warp - 2) * 32 * kStg;
+        // the per-column parameters of all N columns, once; every epilogue thread
+        // reaches this barrier (named barrier 1, the 256 epilogue threads) exactly once
+        if (g.ncol > 0) {
+            for (int n = threadIdx.x - 64; n < g.ncol; n += 32 * kEpiWarps) {
+                float a = 1.f, b = 0.f;
+                if (n < g.N) col_params<EPI>(g, n, a, b);
+                colA[n] = a;
+                colB[n] = b;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        }
         uint32_t tc = 0;
         float lsum = 0.f;
         for (int u = blockIdx.x; u < g.units; u += gridDim.x) {
             const int sp = u / per_split, r = u % per_split, mt = r / g.n_nt, nt = r % g.n_nt;
             const uint32_t acc = tc & 1u, aph = (tc >> 1) & 1u;
+            const int row_base = mt * kBM + 32 * q;
+            ChunkIn cur, nxt;
+            if (c_first < NT && nt * NT + c_first < g.N) chunk_load<EPI>(g, row_base, nt * NT + c_first, lane, cur);
             // one poller per warp: the warp's tensor-memory loads below are collective
             int okw = 1;
-            if (lane == 0) okw = mbar_wait_or_abort(&tfull[acc], aph, g.wait_limit, s_abort) ? 1 : 0;
+            if (lane == 0) okw = mbar_sleep_wait_or_abort(&tfull[acc], aph, polls, s_abort) ? 1 : 0;
             okw = __shfl_sync(0xffffffffu, okw, 0);
             if (!okw) {
                 if (lane == 0) *s_abort = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const int row = mt * kBM + 32 * q + lane;
-            const bool rv = row < g.M;
-            for (int c0 = 0; c0 < NT; c0 += 16) {
+            // the next chunk's tensor-memory load is in flight while this one is worked on
+            const uint32_t tbase = tmem + ((uint32_t)(32 * q) << 16) + acc * (uint32_t)NT;
+            uint32_t ra[16], rb[16];
+            if (c_first < NT && nt * NT + c_first < g.N) {
+                tmem_ld16_issue(tbase + (uint32_t)c_first, ra);
+                tmem_ld_wait();
+                reg_fence16(ra);
+            }
+            // one chunk: the next chunk's inputs and tensor-memory load go out first; the
+            // two register sets swap roles from one chunk to the next
+            const bool pair_ok = EPI == EPI_PRED ? g.pair_f != 0 : true;
+            auto step = [&](uint32_t(&rc)[16], uint32_t(&rn)[16], const ChunkIn &ic, ChunkIn &inx, int c0) -> bool {
                 const int n0 = nt * NT + c0;
-                if (n0 >= g.N) break;
-                float v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + acc * (uint32_t)NT + (uint32_t)c0, v);
-                epi_chunk<EPI>(g, row, rv, n0, sp, v, lsum, lane);
+                const bool more = c0 + 32 < NT && n0 + 32 < g.N;
+                if (more) {
+                    chunk_load<EPI>(g, row_base, n0 + 32, lane, inx);
+                    tmem_ld16_issue(tbase + (uint32_t)(c0 + 32), rn);
+                }
+                if (n0 + 16 <= g.N && row_base + 32 <= g.M && pair_ok)
+                    epi_chunk<EPI, true>(g, row_base, n0, sp, rc, ic, colA, colB, stg, lsum, lane);
+                else
+                    epi_chunk<EPI, false>(g, row_base, n0, sp, rc, ic, colA, colB, stg, lsum, lane);
+                if (more) {
+                    tmem_ld_wait();
+                    reg_fence16(rn);
+                }
+                return more;
+            };
+            if (c_first < NT && nt * NT + c_first < g.N) {
+                for (int c0 = c_first;; c0 += 64) {
+                    if (!step(ra, rb, cur, nxt, c0)) break;
+                    if (!step(rb, ra, nxt, cur, c0 + 32)) break;
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
@@ -592,14 +683,8 @@ cudaError_t make_tmap(CUtensorMap *m, const void *base, int64_t inner, int64_t o
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// widest float vector (4, 2 or 1) for rows starting at p, ld floats apart
-int vec_of(const void *p, int64_t ld)
-{
-    const uintptr_t a = (uintptr_t)p;
-    if (a % 16 == 0 && ld % 4 == 0) return 4;
-    if (a % 8 == 0 && ld % 2 == 0) return 2;
-    return 1;
-}
+// whether rows of ld floats starting at p take 8-byte pair accesses
+int pairable(const void *p, int64_t ld) { return ((uintptr_t)p % 8 == 0 && ld % 2 == 0) ? 1 : 0; }
 
 // A bf16 operand: element (mn, k) at p[mn + k ld] when MN-major, p[k + mn ld] when K-major
 struct Operand {
@@ -645,7 +730,14 @@ cudaError_t gemm(GemmArgs g, Operand A, Operand B, cudaStream_t st, int max_spli
     if (e != cudaSuccess) return e;
     e = B.mn ? make_tmap(&tb, B.p, g.N, g.K, B.ld, 64) : make_tmap(&tb, B.p, g.K, g.N, B.ld, NT);
     if (e != cudaSuccess) return e;
-    const size_t smem = (size_t)kStages * (kATile + (size_t)NT * kBK * 2) + 256 + 1024;
+    // per-column parameter arrays, then as many load stages as fit beside them
+    g.ncol = (EPI == EPI_HID || EPI == EPI_PRED || EPI == EPI_LOSS) ? (g.N + 15) / 16 * 16 : 0;
+    const size_t fixed = kStgBytes + 2 * (size_t)g.ncol * sizeof(float) + 256 + 1024;
+    const size_t stage_bytes = kATile + (size_t)NT * kBK * 2;
+    g.stages = kMaxStages;
+    while (g.stages > 2 && fixed + g.stages * stage_bytes > 227 * 1024) --g.stages;
+    const size_t smem = fixed + g.stages * stage_bytes;
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     static std::atomic<unsigned long long> attr_done{0};   // devices whose attribute is set
     const unsigned long long bit = tpcf::device_bit();
     if (!(attr_done.load(std::memory_order_acquire) & bit)) {
@@ -733,7 +825,6 @@ cudaError_t forward(tpcf_emu e, int64_t rows, bool training, const float *yt, fl
         g.N = L.out;
         g.K = L.in;
         g.bias = e->params + L.b_off;
-        g.vec_bias = vec_of(g.bias, 4);
         const Operand W = {e->wT[l], L.ldi, 0};   // B(o, i) = W[i][o], contiguous in i
         cudaError_t err;
         if (l + 1 < e->nl) {
@@ -741,7 +832,6 @@ cudaError_t forward(tpcf_emu e, int64_t rows, bool training, const float *yt, fl
             g.ld_b = L.ldo;
             g.out_f = training ? e->Z[l] : nullptr;
             g.ld_f = L.ldo;
-            g.vec_f = vec_of(e->Z[l], L.ldo);
             err = gemm<EPI_HID>(g, in, W, st);
             in = {e->act[l], L.ldo, 0};
         } else {
@@ -749,8 +839,8 @@ cudaError_t forward(tpcf_emu e, int64_t rows, bool training, const float *yt, fl
             g.sd = e->out_sd;
             if (training) {
                 g.in_f = yt;
+                g.pair_in = pairable(yt, L.out);
                 g.ld_in = L.out;
-                g.vec_in = vec_of(yt, L.out);
                 g.gscale = (float)(2.0 * inv_count);
                 g.inv_count = (float)inv_count;
                 g.loss = loss;
@@ -760,8 +850,8 @@ cudaError_t forward(tpcf_emu e, int64_t rows, bool training, const float *yt, fl
                 err = gemm<EPI_LOSS>(g, in, W, st);
             } else {
                 g.out_f = y_out;
+                g.pair_f = pairable(y_out, L.out);
                 g.ld_f = L.out;
-                g.vec_f = vec_of(y_out, L.out);
                 err = gemm<EPI_PRED>(g, in, W, st);
             }
         }
@@ -787,7 +877,6 @@ cudaError_t backward(tpcf_emu e, int64_t rows, cudaStream_t st)
         g.K = (int)rows;
         g.out_f = e->ws;
         g.ld_f = L.ldo;
-        g.vec_f = 4;
         int splits = 0;
         const int max_splits = (int)std::max<int64_t>(1, e->ws_floats / ((int64_t)L.in * L.ldo));
         cudaError_t err = gemm<EPI_PART>(g, {aprev, L.ldi, 1}, {gcur, L.ldo, 1}, st, max_splits, &splits);
@@ -804,8 +893,8 @@ cudaError_t backward(tpcf_emu e, int64_t rows, cudaStream_t st)
             h.N = L.in;
             h.K = L.out;
             h.in_f = e->Z[l - 1];
+            h.pair_in = 1;   // rows of ldo floats (a multiple of 8)
             h.ld_in = Lp.ldo;
-            h.vec_in = vec_of(e->Z[l - 1], Lp.ldo);
             h.out_b = gnext;
             h.ld_b = Lp.ldo;
             h.colsum = e->grads + Lp.b_off;
