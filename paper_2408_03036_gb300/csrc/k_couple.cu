@@ -103,19 +103,33 @@ __global__ void __launch_bounds__(256) k_gram_fp32(const float *__restrict__ alm
 }
 
 // T[b1][b2] += sum_i n_b1(i) (n_b2(i) - delta), exact in 64-bit integers.
+// T[b1][b2] += sum_i c_i[b1] (c_i[b2] - [b1 == b2]) over the block's rows: tiles
+// of kTripRows rows staged in shared memory with coalesced loads, one thread per
+// (b1, b2) pair summing from there (integer sums: exact in any order).
+constexpr int kTripRows = 128;
 __global__ void k_triplets(const int32_t *__restrict__ counts, int64_t K, int nb, unsigned long long *T)
 {
+    __shared__ int32_t tile[kTripRows * TPCF_MAX_BINS];
     const int b1 = threadIdx.x / nb, b2 = threadIdx.x % nb;
-    if (threadIdx.x >= nb * nb) return;
+    const bool mine = threadIdx.x < nb * nb;
     const int64_t per = (K + gridDim.x - 1) / gridDim.x;
     const int64_t k0 = blockIdx.x * per, k1 = min(K, k0 + per);
     unsigned long long s = 0;
-    for (int64_t i = k0; i < k1; ++i) {
-        const long long c1 = counts[i * nb + b1];
-        const long long c2 = counts[i * nb + b2] - (b1 == b2 ? 1 : 0);
-        s += (unsigned long long)(c1 * c2);
+    for (int64_t r0 = k0; r0 < k1; r0 += kTripRows) {
+        const int rows = (int)min((int64_t)kTripRows, k1 - r0);
+        __syncthreads();
+        for (int q = threadIdx.x; q < rows * nb; q += blockDim.x) tile[q] = counts[r0 * nb + q];
+        __syncthreads();
+        if (mine) {
+            const int d = b1 == b2 ? 1 : 0;
+            for (int r = 0; r < rows; ++r) {
+                const long long c1 = tile[r * nb + b1];
+                const long long c2 = tile[r * nb + b2] - d;
+                s += (unsigned long long)(c1 * c2);
+            }
+        }
     }
-    if (s) atomicAdd(T + threadIdx.x, s);
+    if (mine && s) atomicAdd(T + threadIdx.x, s);
 }
 
 // nnn[m][l1][l2][b1][b2] from the Gram blocks, the diagonal residuals and the
@@ -317,9 +331,9 @@ cudaError_t couple_gram_fp32_tiles(const float *alm, const float *w, int64_t K, 
 
 cudaError_t triplet_counts(const int32_t *counts, int64_t K, int nb, unsigned long long *T, cudaStream_t st)
 {
-    int64_t g = (K + 4095) / 4096;
+    int64_t g = (K + 1023) / 1024;
     if (g < 1) g = 1;
-    if (g > sm_count() * 4) g = sm_count() * 4;
+    if (g > sm_count() * 8) g = sm_count() * 8;
     if (K > 0) {
         k_triplets<<<(unsigned)g, ((nb * nb + 31) / 32) * 32, 0, st>>>(counts, K, nb, T);
         note_launch();

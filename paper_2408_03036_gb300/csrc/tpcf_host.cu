@@ -1753,7 +1753,10 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
     if ((rc = dev_state(&ds))) return rc;
     *tuned = *cfg;
     const int nb = cfg->n_bins, L1 = cfg->l_max + 1;
-    const int64_t ns = std::min<int64_t>(n, 6144);       // sampled primaries per trial
+    // sampled primaries per trial: enough tiles per CTA (a few dozen at the
+    // catalogue sizes of a covariance batch) that the launch's ramp and tail do
+    // not decide the timing
+    const int64_t ns = std::min<int64_t>(n, 32768);
     const int64_t stride = std::max<int64_t>(1, n / ns);
     Scratch sc(st);
     float *alm = nullptr;
@@ -1800,7 +1803,7 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
                 t.tile_primaries = tp;
                 t.chunk = ch;
                 float ms = 1e30f;
-                for (int rep = 0; rep < 3; ++rep) {
+                for (int rep = 0; rep < 4; ++rep) {   // the first run warms up; best of three
                     cudaEventRecord(e0, st);
                     rc = run_pairs(&t, g, prim, ns, false, -1.0, nullptr, false, alm, cnt, diag, wsp, pc, st);
                     cudaEventRecord(e1, st);
