@@ -298,6 +298,8 @@ def run_ours(args):
     variants = None if args.no_variants else variants_report(cfg, dx, dwt, rx, rwt, dev, stream, tpcf, flush,
                                                              ms_max / args.steps)
 
+    stages = None if (args.no_variants or rank != 0) else stages_report(cfg, dx, dwt, rx, rwt, dev, stream, tpcf)
+
     # end to end through the host-buffer entry point (copies inside the timed region)
     e2e = end_to_end(cfg, d, dw, r, rw, args, stream, tpcf, ws, rank)
 
@@ -320,6 +322,8 @@ def run_ours(args):
         line["plain_fp32"] = plain
     if variants is not None:
         line["variants"] = variants
+    if stages is not None:
+        line["stages"] = stages
     if mocks is not None:
         line["mocks_per_hour"] = mocks
     if not args.no_precision:
@@ -332,6 +336,71 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def _event_ms(fn, stream, dev, reps=3, warm=1):
+    """Median CUDA-event time of fn() on the stream (after `warm` untimed calls)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize(dev)
+    ms = []
+    for _ in range(reps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        torch.cuda.synchronize(dev)
+        ms.append(s.elapsed_time(e))
+    return statistics.median(ms)
+
+
+def stages_report(cfg, dx, dwt, rx, rwt, dev, stream, tpcf):
+    """The steps of the path reported on their own:
+      * grid build of the headline D - R field (1.6 M records): bandwidth with 32
+        algorithmic bytes per point (coordinates and weight read, record written);
+      * the random-only count pass (tpcf_pair_counts on the 1.2 M randoms), the
+        RRR normaliser's pass when the data weights can be negative;
+      * the small configuration: Poisson N = 20,000 in a periodic cube L = 500,
+        10 bins 20-120, l_max 4, the whole estimate per call."""
+    import numpy as np
+    import torch
+    from paper_2408_03036_gb300 import synth
+    out = {}
+    alpha = float(dwt.double().sum().item() / rwt.double().sum().item())
+    fx = torch.cat([dx, rx])
+    fw = torch.cat([dwt, (-alpha * rwt.double()).float()])
+    n = fx.shape[0]
+    grids = []
+
+    def build():
+        grids.append(tpcf.Grid(cfg, fx, fw, stream=stream, device=dev))
+
+    ms = _event_ms(build, stream, dev)
+    for g in grids:
+        g.close()
+    out["grid_build"] = {"points": n, "ms": ms, "points_per_s": n / (ms / 1000.0),
+                         "hbm_gbs": 32.0 * n / (ms / 1000.0) / 1e9, "bytes_per_point": 32}
+    rg = tpcf.Grid(cfg, rx, rwt, stream=stream, device=dev)
+    res = []
+    ms = _event_ms(lambda: res.append(tpcf.pair_counts(rg, cfg, stream=stream)), stream, dev)
+    pairs = int(res[-1][1].sum().item())
+    rg.close()
+    nr = rx.shape[0]
+    out["random_count_pass"] = {"primaries": nr, "pairs": pairs, "ms": ms, "primaries_per_s": nr / (ms / 1000.0),
+                                "pairs_per_s": pairs / (ms / 1000.0)}
+    x, w = synth.poisson(20_000, 1)
+    xd = torch.from_numpy(x.view(np.int32)).to(dev)
+    wd = torch.from_numpy(w).to(dev)
+    small = {"workload": "Poisson N=20000, periodic L=500, 10 bins 20-120, l_max=4, L={0,2,4}"}
+    for prec in ("fp32", "bf16x3"):
+        c = tpcf.Config(r_min=20.0, r_max=120.0, n_bins=10, l_max=4, Ls=(0, 2, 4), periodic=True, box=500.0,
+                        precision=prec)
+        ms = _event_ms(lambda: tpcf.estimate_3pcf(c, xd, wd, stream=stream, device=dev), stream, dev, reps=5)
+        small[prec] = {"ms": ms, "primaries_per_s": 20_000 / (ms / 1000.0)}
+    tpcf.stream_status(stream)
+    out["small_case"] = small
+    return out
 
 
 def variants_report(cfg, dx, dwt, rx, rwt, dev, stream, tpcf, flush, plain_ms, reps=2):
@@ -538,6 +607,7 @@ def precision_report(dev, stream, tpcf):
     Poisson N=20,000 in a periodic cube L=500, l_max 6, 30 bins 5-155, L in
     {0,2,4,6}, for the plain FP32 coupling and the two tensor-core splits."""
     import numpy as np
+    import torch
     from oracle import oracle as ora
     from paper_2408_03036_gb300 import synth
     x, w = synth.poisson(20_000, 5)
@@ -551,6 +621,9 @@ def precision_report(dev, stream, tpcf):
                           precision=prec)
         res = tpcf.estimate_3pcf(cfg, x, w, stream=stream, device=dev)
         tpcf.stream_status(stream)
+        xd = torch.from_numpy(x.view(np.int32)).to(dev)
+        wd = torch.from_numpy(w).to(dev)
+        gms = _event_ms(lambda: tpcf.estimate_3pcf(cfg, xd, wd, stream=stream, device=dev), stream, dev)
         zg = res.zeta.cpu().numpy()
         err = []
         for k in range(len(est.mults)):
@@ -559,7 +632,8 @@ def precision_report(dev, stream, tpcf):
         err = np.array(err)
         out[prec] = {"max_rel_err": float(err.max()), "median_rel_err": float(np.median(err)),
                      "worst": "%d%d%d" % tuple(est.mults[int(err.argmax())]),
-                     "counts_exact": bool(np.array_equal(res.triplet_counts.cpu().numpy(), est.trip_counts))}
+                     "counts_exact": bool(np.array_equal(res.triplet_counts.cpu().numpy(), est.trip_counts)),
+                     "gpu_ms": gms, "gpu_primaries_per_s": 20_000 / (gms / 1000.0)}
     return out
 
 

@@ -138,9 +138,10 @@ int tpcf_grid_info(tpcf_grid grid, int64_t *n_points, int32_t *cells_per_axis);
 int tpcf_grid_points(tpcf_grid grid, uint32_t *xyz, float *w, int64_t *order, void *stream);
 
 /* Testing aid for the device-side failure path (the paper has no counterpart).
- *   polls: how many non-blocking polls a tensor-core kernel (the split-precision
- *     coupling, the emulator's products) spends in each mbarrier wait before it
- *     gives up; 0 restores the default (2^26 polls, far longer than any stage).
+ *   polls: the bound of every mbarrier wait of a tensor-core kernel before it
+ *     gives up: the split-precision coupling makes `polls` non-blocking polls,
+ *     the emulator's products polls / 16 suspending polls of at most a
+ *     microsecond each; 0 restores the default (2^26, far longer than any stage).
  *   unmet_wait: nonzero makes every such kernel, once its own tensor-core work
  *     has completed, wait once more on an mbarrier phase that nothing completes
  *     (a flag that nothing sets), with that limit.

@@ -18,7 +18,9 @@
  *
  * All device pointers are caller-owned and all calls are asynchronous on the
  * given stream (NULL: the legacy default stream); the handle owns its weights,
- * optimiser state and scratch.  Status codes are those of tpcf.h.
+ * optimiser state and scratch.  Batches run in passes of up to 32768 rows; the
+ * per-pass scratch is allocated on first use and grows with the batch (a call
+ * that grows it synchronises its stream first).  Status codes are those of tpcf.h.
  */
 #ifndef TPCF_EMU_H
 #define TPCF_EMU_H

@@ -545,17 +545,45 @@ __global__ void k_scale_in(const float *__restrict__ x, int64_t n, int w, const 
     }
 }
 
-// per-column mean and standard deviation (FP64 sums); one thread per column
-__global__ void k_col_stats(const float *__restrict__ y, int64_t n, int w, float *__restrict__ mean,
+// Per-column FP64 sums of y and y^2 over a block of rows: block (cx, ry) takes 32
+// columns (one per lane, coalesced rows) and rows ry, ry + R, ..., spread over its
+// eight warps and added in a fixed order (deterministic).
+__global__ void k_col_partial(const float *__restrict__ y, int64_t n, int w, double2 *__restrict__ part)
+{
+    __shared__ double2 red[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    const int64_t R = gridDim.y;
+    double s = 0.0, s2 = 0.0;
+    if (c < w)
+        for (int64_t r = blockIdx.y + R * warp; r < n; r += 8 * R) {
+            const double v = y[r * w + c];
+            s += v;
+            s2 += v * v;
+        }
+    red[warp][lane] = make_double2(s, s2);
+    __syncthreads();
+    if (warp == 0 && c < w) {
+        double2 t = red[0][lane];
+        for (int q = 1; q < 8; ++q) {
+            t.x += red[q][lane].x;
+            t.y += red[q][lane].y;
+        }
+        part[(int64_t)blockIdx.y * w + c] = t;
+    }
+}
+
+// per-column mean and standard deviation from the R row-block partial sums
+__global__ void k_col_stats(const double2 *__restrict__ part, int R, int64_t n, int w, float *__restrict__ mean,
                             float *__restrict__ sd)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= w) return;
     double s = 0.0, s2 = 0.0;
-    for (int64_t r = 0; r < n; ++r) {
-        const double v = y[r * w + c];
-        s += v;
-        s2 += v * v;
+    for (int r = 0; r < R; ++r) {
+        const double2 t = part[(int64_t)r * w + c];
+        s += t.x;
+        s2 += t.y;
     }
     const double mu = n > 0 ? s / n : 0.0;
     const double var = n > 1 ? fmax(s2 / n - mu * mu, 0.0) : 0.0;
@@ -1047,8 +1075,14 @@ int tpcf_emu_fit_output_scaling(tpcf_emu e, const float *y, int64_t n, void *str
 {
     if (!e || !y || n < 1) return emu_fail(TPCF_ERR_ARG, "handle and at least one target row are required");
     const int w = e->widths[e->nl];
-    k_col_stats<<<(w + 127) / 128, 128, 0, (cudaStream_t)stream>>>(y, n, w, e->out_mean, e->out_sd);
-    tpcf::note_launch();
+    // row blocks: enough CTAs to fill the GPU, partials in the split-K workspace
+    int R = (int)std::min<int64_t>(256, (n + 1023) / 1024);
+    R = std::max(1, std::min<int>(R, (int)(e->ws_floats * sizeof(float) / (sizeof(double2) * (size_t)w))));
+    double2 *part = reinterpret_cast<double2 *>(e->ws);
+    cudaStream_t st = (cudaStream_t)stream;
+    k_col_partial<<<dim3((w + 31) / 32, R), 256, 0, st>>>(y, n, w, part);
+    k_col_stats<<<(w + 127) / 128, 128, 0, st>>>(part, R, n, w, e->out_mean, e->out_sd);
+    tpcf::note_launch(2);
     ECK(cudaGetLastError());
     return TPCF_OK;
 }
