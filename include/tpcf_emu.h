@@ -73,6 +73,19 @@ int tpcf_emu_set_params(tpcf_emu emu, const float *params, void *stream);
 /* Host copies of the output scaling (host mean, std [out]). */
 int tpcf_emu_get_output_scaling(tpcf_emu emu, float *mean, float *std_dev);
 
+/* Sets the output scaling from host arrays (mean, std [out]; every std > 0), as
+ * a checkpoint restores it. */
+int tpcf_emu_set_output_scaling(tpcf_emu emu, const float *mean, const float *std_dev);
+
+/* Host copies of the input box (host lo, hi [in]). */
+int tpcf_emu_get_input_box(tpcf_emu emu, float *lo, float *hi);
+
+/* The Adam state, for checkpoints: first and second moments (dev m, v
+ * [n_params]) and the step count (host).  Setting it after tpcf_emu_set_params
+ * (which resets the state) resumes training exactly where it was saved. */
+int tpcf_emu_get_optimizer(tpcf_emu emu, float *m, float *v, int64_t *step, void *stream);
+int tpcf_emu_set_optimizer(tpcf_emu emu, const float *m, const float *v, int64_t step, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1160,6 +1160,46 @@ int tpcf_emu_set_params(tpcf_emu e, const float *params, void *stream)
     return TPCF_OK;
 }
 
+int tpcf_emu_set_output_scaling(tpcf_emu e, const float *mean, const float *std_dev)
+{
+    if (!e || !mean || !std_dev) return emu_fail(TPCF_ERR_ARG, "handle, mean and std_dev are required");
+    const int w = e->widths[e->nl];
+    for (int i = 0; i < w; ++i)
+        if (!(std_dev[i] > 0.f) || !(mean[i] == mean[i])) return emu_fail(TPCF_ERR_ARG, "every std must be > 0");
+    ECK(cudaDeviceSynchronize());
+    ECK(cudaMemcpy(e->out_mean, mean, w * sizeof(float), cudaMemcpyHostToDevice));
+    ECK(cudaMemcpy(e->out_sd, std_dev, w * sizeof(float), cudaMemcpyHostToDevice));
+    return TPCF_OK;
+}
+
+int tpcf_emu_get_input_box(tpcf_emu e, float *lo, float *hi)
+{
+    if (!e || !lo || !hi) return emu_fail(TPCF_ERR_ARG, "handle, lo and hi are required");
+    ECK(cudaMemcpy(lo, e->in_lo, e->widths[0] * sizeof(float), cudaMemcpyDeviceToHost));
+    ECK(cudaMemcpy(hi, e->in_hi, e->widths[0] * sizeof(float), cudaMemcpyDeviceToHost));
+    return TPCF_OK;
+}
+
+int tpcf_emu_get_optimizer(tpcf_emu e, float *m, float *v, int64_t *step, void *stream)
+{
+    if (!e || !m || !v || !step) return emu_fail(TPCF_ERR_ARG, "handle, m, v and step are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    ECK(cudaMemcpyAsync(m, e->m, e->n_params * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    ECK(cudaMemcpyAsync(v, e->v, e->n_params * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    *step = e->step;
+    return TPCF_OK;
+}
+
+int tpcf_emu_set_optimizer(tpcf_emu e, const float *m, const float *v, int64_t step, void *stream)
+{
+    if (!e || !m || !v || step < 0) return emu_fail(TPCF_ERR_ARG, "handle, m, v and step >= 0 are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    ECK(cudaMemcpyAsync(e->m, m, e->n_params * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    ECK(cudaMemcpyAsync(e->v, v, e->n_params * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    e->step = step;
+    return TPCF_OK;
+}
+
 int tpcf_emu_get_output_scaling(tpcf_emu e, float *mean, float *std_dev)
 {
     if (!e || !mean || !std_dev) return emu_fail(TPCF_ERR_ARG, "handle, mean and std_dev are required");

@@ -36,7 +36,9 @@ EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_set_wait_limit", "tpcf_kerne
            "tpcf_covariance", "tpcf_covariance_factors", "tpcf_data_vector_index", "tpcf_check_rsqrt",
            "tpcf_emu_create", "tpcf_emu_destroy", "tpcf_emu_param_count", "tpcf_emu_set_input_box",
            "tpcf_emu_fit_output_scaling", "tpcf_emu_train_step", "tpcf_emu_gradients", "tpcf_emu_predict",
-           "tpcf_emu_get_params", "tpcf_emu_set_params", "tpcf_emu_get_output_scaling"]
+           "tpcf_emu_get_params", "tpcf_emu_set_params", "tpcf_emu_get_output_scaling",
+           "tpcf_emu_set_output_scaling", "tpcf_emu_get_input_box", "tpcf_emu_get_optimizer",
+           "tpcf_emu_set_optimizer"]
 
 
 class TpcfError(RuntimeError):
@@ -147,6 +149,10 @@ def lib():
             "tpcf_emu_get_params": ([P, P, P], ctypes.c_int),
             "tpcf_emu_set_params": ([P, P, P], ctypes.c_int),
             "tpcf_emu_get_output_scaling": ([P, P, P], ctypes.c_int),
+            "tpcf_emu_set_output_scaling": ([P, P, P], ctypes.c_int),
+            "tpcf_emu_get_input_box": ([P, P, P], ctypes.c_int),
+            "tpcf_emu_get_optimizer": ([P, P, P, P, P], ctypes.c_int),
+            "tpcf_emu_set_optimizer": ([P, P, P, I64, P], ctypes.c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -651,6 +657,59 @@ class Emulator:
 
     def set_params(self, p, stream=None):
         _check(lib().tpcf_emu_set_params(self.handle, _ptr(p), _stream(stream)))
+
+    def input_box(self):
+        import numpy as np
+        lo = np.empty(self.widths[0], dtype=np.float32)
+        hi = np.empty(self.widths[0], dtype=np.float32)
+        _check(lib().tpcf_emu_get_input_box(self.handle, _ptr(lo), _ptr(hi)))
+        return lo, hi
+
+    def set_output_scaling(self, mean, sd):
+        import numpy as np
+        mean = np.ascontiguousarray(mean, dtype=np.float32)
+        sd = np.ascontiguousarray(sd, dtype=np.float32)
+        _check(lib().tpcf_emu_set_output_scaling(self.handle, _ptr(mean), _ptr(sd)))
+
+    def optimizer_state(self, stream=None):
+        """(m, v, step): the Adam moments (device tensors) and the step count."""
+        m = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        v = torch.empty(self.n_params, dtype=torch.float32, device=self.device)
+        step = ctypes.c_int64(0)
+        _check(lib().tpcf_emu_get_optimizer(self.handle, _ptr(m), _ptr(v), ctypes.addressof(step), _stream(stream)))
+        return m, v, step.value
+
+    def set_optimizer_state(self, m, v, step, stream=None):
+        _check(lib().tpcf_emu_set_optimizer(self.handle, _ptr(m), _ptr(v), int(step), _stream(stream)))
+
+    def save(self, path, stream=None):
+        """Checkpoint (weights, Adam state and step, input box, output scaling) to
+        `path` (.npz), written to a temporary file and renamed into place."""
+        import os
+        import numpy as np
+        p = self.get_params(stream)
+        m, v, step = self.optimizer_state(stream)
+        torch.cuda.synchronize(self.device)
+        lo, hi = self.input_box()
+        mu, sd = self.output_scaling()
+        tmp = str(path) + ".tmp.npz"
+        np.savez(tmp, widths=np.asarray(self.widths, dtype=np.int64), params=p.cpu().numpy(), m=m.cpu().numpy(),
+                 v=v.cpu().numpy(), step=np.int64(step), in_lo=lo, in_hi=hi, out_mean=mu, out_sd=sd)
+        os.replace(tmp, path)
+
+    @classmethod
+    def load(cls, path, device="cuda", stream=None):
+        """A new handle restored from a checkpoint written by save()."""
+        import numpy as np
+        with np.load(path) as f:
+            emu = cls([int(x) for x in f["widths"]], seed=0, device=device)
+            emu.set_input_box(f["in_lo"], f["in_hi"])
+            emu.set_output_scaling(f["out_mean"], f["out_sd"])
+            emu.set_params(torch.from_numpy(f["params"]).to(device), stream)
+            emu.set_optimizer_state(torch.from_numpy(f["m"]).to(device), torch.from_numpy(f["v"]).to(device),
+                                    int(f["step"]), stream)
+            torch.cuda.synchronize(device)
+        return emu
 
     def close(self):
         if self.handle:
