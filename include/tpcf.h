@@ -107,6 +107,14 @@ int tpcf_version(void);
  * (a diagnostic: the difference around a call is that call's launch count). */
 int64_t tpcf_kernel_launches(void);
 
+/* Host positions to the library's fixed-point coordinates: u = floor(x / box *
+ * 2^32), the product taken in FP64 (Sec. 4.1's cube of side L = box), for n
+ * values (host x[n], host u[n]; three per point for xyz).  Every x must lie in
+ * [0, box); TPCF_ERR_DATA (nothing written past the first bad value) for one
+ * outside or not finite, TPCF_ERR_ARG for box <= 0 or missing arrays.  Wrapping
+ * periodic positions into the box is the caller's step.  No device work. */
+int tpcf_quantize_host(const float *x, int64_t n, double box, uint32_t *u);
+
 /* Number of (l1, l2, L) multipoles the configuration produces.  These are all
  * triples with l1, l2 <= l_max, L in cfg->L, |l1 - l2| <= L <= l1 + l2 and
  * l1 + l2 + L even (Eq. slep2sugy with H_{l1 l2 L} != 0), ordered by the

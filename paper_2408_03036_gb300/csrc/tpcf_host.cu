@@ -1217,6 +1217,20 @@ int tpcf_set_wait_limit(int64_t polls, int32_t unmet_wait)
 
 int64_t tpcf_kernel_launches(void) { return (int64_t)g_launches.load(std::memory_order_relaxed); }
 
+int tpcf_quantize_host(const float *x, int64_t n, double box, uint32_t *u)
+{
+    if (!(box > 0.0) || n < 0 || (n > 0 && (!x || !u))) return fail(TPCF_ERR_ARG, "box > 0 and both arrays are required");
+    const double scale = kTwo32 / box;
+    for (int64_t i = 0; i < n; ++i) {
+        const double v = (double)x[i];
+        if (!(v >= 0.0 && v < box))
+            return fail(TPCF_ERR_DATA, "position %lld (%g) outside [0, %g)", (long long)i, v, box);
+        const double q = std::floor(v * scale);
+        u[i] = q >= kTwo32 ? 0xFFFFFFFFu : (uint32_t)q;   // v < box, so q < 2^32 up to the product's rounding
+    }
+    return TPCF_OK;
+}
+
 int tpcf_multipole_count(const tpcf_config *cfg, int32_t *n_mult)
 {
     int rc = check_config(cfg);

@@ -24,7 +24,7 @@ LOS = {"z": 0, "observer": 1}
 CONV = {"S_COEFF": 0, "PAPER_EQ": 1}
 
 # Names of every entry point include/tpcf.h declares (checked by the tests).
-EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_set_wait_limit", "tpcf_kernel_launches", "tpcf_multipole_count", "tpcf_multipole_index",
+EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_set_wait_limit", "tpcf_kernel_launches", "tpcf_quantize_host", "tpcf_multipole_count", "tpcf_multipole_index",
            "tpcf_bin_edges", "tpcf_build_grid", "tpcf_grid_destroy", "tpcf_grid_info", "tpcf_grid_points",
            "tpcf_accumulate_alm", "tpcf_pair_counts", "tpcf_partial_sizes", "tpcf_estimate_3pcf_partial",
            "tpcf_estimate_3pcf_finish", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
@@ -149,6 +149,7 @@ def lib():
             "tpcf_emu_get_params": ([P, P, P], ctypes.c_int),
             "tpcf_emu_set_params": ([P, P, P], ctypes.c_int),
             "tpcf_emu_get_output_scaling": ([P, P, P], ctypes.c_int),
+            "tpcf_quantize_host": ([P, I64, ctypes.c_double, P], ctypes.c_int),
             "tpcf_emu_set_output_scaling": ([P, P, P], ctypes.c_int),
             "tpcf_emu_get_input_box": ([P, P, P], ctypes.c_int),
             "tpcf_emu_get_optimizer": ([P, P, P, P, P], ctypes.c_int),
@@ -721,6 +722,17 @@ class Emulator:
             self.close()
         except Exception:
             pass
+
+
+def quantize_host(x, box: float):
+    """tpcf_quantize_host: host float positions in [0, box) -> uint32 fixed point
+    (floor(x / box * 2^32) in FP64), same shape."""
+    import numpy as np
+    a = np.ascontiguousarray(x, dtype=np.float32)
+    u = np.empty(a.shape, dtype=np.uint32)
+    _check(lib().tpcf_quantize_host(a.ctypes.data_as(ctypes.c_void_p), a.size, ctypes.c_double(box),
+                                    u.ctypes.data_as(ctypes.c_void_p)))
+    return u
 
 
 def kernel_launches() -> int:

@@ -140,3 +140,25 @@ def test_entry_points_reject_bad_arguments_before_device_work(lib):
     vc = tpcf.Config(10.0, 60.0, 5, 2, (0, 2), box=250.0, los="observer", observer=(float("nan"), 0.0, 0.0))
     with pytest.raises(tpcf.TpcfError):
         tpcf.multipole_index(vc)
+
+
+def test_quantize_host_matches_the_fixed_point_rule(lib):
+    """tpcf_quantize_host against the generators' rule (floor(x / box * 2^32) in
+    FP64) bit for bit, the box edges, and out-of-range or non-finite positions."""
+    from paper_2408_03036_gb300 import synth
+    rng = np.random.default_rng(11)
+    box = 1000.0
+    x = rng.uniform(0.0, box, size=(5000, 3)).astype(np.float32)
+    x[0] = [0.0, np.nextafter(np.float32(box), np.float32(0)), 500.0]
+    u = tpcf.quantize_host(x, box)
+    assert u.shape == x.shape and u.dtype == np.uint32
+    assert np.array_equal(u, synth.quantize(x, box))
+    assert u[0, 0] == 0 and u[0, 2] == 2 ** 31
+    for bad in (-1e-3, box, np.inf, np.nan):
+        y = x.copy()
+        y[7, 1] = bad
+        with pytest.raises(tpcf.TpcfError) as ei:
+            tpcf.quantize_host(y, box)
+        assert ei.value.code == -6
+    with pytest.raises(tpcf.TpcfError):
+        tpcf.quantize_host(x, 0.0)
