@@ -317,7 +317,8 @@ def run_ours(args):
                        "parallelism": "z-slab shards, FP64 partials summed (NCCL)" if ws > 1 else "one GPU",
                        "primaries_per_step": prim_per_step, "pairs_per_step": pairs_per_step,
                        "l2": "flushed between timed steps (256 MB write, outside the events)"},
-            "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof, "e2e": e2e}
+            "clocks": clk.summary(), "gpu_launches": int(launches), "roofline": roof, "e2e": e2e,
+            "pairs_per_s": pairs_per_step * args.steps / (ms_max / 1000.0)}
     if plain is not None:
         line["plain_fp32"] = plain
     if variants is not None:
@@ -399,8 +400,28 @@ def stages_report(cfg, dx, dwt, rx, rwt, dev, stream, tpcf):
         ms = _event_ms(lambda: tpcf.estimate_3pcf(c, xd, wd, stream=stream, device=dev), stream, dev, reps=5)
         small[prec] = {"ms": ms, "primaries_per_s": 20_000 / (ms / 1000.0)}
     tpcf.stream_status(stream)
+    # the oracle on the same small case, on the host cores
+    from oracle import oracle as ora
+    o = ora.Config(20.0, 120.0, 10, 4, (0, 2, 4), True, 500.0)
+    t0 = time.perf_counter()
+    ora.estimate(o, x, w)
+    small["oracle"] = {"s": time.perf_counter() - t0, "cores": ora.max_threads(), "cpu": cpu_model()}
     out["small_case"] = small
     return out
+
+
+def cpu_model():
+    """The host CPU's model string (or the architecture if the system gives none)."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
 def variants_report(cfg, dx, dwt, rx, rwt, dev, stream, tpcf, flush, plain_ms, reps=2):
@@ -788,6 +809,7 @@ def roofline(cfg, d, dw, r, rw, dev, stream, tpcf, reps=3):
     t = statistics.median(ms) / 1000.0
     achieved = FLOP_PER_PAIR * pairs / t / 1e12
     peak = fp32_peak_tflops(dev)
+    scalar_tf, paired_tf = tpcf.measure_fp32_peak(stream=stream)
     return {"bound": "alu", "kernel": "k_pairs_q (harmonic pair stage, D-R field)", "achieved": achieved,
             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "traffic": PAIR_DRAM_BYTES_PER_PRIMARY * n_grid,
@@ -795,6 +817,9 @@ def roofline(cfg, d, dw, r, rw, dev, stream, tpcf, reps=3):
             "per_launch": {"pairs": pairs, "flop_per_pair": FLOP_PER_PAIR, "ms": t * 1000.0,
                            "primaries": n_grid},
             "peak_note": "FP32 FMA pipe: 2 x 128 lanes x SMs x 2070 MHz (recipe unit counts and max clock)",
+            "measured_fp32": {"scalar_fma_tflops": scalar_tf, "ffma2_tflops": paired_tf,
+                              "frac_of_scalar_fma": achieved / scalar_tf,
+                              "note": "FMA-chain microbenchmark in this run (tpcf_measure_fp32_peak)"},
             "coupling": coupling}
 
 

@@ -446,6 +446,13 @@ int tpcf_data_vector_index(const tpcf_config *cfg, const int32_t *l1l2L, int32_t
  * Synchronises the stream. */
 int tpcf_check_rsqrt(int64_t n, uint64_t seed, double *stats, void *stream);
 
+/* Measured FP32 FMA throughput of this GPU, the denominator beside the nominal
+ * 2 x 128 x SMs x clock peak of the pair stage's roofline: host tflops[0] with
+ * scalar FMAs, tflops[1] with paired FFMA2 instructions (8 CTAs of 256 threads
+ * per SM, 8 independent chains per thread, best of three timed runs after a
+ * warm-up).  Synchronises the stream. */
+int tpcf_measure_fp32_peak(double *tflops, void *stream);
+
 /* Synchronises the stream and reports any latched device-side error
  * (TPCF_ERR_DATA, TPCF_ERR_TIMEOUT) or CUDA error; clears the latch. */
 int tpcf_stream_status(void *stream);

@@ -183,6 +183,9 @@ cudaError_t edge_solve(const double *nnn, const double *rfull, int nb, int lmax,
                        cudaStream_t st);
 cudaError_t scale_alpha3(double *x, int64_t n, const double *wsums, cudaStream_t st);
 // Self-check of the pair stage's reciprocal square root (see tpcf_check_rsqrt).
+// FP32 FMA throughput microbenchmark (k_check.cu): blocks x 256 threads, 16 FLOP per
+// thread and iteration; sink is never written in practice.
+cudaError_t ffma_peak(bool paired, int blocks, int iters, float *sink, cudaStream_t st);
 cudaError_t check_rsqrt(int64_t n, unsigned long long seed, double *stats, unsigned long long *maxulp,
                         cudaStream_t st);
 cudaError_t i64_from_u64(const unsigned long long *src, int64_t *dst, int n, cudaStream_t st);

@@ -46,7 +46,53 @@ __global__ void k_check_rsqrt(int64_t n, unsigned long long seed, double *stats,
     atomicMax(maxulp, mu);
 }
 
+// FP32 FMA throughput: every thread runs 8 independent chains of `iters` fused
+// multiply-adds (scalar fma.rn.f32 in inline PTX, or the paired FFMA2 form when
+// PAIRED), enough independent work per scheduler to cover the pipe latency.  The
+// chains' sum is written only if it equals an impossible value, so the work stays.
+template <bool PAIRED>
+__global__ void __launch_bounds__(256) k_ffma_peak(int iters, float *sink)
+{
+    const float s = 1.0f + 1e-7f * (float)(threadIdx.x & 7);
+    if (PAIRED) {
+        float2 a[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[j] = make_float2(0.5f + 0.01f * j, 0.25f + 0.01f * j);
+        const float2 m = make_float2(s, s), c = make_float2(1e-6f, -1e-6f);
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) a[j] = __ffma2_rn(a[j], m, c);
+        }
+        float t = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) t += a[j].x + a[j].y;
+        if (t == -12345.f) sink[threadIdx.x] = t;
+    } else {
+        float a[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = 0.5f + 0.01f * j;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(a[j]) : "f"(s), "f"(1e-6f));
+        }
+        float t = 0.f;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t += a[j];
+        if (t == -12345.f) sink[threadIdx.x] = t;
+    }
+}
+
 }  // namespace
+
+// Launches the FMA microbenchmark on `blocks` CTAs of 256 threads; 16 FLOP per
+// thread and iteration.
+cudaError_t ffma_peak(bool paired, int blocks, int iters, float *sink, cudaStream_t st)
+{
+    if (paired) k_ffma_peak<true><<<blocks, 256, 0, st>>>(iters, sink);
+    else k_ffma_peak<false><<<blocks, 256, 0, st>>>(iters, sink);
+    note_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t check_rsqrt(int64_t n, unsigned long long seed, double *stats, unsigned long long *maxulp,
                         cudaStream_t st)

@@ -1926,6 +1926,39 @@ int tpcf_check_rsqrt(int64_t n, uint64_t seed, double *stats, void *stream)
     return TPCF_OK;
 }
 
+int tpcf_measure_fp32_peak(double *tflops, void *stream)
+{
+    if (!tflops) return fail(TPCF_ERR_ARG, "host tflops[2] required");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevState *ds;
+    int rc = dev_state(&ds);
+    if (rc) return rc;
+    Scratch sc(st);
+    float *sink = nullptr;
+    if ((rc = sc.alloc(&sink, 256, false))) return rc;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    cudaError_t e = cudaEventCreate(&e1);
+    const int blocks = ds->sms * 8, iters = 16384;
+    for (int paired = 0; paired < 2 && e == cudaSuccess; ++paired) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // the first run warms up
+            e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = ffma_peak(paired != 0, blocks, iters, sink, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;
+        }
+        tflops[paired] = 16.0 * iters * 256.0 * blocks / (best * 1e-3) / 1e12;
+    }
+    cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    CK(e);
+    return TPCF_OK;
+}
+
 int tpcf_stream_status(void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;

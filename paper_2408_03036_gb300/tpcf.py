@@ -33,7 +33,7 @@ EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_set_wait_limit", "tpcf_kerne
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
            "tpcf_batch_status",
            "tpcf_estimate_3pcf_batched", "tpcf_autotune",
-           "tpcf_covariance", "tpcf_covariance_factors", "tpcf_data_vector_index", "tpcf_check_rsqrt",
+           "tpcf_covariance", "tpcf_covariance_factors", "tpcf_data_vector_index", "tpcf_check_rsqrt", "tpcf_measure_fp32_peak",
            "tpcf_emu_create", "tpcf_emu_destroy", "tpcf_emu_param_count", "tpcf_emu_set_input_box",
            "tpcf_emu_fit_output_scaling", "tpcf_emu_train_step", "tpcf_emu_gradients", "tpcf_emu_predict",
            "tpcf_emu_get_params", "tpcf_emu_set_params", "tpcf_emu_get_output_scaling",
@@ -136,6 +136,7 @@ def lib():
             "tpcf_autotune": ([CFG, P, P, I64, P, CFG], ctypes.c_int),
             "tpcf_covariance": ([P, I64, I64, P, I64, P, P, P], ctypes.c_int),
             "tpcf_check_rsqrt": ([I64, ctypes.c_uint64, P, P], ctypes.c_int),
+            "tpcf_measure_fp32_peak": ([P, P], ctypes.c_int),
             "tpcf_covariance_factors": ([I64, I64, I64, P, P], ctypes.c_int),
             "tpcf_data_vector_index": ([CFG, P, ctypes.c_int32, ctypes.c_int32, P, I64, P], ctypes.c_int),
             "tpcf_emu_create": ([P, ctypes.c_int32, ctypes.c_uint64, P], ctypes.c_int),
@@ -733,6 +734,13 @@ def quantize_host(x, box: float):
     _check(lib().tpcf_quantize_host(a.ctypes.data_as(ctypes.c_void_p), a.size, ctypes.c_double(box),
                                     u.ctypes.data_as(ctypes.c_void_p)))
     return u
+
+
+def measure_fp32_peak(stream=None):
+    """tpcf_measure_fp32_peak: (scalar FMA, paired FFMA2) throughput in TFLOP/s."""
+    out = (ctypes.c_double * 2)()
+    _check(lib().tpcf_measure_fp32_peak(ctypes.addressof(out), _stream(stream)))
+    return float(out[0]), float(out[1])
 
 
 def kernel_launches() -> int:
