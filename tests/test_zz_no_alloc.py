@@ -66,3 +66,37 @@ def test_static_scratch_rejects_oversize_requests():
     with pytest.raises(tpcf.TpcfError) as ei:
         tpcf.couple_multipoles_static(cfg, alm, None, None, diag, wsp)
     assert ei.value.code == -1 and "static scratch" in str(ei.value)
+
+
+def test_static_scratch_coupling_matches_the_oracle(ora):
+    """NNN^m and the triplet counts of the static-scratch coupling against the FP64
+    oracle's (periodic, analytic randoms): FP32 bar per (m, l1, l2) block, counts
+    exact."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2408_03036_gb300 import build as B
+    B.build()
+    cfg = tpcf.Config(r_min=20.0, r_max=120.0, n_bins=10, l_max=4, Ls=(0, 2, 4), box=500.0)
+    o = ora.Config(20.0, 120.0, 10, 4, (0, 2, 4), True, 500.0)
+    xyz, w = synth.poisson(6000, 21)
+    grid = tpcf.Grid(cfg, xyz, w)
+    alm, counts, diag, wsp, _ = tpcf.accumulate_alm(grid, cfg, monopole_weight=float(w.astype(np.float64).sum()))
+    _, pw, _ = grid.points()
+    nnn, tc = tpcf.couple_multipoles_static(cfg, alm, pw, counts, diag, wsp)
+    tpcf.stream_status()
+    grid.close()
+    est = ora.estimate(o, xyz, w)
+    assert np.array_equal(tc.cpu().numpy(), est.trip_counts)
+    ng, L = nnn.cpu().numpy(), cfg.l_max
+    worst = 0.0
+    for m in range(L + 1):
+        for l1 in range(m, L + 1):
+            for l2 in range(m, L + 1):
+                if (l1 + l2) % 2:
+                    continue
+                ref = est.nnn[m + L, l1, l2].real
+                den = np.abs(ref).max()
+                if den > 0:
+                    worst = max(worst, np.abs(ng[m, l1, l2] - ref).max() / den)
+    assert worst <= TOL, worst
