@@ -106,9 +106,10 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parit
 }
 
 // Bounded wait that suspends instead of spinning: each poll is an
-// mbarrier.try_wait with a suspend-time hint of kSuspendNs, so the thread sleeps
-// until the phase completes (or the hint runs out) and takes no issue slots from the
-// warps doing work; gives up after `polls` polls or when *abort is raised.
+// mbarrier.try_wait with a suspend-time hint of kSuspendNs (the thread may sleep
+// until the phase completes), followed after the first polls by a short
+// __nanosleep, so a waiting thread takes few issue slots from the warps doing
+// work; gives up after `polls` polls or when *abort is raised.
 constexpr uint32_t kSuspendNs = 1000;
 __device__ __forceinline__ bool mbar_sleep_wait_or_abort(uint64_t *bar, uint32_t parity, long long polls,
                                                          const volatile int *abort)
@@ -125,6 +126,9 @@ __device__ __forceinline__ bool mbar_sleep_wait_or_abort(uint64_t *bar, uint32_t
             : "memory");
         if (done) return true;
         if (*abort) return false;
+        // try_wait may return at once: back off so that a waiting thread does not
+        // take issue slots from the warps that work
+        if (it >= 2) __nanosleep(it < 16 ? 32 : 128);
     }
     return false;
 }
