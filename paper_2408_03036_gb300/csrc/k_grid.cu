@@ -105,12 +105,15 @@ __global__ void k_scatter_idx(const int32_t *__restrict__ cid, int64_t tot, int3
     }
 }
 
-// Restores input order inside every cell (one warp per cell; insertion sort in
-// registers for small cells, rank counting for large ones), then gathers the
-// records.  Deterministic output.
+// Orders every cell's points by x, ties by input index (one warp per cell: each
+// point's rank is the number of points of its cell with a smaller key, the keys
+// passed round the warp 32 at a time), then gathers the records.  Deterministic
+// output; the x order lets the pair stage trim a row of cells to the sphere at
+// record granularity.
 __global__ void k_sort_cells(const int32_t *__restrict__ start, int64_t ncell, int64_t *__restrict__ order,
                              const int4 *__restrict__ tmp, int4 *__restrict__ rec, int64_t *__restrict__ scratch)
 {
+    constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t wid = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -118,12 +121,23 @@ __global__ void k_sort_cells(const int32_t *__restrict__ start, int64_t ncell, i
         const int a = start[c], b = start[c + 1];
         const int n = b - a;
         if (n <= 0) continue;
-        // rank of each element = number of smaller input indices in the cell
-        for (int i = lane; i < n; i += 32) {
-            const int64_t v = order[a + i];
+        for (int i0 = 0; i0 < n; i0 += 32) {
+            const int i = i0 + lane;
+            const int64_t v = i < n ? order[a + i] : 0;
+            const uint32_t xv = i < n ? (uint32_t)tmp[v].x : 0u;
             int rank = 0;
-            for (int j = 0; j < n; ++j) rank += (order[a + j] < v) ? 1 : 0;
-            scratch[a + rank] = v;
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                const int j = j0 + lane;
+                const int64_t u = j < n ? order[a + j] : 0;
+                const uint32_t xu = j < n ? (uint32_t)tmp[u].x : 0u;
+                const int cnt = min(32, n - j0);
+                for (int q = 0; q < cnt; ++q) {
+                    const uint32_t xq = __shfl_sync(FULL, xu, q);
+                    const int64_t uq = __shfl_sync(FULL, u, q);
+                    rank += (xq < xv || (xq == xv && uq < v)) ? 1 : 0;
+                }
+            }
+            if (i < n) scratch[a + rank] = v;
         }
         __syncwarp();
         for (int i = lane; i < n; i += 32) {

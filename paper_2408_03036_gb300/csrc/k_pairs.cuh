@@ -246,10 +246,25 @@ __device__ __forceinline__ int gcd_int(int a, int b)
     return a;
 }
 
+// First index k in [a, b) whose record has x >= t (records of a cell are sorted
+// by x), by bisection on the x words alone.
+__device__ __forceinline__ int lower_x(const int4 *rec, int a, int b, long long t)
+{
+    const int *xw = reinterpret_cast<const int *>(rec);
+    while (a < b) {
+        const int mid = (a + b) >> 1;
+        if ((long long)(uint32_t)__ldg(xw + 4 * (size_t)mid) < t) a = mid + 1;
+        else b = mid;
+    }
+    return a;
+}
+
 // Candidate record ranges of a tile (all threads): for every (slot, row of cells
 // within reach) up to two contiguous runs of cells along x (two where a periodic
-// row wraps), trimmed to the sphere of radius r_max around the primary; only
-// non-empty runs are listed, in any order, with the count in *s_nr.
+// row wraps), trimmed to the sphere of radius r_max around the primary: to whole
+// cells, then, since every cell's records are sorted by x, to the records of the
+// two end cells that lie inside the row's chord; only non-empty runs are listed,
+// in any order, with the count in *s_nr.
 __device__ inline void tile_ranges(const PairParams &p, int np, long long mock_cells, const int4 *sPc,
                                    const float4 *sPf, int *rstart, int *rlen, int *rslot, int *s_nr)
 {
@@ -286,17 +301,30 @@ __device__ inline void tile_ranges(const PairParams &p, int np, long long mock_c
             }
             if (x1 >= x0) {
                 const long long base = mock_cells + ((long long)wz * nc + wy) * nc;
+                // the chord [pf.x - wx, pf.x + wx] in whole units (wx carries margins
+                // far above the float roundings of pf.x and of these bounds); a
+                // wrapped run's records sit 2^32 units from their unwrapped place
+                const long long clo = (long long)floorf(pf.x - wx), chi = (long long)ceilf(pf.x + wx);
+                long long lo0 = clo, hi1 = chi;
                 int sa = x0, sb = x1, ta = 1, tb = 0;   // second run empty
                 if (p.periodic) {
-                    if (x0 < 0) { sa = x0 + nc; sb = nc - 1; ta = 0; tb = x1; }
-                    else if (x1 >= nc) { sa = x0; sb = nc - 1; ta = 0; tb = x1 - nc; }
+                    if (x0 < 0) { sa = x0 + nc; sb = nc - 1; ta = 0; tb = x1; lo0 += 4294967296ll; }
+                    else if (x1 >= nc) { sa = x0; sb = nc - 1; ta = 0; tb = x1 - nc; hi1 -= 4294967296ll; }
                 }
+                const bool two = tb >= ta;
+                int e0 = p.cell_start[base + sb + 1];
                 a0 = p.cell_start[base + sa];
-                l0 = p.cell_start[base + sb + 1] - a0;
-                if (tb >= ta) {
+                a0 = lower_x(p.rec, a0, p.cell_start[base + sa + 1], lo0);   // low end of the chord
+                if (two) {
                     a1 = p.cell_start[base + ta];
-                    l1 = p.cell_start[base + tb + 1] - a1;
+                    const int e1 = p.cell_start[base + tb + 1];
+                    const int c1 = max(a1, p.cell_start[base + tb]);
+                    l1 = lower_x(p.rec, c1, e1, hi1 + 1) - a1;            // high end of the chord
+                } else {
+                    const int c0 = max(a0, p.cell_start[base + sb]);
+                    e0 = lower_x(p.rec, c0, e0, hi1 + 1);
                 }
+                l0 = e0 - a0;
             }
         }
         if (l0 > 0) {
