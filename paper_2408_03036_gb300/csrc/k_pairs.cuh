@@ -42,6 +42,12 @@ struct HarmTables {
     // jd = (l, m >= 0); the j = k term of the diagonal is K_lm^2 sum_j gd[jd][j] * acc_j.
     float gd_hi[(TPCF_MAX_LMAX + 1) * (TPCF_MAX_LMAX + 2) / 2][TPCF_MAX_LMAX + 1];
     float gd_lo[(TPCF_MAX_LMAX + 1) * (TPCF_MAX_LMAX + 2) / 2][TPCF_MAX_LMAX + 1];
+    // K_lm as an unevaluated float pair (hi, lo) per real index k (l^2 for m = 0,
+    // l^2 + 2m - 1 and l^2 + 2m for m >= 1), and K_lm^2 rounded to float per
+    // jd = (l, m >= 0): the tile epilogue scales in FP32 (FP64 arithmetic runs at a
+    // small fraction of the FP32 rate on this part)
+    float kout[(TPCF_MAX_LMAX + 1) * (TPCF_MAX_LMAX + 1)][2];
+    float k2[(TPCF_MAX_LMAX + 1) * (TPCF_MAX_LMAX + 2) / 2];
 };
 
 // Direct j = k sums for l_max >= 5: sum_j w_j^2 |V_l^m(z_j) (x_j + i y_j)^m|^2 per
@@ -987,11 +993,9 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
                 float v;
                 if (k == 0) {
                     v = a00(raw, b);
-                } else {
-                    int l = 1;
-                    while ((l + 1) * (l + 1) <= k) ++l;
-                    const int m = (k - l * l + 1) >> 1;
-                    v = (float)((double)raw * __ldg(&p.harm->K[l][m]));
+                } else {   // raw K_lm, rounded once up to the rounding of raw K_lo
+                    const float kh = __ldg(&p.harm->kout[k][0]), kl = __ldg(&p.harm->kout[k][1]);
+                    v = fmaf(raw, kh, __fmul_rn(raw, kl));
                 }
                 p.alm[(g0 + slot) * nb * NLM + rem] = v;
             }
@@ -1017,20 +1021,23 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
         // l >= 1 compensated (sq2_minus) on the unnormalised sums, then scaled by K_lm^2;
         // for l = 0 (where the periodic offset enters) in FP64; exactly zero for keys
         // with at most one pair (no j != k term) unless the offset makes a_0^0 differ
-        // from the single pair's own term.  Summed into FP64 every tile.
+        // from the single pair's own term.  For l >= 1 the products with K_lm^2 and
+        // w_i are FP32 (their roundings vary with the sums, so they carry no common
+        // bias) and only the sum is FP64.  Summed into FP64 every tile.
         for (int i = tid; i < nb * NDIAG; i += T) {
             const int b = i / NDIAG, jd = i % NDIAG;
             int l = 0;
             while ((l + 1) * (l + 2) / 2 <= jd) ++l;
             const int m = jd - l * (l + 1) / 2;
-            const double kd = __ldg(&p.harm->K[l][m]);
-            const float k2 = (float)(kd * kd);
+            const float k2 = __ldg(&p.harm->k2[jd]);
             double acc2 = 0.0;
             for (int sl = 0; sl < np; ++sl) {
                 const float *a = sacc + (sl * nb + b) * NACCP;
                 const bool single = cnt[sl * nb + b] <= 1;
-                double d;
+                const float wq = __int_as_float(sPrim[sl].w);
                 if (l == 0) {
+                    const double kd = __ldg(&p.harm->K[0][0]);
+                    double d;
                     const double raw = (double)a[0];
                     double dd = raw * raw - (p.remove_self ? (double)a[NLM] : 0.0);
                     if (p.remove_self && single) dd = 0.0;   // raw^2 = w^2 up to the rounding of the self sum
@@ -1039,13 +1046,15 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
                         const double c = (s_mono_w - 1.0) * p.mono_coef[b];
                         d += c * (c - 2.0 * kd * raw);
                     }
+                    acc2 = fma((double)wq, d, acc2);
                 } else {
                     const float re = a[l * l + (m ? 2 * m - 1 : 0)];
                     const float im = m ? a[l * l + 2 * m] : 0.f;
+                    float dq;
                     if (!p.remove_self) {
-                        d = (double)k2 * (double)fmaf(re, re, im * im);
+                        dq = fmaf(re, re, im * im);
                     } else if (single) {
-                        d = 0.0;
+                        dq = 0.f;
                     } else {
                         float ch = 0.f, cl = 0.f;
                         if constexpr (Direct<LMAX>::ON) {
@@ -1064,10 +1073,10 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
                                 cl = __fadd_rn(cl, __fadd_rn(e, pe));
                             }
                         }
-                        d = (double)k2 * (double)sq2_minus(re, im, ch, cl);
+                        dq = sq2_minus(re, im, ch, cl);
                     }
+                    acc2 += (double)__fmul_rn(__fmul_rn(k2, dq), wq);
                 }
-                acc2 = fma((double)__int_as_float(sPrim[sl].w), d, acc2);
             }
             d64[i] += acc2;
         }
@@ -1075,7 +1084,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
             const int b = i / NSP, j = i % NSP;
             double acc2 = 0.0;
             for (int sl = 0; sl < np; ++sl)
-                acc2 = fma((double)__int_as_float(sPrim[sl].w), (double)sacc[(sl * nb + b) * NACCP + NLM + j], acc2);
+                acc2 += (double)__fmul_rn(__int_as_float(sPrim[sl].w), sacc[(sl * nb + b) * NACCP + NLM + j]);
             w64[i] += acc2;
         }
         // the bin shares for the next tile: half the old estimate, half this tile's counts

@@ -293,7 +293,17 @@ HarmTables make_tables(int lmax)
     HarmTables h;
     std::memset(&h, 0, sizeof(h));
     for (int l = 0; l <= TPCF_MAX_LMAX; ++l)
-        for (int m = 0; m <= l; ++m) h.K[l][m] = k_scale(l, m);
+        for (int m = 0; m <= l; ++m) {
+            const double k = k_scale(l, m);
+            h.K[l][m] = k;
+            h.k2[l * (l + 1) / 2 + m] = (float)(k * k);
+            const float hi = (float)k, lo = (float)(k - (double)hi);
+            for (int part = 0; part < (m ? 2 : 1); ++part) {
+                const int idx = l * l + (m ? 2 * m - 1 + part : 0);
+                h.kout[idx][0] = hi;
+                h.kout[idx][1] = lo;
+            }
+        }
     int jd = 0;
     for (int l = 0; l <= lmax; ++l)
         for (int m = 0; m <= l; ++m, ++jd) {
