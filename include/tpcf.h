@@ -85,8 +85,8 @@ typedef struct {
     int32_t cell_div;       /* cells per r_max along an axis, 1..6; 0 = automatic */
     int32_t tile_primaries; /* primaries processed together by one CTA, 1..8 (capped so that
                                tile_primaries * n_bins <= 128); 0 = automatic */
-    int32_t chunk;          /* staged pairs per CTA (multiple of 256, 512..12288, above 32 per bin);
-                               0 = automatic (3840 up to l_max 4, else 12288) */
+    int32_t chunk;          /* staged pairs per CTA, 4 bytes each (multiple of 256, 512..49152,
+                               above 32 per bin); 0 = automatic (15360 up to l_max 4, else 49152) */
     int32_t los;            /* line of sight: 0 = z for every primary (Sec. 4.1, default);
                                1 = from `observer` to each primary (survey geometry): every
                                separation's harmonics are taken in a frame whose polar axis is
@@ -397,8 +397,8 @@ int tpcf_estimate_3pcf_batched(const tpcf_config *cfg, const uint32_t *xyz, cons
                                int32_t n_mocks, double *zeta, int64_t *triplet_counts, int32_t *status_per_mock,
                                void *stream);
 
-/* Chooses cell_div (2..6), tile_primaries (1, 2, 4) and chunk (3072, 4096,
- * 6144) for a catalogue like this one by timing the pair stage on a strided
+/* Chooses cell_div (2..6), tile_primaries (1, 2, 4) and chunk (12288, 15360,
+ * 24576) for a catalogue like this one by timing the pair stage on a strided
  * sample of at most 32768 of its primaries (dev xyz[n][3], dev w[n] or NULL) for
  * every valid combination (best of three runs after a warm-up run); *tuned =
  * *cfg with the fastest choice.  A nonzero

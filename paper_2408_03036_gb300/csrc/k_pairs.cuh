@@ -624,8 +624,9 @@ __host__ __device__ inline QMap make_qmap(int P, int nb, int s, int chunk, int b
     m.off_lanekey = o; o = align_up(o + 4 * block, 16);
     m.off_hist = o;    o = align_up(o + 4 * TPCF_MAX_BINS, 16);
     m.off_sacc = o;    o = align_up(o + 4 * nk * naccp, 16);
-    // the queues; reused as the [block][NACCP] transpose area at the end of a tile
-    const int qbytes = 16 * chunk, stage = 4 * block * naccp;
+    // the queues (one record index per entry); reused as the [block][NACCP]
+    // transpose area at the end of a tile
+    const int qbytes = 4 * chunk, stage = 4 * block * naccp;
     m.off_queue = o;   o = align_up(o + (qbytes > stage ? qbytes : stage), 16);
     m.off_d64 = o;     o = align_up(o + 8 * nb * Layout<LMAX>::NDIAG, 16);
     m.off_w64 = o;     o = align_up(o + 8 * nb * Layout<LMAX>::NSP, 16);
@@ -671,7 +672,7 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
     int *lanekey = reinterpret_cast<int *>(smem + M.off_lanekey);
     float *hist = reinterpret_cast<float *>(smem + M.off_hist);  // expected share of every bin
     float *sacc = reinterpret_cast<float *>(smem + M.off_sacc);  // [nk][NACCP] tile sums
-    float4 *queue = reinterpret_cast<float4 *>(smem + M.off_queue);
+    int *queue = reinterpret_cast<int *>(smem + M.off_queue);          // record index per entry
     float *stage = reinterpret_cast<float *>(smem + M.off_queue);
     double *d64 = reinterpret_cast<double *>(smem + M.off_d64);
     double *w64 = reinterpret_cast<double *>(smem + M.off_w64);
@@ -858,9 +859,19 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
             if (tid == 0) s_flag = 0;
             if (myk >= 0) {
                 const int n = min(live[myk], mycap);
-                const float4 *qq = queue + myq;
+                const int *qq = queue + myq;
+                // entries are record indices: the record is re-read (from L2) one
+                // entry ahead of its use and its separation from the primary formed
+                // again, exactly as in the sweep
+                int4 nxt = make_int4(0, 0, 0, 0);
+                if (myr < n) nxt = p.rec[qq[myr]];
                 for (int e = myr; e < n; e += myg) {
-                    float4 v = qq[e];
+                    const int4 q = nxt;
+                    if (e + myg < n) nxt = p.rec[qq[e + myg]];
+                    const int4 pr = sPrim[myk / nb];
+                    float4 v = make_float4((float)(int)((uint32_t)q.x - (uint32_t)pr.x),
+                                           (float)(int)((uint32_t)q.y - (uint32_t)pr.y),
+                                           (float)(int)((uint32_t)q.z - (uint32_t)pr.z), __int_as_float(q.w));
                     rcnt += (int)(__float_as_uint(v.w) >> 31);
                     if constexpr (VLOS) {
                         // the separation in the primary's frame (e1, e2, line of sight)
@@ -891,12 +902,12 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
         int my_start = 0, my_len = 0, my_pos = 0, my_sl = 0;
         // two candidates per lane and step (i and i + 32): independent loads and bins
         bool done = false, have0 = false, have1 = false;
-        float4 ent0 = make_float4(0.f, 0.f, 0.f, 0.f), ent1 = ent0;
+        int ent0 = 0, ent1 = 0;   // record indices
         int ek0 = 0, ek1 = 0;
         // appends a pending entry (one shared atomic); an entry that finds its queue
         // full stays pending and raises the flag.  (Aggregating equal keys across the
         // warp with a match instruction measured slower.)
-        auto append = [&](bool &have, const float4 &ent, int ek) {
+        auto append = [&](bool &have, int ent, int ek) {
             if (!have) return;
             const int pos = atomicAdd(&qcnt[par * nkmax + ek], 1);
             const int2 qi = qinfo[ek];
@@ -933,8 +944,9 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
                 }
                 const int i0 = my_pos + lane, i1 = i0 + 32;
                 const bool v0 = i0 < my_len, v1 = i1 < my_len;
-                const int4 q0 = p.rec[my_start + min(i0, my_len - 1)];
-                const int4 q1 = p.rec[my_start + min(i1, my_len - 1)];
+                const int j0 = my_start + min(i0, my_len - 1), j1 = my_start + min(i1, my_len - 1);
+                const int4 q0 = p.rec[j0];
+                const int4 q1 = p.rec[j1];
                 my_pos += 64;
                 // the range's primary, re-read every step (fewer registers live across the
                 // drains; a register prefetch of the next step measured 2 % at two CTAs per
@@ -952,8 +964,8 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
                 const int b0 = bb.x, b1 = bb.y;
                 have0 = b0 >= 0;
                 have1 = b1 >= 0;
-                ent0 = make_float4(fx0, fy0, fz0, __int_as_float(q0.w));
-                ent1 = make_float4(fx1, fy1, fz1, __int_as_float(q1.w));
+                ent0 = j0;
+                ent1 = j1;
                 ek0 = kb + b0;
                 ek1 = kb + b1;
             }

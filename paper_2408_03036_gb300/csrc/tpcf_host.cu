@@ -149,8 +149,8 @@ int check_config(const tpcf_config *c)
         for (int k = 0; k < 3; ++k)
             if (!std::isfinite(c->observer[k]) || std::fabs(c->observer[k]) > 1e6 * c->box)
                 return fail(TPCF_ERR_ARG, "observer coordinates must be finite and within 1e6 box lengths");
-    if (c->chunk != 0 && (c->chunk < 512 || (c->chunk % 256) != 0 || c->chunk > 12288))
-        return fail(TPCF_ERR_ARG, "chunk must be 0 or a multiple of 256 in 512..12288");
+    if (c->chunk != 0 && (c->chunk < 512 || (c->chunk % 256) != 0 || c->chunk > 49152))
+        return fail(TPCF_ERR_ARG, "chunk must be 0 or a multiple of 256 in 512..49152");
     return TPCF_OK;
 }
 
@@ -395,8 +395,8 @@ Plan make_plan(const tpcf_config *c, int64_t n_sec, int64_t n_prim_hint)
     // the chunk's lane groups need P * n_bins <= 128 keys (half the CTA's lanes)
     P = std::min(P, std::max(1, 128 / c->n_bins));
     p.P = P;
-    // queue entries per CTA: three CTAs per SM up to l_max 4, one above
-    p.chunk = c->chunk ? c->chunk : (c->l_max <= 4 ? 3840 : 12288);
+    // queue entries (4 bytes each) per CTA: three CTAs per SM up to l_max 4, one above
+    p.chunk = c->chunk ? c->chunk : (c->l_max <= 4 ? 15360 : 49152);
     (void)n_prim_hint;
     return p;
 }
@@ -1809,7 +1809,7 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
     const int tiles_all[] = {1, 2, 4};
     const int tiles_fixed[] = {cfg->tile_primaries};
     const bool fixed_tile = cfg->tile_primaries > 0;   // a batch runs one primary per tile
-    const int chunks[] = {3072, 4096, 6144};
+    const int chunks[] = {12288, 15360, 24576};
     for (int dv : divs) {
         tpcf_config t = *cfg;
         t.cell_div = dv;

@@ -182,7 +182,7 @@ def test_autotune_returns_a_valid_faster_choice(gpu, ora):
     tuned = tpcf.autotune(cfg, xyz, w)
     assert tuned.cell_div in (2, 3, 4, 5, 6)
     assert tuned.tile_primaries in (1, 2, 4)
-    assert tuned.chunk in (3072, 4096, 6144)
+    assert tuned.chunk in (12288, 15360, 24576)
     res = tpcf.estimate_3pcf(tuned, xyz[:4000], w[:4000])
     tpcf.stream_status()
     ocfg = ora.Config(20.0, 120.0, 10, 4, (0, 2, 4), True, 500.0, True, "S_COEFF")
