@@ -457,6 +457,18 @@ int tpcf_measure_fp32_peak(double *tflops, void *stream);
  * (TPCF_ERR_DATA, TPCF_ERR_TIMEOUT) or CUDA error; clears the latch. */
 int tpcf_stream_status(void *stream);
 
+/* Memory housekeeping (the paper has no counterpart).  Device scratch and grids
+ * come, outside stream capture, from a memory pool that the library owns on each
+ * device; freed blocks stay cached there for the next call instead of going back
+ * to the driver at every synchronisation (for the clustered D - R field that is
+ * the 3.2 GB of per-primary harmonic sums of every estimate).  This call hands
+ * the cached blocks of the current device back to the driver: blocks whose
+ * stream-ordered release has completed (synchronise the streams that used the
+ * library first to return all of them).  Blocks still in use, and grids not yet
+ * destroyed, are kept.  Host only; no stream work; TPCF_OK when the device has no
+ * pool yet. */
+int tpcf_trim_memory(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -190,6 +190,16 @@ cudaError_t check_rsqrt(int64_t n, unsigned long long seed, double *stats, unsig
                         cudaStream_t st);
 cudaError_t i64_from_u64(const unsigned long long *src, int64_t *dst, int n, cudaStream_t st);
 
+// Stream-ordered allocation of the library's device scratch and grids (released
+// with cudaFreeAsync).  Outside a stream capture the memory comes from a pool of
+// the library's own on the current device, which keeps freed blocks for later
+// calls instead of handing them back to the driver at every synchronisation
+// (tpcf_trim_memory hands them back); inside a capture from the device's default
+// pool, as the graph's own allocations.
+cudaError_t scratch_malloc(void **p, size_t bytes, cudaStream_t st);
+// Unique id of the current CUDA context (0 if the driver does not report one).
+unsigned long long context_id();
+
 // Offsets of the per-m Gram blocks in the packed G array: block m is
 // n_m x n_m doubles with n_m = nb * (lmax - m + 1); row index (l - m) * nb + b.
 __host__ __device__ inline int64_t gram_offset(int nb, int lmax, int m)

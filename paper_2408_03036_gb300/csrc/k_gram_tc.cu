@@ -648,7 +648,7 @@ cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, 
         attr_done[tf32].fetch_or(bit, std::memory_order_acq_rel);
     }
     const size_t pbytes = (size_t)slices * p.plan.slice_size * sizeof(double);
-    e = cudaMallocAsync((void **)&p.partial, pbytes, st);
+    e = scratch_malloc((void **)&p.partial, pbytes, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p.partial, 0, pbytes, st);
     if (e == cudaSuccess) {
@@ -693,7 +693,7 @@ cudaError_t couple_gram_simt(const float *alm, const float *w, int64_t K, int nb
     p.wait_limit = device_wait_limit();
     p.wait_unmet = 0;
     const size_t pbytes = (size_t)slices * p.plan.slice_size * sizeof(double);
-    cudaError_t e = cudaMallocAsync((void **)&p.partial, pbytes, st);
+    cudaError_t e = scratch_malloc((void **)&p.partial, pbytes, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(p.partial, 0, pbytes, st);
     if (e == cudaSuccess) {

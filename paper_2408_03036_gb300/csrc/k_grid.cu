@@ -300,7 +300,7 @@ struct Temps {
     template <class T>
     cudaError_t alloc(T **q, size_t bytes)
     {
-        const cudaError_t e = cudaMallocAsync((void **)q, bytes, st);
+        const cudaError_t e = scratch_malloc((void **)q, bytes, st);
         if (e == cudaSuccess) p[n++] = *q;
         return e;
     }
@@ -327,9 +327,9 @@ cudaError_t build_grid_dev(const uint32_t *xyz, const float *w, int64_t n,
     int4 *tmp = nullptr;
     int64_t *scratch = nullptr;
     const int64_t alloc_n = tot > 0 ? tot : 1;
-    if ((e = cudaMallocAsync((void **)&g.rec, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&g.order, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&g.cell_start, (ncell + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = scratch_malloc((void **)&g.rec, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
+    if ((e = scratch_malloc((void **)&g.order, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
+    if ((e = scratch_malloc((void **)&g.cell_start, (ncell + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
     if ((e = tmps.alloc(&cid, alloc_n * sizeof(int32_t))) != cudaSuccess) return e;
     if ((e = tmps.alloc(&tmp, alloc_n * sizeof(int4))) != cudaSuccess) return e;
     if ((e = tmps.alloc(&scratch, alloc_n * sizeof(int64_t))) != cudaSuccess) return e;
@@ -367,9 +367,9 @@ cudaError_t build_grid_batched_dev(const uint32_t *xyz, const float *w, int64_t 
     int4 *tmp = nullptr;
     int64_t *scratch = nullptr;
     const int64_t alloc_n = n > 0 ? n : 1;
-    if ((e = cudaMallocAsync((void **)&g.rec, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&g.order, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync((void **)&g.cell_start, (ncell + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
+    if ((e = scratch_malloc((void **)&g.rec, alloc_n * sizeof(int4), st)) != cudaSuccess) return e;
+    if ((e = scratch_malloc((void **)&g.order, alloc_n * sizeof(int64_t), st)) != cudaSuccess) return e;
+    if ((e = scratch_malloc((void **)&g.cell_start, (ncell + 1) * sizeof(int32_t), st)) != cudaSuccess) return e;
     if ((e = tmps.alloc(&cid, alloc_n * sizeof(int32_t))) != cudaSuccess) return e;
     if ((e = tmps.alloc(&mock_of, alloc_n * sizeof(int32_t))) != cudaSuccess) return e;
     if ((e = tmps.alloc(&tmp, alloc_n * sizeof(int4))) != cudaSuccess) return e;

@@ -342,6 +342,15 @@ struct DevState {
 std::mutex g_mu;
 DevState g_dev[64];
 
+// Per-device scratch pools (scratch_malloc), each tagged with the context it was
+// made in: cudaDeviceReset ends the context and its pools with it.
+struct ScratchPool {
+    cudaMemPool_t pool = nullptr;
+    unsigned long long ctx = 0;
+};
+std::mutex g_pool_mu;
+ScratchPool g_pool[64];
+
 int dev_state(DevState **out)
 {
     int d = 0;
@@ -441,11 +450,79 @@ cudaError_t pair_launch(int lmax, bool counts, const PairParams &p, const HarmTa
     }
 }
 
+}  // namespace
+
+// Unique id of the current CUDA context (the driver's cuCtxGetId, reached through
+// the runtime's entry-point query so the library does not link libcuda); 0 if
+// unavailable.  cudaDeviceReset replaces the primary context, and its id.
+unsigned long long tpcf::context_id()
+{
+    using GetCurrent = int (*)(void **);
+    using GetId = int (*)(void *, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+    return 0;
+}
+
+cudaError_t tpcf::scratch_malloc(void **p, size_t bytes, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusNone) return cudaMallocAsync(p, bytes, st);
+    int d = 0;
+    if ((e = cudaGetDevice(&d)) != cudaSuccess) return e;
+    if (d < 0 || d >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool = nullptr;
+    {
+        const unsigned long long ctx = context_id();
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        ScratchPool &sp = g_pool[d];
+        if (!sp.pool || sp.ctx != ctx) {
+            // a pool left from an earlier context went with that context
+            cudaMemPoolProps props;
+            std::memset(&props, 0, sizeof(props));
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = d;
+            cudaMemPool_t np = nullptr;
+            if ((e = cudaMemPoolCreate(&np, &props)) != cudaSuccess) return e;
+            uint64_t keep = ~0ull;
+            if ((e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+                cudaMemPoolDestroy(np);
+                return e;
+            }
+            sp.pool = np;
+            sp.ctx = ctx;
+        }
+        pool = sp.pool;
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+
+namespace {
+
 // Runs the pair stage over `n_prim` primary records against grid g.
 template <class T>
 int dalloc(T **p, size_t n, cudaStream_t st, bool zero)
 {
-    CK(cudaMallocAsync((void **)p, (n ? n : 1) * sizeof(T), st));
+    CK(scratch_malloc((void **)p, (n ? n : 1) * sizeof(T), st));
     if (zero) CK(cudaMemsetAsync(*p, 0, (n ? n : 1) * sizeof(T), st));
     return TPCF_OK;
 }
@@ -769,7 +846,7 @@ int mono_coef_dev(const tpcf_config *c, double **out, cudaStream_t st)
         const double vb = 4.0 * kPi / 3.0 * (r[b + 1] * r[b + 1] * r[b + 1] - r[b] * r[b] * r[b]);
         coef[b] = vb / (c->box * c->box * c->box) / std::sqrt(4.0 * kPi);
     }
-    CK(cudaMallocAsync((void **)out, c->n_bins * sizeof(double), st));
+    CK(scratch_malloc((void **)out, c->n_bins * sizeof(double), st));
     CK(cudaMemcpyAsync(*out, coef.data(), c->n_bins * sizeof(double), cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
     return TPCF_OK;
@@ -789,7 +866,7 @@ int randoms_are_negative(const float *w1, int64_t n1, const float *w2, int64_t n
         return TPCF_OK;
     }
     int *d = nullptr;
-    CK(cudaMallocAsync((void **)&d, 2 * sizeof(int), st));
+    CK(scratch_malloc((void **)&d, 2 * sizeof(int), st));
     cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(int), st);
     if (e == cudaSuccess && w1) e = weight_signs(w1, n1, d, st);
     if (e == cudaSuccess && w2) e = weight_signs(w2, n2, d, st);
@@ -1966,6 +2043,19 @@ int tpcf_measure_fp32_peak(double *tflops, void *stream)
     cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     CK(e);
+    return TPCF_OK;
+}
+
+int tpcf_trim_memory(void)
+{
+    int d = 0;
+    CK(cudaGetDevice(&d));
+    if (d < 0 || d >= 64) return fail(TPCF_ERR_CUDA, "device index out of range");
+    const unsigned long long ctx = context_id();
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    ScratchPool &sp = g_pool[d];
+    if (!sp.pool || sp.ctx != ctx) return TPCF_OK;
+    CK(cudaMemPoolTrimTo(sp.pool, 0));
     return TPCF_OK;
 }
 

@@ -71,34 +71,6 @@ std::mutex g_mu;
 unsigned char *g_ptr[64] = {nullptr};
 unsigned long long g_ctx[64] = {0};   // id of the context the block was set up in
 
-// Unique id of the current CUDA context (the driver's cuCtxGetId, reached through
-// the runtime's entry-point query so the library does not link libcuda); 0 if
-// unavailable.  cudaDeviceReset replaces the primary context, and its id.
-unsigned long long context_id()
-{
-    using GetCurrent = int (*)(void **);
-    using GetId = int (*)(void *, unsigned long long *);
-    static GetCurrent get_current = nullptr;
-    static GetId get_id = nullptr;
-    static bool looked = false;
-    if (!looked) {
-        looked = true;
-        void *f = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            get_current = reinterpret_cast<GetCurrent>(f);
-        f = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            get_id = reinterpret_cast<GetId>(f);
-    }
-    void *ctx = nullptr;
-    unsigned long long id = 0;
-    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
-    return 0;
-}
-
 // Device address of the scratch block on the current device, set up on first use
 // in the current context.
 int scratch_on(unsigned char **out)
@@ -111,7 +83,7 @@ int scratch_on(unsigned char **out)
     void *p = nullptr;
     e = cudaGetSymbolAddress(&p, g_couple_scratch);
     if (e != cudaSuccess || !p) return tpcf::set_error(TPCF_ERR_CUDA, "cudaGetSymbolAddress failed for the static scratch");
-    const unsigned long long ctx = context_id();
+    const unsigned long long ctx = tpcf::context_id();
     std::lock_guard<std::mutex> lk(g_mu);
     if (g_ptr[dev] != (unsigned char *)p || g_ctx[dev] != ctx) {
         static double tables[kSelfDoubles];

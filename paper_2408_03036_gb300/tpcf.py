@@ -29,7 +29,7 @@ EXPORTS = ["tpcf_last_error", "tpcf_version", "tpcf_set_wait_limit", "tpcf_kerne
            "tpcf_accumulate_alm", "tpcf_pair_counts", "tpcf_partial_sizes", "tpcf_estimate_3pcf_partial",
            "tpcf_estimate_3pcf_finish", "tpcf_couple_multipoles", "tpcf_project", "tpcf_estimate_3pcf",
            "tpcf_estimate_3pcf_xi", "tpcf_estimate_3pcf_full_edge",
-           "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_couple_multipoles_static",
+           "tpcf_estimate_3pcf_host", "tpcf_stream_status", "tpcf_trim_memory", "tpcf_couple_multipoles_static",
            "tpcf_batch_create", "tpcf_batch_info", "tpcf_batch_run", "tpcf_batch_run_graph", "tpcf_batch_destroy",
            "tpcf_batch_status",
            "tpcf_estimate_3pcf_batched", "tpcf_autotune",
@@ -125,6 +125,7 @@ def lib():
             "tpcf_estimate_3pcf_full_edge": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P], ctypes.c_int),
             "tpcf_estimate_3pcf_host": ([CFG, P, P, I64, P, P, I64, P, P, P, P, P, P], ctypes.c_int),
             "tpcf_stream_status": ([P], ctypes.c_int),
+            "tpcf_trim_memory": ([], ctypes.c_int),
             "tpcf_couple_multipoles_static": ([P, P, P, I64, CFG, P, P, P, P, P], ctypes.c_int),
             "tpcf_batch_create": ([CFG, P, ctypes.c_int32, I64, P], ctypes.c_int),
             "tpcf_batch_info": ([P, P, P], ctypes.c_int),
@@ -750,3 +751,9 @@ def kernel_launches() -> int:
 
 def stream_status(stream=None):
     _check(lib().tpcf_stream_status(_stream(stream)))
+
+
+def trim_memory():
+    """tpcf_trim_memory: hands the library's cached device scratch of the current
+    device back to the driver (blocks whose stream-ordered release has completed)."""
+    _check(lib().tpcf_trim_memory())
