@@ -252,17 +252,27 @@ __device__ __forceinline__ int gcd_int(int a, int b)
     return a;
 }
 
-// First index k in [a, b) whose record has x >= t (records of a cell are sorted
-// by x), by bisection on the x words alone.
-__device__ __forceinline__ int lower_x(const int4 *rec, int a, int b, long long t)
+// Two independent bisections in lockstep on the x words of the records (the
+// records of a cell are sorted by x): on return a is the first index in [a, b)
+// whose record has x >= ta, and c the first in [c, d) with x >= tc.  The two
+// loads of a round are in flight together, so a row's two chord ends cost one
+// chain of L2 round trips, not two.
+__device__ __forceinline__ void lower_x2(const int4 *rec, int &a, int b, long long ta, int &c, int d, long long tc)
 {
     const int *xw = reinterpret_cast<const int *>(rec);
-    while (a < b) {
-        const int mid = (a + b) >> 1;
-        if ((long long)(uint32_t)__ldg(xw + 4 * (size_t)mid) < t) a = mid + 1;
-        else b = mid;
+    while (a < b || c < d) {
+        const int ma = (a + b) >> 1, mc = (c + d) >> 1;
+        const long long va = a < b ? (long long)(uint32_t)__ldg(xw + 4 * (size_t)ma) : 0;
+        const long long vc = c < d ? (long long)(uint32_t)__ldg(xw + 4 * (size_t)mc) : 0;
+        if (a < b) {
+            if (va < ta) a = ma + 1;
+            else b = ma;
+        }
+        if (c < d) {
+            if (vc < tc) c = mc + 1;
+            else d = mc;
+        }
     }
-    return a;
 }
 
 // Candidate record ranges of a tile (all threads): for every (slot, row of cells
@@ -318,19 +328,26 @@ __device__ inline void tile_ranges(const PairParams &p, int np, long long mock_c
                     else if (x1 >= nc) { sa = x0; sb = nc - 1; ta = 0; tb = x1 - nc; hi1 -= 4294967296ll; }
                 }
                 const bool two = tb >= ta;
-                int e0 = p.cell_start[base + sb + 1];
-                a0 = p.cell_start[base + sa];
-                a0 = lower_x(p.rec, a0, p.cell_start[base + sa + 1], lo0);   // low end of the chord
+                // the low end of the chord lies in cell sa, the high end in the last
+                // cell of the run that ends the row (tb when the row wraps, else sb);
+                // the two searches are independent (same sorted cell when sa = sb,
+                // later cells otherwise)
+                const int hc = two ? tb : sb;
+                int lo_a = p.cell_start[base + sa];
+                const int lo_b = p.cell_start[base + sa + 1];
+                int hi_a = p.cell_start[base + hc];
+                const int hi_b = p.cell_start[base + hc + 1];
+                const int end0 = two ? p.cell_start[base + sb + 1] : 0;
+                const int start1 = two ? p.cell_start[base + ta] : 0;
+                lower_x2(p.rec, lo_a, lo_b, lo0, hi_a, hi_b, hi1 + 1);
+                a0 = lo_a;
                 if (two) {
-                    a1 = p.cell_start[base + ta];
-                    const int e1 = p.cell_start[base + tb + 1];
-                    const int c1 = max(a1, p.cell_start[base + tb]);
-                    l1 = lower_x(p.rec, c1, e1, hi1 + 1) - a1;            // high end of the chord
+                    a1 = start1;
+                    l1 = hi_a - a1;
+                    l0 = end0 - a0;
                 } else {
-                    const int c0 = max(a0, p.cell_start[base + sb]);
-                    e0 = lower_x(p.rec, c0, e0, hi1 + 1);
+                    l0 = hi_a - a0;
                 }
-                l0 = e0 - a0;
             }
         }
         if (l0 > 0) {
