@@ -45,6 +45,10 @@ PAIR_DRAM_BYTES_PER_PRIMARY = 1987.0
 # covariance batch: lognormal mocks (same field recipe, 256^3 mesh) in a periodic
 # cube of side 1000 Mpc/h, sizes uniform in [100k, 400k], analytic randoms
 N_MOCKS, MOCK_LO, MOCK_HI, MOCK_MESH, SEED_MOCKS = 256, 100_000, 400_000, 256, 77
+# many small mocks of the same recipe (10k-20k points, 128^3 mesh), where a call
+# per mock pays its fixed cost (host set-up, synchronisations, launches) against
+# about 0.1 ms of pair work
+N_SMALL, SMALL_LO, SMALL_HI, SMALL_MESH = 1024, 10_000, 20_000, 128
 
 
 def config(precision="fp32"):
@@ -536,6 +540,66 @@ def batch_mocks(args, dev, stream, tpcf, flush, rank=0):
         t = s.elapsed_time(e) / 1000.0
         out["sequential"][prec] = {"mocks_per_hour": n_mocks / t * 3600.0, "s_per_batch": t}
         out["batched_over_sequential_" + prec] = out[prec]["mocks_per_hour"] / (n_mocks / t * 3600.0)
+    del xyz, w
+    out["small_mocks"] = small_mock_batch(dev, stream, tpcf, flush, rank)
+    return out
+
+
+def small_mock_batch(dev, stream, tpcf, flush, rank=0):
+    """The batch against one tpcf_estimate_3pcf call per mock on many small mocks
+    (N_SMALL lognormal mocks of SMALL_LO..SMALL_HI points in the same periodic box),
+    where a call's fixed cost is comparable with its pair work: one graph launch of
+    the whole batch against the loop of calls, each with its default tiles, both
+    couplings."""
+    import numpy as np
+    import torch
+    from paper_2408_03036_gb300 import synth
+    seed0 = SEED_MOCKS + 500 + 1000 * rank
+    sizes = synth.mock_sizes(N_SMALL, SMALL_LO, SMALL_HI, seed0)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    xyz = torch.empty((int(off[-1]), 3), dtype=torch.int32, device=dev)
+    for k, n in enumerate(sizes):
+        x, _ = synth.lognormal_device(int(n), BOX, seed0 + 1 + k, mesh=SMALL_MESH, device=dev)
+        xyz[off[k]:off[k + 1]] = x
+        del x
+    w = torch.ones(int(off[-1]), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    out = {"mocks": N_SMALL, "points": int(off[-1]), "sizes": [int(sizes.min()), int(sizes.max())],
+           "note": "one graph launch of the batch vs one tpcf_estimate_3pcf call per mock; default tiles"}
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for prec in ("fp32", "bf16x3"):
+        cfg = mock_config(prec, tile_primaries=1)
+        b = tpcf.Batch(cfg, off)
+        z = b.zeta_buffer(dev)
+        b.run_graph(xyz, w, z, stream=stream)          # eager run + capture (warm-up)
+        b.run_graph(xyz, w, z, stream=stream)          # first graph launch (warm-up)
+        torch.cuda.synchronize(dev)
+        tpcf.stream_status(stream)
+        flush.zero_()
+        s.record(stream)
+        b.run_graph(xyz, w, z, stream=stream)
+        e.record(stream)
+        torch.cuda.synchronize(dev)
+        tpcf.stream_status(stream)
+        tb = s.elapsed_time(e) / 1000.0
+        b.close()
+        del z
+        cfg1 = mock_config(prec)
+        for k in range(2):
+            tpcf.estimate_3pcf(cfg1, xyz[off[k]:off[k + 1]], w[off[k]:off[k + 1]], stream=stream, device=dev,
+                               want_all=False)
+        torch.cuda.synchronize(dev)
+        flush.zero_()
+        s.record(stream)
+        for k in range(N_SMALL):
+            tpcf.estimate_3pcf(cfg1, xyz[off[k]:off[k + 1]], w[off[k]:off[k + 1]], stream=stream, device=dev,
+                               want_all=False)
+        e.record(stream)
+        torch.cuda.synchronize(dev)
+        tpcf.stream_status(stream)
+        ts = s.elapsed_time(e) / 1000.0
+        out[prec] = {"batched_mocks_per_hour": N_SMALL / tb * 3600.0, "sequential_mocks_per_hour": N_SMALL / ts * 3600.0,
+                     "batched_over_sequential": ts / tb}
     return out
 
 

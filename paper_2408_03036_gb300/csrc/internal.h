@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/tpcf.h"
@@ -148,6 +149,18 @@ cudaError_t couple_gram_simt(const float *alm, const float *w, int64_t K, int nb
 // Tensor-core (tcgen05) Gram with bf16 or tf32 hi/lo splits; fills all of G.
 cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, int lmax, bool tf32, double *G,
                            int *err, int sms, cudaStream_t st);
+// The Gram of every catalogue of a batch group in one launch (precision: a
+// TPCF_PREC_* value): catalogue c owns the slices [mslice[c], mslice[c + 1]) of
+// the slice boundaries slice_k (primaries relative to alm / w, in device memory,
+// made by gram_batch_slices: no slice straddles two catalogues) and its G goes to
+// G + c * gram_offset(nb, lmax, lmax + 1).
+cudaError_t couple_gram_batched(const float *alm, const float *w, int n_cat, const int64_t *d_slice_k,
+                                int n_slices, const int *d_mslice, int nb, int lmax, int precision, double *G,
+                                int *err, int sms, cudaStream_t st);
+// Host slice table of a batch group with catalogue offsets off[0..n_cat] (off[0]
+// need not be 0); empty when no tile plan exists for (nb, lmax).
+void gram_batch_slices(const int64_t *off, int n_cat, int nb, int lmax, bool simt, int sms,
+                       std::vector<int64_t> &slice_k, std::vector<int> &mslice);
 // The FP32 Gram with a caller-provided tile table and no allocation (accumulates into G).
 cudaError_t couple_gram_fp32_tiles(const float *alm, const float *w, int64_t K, int nb, int lmax, int *d_tiles,
                                    double *G, cudaStream_t st);

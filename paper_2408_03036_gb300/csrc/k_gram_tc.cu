@@ -23,10 +23,12 @@
 // per buffer.  Every wait is bounded; a timeout latches an error flag, waits for
 // the MMAs in flight, releases tensor memory and returns.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstring>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <vector>
 
 #include "internal.h"
 #include "tc_common.cuh"
@@ -39,18 +41,6 @@ using namespace tc;
 
 constexpr int kThreads = 512;
 constexpr int kRowTile = 128;                 // M of every MMA (TMEM lanes)
-constexpr int kStageBytesRow = 32;            // one K step = 32 bytes per operand row
-constexpr int kFlushK = 1024;                 // K rows accumulated in FP32 per flush
-
-// Splits x into hi + lo in the MMA type, returned as the 16-bit (bf16) or
-// 32-bit (tf32, low 13 mantissa bits zero) storage words.
-__device__ __forceinline__ void split_bf16(float x, uint16_t &hi, uint16_t &lo)
-{
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-    hi = __bfloat16_as_ushort(h);
-    lo = __bfloat16_as_ushort(l);
-}
 
 // Two values at once: hi = bf16x2(a, b) rounded to nearest, lo = bf16x2 of the
 // exact FP32 remainders; element a in the low half (lower K index).
@@ -115,6 +105,9 @@ struct TcParams {
     int nb, lmax;
     int64_t per_slice;    // primaries per slice
     int n_slices;
+    // slice boundaries [n_slices + 1] in device memory (a batch: slices never
+    // straddle two catalogues); null: slice s is [s per_slice, (s + 1) per_slice) of K
+    const int64_t *slice_k;
     double *partial;      // [n_slices][slice_size], zeroed before the launch
     int *err;
     long long wait_limit; // polls of a per-stage mbarrier wait before giving up
@@ -247,8 +240,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const TcParams p)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + 2 * stage_bytes + 16 * R + 16);
     volatile int *s_abort = reinterpret_cast<int *>(smem + 2 * stage_bytes + 16 * R + 20);
 
-    const int64_t i_beg = (int64_t)slice * p.per_slice;
-    const int64_t i_end = min(p.K, i_beg + p.per_slice);
+    const int64_t i_beg = p.slice_k ? p.slice_k[slice] : (int64_t)slice * p.per_slice;
+    const int64_t i_end = p.slice_k ? p.slice_k[slice + 1] : min(p.K, i_beg + p.per_slice);
     const int64_t nst = i_end > i_beg ? (i_end - i_beg + KP - 1) / KP : 0;
 
     // row table; unused rows stay zero in both stages for the whole launch
@@ -465,11 +458,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const TcParams p)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.tmem_alloc));
 }
 
-// G_m[i][j] = sum over slices of the unit entries that hold it.
+// G_m[i][j] = sum over slices of the unit entries that hold it.  With a slice
+// range per catalogue (mslice [n_cat + 1], grid y = catalogue), catalogue c sums
+// its own slices into G + c * gram_offset(nb, lmax, lmax + 1).
 __global__ void k_gram_tc_reduce(const double *partial, int n_slices, long long slice_size, int nb, int lmax,
-                                 TcPlan plan, double *G)
+                                 TcPlan plan, double *G, const int *mslice = nullptr)
 {
     const int64_t total = gram_offset(nb, lmax, lmax + 1);
+    int s0 = 0, s1 = n_slices;
+    if (mslice) {
+        s0 = mslice[blockIdx.y];
+        s1 = mslice[blockIdx.y + 1];
+        G += (int64_t)blockIdx.y * total;
+    }
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
          idx += (int64_t)gridDim.x * blockDim.x) {
         int m = 0;
@@ -487,7 +488,7 @@ __global__ void k_gram_tc_reduce(const double *partial, int n_slices, long long 
         const TcUnit u = plan.u[unit];
         const int64_t src = u.part_off + (int64_t)ri * u.n + cj;
         double s = 0.0;
-        for (int sl = 0; sl < n_slices; ++sl) s += partial[sl * slice_size + src];
+        for (int sl = s0; sl < s1; ++sl) s += partial[sl * slice_size + src];
         G[idx] = s;
     }
 }
@@ -537,8 +538,8 @@ __global__ void __launch_bounds__(256, 2) k_gram_simt(const TcParams p)
         if (r < 128) rowinfoA[r] = ri;
         else rowinfoB[r - 128] = ri;
     }
-    const int64_t i_beg = (int64_t)blockIdx.y * p.per_slice;
-    const int64_t i_end = min(p.K, i_beg + p.per_slice);
+    const int64_t i_beg = p.slice_k ? p.slice_k[blockIdx.y] : (int64_t)blockIdx.y * p.per_slice;
+    const int64_t i_end = p.slice_k ? p.slice_k[blockIdx.y + 1] : min(p.K, i_beg + p.per_slice);
     double *part = p.partial + (int64_t)blockIdx.y * p.plan.slice_size + U.part_off;
     float acc[8][8];
 #pragma unroll
@@ -606,6 +607,21 @@ __global__ void __launch_bounds__(256, 2) k_gram_simt(const TcParams p)
     if (since > 0) flush();
 }
 
+// The tensor-core Gram's shared-memory limit, set once per device (before any
+// stream capture: the first call runs eagerly).
+cudaError_t tc_smem_attr(bool tf32)
+{
+    static std::atomic<unsigned long long> attr_done[2];   // devices whose attribute is set
+    const unsigned long long bit = device_bit();
+    if (!(attr_done[tf32].load(std::memory_order_acquire) & bit)) {
+        const cudaError_t e = cudaFuncSetAttribute(tf32 ? k_gram_tc<true> : k_gram_tc<false>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_done[tf32].fetch_or(bit, std::memory_order_acq_rel);
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, int lmax, bool tf32, double *G,
@@ -627,6 +643,7 @@ cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, 
     p.lmax = lmax;
     p.per_slice = (K + slices - 1) / slices;
     p.n_slices = slices;
+    p.slice_k = nullptr;
     p.err = err;
     p.wait_limit = device_wait_limit();
     p.wait_unmet = device_wait_unmet();
@@ -638,15 +655,8 @@ cudaError_t couple_gram_tc(const float *alm, const float *w, int64_t K, int nb, 
     size_t smem = 2 * 4 * (size_t)rmax * ks * esz + 16 * (size_t)rmax + 64;
     if (smem < 116 * 1024) smem = 116 * 1024;
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    static std::atomic<unsigned long long> attr_done[2];   // devices whose attribute is set
-    const unsigned long long bit = device_bit();
-    cudaError_t e;
-    if (!(attr_done[tf32].load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(tf32 ? k_gram_tc<true> : k_gram_tc<false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return e;
-        attr_done[tf32].fetch_or(bit, std::memory_order_acq_rel);
-    }
+    cudaError_t e = tc_smem_attr(tf32);
+    if (e != cudaSuccess) return e;
     const size_t pbytes = (size_t)slices * p.plan.slice_size * sizeof(double);
     e = scratch_malloc((void **)&p.partial, pbytes, st);
     if (e != cudaSuccess) return e;
@@ -689,6 +699,7 @@ cudaError_t couple_gram_simt(const float *alm, const float *w, int64_t K, int nb
     p.lmax = lmax;
     p.per_slice = (K + slices - 1) / slices;
     p.n_slices = slices;
+    p.slice_k = nullptr;
     p.err = nullptr;
     p.wait_limit = device_wait_limit();
     p.wait_unmet = 0;
@@ -706,6 +717,102 @@ cudaError_t couple_gram_simt(const float *alm, const float *w, int64_t K, int nb
         int g = (int)((tot + 255) / 256);
         if (g > 4096) g = 4096;
         k_gram_tc_reduce<<<g, 256, 0, st>>>(p.partial, slices, p.plan.slice_size, nb, lmax, p.plan, G);
+        note_launch();
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(p.partial, st);
+    return e;
+}
+
+namespace {
+
+// Work items of the FP32 Gram: 128-row tiles of every unit.
+int simt_items(const TcPlan &plan)
+{
+    int items = 0;
+    for (int u = 0; u < plan.n_units; ++u) items += (plan.u[u].n + 127) / 128;
+    return items;
+}
+
+}  // namespace
+
+void gram_batch_slices(const int64_t *off, int n_cat, int nb, int lmax, bool simt, int sms,
+                       std::vector<int64_t> &slice_k, std::vector<int> &mslice)
+{
+    slice_k.clear();
+    mslice.clear();
+    TcPlan plan;
+    if (!make_tc_plan(nb, lmax, plan)) return;
+    // about one launch wave over the whole group (two FP32 CTAs per SM, one
+    // tensor-core CTA), slices of 1024 (tensor) / 2048 (FP32) to 65536 primaries
+    const int per_wave = simt ? std::max(1, 2 * sms / std::max(1, simt_items(plan)))
+                              : std::max(1, sms / std::max(1, plan.n_groups));
+    const int64_t K = off[n_cat] - off[0];
+    int64_t per = (K + per_wave - 1) / per_wave;
+    per = std::max<int64_t>(per, simt ? 2048 : 1024);
+    per = std::min<int64_t>(per, 65536);
+    slice_k.push_back(0);
+    for (int c = 0; c < n_cat; ++c) {
+        mslice.push_back((int)slice_k.size() - 1);
+        const int64_t a = off[c] - off[0], b = off[c + 1] - off[0];
+        const int64_t ns = (b - a + per - 1) / per;
+        for (int64_t q = 1; q <= ns; ++q) slice_k.push_back(a + ((b - a) * q) / ns);
+    }
+    mslice.push_back((int)slice_k.size() - 1);
+}
+
+cudaError_t couple_gram_batched(const float *alm, const float *w, int n_cat, const int64_t *d_slice_k,
+                                int n_slices, const int *d_mslice, int nb, int lmax, int precision, double *G,
+                                int *err, int sms, cudaStream_t st)
+{
+    TcParams p;
+    if (!make_tc_plan(nb, lmax, p.plan)) return cudaErrorInvalidValue;
+    const int64_t gsz = gram_offset(nb, lmax, lmax + 1);
+    if (n_slices < 1) return cudaMemsetAsync(G, 0, (size_t)n_cat * gsz * sizeof(double), st);
+    const bool simt = precision == TPCF_PREC_FP32, tf32 = precision == TPCF_PREC_TF32X3;
+    p.alm = alm;
+    p.w = w;
+    p.K = 0;
+    p.nb = nb;
+    p.lmax = lmax;
+    p.per_slice = 0;
+    p.n_slices = n_slices;
+    p.slice_k = d_slice_k;
+    p.err = simt ? nullptr : err;
+    p.wait_limit = device_wait_limit();
+    p.wait_unmet = simt ? 0 : device_wait_unmet();
+    size_t smem = 0;
+    cudaError_t e = cudaSuccess;
+    if (!simt) {
+        int rmax = 0;
+        for (int g = 0; g < p.plan.n_groups; ++g) rmax = std::max(rmax, p.plan.g[g].rows_alloc);
+        const int ks = tf32 ? 16 : 32, esz = tf32 ? 4 : 2;
+        smem = 2 * 4 * (size_t)rmax * ks * esz + 16 * (size_t)rmax + 64;
+        if (smem < 116 * 1024) smem = 116 * 1024;
+        if (smem > 227 * 1024) return cudaErrorInvalidValue;
+        e = tc_smem_attr(tf32);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t pbytes = (size_t)n_slices * p.plan.slice_size * sizeof(double);
+    e = scratch_malloc((void **)&p.partial, pbytes, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(p.partial, 0, pbytes, st);
+    if (e == cudaSuccess) {
+        if (simt) {
+            k_gram_simt<<<dim3(simt_items(p.plan), n_slices), 256, 0, st>>>(p);
+        } else {
+            const dim3 grid(p.plan.n_groups, n_slices);
+            if (tf32) k_gram_tc<true><<<grid, kThreads, smem, st>>>(p);
+            else k_gram_tc<false><<<grid, kThreads, smem, st>>>(p);
+        }
+        note_launch();
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        int g = (int)((gsz + 255) / 256);
+        if (g > 4096) g = 4096;
+        k_gram_tc_reduce<<<dim3(g, n_cat), 256, 0, st>>>(p.partial, n_slices, p.plan.slice_size, nb, lmax, p.plan, G,
+                                                         d_mslice);
         note_launch();
         e = cudaGetLastError();
     }

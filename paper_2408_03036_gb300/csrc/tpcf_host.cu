@@ -87,6 +87,13 @@ struct tpcf_batch_s {
     double *wsum = nullptr, *diag = nullptr, *wsp = nullptr, *G = nullptr, *nnn = nullptr, *rrr = nullptr;
     unsigned long long *pairs = nullptr, *T = nullptr;
     int *d_status = nullptr;             // [n_mocks] DEV_ERR_* of every mock's last run
+    // the one-launch Gram of every group: slice boundaries (primaries from the
+    // group's first) and every mock's first slice, concatenated over groups
+    int64_t *d_slice_k = nullptr;
+    int *d_mslice = nullptr;
+    std::vector<size_t> gs_at, gm_at;    // per group: offsets into d_slice_k and d_mslice
+    std::vector<int> gs_n;               // per group: slices
+    int max_group_mocks = 0;
     // graph of one run, captured for the buffers in gp
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1639,6 +1646,24 @@ int tpcf_batch_create(const tpcf_config *cfg, const int64_t *offsets, int32_t n_
     std::vector<int64_t> goff;
     for (size_t g = 0; g + 1 < b->group.size(); ++g)
         for (int k = b->group[g]; k <= b->group[g + 1]; ++k) goff.push_back(offsets[k] - offsets[b->group[g]]);
+    std::vector<int64_t> all_sk;
+    std::vector<int> all_ms;
+    for (size_t g = 0; g + 1 < b->group.size(); ++g) {
+        const int m0 = b->group[g], m1 = b->group[g + 1];
+        std::vector<int64_t> sk;
+        std::vector<int> ms;
+        gram_batch_slices(offsets + m0, m1 - m0, nb, L, cfg->precision == TPCF_PREC_FP32, ds->sms, sk, ms);
+        if (sk.empty()) {
+            delete b;
+            return fail(TPCF_ERR_UNSUPPORTED, "Gram: no tile plan for this shape");
+        }
+        b->gs_at.push_back(all_sk.size());
+        b->gm_at.push_back(all_ms.size());
+        b->gs_n.push_back((int)sk.size() - 1);
+        all_sk.insert(all_sk.end(), sk.begin(), sk.end());
+        all_ms.insert(all_ms.end(), ms.begin(), ms.end());
+        b->max_group_mocks = std::max(b->max_group_mocks, m1 - m0);
+    }
     std::vector<double> coef;
     std::vector<int> ml;
     projection_tables(cfg, coef, ml);
@@ -1671,7 +1696,9 @@ int tpcf_batch_create(const tpcf_config *cfg, const int64_t *offsets, int32_t n_
     A((void **)&b->wsum, n_mocks * sizeof(double));
     A((void **)&b->diag, (size_t)n_mocks * ndiag * nb * sizeof(double));
     A((void **)&b->wsp, (size_t)n_mocks * L1 * nb * sizeof(double));
-    A((void **)&b->G, gram_offset(nb, L, L + 1) * sizeof(double));
+    A((void **)&b->G, (size_t)b->max_group_mocks * gram_offset(nb, L, L + 1) * sizeof(double));
+    A((void **)&b->d_slice_k, all_sk.size() * sizeof(int64_t));
+    A((void **)&b->d_mslice, all_ms.size() * sizeof(int));
     A((void **)&b->nnn, (size_t)L1 * L1 * L1 * nb * nb * sizeof(double));
     A((void **)&b->rrr, (size_t)nb * nb * sizeof(double));
     A((void **)&b->pairs, (size_t)n_mocks * nb * sizeof(unsigned long long));
@@ -1684,6 +1711,9 @@ int tpcf_batch_create(const tpcf_config *cfg, const int64_t *offsets, int32_t n_
     if (e == cudaSuccess) e = cudaMemcpy(b->d_coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_mults, ml.data(), ml.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_mono, mono.data(), nb * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_slice_k, all_sk.data(), all_sk.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_mslice, all_ms.data(), all_ms.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         tpcf_batch_destroy(b);
         return cuda_fail(e, "batch buffers");
@@ -1699,7 +1729,8 @@ int tpcf_batch_destroy(tpcf_batch b)
     for (void *ptr : {(void *)b->d_off, (void *)b->d_goff, (void *)b->d_gaunt, (void *)b->d_coef, (void *)b->d_mults,
                       (void *)b->d_mono, (void *)b->d_tiles, (void *)b->rec_mock, (void *)b->alm, (void *)b->wprim,
                       (void *)b->counts, (void *)b->wsum, (void *)b->diag, (void *)b->wsp, (void *)b->G,
-                      (void *)b->nnn, (void *)b->rrr, (void *)b->pairs, (void *)b->T, (void *)b->d_status})
+                      (void *)b->nnn, (void *)b->rrr, (void *)b->pairs, (void *)b->T, (void *)b->d_status,
+                      (void *)b->d_slice_k, (void *)b->d_mslice})
         if (ptr) cudaFree(ptr);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -1726,7 +1757,7 @@ int tpcf_batch_run(tpcf_batch b, const uint32_t *xyz, const float *w, double *ze
     if (rc) return rc;
     const tpcf_config *c = &b->cfg;
     const int nb = c->n_bins, L = c->l_max, L1 = L + 1;
-    const int nlm = L1 * L1, ndiag = L1 * (L1 + 1) / 2;
+    const int ndiag = L1 * (L1 + 1) / 2;
     const int64_t ncell1 = (int64_t)b->nc * b->nc * b->nc;
     CK(cudaMemsetAsync(b->diag, 0, (size_t)b->n_mocks * ndiag * nb * sizeof(double), st));
     CK(cudaMemsetAsync(b->wsp, 0, (size_t)b->n_mocks * L1 * nb * sizeof(double), st));
@@ -1751,19 +1782,13 @@ int tpcf_batch_run(tpcf_batch b, const uint32_t *xyz, const float *w, double *ze
         if (rc) return rc;
         if (np > 0)
             CK(cudaMemcpy2DAsync(b->wprim, 4, (const char *)grid.rec + 12, 16, 4, np, cudaMemcpyDeviceToDevice, st));
+        // every mock's Gram in one launch (slices never straddle two mocks)
+        const int64_t gsz = gram_offset(nb, L, L + 1);
+        CK(couple_gram_batched(b->alm, b->wprim, nm, b->d_slice_k + b->gs_at[g], b->gs_n[g], b->d_mslice + b->gm_at[g],
+                               nb, L, c->precision, b->G, ds->err, ds->sms, st));
         for (int k = m0; k < m1; ++k) {
             const int64_t r0 = b->off[k] - p0, K = b->off[k + 1] - b->off[k];
-            const float *alm_k = b->alm + (size_t)r0 * nb * nlm;
-            if (c->precision == TPCF_PREC_FP32) {
-                CK(couple_gram_simt(alm_k, b->wprim + r0, K, nb, L, b->G, ds->sms, st));
-            } else {
-                cudaError_t e = couple_gram_tc(alm_k, b->wprim + r0, K, nb, L, c->precision == TPCF_PREC_TF32X3, b->G,
-                                               ds->err, ds->sms, st);
-                if (e == cudaErrorInvalidValue)
-                    return fail(TPCF_ERR_UNSUPPORTED, "tensor-core Gram: no tile plan for this shape");
-                CK(e);
-            }
-            CK(assemble_nnn(b->G, b->diag + (size_t)k * ndiag * nb, b->wsp + (size_t)k * L1 * nb, nb, L,
+            CK(assemble_nnn(b->G + (size_t)(k - m0) * gsz, b->diag + (size_t)k * ndiag * nb, b->wsp + (size_t)k * L1 * nb, nb, L,
                             c->remove_self, b->d_gaunt, b->nnn, st));
             CK(tpcf::triplet_counts(b->counts + (size_t)r0 * nb, K, nb, b->T + (size_t)k * nb * nb, st));
             CK(rrr_analytic(b->wsum + k, b->d_mono, nb, b->rrr, st));
