@@ -481,14 +481,14 @@ def batch_mocks(args, dev, stream, tpcf, flush, rank=0):
         del x
     w = torch.ones(int(off[-1]), dtype=torch.float32, device=dev)
     torch.cuda.synchronize(dev)
-    # tile shapes for this density from the autotuner (one primary per tile in a batch)
-    tuned = tpcf.autotune(mock_config("fp32", tile_primaries=1), xyz[:int(off[1])], w[:int(off[1])],
-                          stream=stream, device=dev)
+    # tile shapes for this density from the autotuner (a batch's tiles hold
+    # primaries of one mock only)
+    tuned = tpcf.autotune(mock_config("fp32"), xyz[:int(off[1])], w[:int(off[1])], stream=stream, device=dev)
     out = {"mocks": n_mocks, "points": int(off[-1]), "sizes": [int(sizes.min()), int(sizes.max())],
-           "tuned": {"cell_div": tuned.cell_div, "chunk": tuned.chunk}}
+           "tuned": {"cell_div": tuned.cell_div, "chunk": tuned.chunk, "tile_primaries": tuned.tile_primaries}}
     zs = {}
     for prec in ("fp32", "bf16x3"):
-        cfg = mock_config(prec, cell_div=tuned.cell_div, chunk=tuned.chunk, tile_primaries=1)
+        cfg = mock_config(prec, cell_div=tuned.cell_div, chunk=tuned.chunk, tile_primaries=tuned.tile_primaries)
         b = tpcf.Batch(cfg, off)
         z = b.zeta_buffer(dev)
         b.run_graph(xyz, w, z, stream=stream)          # eager run + capture (warm-up)
@@ -521,9 +521,9 @@ def batch_mocks(args, dev, stream, tpcf, flush, rank=0):
     out["mixed_over_plain"] = out["bf16x3"]["mocks_per_hour"] / out["fp32"]["mocks_per_hour"]
     # unbatched: one tpcf_estimate_3pcf per mock over every mock of the batch (the
     # same tuned cells and queues), timed the same way
-    out["sequential"] = {"note": "one tpcf_estimate_3pcf call per mock, all mocks, same tuned cell size and queue"}
+    out["sequential"] = {"note": "one tpcf_estimate_3pcf call per mock, all mocks, same tuned cells, queue and tiles"}
     for prec in ("fp32", "bf16x3"):
-        cfg = mock_config(prec, cell_div=tuned.cell_div, chunk=tuned.chunk)
+        cfg = mock_config(prec, cell_div=tuned.cell_div, chunk=tuned.chunk, tile_primaries=tuned.tile_primaries)
         for k in range(2):
             tpcf.estimate_3pcf(cfg, xyz[off[k]:off[k + 1]], w[off[k]:off[k + 1]], stream=stream, device=dev,
                                want_all=False)
@@ -568,7 +568,7 @@ def small_mock_batch(dev, stream, tpcf, flush, rank=0):
            "note": "one graph launch of the batch vs one tpcf_estimate_3pcf call per mock; default tiles"}
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for prec in ("fp32", "bf16x3"):
-        cfg = mock_config(prec, tile_primaries=1)
+        cfg = mock_config(prec)
         b = tpcf.Batch(cfg, off)
         z = b.zeta_buffer(dev)
         b.run_graph(xyz, w, z, stream=stream)          # eager run + capture (warm-up)

@@ -350,8 +350,12 @@ int tpcf_estimate_3pcf_host(const tpcf_config *cfg,
  * use Sec. 4.3 motivates), each estimated with analytic randoms.  The points of
  * all mocks are concatenated: mock k is points [offsets[k], offsets[k+1]).  The
  * pair stage of a whole group of mocks is one persistent launch whose tiles may
- * come from any mock; all mocks fit one group unless the per-point buffers
- * would take more than half of the free device memory. */
+ * come from any mock (each tile holds primaries of one mock only: up to
+ * cfg->tile_primaries of them, or, for 0, the single-catalogue rule of about
+ * 3000 pairs per tile at the mean mock density), and so is the coupling (every
+ * mock's Gram in one launch whose slices never cross a mock); all mocks fit one
+ * group unless the per-point buffers would take more than half of the free
+ * device memory. */
 typedef struct tpcf_batch_s *tpcf_batch;
 
 /* Plans a batch: host offsets[n_mocks + 1] (offsets[0] = 0, non-decreasing,
@@ -402,8 +406,7 @@ int tpcf_estimate_3pcf_batched(const tpcf_config *cfg, const uint32_t *xyz, cons
  * sample of at most 32768 of its primaries (dev xyz[n][3], dev w[n] or NULL) for
  * every valid combination (best of three runs after a warm-up run); *tuned =
  * *cfg with the fastest choice.  A nonzero
- * cfg->tile_primaries is kept fixed (batches run one primary per tile).
- * Synchronises the stream. */
+ * cfg->tile_primaries is kept fixed.  Synchronises the stream. */
 int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, int64_t n, void *stream,
                   tpcf_config *tuned);
 

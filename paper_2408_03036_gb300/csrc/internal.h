@@ -75,12 +75,17 @@ struct PairParams {
     // Batches of catalogues (null prim_mock: one catalogue).  Primary i belongs to
     // mock prim_mock[i]; its cells start at mock * ncell_mock in cell_start, its
     // W is mono_w_mock[mock], and its diag / wsp / pair_counts go to that mock's
-    // slice of the outputs.  Requires one primary per tile (P = 1).
+    // slice of the outputs.  Requires tiles within one mock: P = 1, or tile_start.
     const int *prim_mock;
     int64_t ncell_mock;
     const double *mono_w_mock;
     // batches: bad input latches the mock's own status (DEV_ERR_*) instead of err
     int *mock_status;
+    // batches with several primaries per tile: tile t is primaries
+    // [tile_start[t], tile_start[t + 1]) (at most P, all of one catalogue);
+    // null: tile t is [t P, min((t + 1) P, n_prim))
+    const int64_t *tile_start;
+    int64_t n_tiles;
 };
 
 // Bit of the current device in a per-device "done" mask (one-time attribute set-up).

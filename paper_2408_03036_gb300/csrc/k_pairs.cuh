@@ -760,9 +760,17 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
             s_nr = 0;
         }
         __syncthreads();
-        const long long t0 = (long long)s_tile * P;
-        if (t0 >= p.n_prim) break;
-        const int np = (int)min((long long)P, p.n_prim - t0);
+        long long t0;
+        int np;
+        if (p.tile_start) {
+            if (s_tile >= p.n_tiles) break;
+            t0 = p.tile_start[s_tile];
+            np = (int)(p.tile_start[s_tile + 1] - t0);
+        } else {
+            t0 = (long long)s_tile * P;
+            if (t0 >= p.n_prim) break;
+            np = (int)min((long long)P, p.n_prim - t0);
+        }
         const int nk = np * nb;
         const int mock = p.prim_mock ? p.prim_mock[t0] : 0;
         if (mock != cta_mock) {
@@ -1013,7 +1021,8 @@ __global__ void __launch_bounds__(256, (LMAX <= 4 ? 3 : 1)) k_pairs_q(const Pair
         __syncthreads();
 
         // ----- tile outputs (as in k_pairs)
-        const long long g0 = (long long)s_tile * P;   // the tile's first primary (re-read: t0 is not kept)
+        // the tile's first primary (re-read: t0 is not kept)
+        const long long g0 = p.tile_start ? p.tile_start[s_tile] : (long long)s_tile * P;
         if (p.alm) {
             for (int i = tid; i < np * nb * NLM; i += T) {
                 const int slot = i / (nb * NLM), rem = i % (nb * NLM);

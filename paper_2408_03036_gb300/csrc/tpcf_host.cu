@@ -94,6 +94,12 @@ struct tpcf_batch_s {
     std::vector<size_t> gs_at, gm_at;    // per group: offsets into d_slice_k and d_mslice
     std::vector<int> gs_n;               // per group: slices
     int max_group_mocks = 0;
+    // pair-stage tiles of up to tile_p primaries of one mock (tile_p > 1), starts
+    // relative to the group's first primary, concatenated over groups
+    int tile_p = 1;
+    int64_t *d_tile_start = nullptr;
+    std::vector<size_t> gt_at;           // per group: offset into d_tile_start
+    std::vector<int64_t> gt_n;           // per group: tiles
     // graph of one run, captured for the buffers in gp
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -570,6 +576,9 @@ struct BatchInfo {
     int64_t ncell_mock;         // cells per mock
     const double *mono_w_mock;  // W per mock
     int *mock_status;           // per-mock device status (the group's first mock at index 0)
+    int P = 1;                  // primaries per tile of tile_start (1: no table)
+    const int64_t *tile_start = nullptr;   // [n_tiles + 1] tiles within single mocks, or null
+    int64_t n_tiles = 0;
 };
 
 // Random-random pair counts taken during a D - R pass (PairParams::counts_r):
@@ -677,8 +686,22 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
         smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
     }
     if (bi) {
-        pl.P = 1;   // one primary per tile: a tile never straddles two catalogues
+        // a tile never straddles two catalogues: the batch's own tiles (at most
+        // bi->P primaries of one mock) when the plan allows that many, else one
+        // primary per tile
+        bool table = false;
+        if (bi->tile_start && bi->P > 1 && !counts_only) {
+            Plan q = pl;
+            q.P = bi->P;
+            table = pair_smem(c->l_max, counts_only, q, c->n_bins) <= smem_cap &&
+                    (counts_only || q.chunk >= 32 * (q.P * c->n_bins + 1));
+        }
+        pl.P = table ? bi->P : 1;
         smem = pair_smem(c->l_max, counts_only, pl, c->n_bins);
+        if (table) {
+            p.tile_start = bi->tile_start;
+            p.n_tiles = bi->n_tiles;
+        }
         p.prim_mock = bi->prim_mock;
         p.ncell_mock = bi->ncell_mock;
         p.mono_w_mock = bi->mono_w_mock;
@@ -693,7 +716,7 @@ int run_pairs(const tpcf_config *c, const GridDev &g, const int4 *prim, int64_t 
     // resident CTAs per SM from the occupancy calculator (registers and shared memory)
     const int per_sm = pair_per_sm(c->l_max, counts_only, p.vlos != 0, smem);
     int grid = ds->sms * per_sm;
-    const int64_t tiles = (n_prim + pl.P - 1) / pl.P;
+    const int64_t tiles = p.tile_start ? p.n_tiles : (n_prim + pl.P - 1) / pl.P;
     if (grid > tiles) grid = (int)tiles;
     cudaError_t e = pair_launch(c->l_max, counts_only, p, h, grid, smem, st);
     if (e != cudaSuccess) return cuda_fail(e, "pair stage launch");
@@ -1664,6 +1687,32 @@ int tpcf_batch_create(const tpcf_config *cfg, const int64_t *offsets, int32_t n_
         all_ms.insert(all_ms.end(), ms.begin(), ms.end());
         b->max_group_mocks = std::max(b->max_group_mocks, m1 - m0);
     }
+    // pair-stage tiles: the plan's primaries per tile at the mean mock density
+    // (about 3000 pairs per tile), never straddling two mocks
+    std::vector<int64_t> all_ts;
+    {
+        const double nbar = (double)n_total / n_mocks / (cfg->box * cfg->box * cfg->box);
+        const double vol =
+            4.0 / 3.0 * kPi * (cfg->r_max * cfg->r_max * cfg->r_max - cfg->r_min * cfg->r_min * cfg->r_min);
+        int P = cfg->tile_primaries;
+        if (P == 0) P = (int)std::lround(3000.0 / std::max(nbar * vol, 1.0));
+        P = std::max(1, std::min(P, std::min(TPCF_MAX_TILE, std::max(1, 128 / nb))));
+        b->tile_p = P;
+        for (size_t g = 0; g + 1 < b->group.size(); ++g) {
+            const int m0 = b->group[g], m1 = b->group[g + 1];
+            const int64_t p0 = offsets[m0];
+            b->gt_at.push_back(all_ts.size());
+            if (P > 1) {
+                const size_t first = all_ts.size();
+                for (int k = m0; k < m1; ++k)
+                    for (int64_t t = offsets[k]; t < offsets[k + 1]; t += P) all_ts.push_back(t - p0);
+                all_ts.push_back(offsets[m1] - p0);
+                b->gt_n.push_back((int64_t)(all_ts.size() - first) - 1);
+            } else {
+                b->gt_n.push_back(0);
+            }
+        }
+    }
     std::vector<double> coef;
     std::vector<int> ml;
     projection_tables(cfg, coef, ml);
@@ -1699,6 +1748,7 @@ int tpcf_batch_create(const tpcf_config *cfg, const int64_t *offsets, int32_t n_
     A((void **)&b->G, (size_t)b->max_group_mocks * gram_offset(nb, L, L + 1) * sizeof(double));
     A((void **)&b->d_slice_k, all_sk.size() * sizeof(int64_t));
     A((void **)&b->d_mslice, all_ms.size() * sizeof(int));
+    A((void **)&b->d_tile_start, all_ts.size() * sizeof(int64_t));
     A((void **)&b->nnn, (size_t)L1 * L1 * L1 * nb * nb * sizeof(double));
     A((void **)&b->rrr, (size_t)nb * nb * sizeof(double));
     A((void **)&b->pairs, (size_t)n_mocks * nb * sizeof(unsigned long long));
@@ -1714,6 +1764,8 @@ int tpcf_batch_create(const tpcf_config *cfg, const int64_t *offsets, int32_t n_
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_slice_k, all_sk.data(), all_sk.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_mslice, all_ms.data(), all_ms.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !all_ts.empty())
+        e = cudaMemcpy(b->d_tile_start, all_ts.data(), all_ts.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         tpcf_batch_destroy(b);
         return cuda_fail(e, "batch buffers");
@@ -1730,7 +1782,7 @@ int tpcf_batch_destroy(tpcf_batch b)
                       (void *)b->d_mono, (void *)b->d_tiles, (void *)b->rec_mock, (void *)b->alm, (void *)b->wprim,
                       (void *)b->counts, (void *)b->wsum, (void *)b->diag, (void *)b->wsp, (void *)b->G,
                       (void *)b->nnn, (void *)b->rrr, (void *)b->pairs, (void *)b->T, (void *)b->d_status,
-                      (void *)b->d_slice_k, (void *)b->d_mslice})
+                      (void *)b->d_slice_k, (void *)b->d_mslice, (void *)b->d_tile_start})
         if (ptr) cudaFree(ptr);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -1776,6 +1828,11 @@ int tpcf_batch_run(tpcf_batch b, const uint32_t *xyz, const float *w, double *ze
         CK(build_grid_batched_dev(xyz + 3 * p0, wg, np, d_goff, nm, b->nc, grid, b->rec_mock, ds->err, st,
                                   b->d_status + m0));
         BatchInfo bi{b->rec_mock, ncell1, b->wsum + m0, b->d_status + m0};
+        if (b->tile_p > 1) {
+            bi.P = b->tile_p;
+            bi.tile_start = b->d_tile_start + b->gt_at[g];
+            bi.n_tiles = b->gt_n[g];
+        }
         rc = run_pairs(c, grid, grid.rec, np, false, 0.0, nullptr, true, b->alm, b->counts,
                        b->diag + (size_t)m0 * ndiag * nb, b->wsp + (size_t)m0 * L1 * nb, b->pairs + (size_t)m0 * nb,
                        st, &bi);
@@ -1910,7 +1967,7 @@ int tpcf_autotune(const tpcf_config *cfg, const uint32_t *xyz, const float *w, i
     const int divs[] = {2, 3, 4, 5, 6};
     const int tiles_all[] = {1, 2, 4};
     const int tiles_fixed[] = {cfg->tile_primaries};
-    const bool fixed_tile = cfg->tile_primaries > 0;   // a batch runs one primary per tile
+    const bool fixed_tile = cfg->tile_primaries > 0;   // the caller fixed the tile size
     const int chunks[] = {12288, 15360, 24576};
     for (int dv : divs) {
         tpcf_config t = *cfg;

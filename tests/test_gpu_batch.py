@@ -87,6 +87,31 @@ def test_batch_matches_single_and_oracle(gpu, ora):
         assert err.max() <= TOL_FP32, (k, dict(zip(map(str, est.mults), err)))
 
 
+def test_batch_tile_sizes_agree(gpu):
+    """Tiles of 1, 3 and the automatic number of primaries (8 here), each within
+    one mock, over mocks of uneven sizes (empty and one-point mocks included) and
+    two groups: triplet counts identical, multipoles at the FP32 bar."""
+    sizes = [1700, 0, 2300, 1, 900, 2600, 5]
+    xyz, w, off = make_mocks(sizes, seed=300, clustered=(2,))
+    ref = None
+    for tp in (1, 3, 0):
+        cfg = tpcf.Config(**base_cfg(tile_primaries=tp))
+        b = tpcf.Batch(cfg, off, group_points=5000)
+        z = b.zeta_buffer()
+        t = gpu.zeros((len(sizes), cfg.n_bins, cfg.n_bins), dtype=gpu.int64, device="cuda")
+        b.run(gpu.from_numpy(synth.as_int32_bits(xyz)).cuda(), gpu.from_numpy(w).cuda(), z, t)
+        tpcf.stream_status()
+        b.close()
+        z, t = z.cpu().numpy(), t.cpu().numpy()
+        if ref is None:
+            ref = (z, t)
+            continue
+        assert np.array_equal(t, ref[1]), tp
+        for k in range(len(sizes)):
+            if sizes[k] >= 2:
+                assert per_mult_err(z[k], ref[0][k]).max() <= TOL_FP32, (tp, k)
+
+
 def test_batch_weighted_and_grouped(gpu):
     """Positive weights, and the batch split into several groups (persistent launches)."""
     sizes = [1500, 2600, 900, 2000, 1700]
