@@ -51,7 +51,7 @@ typedef enum {
     TPCF_ERR_OOM = -2,          /* device allocation failed */
     TPCF_ERR_CUDA = -3,         /* a CUDA runtime call failed */
     TPCF_ERR_TIMEOUT = -4,      /* a bounded device-side wait ran out */
-    TPCF_ERR_UNSUPPORTED = -5,  /* valid request this build does not implement */
+    TPCF_ERR_UNSUPPORTED = -5,  /* valid request the library does not implement */
     TPCF_ERR_DATA = -6          /* bad input data detected on the device */
 } tpcf_status;
 
