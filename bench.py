@@ -39,9 +39,9 @@ WORKLOAD = ("clustered lognormal halos N_D=400000 (512^3 mesh, P~k^-1.5 exp(-(k/
 FLOP_PER_PAIR = 4 * 25 + 15   # algorithmic FP32 work per accepted pair at l_max = 4
 # DRAM bytes (read + write) per primary of the harmonic pair kernel, from one ncu
 # capture of the current kernel at this workload's density (400,000 primaries in
-# a 630 Mpc/h cube: 17.6 MB read + 777.4 MB written, the a_lm output); the
+# a 630 Mpc/h cube: 19.7 MB read + 778.2 MB written, the a_lm output); the
 # traffic grows with the primaries, so a launch moves this times its primaries
-PAIR_DRAM_BYTES_PER_PRIMARY = 1987.0
+PAIR_DRAM_BYTES_PER_PRIMARY = 1995.0
 # covariance batch: lognormal mocks (same field recipe, 256^3 mesh) in a periodic
 # cube of side 1000 Mpc/h, sizes uniform in [100k, 400k], analytic randoms
 N_MOCKS, MOCK_LO, MOCK_HI, MOCK_MESH, SEED_MOCKS = 256, 100_000, 400_000, 256, 77
